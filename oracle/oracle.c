@@ -1,0 +1,575 @@
+/*
+ * Serial FP64 CPU oracle of the edge-based finite-volume loops.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path calls this file:
+ * only the tests, the smoke check and the benchmark's CPU baseline load it.
+ * It shares no code with the CUDA kernels (no headers, helpers or tables).
+ *
+ * Plain definitions, one edge after another, in the order the method
+ * states them.  The paper (Sec. 2 and Sec. 3.1, Fig. "OP2loop") defines the
+ * loop structure: a loop over the edge set that reads node data through the
+ * edge->node map and increments both end nodes (OP_INC).  It does not print
+ * the numerics, so the formulas below are the textbook ones chosen for the
+ * edge-based solver (Sec. 1: Hydra, explicit 5-step Runge-Kutta):
+ *
+ *   Euler flux     f(q).n = (rho un, rho u un + p n, (rho E + p) un, c un)
+ *   Rusanov        F = (f(qL).n + f(qR).n)/2 - s (qR - qL)/2,
+ *                  s = max(|uL.n| + aL|n|, |uR.n| + aR|n|), a = sqrt(g p/rho)
+ *   Green-Gauss    Graw_i += (q_i+q_j)/2 (x) n_e,  Graw_j -= same;  G = Graw/V
+ *   van Albada     phi(a,b) = (a(b^2+eps) + b(a^2+eps)) / (a^2+b^2+2 eps)
+ *   reconstruction qL = q_i + phi(G_i.dx, q_j-q_i)/2,
+ *                  qR = q_j - phi(G_j.dx, q_j-q_i)/2
+ *   residual       R_i += F_e, R_j -= F_e    (F is the flux out of i)
+ *   time step      Lambda_i = sum_e s_e(q_i, q_j), dt_i = CFL V_i / Lambda_i
+ *   RK stage       q = q0 - alpha_k (dt_i / V_i) R(q_prev),
+ *                  alpha = (1/4, 1/6, 3/8, 1/2, 1) (Jameson's 5 stages)
+ *
+ * Layout (the oracle's own, node-major): q[i*6+k], G[i*18+k*3+d],
+ * n[e*3+d], dx[e*3+d], edge[e*2+0] = i, edge[e*2+1] = j.
+ *
+ * Parity pins (tests/test_oracle_*.py): closed forms on the 8-node cube,
+ * linear exactness of the gradient and the reconstruction on the lattice,
+ * flux consistency and antisymmetry, global conservation, freestream,
+ * finite differences and the dot-product test for the two sweeps.
+ * The choices of wave-speed estimate, limiter and RK coefficients are not
+ * fixed by the paper: against the paper they are parity unpinned, and are
+ * pinned only by those self-consistency properties.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#define NV 6   /* conserved variables per node */
+#define NG 18  /* gradient values per node: 6 variables x 3 directions */
+
+/* ---------------------------------------------------------------- pieces */
+
+/* pressure of a conserved state */
+static double pressure(const double q[NV], double gamma) {
+  double rho = q[0];
+  double ke = 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / rho;
+  return (gamma - 1.0) * (q[4] - ke);
+}
+
+/* physical flux through the face with normal n */
+void ora_euler_flux(const double q[NV], const double n[3], double gamma,
+                    double f[NV]) {
+  double rho = q[0];
+  double un = (q[1] * n[0] + q[2] * n[1] + q[3] * n[2]) / rho;
+  double p = pressure(q, gamma);
+  f[0] = q[0] * un;
+  f[1] = q[1] * un + p * n[0];
+  f[2] = q[2] * un + p * n[1];
+  f[3] = q[3] * un + p * n[2];
+  f[4] = (q[4] + p) * un;
+  f[5] = q[5] * un;
+}
+
+/* largest wave speed |u.n| + a|n| of one state */
+double ora_wave_speed(const double q[NV], const double n[3], double gamma) {
+  double rho = q[0];
+  double un = (q[1] * n[0] + q[2] * n[1] + q[3] * n[2]) / rho;
+  double p = pressure(q, gamma);
+  double a = sqrt(gamma * p / rho);
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  return fabs(un) + a * nn;
+}
+
+/* Rusanov (local Lax-Friedrichs) flux; ties of the two wave speeds pick L */
+void ora_rusanov(const double qL[NV], const double qR[NV], const double n[3],
+                 double gamma, double F[NV]) {
+  double fL[NV], fR[NV];
+  ora_euler_flux(qL, n, gamma, fL);
+  ora_euler_flux(qR, n, gamma, fR);
+  double sL = ora_wave_speed(qL, n, gamma);
+  double sR = ora_wave_speed(qR, n, gamma);
+  double s = (sL >= sR) ? sL : sR;
+  for (int k = 0; k < NV; k++)
+    F[k] = 0.5 * (fL[k] + fR[k]) - 0.5 * s * (qR[k] - qL[k]);
+}
+
+double ora_van_albada(double a, double b, double eps) {
+  return (a * (b * b + eps) + b * (a * a + eps)) / (a * a + b * b + 2.0 * eps);
+}
+
+/* limited linear reconstruction of the two face states of edge (i, j) */
+void ora_reconstruct(const double qi[NV], const double qj[NV],
+                     const double Gi[NG], const double Gj[NG],
+                     const double dx[3], double eps, double qL[NV],
+                     double qR[NV]) {
+  for (int k = 0; k < NV; k++) {
+    double b = qj[k] - qi[k];
+    double ai = Gi[k * 3 + 0] * dx[0] + Gi[k * 3 + 1] * dx[1] + Gi[k * 3 + 2] * dx[2];
+    double aj = Gj[k * 3 + 0] * dx[0] + Gj[k * 3 + 1] * dx[1] + Gj[k * 3 + 2] * dx[2];
+    qL[k] = qi[k] + 0.5 * ora_van_albada(ai, b, eps);
+    qR[k] = qj[k] - 0.5 * ora_van_albada(aj, b, eps);
+  }
+}
+
+/* ------------------------------------------------------------- the loops */
+
+/* first-order residual: R = sum over edges of +-F(q_i, q_j, n_e).
+ * Rabs (nullable) receives sum_e |F_e,k| per node (the scale of R). */
+void ora_flux1(int64_t N, int64_t E, const int32_t* edge, const double* q,
+               const double* n, double gamma, double* R, double* Rabs) {
+  memset(R, 0, sizeof(double) * NV * N);
+  if (Rabs) memset(Rabs, 0, sizeof(double) * NV * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    double F[NV];
+    ora_rusanov(q + NV * i, q + NV * j, n + 3 * e, gamma, F);
+    for (int k = 0; k < NV; k++) {
+      R[NV * i + k] += F[k];
+      R[NV * j + k] -= F[k];
+      if (Rabs) {
+        Rabs[NV * i + k] += fabs(F[k]);
+        Rabs[NV * j + k] += fabs(F[k]);
+      }
+    }
+  }
+}
+
+/* Green-Gauss edge loop, unscaled: Graw.  Gabs (nullable) gets the sum of
+ * the absolute values of the contributions. */
+void ora_green_gauss(int64_t N, int64_t E, const int32_t* edge,
+                     const double* q, const double* n, double* Graw,
+                     double* Gabs) {
+  memset(Graw, 0, sizeof(double) * NG * N);
+  if (Gabs) memset(Gabs, 0, sizeof(double) * NG * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    for (int k = 0; k < NV; k++) {
+      double qf = 0.5 * (q[NV * i + k] + q[NV * j + k]);
+      for (int d = 0; d < 3; d++) {
+        double c = qf * n[3 * e + d];
+        Graw[NG * i + 3 * k + d] += c;
+        Graw[NG * j + 3 * k + d] -= c;
+        if (Gabs) {
+          Gabs[NG * i + 3 * k + d] += fabs(c);
+          Gabs[NG * j + 3 * k + d] += fabs(c);
+        }
+      }
+    }
+  }
+}
+
+/* direct node loop: G = Graw / V */
+void ora_grad_scale(int64_t N, const double* Graw, const double* V, double* G) {
+  for (int64_t i = 0; i < N; i++)
+    for (int c = 0; c < NG; c++) G[NG * i + c] = Graw[NG * i + c] / V[i];
+}
+
+/* second-order residual from given q and G */
+void ora_flux2(int64_t N, int64_t E, const int32_t* edge, const double* q,
+               const double* G, const double* n, const double* dx,
+               double gamma, double eps, double* R, double* Rabs) {
+  memset(R, 0, sizeof(double) * NV * N);
+  if (Rabs) memset(Rabs, 0, sizeof(double) * NV * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    double qL[NV], qR[NV], F[NV];
+    ora_reconstruct(q + NV * i, q + NV * j, G + NG * i, G + NG * j, dx + 3 * e,
+                    eps, qL, qR);
+    ora_rusanov(qL, qR, n + 3 * e, gamma, F);
+    for (int k = 0; k < NV; k++) {
+      R[NV * i + k] += F[k];
+      R[NV * j + k] -= F[k];
+      if (Rabs) {
+        Rabs[NV * i + k] += fabs(F[k]);
+        Rabs[NV * j + k] += fabs(F[k]);
+      }
+    }
+  }
+}
+
+/* full residual R(q, n): order 1 = flux1; order 2 = GG, scale, flux2.
+ * G (nullable) receives the scaled gradient (N x 18). */
+void ora_residual(int order, int64_t N, int64_t E, const int32_t* edge,
+                  const double* q, const double* n, const double* dx,
+                  const double* V, double gamma, double eps, double* G_work,
+                  double* R, double* Rabs) {
+  if (order == 1) {
+    ora_flux1(N, E, edge, q, n, gamma, R, Rabs);
+    return;
+  }
+  ora_green_gauss(N, E, edge, q, n, G_work, 0);
+  ora_grad_scale(N, G_work, V, G_work);
+  ora_flux2(N, E, edge, q, G_work, n, dx, gamma, eps, R, Rabs);
+}
+
+/* setup edge loop: Lambda_i = sum over incident edges of s_e(q_i, q_j) */
+void ora_spectral_radius(int64_t N, int64_t E, const int32_t* edge,
+                         const double* q, const double* n, double gamma,
+                         double* Lam) {
+  memset(Lam, 0, sizeof(double) * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    double sL = ora_wave_speed(q + NV * i, n + 3 * e, gamma);
+    double sR = ora_wave_speed(q + NV * j, n + 3 * e, gamma);
+    double s = (sL >= sR) ? sL : sR;
+    Lam[i] += s;
+    Lam[j] += s;
+  }
+}
+
+/* local time step dt_i = CFL V_i / Lambda_i */
+void ora_time_step(int64_t N, const double* V, const double* Lam, double cfl,
+                   double* dt) {
+  for (int64_t i = 0; i < N; i++) dt[i] = cfl * V[i] / Lam[i];
+}
+
+/* RK stage node update q = q0 - alpha (dt/V) R */
+void ora_rk_update(int64_t N, const double* q0, const double* R,
+                   const double* V, const double* dt, double alpha,
+                   double* q) {
+  for (int64_t i = 0; i < N; i++)
+    for (int k = 0; k < NV; k++)
+      q[NV * i + k] = q0[NV * i + k] - alpha * (dt[i] / V[i]) * R[NV * i + k];
+}
+
+/* 0 if every node has rho > 0 and p > 0, else 1 + the first bad node */
+int64_t ora_check_state(int64_t N, const double* q, double gamma) {
+  for (int64_t i = 0; i < N; i++)
+    if (!(q[NV * i] > 0.0) || !(pressure(q + NV * i, gamma) > 0.0)) return 1 + i;
+  return 0;
+}
+
+static const double RK_ALPHA[5] = {0.25, 1.0 / 6.0, 0.375, 0.5, 1.0};
+
+/* explicit march: `steps` RK steps of `stages` stages (<= 5, Jameson's
+ * coefficients taken from the last `stages`), dt frozen from the initial
+ * state.  Work arrays: q0 (N*6), R (N*6), G (N*18), Lam (N), dt (N).
+ * Returns 0, or -(1 + stage index) at the first positivity failure. */
+int64_t ora_march(int order, int steps, int stages, int64_t N, int64_t E,
+                  const int32_t* edge, double* q, const double* n,
+                  const double* dx, const double* V, double gamma, double eps,
+                  double cfl, double* q0, double* R, double* G, double* Lam,
+                  double* dt) {
+  ora_spectral_radius(N, E, edge, q, n, gamma, Lam);
+  ora_time_step(N, V, Lam, cfl, dt);
+  int64_t count = 0;
+  for (int st = 0; st < steps; st++) {
+    memcpy(q0, q, sizeof(double) * NV * N);
+    for (int k = 0; k < stages; k++) {
+      ora_residual(order, N, E, edge, q, n, dx, V, gamma, eps, G, R, 0);
+      ora_rk_update(N, q0, R, V, dt, RK_ALPHA[5 - stages + k], q);
+      if (ora_check_state(N, q, gamma)) return -(1 + count);
+      count++;
+    }
+  }
+  return 0;
+}
+
+/* --------------------------------------------- tangent (forward) sweep
+ * Linearisation of R(q, n) in the direction (qd, nd); dx and V fixed.
+ * d|x|/dx = sign(x) with sign(0) = 0; the max picks L on ties. */
+
+static double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+/* one side of the Rusanov flux: f(q).n and its wave speed, with tangents */
+static void side_tangent(const double q[NV], const double qd[NV],
+                         const double n[3], const double nd[3], double gamma,
+                         double f[NV], double fd[NV], double* lam,
+                         double* lamd) {
+  double rho = q[0], rhod = qd[0];
+  double mn = q[1] * n[0] + q[2] * n[1] + q[3] * n[2];
+  double mnd = qd[1] * n[0] + qd[2] * n[1] + qd[3] * n[2] +
+               q[1] * nd[0] + q[2] * nd[1] + q[3] * nd[2];
+  double un = mn / rho;
+  double und = mnd / rho - un * rhod / rho;
+  double mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  double mmd = 2.0 * (q[1] * qd[1] + q[2] * qd[2] + q[3] * qd[3]);
+  double p = (gamma - 1.0) * (q[4] - 0.5 * mm / rho);
+  double pd = (gamma - 1.0) *
+              (qd[4] - 0.5 * mmd / rho + 0.5 * mm * rhod / (rho * rho));
+  double a = sqrt(gamma * p / rho);
+  double ad = gamma * pd / (2.0 * a * rho) - a * rhod / (2.0 * rho);
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  double nnd = (n[0] * nd[0] + n[1] * nd[1] + n[2] * nd[2]) / nn;
+  *lam = fabs(un) + a * nn;
+  *lamd = sgn(un) * und + ad * nn + a * nnd;
+  for (int k = 0; k < NV; k++) {
+    f[k] = q[k] * un;
+    fd[k] = qd[k] * un + q[k] * und;
+  }
+  for (int d = 0; d < 3; d++) {
+    f[1 + d] += p * n[d];
+    fd[1 + d] += pd * n[d] + p * nd[d];
+  }
+  f[4] += p * un;
+  fd[4] += pd * un + p * und;
+}
+
+static void rusanov_tangent(const double qL[NV], const double qLd[NV],
+                            const double qR[NV], const double qRd[NV],
+                            const double n[3], const double nd[3],
+                            double gamma, double F[NV], double Fd[NV]) {
+  double fL[NV], fLd[NV], fR[NV], fRd[NV], lL, lLd, lR, lRd;
+  side_tangent(qL, qLd, n, nd, gamma, fL, fLd, &lL, &lLd);
+  side_tangent(qR, qRd, n, nd, gamma, fR, fRd, &lR, &lRd);
+  double s = (lL >= lR) ? lL : lR;
+  double sd = (lL >= lR) ? lLd : lRd;
+  for (int k = 0; k < NV; k++) {
+    F[k] = 0.5 * (fL[k] + fR[k]) - 0.5 * s * (qR[k] - qL[k]);
+    Fd[k] = 0.5 * (fLd[k] + fRd[k]) - 0.5 * sd * (qR[k] - qL[k]) -
+            0.5 * s * (qRd[k] - qLd[k]);
+  }
+}
+
+/* partial derivatives of the van Albada function */
+static void van_albada_partials(double a, double b, double eps, double* phi,
+                                double* pa, double* pb) {
+  double num = a * (b * b + eps) + b * (a * a + eps);
+  double den = a * a + b * b + 2.0 * eps;
+  *phi = num / den;
+  *pa = (b * b + eps + 2.0 * a * b - 2.0 * a * (*phi)) / den;
+  *pb = (a * a + eps + 2.0 * a * b - 2.0 * b * (*phi)) / den;
+}
+
+void ora_residual_tangent(int order, int64_t N, int64_t E,
+                          const int32_t* edge, const double* q,
+                          const double* n, const double* dx, const double* V,
+                          double gamma, double eps, const double* qd,
+                          const double* nd, double* G, double* Gd,
+                          double* Rd) {
+  memset(Rd, 0, sizeof(double) * NV * N);
+  if (order == 2) {
+    /* gradient and its tangent */
+    memset(G, 0, sizeof(double) * NG * N);
+    memset(Gd, 0, sizeof(double) * NG * N);
+    for (int64_t e = 0; e < E; e++) {
+      int64_t i = edge[2 * e], j = edge[2 * e + 1];
+      for (int k = 0; k < NV; k++) {
+        double qf = 0.5 * (q[NV * i + k] + q[NV * j + k]);
+        double qfd = 0.5 * (qd[NV * i + k] + qd[NV * j + k]);
+        for (int d = 0; d < 3; d++) {
+          double c = qf * n[3 * e + d];
+          double cd = qfd * n[3 * e + d] + qf * nd[3 * e + d];
+          G[NG * i + 3 * k + d] += c;
+          G[NG * j + 3 * k + d] -= c;
+          Gd[NG * i + 3 * k + d] += cd;
+          Gd[NG * j + 3 * k + d] -= cd;
+        }
+      }
+    }
+    for (int64_t i = 0; i < N; i++)
+      for (int c = 0; c < NG; c++) {
+        G[NG * i + c] /= V[i];
+        Gd[NG * i + c] /= V[i];
+      }
+  }
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    const double *qi = q + NV * i, *qj = q + NV * j;
+    const double *qid = qd + NV * i, *qjd = qd + NV * j;
+    double qL[NV], qR[NV], qLd[NV], qRd[NV], F[NV], Fd[NV];
+    if (order == 1) {
+      for (int k = 0; k < NV; k++) {
+        qL[k] = qi[k]; qLd[k] = qid[k];
+        qR[k] = qj[k]; qRd[k] = qjd[k];
+      }
+    } else {
+      const double *Gi = G + NG * i, *Gj = G + NG * j;
+      const double *Gid = Gd + NG * i, *Gjd = Gd + NG * j;
+      const double* x = dx + 3 * e;
+      for (int k = 0; k < NV; k++) {
+        double b = qj[k] - qi[k], bd = qjd[k] - qid[k];
+        double ai = Gi[3 * k] * x[0] + Gi[3 * k + 1] * x[1] + Gi[3 * k + 2] * x[2];
+        double aid = Gid[3 * k] * x[0] + Gid[3 * k + 1] * x[1] + Gid[3 * k + 2] * x[2];
+        double aj = Gj[3 * k] * x[0] + Gj[3 * k + 1] * x[1] + Gj[3 * k + 2] * x[2];
+        double ajd = Gjd[3 * k] * x[0] + Gjd[3 * k + 1] * x[1] + Gjd[3 * k + 2] * x[2];
+        double phi, pa, pb, phj, paj, pbj;
+        van_albada_partials(ai, b, eps, &phi, &pa, &pb);
+        van_albada_partials(aj, b, eps, &phj, &paj, &pbj);
+        qL[k] = qi[k] + 0.5 * phi;
+        qLd[k] = qid[k] + 0.5 * (pa * aid + pb * bd);
+        qR[k] = qj[k] - 0.5 * phj;
+        qRd[k] = qjd[k] - 0.5 * (paj * ajd + pbj * bd);
+      }
+    }
+    rusanov_tangent(qL, qLd, qR, qRd, n + 3 * e, nd + 3 * e, gamma, F, Fd);
+    for (int k = 0; k < NV; k++) {
+      Rd[NV * i + k] += Fd[k];
+      Rd[NV * j + k] -= Fd[k];
+    }
+  }
+}
+
+/* --------------------------------------------- reverse (adjoint) sweep
+ * J = lam . R(q, n) = sum_e (lam_i - lam_j) . F_e.  Outputs qb = dJ/dq
+ * (N x 6) and nb = dJ/dn (E x 3).  Work: G (N*18), Gb (N*18). */
+
+/* reverse of one side: given fb (adjoint of f) and lamb (adjoint of the
+ * wave speed), accumulate into qb (6) and nb (3) */
+static void side_reverse(const double q[NV], const double n[3], double gamma,
+                         const double fb[NV], double lamb, double qb[NV],
+                         double nb[3]) {
+  double rho = q[0];
+  double mn = q[1] * n[0] + q[2] * n[1] + q[3] * n[2];
+  double un = mn / rho;
+  double mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  double p = (gamma - 1.0) * (q[4] - 0.5 * mm / rho);
+  double a = sqrt(gamma * p / rho);
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  /* forward: lam = |un| + a nn;  f_k = q_k un (+ p n_d, + p un) */
+  double unb = sgn(un) * lamb;
+  double ab = lamb * nn;
+  double nnb = lamb * a;
+  double pb = 0.0;
+  for (int k = 0; k < NV; k++) {
+    qb[k] += fb[k] * un;
+    unb += fb[k] * q[k];
+  }
+  for (int d = 0; d < 3; d++) {
+    pb += fb[1 + d] * n[d];
+    nb[d] += fb[1 + d] * p;
+  }
+  pb += fb[4] * un;
+  unb += fb[4] * p;
+  /* nn = |n| */
+  for (int d = 0; d < 3; d++) nb[d] += nnb * n[d] / nn;
+  /* a = sqrt(gamma p / rho) */
+  pb += ab * gamma / (2.0 * a * rho);
+  double rhob = -ab * a / (2.0 * rho);
+  /* p = (gamma-1)(q4 - mm/(2 rho)) */
+  qb[4] += (gamma - 1.0) * pb;
+  for (int d = 0; d < 3; d++) qb[1 + d] -= (gamma - 1.0) * pb * q[1 + d] / rho;
+  rhob += (gamma - 1.0) * pb * 0.5 * mm / (rho * rho);
+  /* un = mn / rho */
+  for (int d = 0; d < 3; d++) {
+    qb[1 + d] += unb * n[d] / rho;
+    nb[d] += unb * q[1 + d] / rho;
+  }
+  rhob -= unb * un / rho;
+  qb[0] += rhob;
+}
+
+/* reverse of the Rusanov flux with adjoint weights w = dJ/dF */
+static void rusanov_reverse(const double qL[NV], const double qR[NV],
+                            const double n[3], double gamma,
+                            const double w[NV], double qLb[NV], double qRb[NV],
+                            double nb[3]) {
+  double sL = ora_wave_speed(qL, n, gamma);
+  double sR = ora_wave_speed(qR, n, gamma);
+  double s = (sL >= sR) ? sL : sR;
+  double fb[NV], sb = 0.0;
+  for (int k = 0; k < NV; k++) {
+    fb[k] = 0.5 * w[k];
+    sb -= 0.5 * w[k] * (qR[k] - qL[k]);
+    qRb[k] -= 0.5 * s * w[k];
+    qLb[k] += 0.5 * s * w[k];
+  }
+  double lLb = (sL >= sR) ? sb : 0.0;
+  double lRb = (sL >= sR) ? 0.0 : sb;
+  side_reverse(qL, n, gamma, fb, lLb, qLb, nb);
+  side_reverse(qR, n, gamma, fb, lRb, qRb, nb);
+}
+
+void ora_residual_reverse(int order, int64_t N, int64_t E,
+                          const int32_t* edge, const double* q,
+                          const double* n, const double* dx, const double* V,
+                          double gamma, double eps, const double* lam,
+                          double* G, double* Gb, double* qb, double* nb) {
+  memset(qb, 0, sizeof(double) * NV * N);
+  memset(nb, 0, sizeof(double) * 3 * E);
+  if (order == 2) {
+    ora_green_gauss(N, E, edge, q, n, G, 0);
+    ora_grad_scale(N, G, V, G);
+    memset(Gb, 0, sizeof(double) * NG * N);
+  }
+  /* flux edge loop, reversed */
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    const double *qi = q + NV * i, *qj = q + NV * j;
+    double w[NV];
+    for (int k = 0; k < NV; k++) w[k] = lam[NV * i + k] - lam[NV * j + k];
+    double qL[NV], qR[NV], qLb[NV] = {0}, qRb[NV] = {0};
+    if (order == 1) {
+      for (int k = 0; k < NV; k++) { qL[k] = qi[k]; qR[k] = qj[k]; }
+    } else {
+      ora_reconstruct(qi, qj, G + NG * i, G + NG * j, dx + 3 * e, eps, qL, qR);
+    }
+    rusanov_reverse(qL, qR, n + 3 * e, gamma, w, qLb, qRb, nb + 3 * e);
+    if (order == 1) {
+      for (int k = 0; k < NV; k++) {
+        qb[NV * i + k] += qLb[k];
+        qb[NV * j + k] += qRb[k];
+      }
+      continue;
+    }
+    const double *Gi = G + NG * i, *Gj = G + NG * j;
+    const double* x = dx + 3 * e;
+    for (int k = 0; k < NV; k++) {
+      double b = qj[k] - qi[k];
+      double ai = Gi[3 * k] * x[0] + Gi[3 * k + 1] * x[1] + Gi[3 * k + 2] * x[2];
+      double aj = Gj[3 * k] * x[0] + Gj[3 * k + 1] * x[1] + Gj[3 * k + 2] * x[2];
+      double phi, pa, pb, phj, paj, pbj;
+      van_albada_partials(ai, b, eps, &phi, &pa, &pb);
+      van_albada_partials(aj, b, eps, &phj, &paj, &pbj);
+      /* qL = qi + phi/2 ; qR = qj - phj/2 */
+      qb[NV * i + k] += qLb[k];
+      qb[NV * j + k] += qRb[k];
+      double phib = 0.5 * qLb[k];
+      double phjb = -0.5 * qRb[k];
+      double aib = phib * pa, ajb = phjb * paj;
+      double bb = phib * pb + phjb * pbj;
+      /* b = qj - qi */
+      qb[NV * j + k] += bb;
+      qb[NV * i + k] -= bb;
+      /* ai = Gi[k].dx, aj = Gj[k].dx */
+      for (int d = 0; d < 3; d++) {
+        Gb[NG * i + 3 * k + d] += aib * x[d];
+        Gb[NG * j + 3 * k + d] += ajb * x[d];
+      }
+    }
+  }
+  if (order == 1) return;
+  /* scaling G = Graw / V, reversed */
+  for (int64_t i = 0; i < N; i++)
+    for (int c = 0; c < NG; c++) Gb[NG * i + c] /= V[i];
+  /* Green-Gauss edge loop, reversed */
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    for (int k = 0; k < NV; k++) {
+      double qf = 0.5 * (q[NV * i + k] + q[NV * j + k]);
+      double qfb = 0.0;
+      for (int d = 0; d < 3; d++) {
+        double cb = Gb[NG * i + 3 * k + d] - Gb[NG * j + 3 * k + d];
+        qfb += cb * n[3 * e + d];
+        nb[3 * e + d] += cb * qf;
+      }
+      qb[NV * i + k] += 0.5 * qfb;
+      qb[NV * j + k] += 0.5 * qfb;
+    }
+  }
+}
+
+/* per-edge distance to the non-differentiable points: min(|uL.n|, |uR.n|,
+ * |sL - sR|) of the face states (used to keep finite differences away) */
+void ora_kink_margin(int order, int64_t N, int64_t E, const int32_t* edge,
+                     const double* q, const double* n, const double* dx,
+                     const double* V, double gamma, double eps, double* G,
+                     double* margin) {
+  if (order == 2) {
+    ora_green_gauss(N, E, edge, q, n, G, 0);
+    ora_grad_scale(N, G, V, G);
+  }
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    double qL[NV], qR[NV];
+    if (order == 1) {
+      for (int k = 0; k < NV; k++) { qL[k] = q[NV * i + k]; qR[k] = q[NV * j + k]; }
+    } else {
+      ora_reconstruct(q + NV * i, q + NV * j, G + NG * i, G + NG * j,
+                      dx + 3 * e, eps, qL, qR);
+    }
+    const double* ne = n + 3 * e;
+    double unL = (qL[1] * ne[0] + qL[2] * ne[1] + qL[3] * ne[2]) / qL[0];
+    double unR = (qR[1] * ne[0] + qR[2] * ne[1] + qR[3] * ne[2]) / qR[0];
+    double m = fabs(unL);
+    if (fabs(unR) < m) m = fabs(unR);
+    double ds = fabs(ora_wave_speed(qL, ne, gamma) - ora_wave_speed(qR, ne, gamma));
+    if (ds < m) m = ds;
+    margin[e] = m;
+  }
+}

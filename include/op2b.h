@@ -1,0 +1,295 @@
+/*
+ * op2b: edge loops of an edge-based unstructured finite-volume solver on
+ * one GB300 (sm_103a), behind a C ABI in the set / map / dat / parallel-loop
+ * model of the paper (Reguly et al., "Acceleration of a Full-scale
+ * Industrial CFD Application with OP2", Sec. 3.1 "The OP2 API",
+ * Fig. "declOP2" and Fig. "OP2loop").
+ *
+ * Conventions for every entry point:
+ *  - return 0 (OP2B_OK) or a negative OP2B_E* code; no C++ exception ever
+ *    crosses the ABI; the text of the last error of a context is returned by
+ *    op2b_last_error().
+ *  - device pointers are borrowed: the caller allocates and frees the device
+ *    memory behind every dat (it must outlive the dat's use).  The library
+ *    owns its copies of the maps, its execution plans and its scratch.
+ *  - work is launched asynchronously on the context's stream; launch errors
+ *    are reported with OP2B_ECUDA, never by aborting.
+ *  - dats are structure-of-arrays: component k of element i lives at
+ *    ptr[k * ld + i], ld >= set size (Sec. 4.1.2 of the paper: SoA gave
+ *    +40% on the GPU).  Maps are element-major on input, as in Fig.
+ *    "declOP2" (entry k of element e at data[e * arity + k]) and 0-based.
+ *  - loops take OP2-style argument lists (dat, map index, map, access).
+ *    A direct argument has map = OP2B_ID and idx = -1.  The INC race on
+ *    indirectly incremented dats is resolved by the strategy chosen for the
+ *    loop (block colouring, FP64/FP32 atomics or sorted segmented
+ *    reductions, Sec. 4.1 "execution plan"), set by op2b_set_strategy() or
+ *    picked by the autotuner on measured time.
+ */
+#ifndef OP2B_H
+#define OP2B_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define OP2B_OK 0
+#define OP2B_EINVAL (-1)   /* bad handle, null pointer, bad size or flag */
+#define OP2B_EDIM (-2)     /* dat dimension does not match the loop */
+#define OP2B_ETYPE (-3)    /* dat element type does not match the loop */
+#define OP2B_EACCESS (-4)  /* wrong access mode (e.g. INC on a direct arg) */
+#define OP2B_ESET (-5)     /* dat lives on another set than the map/loop */
+#define OP2B_ENOMEM (-6)   /* device or host allocation failed */
+#define OP2B_ECUDA (-7)    /* a CUDA call or kernel launch failed */
+#define OP2B_ETIMEOUT (-8) /* an autotuner candidate exceeded its deadline */
+#define OP2B_EPLAN (-9)    /* an execution plan could not be built */
+#define OP2B_ERANGE (-10)  /* a size exceeds what the library supports */
+
+typedef struct op2b_ctx_s* op2b_ctx;
+typedef int32_t op2b_set;
+typedef int32_t op2b_map;
+typedef int32_t op2b_dat;
+
+/* access descriptors (Fig. "OP2loop": OP_READ, OP_WRITE, OP_RW, OP_INC) */
+#define OP2B_READ 1
+#define OP2B_WRITE 2
+#define OP2B_RW 3
+#define OP2B_INC 4
+
+/* element types */
+#define OP2B_F64 0
+#define OP2B_F32 1
+#define OP2B_I32 2
+
+/* the identity "map" of a direct argument (OP_ID in the paper) */
+#define OP2B_ID (-1)
+
+/* one loop argument, like op_arg_dat(dat, idx, map, dim, type, access) */
+typedef struct {
+  op2b_dat dat;
+  int32_t idx; /* which map entry (0 or 1 for an edge->node map); -1 direct */
+  op2b_map map;
+  int32_t acc; /* OP2B_READ / WRITE / RW / INC */
+} op2b_arg;
+
+/* loop identifiers, for strategies, the autotuner and plan statistics */
+#define OP2B_LOOP_GREEN_GAUSS 0
+#define OP2B_LOOP_FLUX1 1
+#define OP2B_LOOP_FLUX2 2
+#define OP2B_LOOP_SPECTRAL 3
+#define OP2B_LOOP_FLUX1_ADJ 4
+#define OP2B_LOOP_FLUX2_ADJ 5
+#define OP2B_LOOP_GG_ADJ 6
+#define OP2B_NUM_LOOPS 7
+
+/* arithmetic variant of a loop: all-FP64, or FP32 node data and arithmetic
+ * (the INC precision is then fixed by the loop: FP64 residuals, FP32
+ * gradients) */
+#define OP2B_PREC_F64 0
+#define OP2B_PREC_F32 1
+
+/* race-resolution strategies (Sec. 4.1: mini-partitions with block
+ * colouring; the other two are not in the paper) */
+#define OP2B_STRAT_AUTO 0      /* autotune on the next call, then reuse */
+#define OP2B_STRAT_ATOMIC 1    /* one thread per edge, atomic adds */
+#define OP2B_STRAT_COLOUR 2    /* coloured edge blocks, shared-memory sums */
+#define OP2B_STRAT_SEGMENTED 3 /* per-edge results, then per-node sums over
+                                  the node-sorted edge ends */
+
+/* loop flags */
+#define OP2B_ZERO_INC 1 /* zero the INC targets first (they receive the sum) */
+
+typedef struct {
+  int32_t order;  /* 1: first order (q_i, q_j); 2: limited reconstruction */
+  int32_t flags;  /* OP2B_ZERO_INC */
+  double gamma;   /* ratio of specific heats */
+  double eps_lim; /* van Albada epsilon (absolute) */
+} op2b_flux_params;
+
+typedef struct {
+  int32_t strategy, block, part, staged; /* what the loop runs with */
+  int64_t nblocks;     /* edge blocks (mini-partitions) of the plan */
+  int64_t ncolours;    /* block colours */
+  int64_t min_blocks_per_colour, max_blocks_per_colour;
+  int64_t max_unique_nodes; /* largest number of distinct nodes of a block */
+  double avg_unique_nodes;  /* mean distinct nodes per block */
+  double tuned_ms;     /* autotuner's best time (0 if not tuned) */
+} op2b_plan_stats_t;
+
+/* ------------------------------------------------------------ lifecycle */
+/* Create a context on CUDA device `device`, launching on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+int op2b_init(op2b_ctx* out, int32_t device, void* cuda_stream);
+/* Free every library-owned allocation of the context. */
+int op2b_finalize(op2b_ctx ctx);
+/* Launch subsequent work on another stream. */
+int op2b_set_stream(op2b_ctx ctx, void* cuda_stream);
+/* Text of the context's last error ("" if none).  Valid until the next
+ * call on the context.  With ctx == NULL: the last init failure. */
+const char* op2b_last_error(op2b_ctx ctx);
+const char* op2b_version(void);
+
+/* --------------------------------------------------------- declarations
+ * Sec. 3.1, Fig. "declOP2": sets, maps between sets and data on sets. */
+
+/* A named iteration space of `size` elements (size >= 0). */
+int op2b_decl_set(op2b_ctx ctx, int64_t size, const char* name, op2b_set* out);
+/* A map from every element of `from` to `arity` elements of `to`;
+ * host_data holds from.size * arity 0-based indices, element-major.  The
+ * data is copied (host and device).  Indices outside [0, to.size) give
+ * OP2B_EINVAL.  Only arity 2 maps can drive the edge loops. */
+int op2b_decl_map(op2b_ctx ctx, op2b_set from, op2b_set to, int32_t arity,
+                  const int32_t* host_data, const char* name, op2b_map* out);
+/* Data of `dim` components per element of `set` in caller-owned device
+ * memory (SoA with leading dimension ld >= set size; ld = 0 means the set
+ * size).  type is OP2B_F64, OP2B_F32 or OP2B_I32. */
+int op2b_decl_dat(op2b_ctx ctx, op2b_set set, int32_t dim, int32_t type,
+                  void* device_ptr, int64_t ld, const char* name,
+                  op2b_dat* out);
+/* Point a dat at another buffer of the same shape (e.g. a new tensor). */
+int op2b_rebind_dat(op2b_ctx ctx, op2b_dat dat, void* device_ptr);
+/* Copy the map's current (possibly renumbered) table to host memory,
+ * element-major, from.size * arity entries. */
+int op2b_fetch_map(op2b_ctx ctx, op2b_map map, int32_t* host_out);
+
+/* ---------------------------------------------------------- renumbering
+ * Sec. 4: renumbering the sets for cache locality (+17% for Hydra).
+ * method: 0 none (edges are still sorted), 1 random (seeded SplitMix64),
+ * 2 reverse Cuthill-McKee.  The node permutation is applied in place to
+ * every dat declared on the map's to-set, and the edge order (edges sorted
+ * by (min end, max end), orientation kept) to every dat on its from-set,
+ * through a library scratch buffer.  node_perm_out (host, nullable) gets
+ * new id of each old node; edge_order_out (host, nullable) the old index
+ * of each new edge.  Plans of the map are rebuilt on their next use. */
+int op2b_renumber(op2b_ctx ctx, op2b_map edge2node, int32_t method,
+                  uint64_t seed, int32_t* node_perm_out,
+                  int64_t* edge_order_out);
+
+/* ----------------------------------------------------------- edge loops
+ * Sec. 3.1, Fig. "OP2loop": a loop over the edge set that reads node data
+ * through an arity-2 edge->node map and increments both end nodes (INC).
+ * All indirect arguments must use the same map.  With OP2B_ZERO_INC the
+ * INC dats are zeroed first; otherwise the loop adds to them.  The loop's
+ * precision (OP2B_PREC_F64 / F32) is the type of its READ node dats. */
+
+/* Green-Gauss gradient sums, per edge (i, j) with normal n:
+ *   Graw_i[k][d] += (q_i,k + q_j,k)/2 * n_d,  Graw_j[k][d] -= the same.
+ * args (5): q idx 0 READ, q idx 1 READ (node, dim 6), n OP2B_ID READ
+ * (edge, dim 3), G idx 0 INC, G idx 1 INC (node, dim 18, component 3k+d).
+ * All five of one type (F64, or F32 with FP32 sums). */
+int op2b_green_gauss(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                     int32_t flags);
+
+/* Rusanov edge flux (Euler, 6 conserved variables incl. a passive scalar):
+ *   R_i += F(qL, qR, n),  R_j -= F(qL, qR, n).
+ * order 1: qL = q_i, qR = q_j.  args (5): q 0 READ, q 1 READ, n ID READ,
+ *   R 0 INC, R 1 INC.
+ * order 2: van Albada-limited linear reconstruction
+ *   qL = q_i + phi(G_i.dx, q_j - q_i)/2,  qR = q_j - phi(G_j.dx, q_j - q_i)/2.
+ *   args (8): q 0 READ, q 1 READ, G 0 READ, G 1 READ, n ID READ,
+ *   dx ID READ (edge, dim 3), R 0 INC, R 1 INC.
+ * R is always F64 (dim 6).  q, G, n, dx are all F64 or all F32; with F32 the
+ * flux arithmetic is FP32 and each edge's flux is converted to FP64 before
+ * it is added into R. */
+int op2b_edge_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                   const op2b_flux_params* prm);
+
+/* Spectral radius for the local time step:
+ *   Lam_i += s_e, Lam_j += s_e,  s_e = max over the two end states of
+ *   |u.n| + a|n|.
+ * args (5): q 0 READ, q 1 READ (F64 dim 6), n ID READ (F64), Lam 0 INC,
+ * Lam 1 INC (F64 dim 1). */
+int op2b_spectral_radius(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                         double gamma, int32_t flags);
+
+/* Adjoint (transpose) of the flux loop for J = lam . R:
+ * per edge w = lam_i - lam_j; the face states are recomputed from the node
+ * data and the flux Jacobian-transpose products are scattered to both ends.
+ * order 1 args (8): lam 0 READ, lam 1 READ, q 0 READ, q 1 READ, n ID READ,
+ *   qbar 0 INC, qbar 1 INC, nbar ID WRITE.
+ * order 2 args (13): lam 0, lam 1, q 0, q 1, G 0, G 1 (READ), n ID READ,
+ *   dx ID READ, qbar 0 INC, qbar 1 INC, Gbar 0 INC, Gbar 1 INC (dim 18),
+ *   nbar ID WRITE (edge, dim 3).  All F64. */
+int op2b_edge_flux_adjoint(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                           const op2b_flux_params* prm);
+
+/* Adjoint of the Green-Gauss loop: with d = Gbar_i - Gbar_j (unscaled),
+ *   qbar_i,k += sum_d d[k][d] n_d / 2,  qbar_j,k += the same,
+ *   nbar_e[d] += sum_k (q_i,k + q_j,k)/2 d[k][d].
+ * args (8): Gbar 0 READ, Gbar 1 READ (dim 18), q 0 READ, q 1 READ,
+ * n ID READ, qbar 0 INC, qbar 1 INC, nbar ID RW.  All F64. */
+int op2b_green_gauss_adjoint(op2b_ctx ctx, const op2b_arg* args,
+                             int32_t nargs, int32_t flags);
+
+/* ----------------------------------------------------------- node loops
+ * Direct loops over the node set (no map). */
+
+/* G <- G / V (G dim 18 F64 or F32, RW; V dim 1 F64, READ). */
+int op2b_grad_scale(op2b_ctx ctx, op2b_dat G, op2b_dat V);
+/* Reverse of the scaling: Gbar <- Gbar / V. */
+int op2b_grad_scale_adjoint(op2b_ctx ctx, op2b_dat Gbar, op2b_dat V);
+/* dt_i = cfl V_i / Lam_i (all F64 dim 1). */
+int op2b_time_step(op2b_ctx ctx, op2b_dat V, op2b_dat lam, double cfl,
+                   op2b_dat dt);
+/* Runge-Kutta stage update q = q0 - alpha (dt/V) R (F64 dim 6, F64 dim 1);
+ * q32 (F32 dim 6, or -1) receives the FP32 shadow of the new q. */
+int op2b_node_update(op2b_ctx ctx, op2b_dat q0, op2b_dat q, op2b_dat R,
+                     op2b_dat V, op2b_dat dt, double alpha, op2b_dat q32);
+/* Set every component of a dat to `value`. */
+int op2b_dat_fill(op2b_ctx ctx, op2b_dat dat, double value);
+/* dst = src component-wise (same set and dim; F64 <-> F32 conversion). */
+int op2b_dat_copy(op2b_ctx ctx, op2b_dat dst, op2b_dat src);
+
+/* ------------------------------------------------ planner and autotuner
+ * Sec. 4.1: the execution plan (mini-partitions, block colours) is built
+ * once per loop and reused; block sizes were autotuned into a lookup table
+ * (Sec. 4.1.2).  Here the tuner also picks the race-resolution strategy. */
+
+/* Fix the strategy of (loop, prec).  block: threads per CTA (32..1024,
+ * 0 = default); part: edges per block for OP2B_STRAT_COLOUR (64..8192,
+ * 0 = default); staged: stage each block's node data in shared memory
+ * (COLOUR only).  OP2B_STRAT_AUTO makes the next call of the loop time the
+ * candidates (writing into scratch copies of its INC dats) and keep the
+ * fastest. */
+int op2b_set_strategy(op2b_ctx ctx, int32_t loop, int32_t prec,
+                      int32_t strategy, int32_t block, int32_t part,
+                      int32_t staged);
+/* Deadline for one autotuner candidate in milliseconds (default 20000);
+ * a candidate that has not finished by then gives OP2B_ETIMEOUT. */
+int op2b_set_tune_deadline(op2b_ctx ctx, double ms);
+/* Save / load the tuned strategies as a JSON object keyed by loop,
+ * precision and set sizes. */
+int op2b_save_tuning(op2b_ctx ctx, const char* path);
+int op2b_load_tuning(op2b_ctx ctx, const char* path);
+/* Strategy and plan statistics of (loop, prec) on `map`. */
+int op2b_plan_stats(op2b_ctx ctx, int32_t loop, int32_t prec, op2b_map map,
+                    op2b_plan_stats_t* out);
+/* Number of kernels the context has launched so far. */
+int64_t op2b_launch_count(op2b_ctx ctx);
+
+/* ------------------------------------------------ host-only planners
+ * Pure host functions (no context, no GPU), exported for validation. */
+
+/* Reverse Cuthill-McKee: new id of every node.  edge: E x 2 element-major. */
+int op2b_host_rcm(int64_t N, int64_t E, const int32_t* edge,
+                  int32_t* new_of_old);
+/* Node permutation of `method` (as op2b_renumber) and the resulting edge
+ * order (old index of each new edge). */
+int op2b_host_renumber(int64_t N, int64_t E, const int32_t* edge,
+                       int32_t method, uint64_t seed, int32_t* new_of_old,
+                       int64_t* edge_order);
+/* Block colouring of consecutive edge blocks of `part` edges: colour of
+ * each of the ceil(E/part) blocks; *ncolours receives the colour count. */
+int op2b_host_colour_blocks(int64_t N, int64_t E, const int32_t* edge,
+                            int32_t part, int32_t* block_colour,
+                            int64_t* ncolours);
+/* Node-sorted edge ends: rowptr (N+1) and ends (2E, value 2e + side). */
+int op2b_host_node_csr(int64_t N, int64_t E, const int32_t* edge,
+                       int64_t* rowptr, int64_t* ends);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OP2B_H */

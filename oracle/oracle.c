@@ -10,7 +10,8 @@
  * loop structure: a loop over the edge set that reads node data through the
  * edge->node map and increments both end nodes (OP_INC).  It does not print
  * the numerics, so the formulas below are the textbook ones chosen for the
- * edge-based solver (Sec. 1: Hydra, explicit 5-step Runge-Kutta):
+ * edge-based solver (Sec. 2: Hydra marches with a 5-step Runge-Kutta
+ * scheme):
  *
  *   Euler flux     f(q).n = (rho un, rho u un + p n, (rho E + p) un, c un)
  *   Rusanov        F = (f(qL).n + f(qR).n)/2 - s (qR - qL)/2,

@@ -1,0 +1,47 @@
+"""R(q, n) as a differentiable torch function backed by the adjoint kernels.
+
+``residual(solver, q, n)`` returns the edge-loop residual R (6, N) of the
+state q (6, N) and the edge normals n (3, E) (library numbering, FP64 CUDA
+tensors).  Its backward pass runs the hand-written adjoint edge loops: for
+an incoming gradient lam = dL/dR it returns qbar = lam . dR/dq and
+nbar = lam . dR/dn, recomputing the edge states from q, G and n instead of
+storing them.
+"""
+from __future__ import annotations
+
+import torch
+
+
+class ResidualFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, q, n, solver, order):
+        s = solver
+        s.rebind("q", q.detach().contiguous())
+        s.rebind("n", n.detach().contiguous())
+        out = torch.empty_like(s.t["R"])
+        s.rebind("R", out)
+        s.residual(order)
+        ctx.solver, ctx.order = s, order
+        ctx.save_for_backward(q, n)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_r):
+        s = ctx.solver
+        q, n = ctx.saved_tensors
+        s.rebind("q", q.detach().contiguous())
+        s.rebind("n", n.detach().contiguous())
+        s.rebind("lam", grad_r.detach().double().contiguous())
+        qbar = torch.empty_like(s.t["qbar"])
+        nbar = torch.empty_like(s.t["nbar"])
+        s.rebind("qbar", qbar)
+        s.rebind("nbar", nbar)
+        s.adjoint(ctx.order)
+        return qbar, nbar, None, None
+
+
+def residual(solver, q, n, order=2):
+    """Differentiable R(q, n); the solver must be built with adjoint=True."""
+    if not solver.has_adjoint:
+        raise ValueError("build the EdgeSolver with adjoint=True")
+    return ResidualFn.apply(q, n, solver, order)

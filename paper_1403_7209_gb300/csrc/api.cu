@@ -1,0 +1,1054 @@
+// The op2b C ABI: contexts, sets / maps / dats (Sec. 3.1 of the paper),
+// renumbering (Sec. 4), argument validation of the parallel loops, the
+// execution plans and the autotuner (Sec. 4.1).
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <thread>
+
+#include "internal.h"
+
+using namespace op2b;
+
+static thread_local std::string g_init_err;
+
+#define OP2B_VERSION_STR "op2b 0.1 (sm_103a)"
+
+static const char* kLoopName[OP2B_NUM_LOOPS] = {
+    "green_gauss", "flux1", "flux2", "spectral", "flux1_adj", "flux2_adj", "gg_adj"};
+
+// ------------------------------------------------------------------ Ctx
+namespace op2b {
+
+int Ctx::launched(const char* what) {
+  launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(OP2B_ECUDA, std::string("kernel launch (") + what + "): " + cudaGetErrorString(e));
+  return OP2B_OK;
+}
+
+int Ctx::need_scratch(size_t bytes, void** out) {
+  if (bytes > scratch_bytes) {
+    if (scratch) {
+      cudaStreamSynchronize(stream);
+      cudaFree(scratch);
+      scratch = nullptr;
+      scratch_bytes = 0;
+    }
+    if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(OP2B_ENOMEM, "scratch allocation of " + std::to_string(bytes) + " B failed");
+    }
+    scratch_bytes = bytes;
+  }
+  *out = scratch;
+  return OP2B_OK;
+}
+
+template <typename T>
+static int upload(Ctx* c, T** dst, const std::vector<T>& v) {
+  size_t b = std::max<size_t>(1, v.size() * sizeof(T));
+  if (cudaMalloc((void**)dst, b) != cudaSuccess) {
+    cudaGetLastError();
+    return c->fail(OP2B_ENOMEM, "plan allocation failed");
+  }
+  if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return c->fail(OP2B_ECUDA, "plan upload failed");
+  return OP2B_OK;
+}
+
+static void free_block_plan(DevBlockPlan& p) {
+  cudaFree(p.bn_off);
+  cudaFree(p.bnodes);
+  cudaFree(p.lrow);
+  cudaFree(p.cblocks);
+  cudaFree(p.eloc);
+  cudaFree(p.lent);
+  p = DevBlockPlan();
+}
+
+static void free_seg_plan(DevSegPlan& p) {
+  cudaFree(p.rowptr);
+  cudaFree(p.ends);
+  p = DevSegPlan();
+}
+
+static void split_map(const MapRec& m, std::vector<int32_t>& m0, std::vector<int32_t>& m1) {
+  int64_t E = (int64_t)m.host.size() / 2;
+  m0.resize(E);
+  m1.resize(E);
+  for (int64_t e = 0; e < E; e++) {
+    m0[e] = m.host[2 * e];
+    m1[e] = m.host[2 * e + 1];
+  }
+}
+
+int Ctx::block_plan(int map, int32_t part, DevBlockPlan** out) {
+  if (part <= 0) part = 512;
+  if (part > 8192) return fail(OP2B_EINVAL, "partition size must be <= 8192");
+  MapRec& m = maps[map];
+  // a partition never needs to be longer than the edge set
+  const int64_t E = sets[m.from].size;
+  if (E < part) part = (int32_t)std::max<int64_t>(1, E);
+  auto key = std::make_pair(map, (int)part);
+  auto it = bplans.find(key);
+  if (it != bplans.end() && it->second.map_version == m.version) {
+    *out = &it->second;
+    return OP2B_OK;
+  }
+  if (it != bplans.end()) {
+    cudaStreamSynchronize(stream);
+    free_block_plan(it->second);
+  }
+  std::vector<int32_t> m0, m1;
+  split_map(m, m0, m1);
+  BlockPlan hp;
+  std::string e;
+  if (!build_block_plan(sets[m.to].size, (int64_t)m0.size(), m0.data(), m1.data(), part, &hp, &e))
+    return fail(OP2B_EPLAN, e);
+  DevBlockPlan& d = bplans[key];
+  d.map_version = m.version;
+  d.part = part;
+  d.nblocks = hp.nblocks;
+  d.ncolours = hp.ncolours;
+  d.max_unique = hp.max_unique;
+  d.avg_unique = hp.avg_unique;
+  d.coff = hp.coff;
+  d.min_per_colour = hp.nblocks;
+  d.max_per_colour = 0;
+  for (int32_t k = 0; k < hp.ncolours; k++) {
+    int64_t nbk = hp.coff[k + 1] - hp.coff[k];
+    d.min_per_colour = std::min(d.min_per_colour, nbk);
+    d.max_per_colour = std::max(d.max_per_colour, nbk);
+  }
+  int rc;
+  if ((rc = upload(this, &d.bn_off, hp.bn_off)) || (rc = upload(this, &d.bnodes, hp.bnodes)) ||
+      (rc = upload(this, &d.eloc, hp.eloc)) || (rc = upload(this, &d.lrow, hp.lrow)) ||
+      (rc = upload(this, &d.lent, hp.lent)) || (rc = upload(this, &d.cblocks, hp.cblocks))) {
+    free_block_plan(d);
+    bplans.erase(key);
+    return rc;
+  }
+  *out = &d;
+  return OP2B_OK;
+}
+
+int Ctx::seg_plan(int map, DevSegPlan** out) {
+  MapRec& m = maps[map];
+  auto it = splans.find(map);
+  if (it != splans.end() && it->second.map_version == m.version) {
+    *out = &it->second;
+    return OP2B_OK;
+  }
+  if (it != splans.end()) {
+    cudaStreamSynchronize(stream);
+    free_seg_plan(it->second);
+  }
+  std::vector<int32_t> m0, m1;
+  split_map(m, m0, m1);
+  if ((int64_t)m0.size() * 2 >= ((int64_t)1 << 31))
+    return fail(OP2B_ERANGE, "segmented plan: more than 2^30 edges");
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ends;
+  node_csr(sets[m.to].size, (int64_t)m0.size(), m0.data(), m1.data(), &rp, &ends);
+  DevSegPlan& d = splans[map];
+  d.map_version = m.version;
+  int rc;
+  if ((rc = upload(this, &d.rowptr, rp)) || (rc = upload(this, &d.ends, ends))) {
+    free_seg_plan(d);
+    splans.erase(map);
+    return rc;
+  }
+  *out = &d;
+  return OP2B_OK;
+}
+
+}  // namespace op2b
+
+// ------------------------------------------------------------- lifecycle
+#define CTX_CHECK(c)                                  \
+  do {                                                \
+    if (!(c)) return OP2B_EINVAL;                     \
+  } while (0)
+
+struct op2b_ctx_s {
+  Ctx c;
+};
+
+extern "C" const char* op2b_version(void) { return OP2B_VERSION_STR; }
+
+extern "C" int op2b_init(op2b_ctx* out, int32_t device, void* stream) {
+  if (!out) return OP2B_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    g_init_err = std::string("no usable CUDA device: ") +
+                 (e != cudaSuccess ? cudaGetErrorString(e) : "device index out of range");
+    return OP2B_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    g_init_err = "cudaSetDevice failed";
+    return OP2B_ECUDA;
+  }
+  auto* h = new (std::nothrow) op2b_ctx_s();
+  if (!h) return OP2B_ENOMEM;
+  Ctx& c = h->c;
+  c.device = device;
+  c.stream = (cudaStream_t)stream;
+  cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c.smem_optin = (size_t)optin;
+  // defaults: FP64 atomics everywhere until told or tuned otherwise
+  for (int l = 0; l < OP2B_NUM_LOOPS; l++)
+    for (int p = 0; p < 2; p++) c.strat[l][p] = Strategy();
+  *out = h;
+  return OP2B_OK;
+}
+
+extern "C" int op2b_finalize(op2b_ctx h) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  cudaStreamSynchronize(c.stream);
+  for (auto& kv : c.bplans) free_block_plan(kv.second);
+  for (auto& kv : c.splans) free_seg_plan(kv.second);
+  for (auto& m : c.maps) cudaFree(m.dev);
+  cudaFree(c.scratch);
+  delete h;
+  return OP2B_OK;
+}
+
+extern "C" int op2b_set_stream(op2b_ctx h, void* stream) {
+  CTX_CHECK(h);
+  h->c.stream = (cudaStream_t)stream;
+  return OP2B_OK;
+}
+
+extern "C" const char* op2b_last_error(op2b_ctx h) {
+  return h ? h->c.err.c_str() : g_init_err.c_str();
+}
+
+extern "C" int64_t op2b_launch_count(op2b_ctx h) { return h ? h->c.launches : -1; }
+
+// ---------------------------------------------------------- declarations
+extern "C" int op2b_decl_set(op2b_ctx h, int64_t size, const char* name, op2b_set* out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!out || size < 0) return c.fail(OP2B_EINVAL, "decl_set: bad size or output");
+  if (size >= ((int64_t)1 << 31) - 1) return c.fail(OP2B_ERANGE, "decl_set: sets are limited to 2^31-2 elements");
+  c.sets.push_back({size, name ? name : ""});
+  *out = (op2b_set)(c.sets.size() - 1);
+  return OP2B_OK;
+}
+
+static bool valid_set(Ctx& c, op2b_set s) { return s >= 0 && s < (op2b_set)c.sets.size(); }
+static bool valid_map(Ctx& c, op2b_map m) { return m >= 0 && m < (op2b_map)c.maps.size(); }
+static bool valid_dat(Ctx& c, op2b_dat d) { return d >= 0 && d < (op2b_dat)c.dats.size(); }
+
+static int upload_map(Ctx& c, MapRec& m) {
+  int64_t F = c.sets[m.from].size;
+  std::vector<int32_t> soa((size_t)F * m.arity);
+  for (int64_t e = 0; e < F; e++)
+    for (int k = 0; k < m.arity; k++) soa[(size_t)k * F + e] = m.host[(size_t)e * m.arity + k];
+  if (!m.dev) {
+    if (cudaMalloc((void**)&m.dev, std::max<size_t>(1, soa.size() * 4)) != cudaSuccess) {
+      cudaGetLastError();
+      return c.fail(OP2B_ENOMEM, "map allocation failed");
+    }
+  }
+  if (!soa.empty() && cudaMemcpy(m.dev, soa.data(), soa.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return c.fail(OP2B_ECUDA, "map upload failed");
+  return OP2B_OK;
+}
+
+extern "C" int op2b_decl_map(op2b_ctx h, op2b_set from, op2b_set to, int32_t arity,
+                             const int32_t* data, const char* name, op2b_map* out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!out || !valid_set(c, from) || !valid_set(c, to) || arity < 1 || arity > 16)
+    return c.fail(OP2B_EINVAL, "decl_map: bad set, arity or output");
+  int64_t F = c.sets[from].size, T = c.sets[to].size;
+  if (F > 0 && !data) return c.fail(OP2B_EINVAL, "decl_map: null data");
+  MapRec m;
+  m.from = from;
+  m.to = to;
+  m.arity = arity;
+  m.name = name ? name : "";
+  m.host.assign(data, data + (size_t)F * arity);
+  for (int32_t v : m.host)
+    if (v < 0 || v >= T) return c.fail(OP2B_EINVAL, "decl_map: index outside the to-set");
+  int rc = upload_map(c, m);
+  if (rc) {
+    cudaFree(m.dev);
+    return rc;
+  }
+  c.maps.push_back(std::move(m));
+  *out = (op2b_map)(c.maps.size() - 1);
+  return OP2B_OK;
+}
+
+static int esize(int type) { return type == OP2B_F64 ? 8 : 4; }
+
+extern "C" int op2b_decl_dat(op2b_ctx h, op2b_set set, int32_t dim, int32_t type, void* ptr,
+                             int64_t ld, const char* name, op2b_dat* out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!out || !valid_set(c, set) || dim < 1 || dim > 64)
+    return c.fail(OP2B_EINVAL, "decl_dat: bad set, dim or output");
+  if (type != OP2B_F64 && type != OP2B_F32 && type != OP2B_I32)
+    return c.fail(OP2B_ETYPE, "decl_dat: unknown type");
+  int64_t n = c.sets[set].size;
+  if (ld == 0) ld = n;
+  if (ld < n) return c.fail(OP2B_EINVAL, "decl_dat: ld smaller than the set size");
+  if (!ptr && n > 0) return c.fail(OP2B_EINVAL, "decl_dat: null device pointer");
+  c.dats.push_back({set, dim, type, ptr, ld, name ? name : ""});
+  *out = (op2b_dat)(c.dats.size() - 1);
+  return OP2B_OK;
+}
+
+extern "C" int op2b_rebind_dat(op2b_ctx h, op2b_dat d, void* ptr) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_dat(c, d)) return c.fail(OP2B_EINVAL, "rebind_dat: bad dat");
+  if (!ptr && c.sets[c.dats[d].set].size > 0) return c.fail(OP2B_EINVAL, "rebind_dat: null pointer");
+  c.dats[d].ptr = ptr;
+  return OP2B_OK;
+}
+
+extern "C" int op2b_fetch_map(op2b_ctx h, op2b_map m, int32_t* out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_map(c, m) || !out) return c.fail(OP2B_EINVAL, "fetch_map: bad map or output");
+  std::copy(c.maps[m].host.begin(), c.maps[m].host.end(), out);
+  return OP2B_OK;
+}
+
+// ----------------------------------------------------------- renumbering
+static int permute_dat(Ctx& c, DatRec& d, const int64_t* idx_dev, int64_t n) {
+  if (n == 0) return OP2B_OK;
+  int es = esize(d.type);
+  void* tmp = nullptr;
+  int rc = c.need_scratch((size_t)d.dim * d.ld * es, &tmp);
+  if (rc) return rc;
+  if ((rc = node_gather(&c, tmp, d.ptr, es, d.ld, d.dim, idx_dev, n))) return rc;
+  if (cudaMemcpy2DAsync(d.ptr, d.ld * es, tmp, d.ld * es, n * es, d.dim, cudaMemcpyDeviceToDevice,
+                        c.stream) != cudaSuccess)
+    return c.fail(OP2B_ECUDA, "renumber: copy back failed");
+  return OP2B_OK;
+}
+
+extern "C" int op2b_renumber(op2b_ctx h, op2b_map mid, int32_t method, uint64_t seed,
+                             int32_t* node_perm_out, int64_t* edge_order_out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_map(c, mid) || c.maps[mid].arity != 2)
+    return c.fail(OP2B_EINVAL, "renumber: needs an arity-2 map");
+  MapRec& m = c.maps[mid];
+  const op2b_set eset = m.from, nset = m.to;
+  const int64_t N = c.sets[nset].size, E = c.sets[eset].size;
+  std::vector<int32_t> nperm(N);
+  std::vector<int64_t> order(E);
+  int rc = op2b_host_renumber(N, E, m.host.data(), method, seed, nperm.data(), order.data());
+  if (rc) return c.fail(rc, "renumber: bad method or map");
+  std::vector<int64_t> old_of_new(N), new_edge(E);
+  for (int64_t i = 0; i < N; i++) old_of_new[nperm[i]] = i;
+  for (int64_t t = 0; t < E; t++) new_edge[order[t]] = t;
+  // maps: reorder rows of maps from a renumbered set, relabel entries into one
+  for (auto& mm : c.maps) {
+    std::vector<int32_t> nh(mm.host.size());
+    int64_t F = c.sets[mm.from].size;
+    for (int64_t r = 0; r < F; r++) {
+      int64_t src = r;
+      if (mm.from == eset) src = order[r];
+      else if (mm.from == nset) src = old_of_new[r];
+      for (int k = 0; k < mm.arity; k++) {
+        int64_t v = mm.host[(size_t)src * mm.arity + k];
+        if (mm.to == nset) v = nperm[v];
+        else if (mm.to == eset) v = new_edge[v];
+        nh[(size_t)r * mm.arity + k] = (int32_t)v;
+      }
+    }
+    if (mm.from == eset || mm.from == nset || mm.to == nset || mm.to == eset) {
+      mm.host.swap(nh);
+      mm.version++;
+      if ((rc = upload_map(c, mm))) return rc;
+    }
+  }
+  // dats on the two sets, through the scratch buffer
+  int64_t* idx = nullptr;
+  if (cudaMalloc((void**)&idx, std::max<int64_t>(1, std::max(N, E)) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(OP2B_ENOMEM, "renumber: index allocation failed");
+  }
+  if (N > 0) cudaMemcpy(idx, old_of_new.data(), N * 8, cudaMemcpyHostToDevice);
+  for (auto& d : c.dats)
+    if (d.set == nset && (rc = permute_dat(c, d, idx, N))) break;
+  if (!rc) {
+    cudaStreamSynchronize(c.stream);
+    if (E > 0) cudaMemcpy(idx, order.data(), E * 8, cudaMemcpyHostToDevice);
+    if (eset != nset)
+      for (auto& d : c.dats)
+        if (d.set == eset && (rc = permute_dat(c, d, idx, E))) break;
+  }
+  cudaStreamSynchronize(c.stream);
+  cudaFree(idx);
+  if (rc) return rc;
+  if (node_perm_out) std::copy(nperm.begin(), nperm.end(), node_perm_out);
+  if (edge_order_out) std::copy(order.begin(), order.end(), edge_order_out);
+  return OP2B_OK;
+}
+
+// ------------------------------------------------------ argument checks
+namespace {
+
+// expected argument: map entry (0/1) or -1 for direct; access; dim;
+// type class: 'P' the loop's precision, 'D' always F64
+struct Spec {
+  int idx;
+  int acc;
+  int dim;
+  char tcls;
+};
+
+struct Checked {
+  int map = -1;
+  int prec = OP2B_PREC_F64;
+  int64_t N = 0, E = 0;
+};
+
+int check_args(Ctx& c, const char* loop, const op2b_arg* a, int nargs, const Spec* sp, int ns,
+               Checked* out) {
+  if (!a || nargs != ns)
+    return c.fail(OP2B_EINVAL, std::string(loop) + ": expected " + std::to_string(ns) + " arguments");
+  int map = -1, ptype = -1;
+  for (int k = 0; k < ns; k++) {
+    if (!valid_dat(c, a[k].dat))
+      return c.fail(OP2B_EINVAL, std::string(loop) + ": argument " + std::to_string(k) + " is not a dat");
+    if (sp[k].idx >= 0) {
+      if (a[k].map == OP2B_ID || !valid_map(c, a[k].map))
+        return c.fail(OP2B_EINVAL, std::string(loop) + ": argument " + std::to_string(k) + " needs a map");
+      if (map < 0) map = a[k].map;
+      if (a[k].map != map)
+        return c.fail(OP2B_EINVAL, std::string(loop) + ": all indirect arguments must use one map");
+    }
+  }
+  if (map < 0) return c.fail(OP2B_EINVAL, std::string(loop) + ": no indirect argument");
+  const MapRec& m = c.maps[map];
+  if (m.arity != 2) return c.fail(OP2B_EINVAL, std::string(loop) + ": the map must have arity 2");
+  for (int k = 0; k < ns; k++) {
+    const op2b_arg& x = a[k];
+    const DatRec& d = c.dats[x.dat];
+    std::string at = std::string(loop) + ": argument " + std::to_string(k) + " (" + d.name + ")";
+    if (sp[k].idx >= 0) {
+      if (x.idx != sp[k].idx) return c.fail(OP2B_EINVAL, at + ": wrong map index");
+      if (d.set != m.to) return c.fail(OP2B_ESET, at + ": dat is not on the map's to-set");
+      if (x.acc == OP2B_WRITE || x.acc == OP2B_RW)
+        return c.fail(OP2B_EACCESS, at + ": WRITE/RW through a map is not allowed (use INC)");
+    } else {
+      if (x.map != OP2B_ID || x.idx != -1) return c.fail(OP2B_EINVAL, at + ": expected a direct argument");
+      if (d.set != m.from) return c.fail(OP2B_ESET, at + ": dat is not on the loop's set");
+      if (x.acc == OP2B_INC) return c.fail(OP2B_EACCESS, at + ": INC on a direct argument");
+    }
+    if (x.acc != sp[k].acc) return c.fail(OP2B_EACCESS, at + ": wrong access mode");
+    if (d.dim != sp[k].dim)
+      return c.fail(OP2B_EDIM, at + ": dim " + std::to_string(d.dim) + ", expected " + std::to_string(sp[k].dim));
+    if (sp[k].tcls == 'D') {
+      if (d.type != OP2B_F64) return c.fail(OP2B_ETYPE, at + ": must be F64");
+    } else {
+      if (d.type != OP2B_F64 && d.type != OP2B_F32) return c.fail(OP2B_ETYPE, at + ": must be F64 or F32");
+      if (ptype < 0) ptype = d.type;
+      if (d.type != ptype) return c.fail(OP2B_ETYPE, at + ": mixed F64/F32 data");
+    }
+  }
+  // the two ends of an indirect dat (adjacent entries 0 and 1) are one dat
+  for (int k = 0; k + 1 < ns; k++)
+    if (sp[k].idx == 0 && sp[k + 1].idx == 1 && a[k].dat != a[k + 1].dat)
+      return c.fail(OP2B_EINVAL, std::string(loop) + ": map entries 0 and 1 of one argument use different dats");
+  out->map = map;
+  out->prec = ptype == OP2B_F32 ? OP2B_PREC_F32 : OP2B_PREC_F64;
+  out->N = c.sets[m.to].size;
+  out->E = c.sets[m.from].size;
+  return OP2B_OK;
+}
+
+const DatRec& D(Ctx& c, const op2b_arg& a) { return c.dats[a.dat]; }
+
+std::string tune_key(const LoopLaunch& L) {
+  return std::string(kLoopName[L.loop]) + ":p" + std::to_string(L.prec) + ":N" + std::to_string(L.N) +
+         ":E" + std::to_string(L.E);
+}
+
+int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
+  if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
+  return L.prec == OP2B_PREC_F32 ? launch_f32(&c, L, s) : launch_f64(&c, L, s);
+}
+
+// wait for an event with a host-side deadline
+int wait_deadline(Ctx& c, cudaEvent_t ev, double ms) {
+  auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return OP2B_OK;
+    if (e != cudaErrorNotReady) return c.fail(OP2B_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (el > ms) return c.fail(OP2B_ETIMEOUT, "autotune: candidate exceeded its deadline");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+std::vector<Strategy> candidates(const LoopLaunch& L) {
+  std::vector<Strategy> v;
+  for (int b : {128, 256, 512}) {
+    Strategy s;
+    s.strategy = OP2B_STRAT_ATOMIC;
+    s.block = b;
+    v.push_back(s);
+  }
+  for (int part : {256, 512, 1024, 2048})
+    for (int st : {0, 1}) {
+      Strategy s;
+      s.strategy = OP2B_STRAT_COLOUR;
+      s.part = part;
+      s.block = std::min(part, 256);
+      s.staged = st;
+      v.push_back(s);
+    }
+  for (int b : {128, 256}) {
+    Strategy s;
+    s.strategy = OP2B_STRAT_SEGMENTED;
+    s.block = b;
+    v.push_back(s);
+  }
+  return v;
+}
+
+// Time every candidate on scratch copies of the outputs; keep the fastest.
+int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, Strategy* best) {
+  LoopLaunch T = L;
+  void *t0 = nullptr, *t1 = nullptr, *td = nullptr;
+  auto alloc = [&](size_t b, void** p) {
+    if (!b) return true;
+    if (cudaMalloc(p, b) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaMemsetAsync(*p, 0, b, c.stream);
+    return true;
+  };
+  if (!alloc(b0, &t0) || !alloc(b1, &t1) || !alloc(bd, &td)) {
+    cudaFree(t0);
+    cudaFree(t1);
+    cudaFree(td);
+    return c.fail(OP2B_ENOMEM, "autotune: scratch outputs");
+  }
+  T.t0 = t0;
+  T.t1 = t1 ? t1 : t0;
+  T.direct = td;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_ms = 1e300;
+  int rc = OP2B_OK, found = 0;
+  for (const Strategy& s : candidates(L)) {
+    int r = dispatch(c, T, s);  // warm-up (also builds the plan)
+    if (r == OP2B_ERANGE) continue;  // does not fit (shared memory)
+    if (r) {
+      rc = r;
+      break;
+    }
+    cudaEventRecord(e0, c.stream);
+    const int reps = 3;
+    for (int k = 0; k < reps && !r; k++) r = dispatch(c, T, s);
+    cudaEventRecord(e1, c.stream);
+    if (r) {
+      rc = r;
+      break;
+    }
+    if ((r = wait_deadline(c, e1, c.tune_deadline_ms))) {
+      rc = r;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    double per = ms / reps;
+    if (per < best_ms) {
+      best_ms = per;
+      *best = s;
+      best->tuned_ms = per;
+      found = 1;
+    }
+  }
+  if (rc == OP2B_ETIMEOUT) {
+    // let the candidate finish before its scratch outputs are freed
+    cudaStreamSynchronize(c.stream);
+  } else {
+    cudaStreamSynchronize(c.stream);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(t0);
+  cudaFree(t1);
+  cudaFree(td);
+  if (rc) return rc;
+  if (!found) return c.fail(OP2B_EPLAN, "autotune: no candidate could run");
+  return OP2B_OK;
+}
+
+size_t dat_bytes(Ctx& c, const DatRec& d) { return (size_t)d.dim * d.ld * esize(d.type); }
+
+// strategy lookup / tuning, optional zeroing, then the launch
+int run_loop(Ctx& c, LoopLaunch& L, int flags, const DatRec* z0, const DatRec* z1,
+             const DatRec* direct) {
+  if ((flags & OP2B_ZERO_INC)) {
+    int rc;
+    if (z0 && (rc = node_fill(&c, z0->ptr, z0->type, z0->ld, z0->dim, L.N, 0.0))) return rc;
+    if (z1 && (rc = node_fill(&c, z1->ptr, z1->type, z1->ld, z1->dim, L.N, 0.0))) return rc;
+  }
+  Strategy& s = c.strat[L.loop][L.prec];
+  if (s.strategy == OP2B_STRAT_AUTO) {
+    auto it = c.tuned.find(tune_key(L));
+    Strategy best;
+    if (it != c.tuned.end()) {
+      best = it->second;
+    } else {
+      int rc = autotune(c, L, z0 ? dat_bytes(c, *z0) : 0, z1 ? dat_bytes(c, *z1) : 0,
+                        direct ? dat_bytes(c, *direct) : 0, &best);
+      if (rc) return rc;
+      c.tuned[tune_key(L)] = best;
+    }
+    s = best;
+  }
+  return dispatch(c, L, s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ edge loops
+extern "C" int op2b_green_gauss(op2b_ctx h, const op2b_arg* a, int32_t nargs, int32_t flags) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  static const Spec sp[5] = {{0, OP2B_READ, 6, 'P'}, {1, OP2B_READ, 6, 'P'}, {-1, OP2B_READ, 3, 'P'},
+                             {0, OP2B_INC, 18, 'P'}, {1, OP2B_INC, 18, 'P'}};
+  Checked ck;
+  int rc = check_args(c, "green_gauss", a, nargs, sp, 5, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = OP2B_LOOP_GREEN_GAUSS;
+  L.prec = ck.prec;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  L.n = D(c, a[2]).ptr;
+  L.ldn = D(c, a[2]).ld;
+  L.t0 = D(c, a[3]).ptr;
+  L.ldt0 = D(c, a[3]).ld;
+  return run_loop(c, L, flags, &D(c, a[3]), nullptr, nullptr);
+}
+
+extern "C" int op2b_edge_flux(op2b_ctx h, const op2b_arg* a, int32_t nargs, const op2b_flux_params* p) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!p || (p->order != 1 && p->order != 2)) return c.fail(OP2B_EINVAL, "edge_flux: order must be 1 or 2");
+  if (!(p->gamma > 1.0) || !(p->eps_lim > 0.0)) return c.fail(OP2B_EINVAL, "edge_flux: need gamma > 1, eps > 0");
+  static const Spec s1[5] = {{0, OP2B_READ, 6, 'P'}, {1, OP2B_READ, 6, 'P'}, {-1, OP2B_READ, 3, 'P'},
+                             {0, OP2B_INC, 6, 'D'}, {1, OP2B_INC, 6, 'D'}};
+  static const Spec s2[8] = {{0, OP2B_READ, 6, 'P'},  {1, OP2B_READ, 6, 'P'},  {0, OP2B_READ, 18, 'P'},
+                             {1, OP2B_READ, 18, 'P'}, {-1, OP2B_READ, 3, 'P'}, {-1, OP2B_READ, 3, 'P'},
+                             {0, OP2B_INC, 6, 'D'},   {1, OP2B_INC, 6, 'D'}};
+  Checked ck;
+  int rc = p->order == 1 ? check_args(c, "edge_flux", a, nargs, s1, 5, &ck)
+                         : check_args(c, "edge_flux", a, nargs, s2, 8, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = p->order == 1 ? OP2B_LOOP_FLUX1 : OP2B_LOOP_FLUX2;
+  L.prec = ck.prec;
+  L.order = p->order;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.gamma = p->gamma;
+  L.eps = p->eps_lim;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  const op2b_arg* R;
+  if (p->order == 1) {
+    L.n = D(c, a[2]).ptr;
+    L.ldn = D(c, a[2]).ld;
+    R = &a[3];
+  } else {
+    L.G = D(c, a[2]).ptr;
+    L.ldG = D(c, a[2]).ld;
+    L.n = D(c, a[4]).ptr;
+    L.ldn = D(c, a[4]).ld;
+    L.dx = D(c, a[5]).ptr;
+    L.lddx = D(c, a[5]).ld;
+    R = &a[6];
+  }
+  L.t0 = D(c, *R).ptr;
+  L.ldt0 = D(c, *R).ld;
+  return run_loop(c, L, p->flags, &D(c, *R), nullptr, nullptr);
+}
+
+extern "C" int op2b_spectral_radius(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamma,
+                                    int32_t flags) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  static const Spec sp[5] = {{0, OP2B_READ, 6, 'D'}, {1, OP2B_READ, 6, 'D'}, {-1, OP2B_READ, 3, 'D'},
+                             {0, OP2B_INC, 1, 'D'}, {1, OP2B_INC, 1, 'D'}};
+  Checked ck;
+  int rc = check_args(c, "spectral_radius", a, nargs, sp, 5, &ck);
+  if (rc) return rc;
+  if (!(gamma > 1.0)) return c.fail(OP2B_EINVAL, "spectral_radius: need gamma > 1");
+  LoopLaunch L;
+  L.loop = OP2B_LOOP_SPECTRAL;
+  L.prec = OP2B_PREC_F64;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.gamma = gamma;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  L.n = D(c, a[2]).ptr;
+  L.ldn = D(c, a[2]).ld;
+  L.t0 = D(c, a[3]).ptr;
+  L.ldt0 = D(c, a[3]).ld;
+  return run_loop(c, L, flags, &D(c, a[3]), nullptr, nullptr);
+}
+
+extern "C" int op2b_edge_flux_adjoint(op2b_ctx h, const op2b_arg* a, int32_t nargs,
+                                      const op2b_flux_params* p) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!p || (p->order != 1 && p->order != 2)) return c.fail(OP2B_EINVAL, "edge_flux_adjoint: order must be 1 or 2");
+  if (!(p->gamma > 1.0) || !(p->eps_lim > 0.0))
+    return c.fail(OP2B_EINVAL, "edge_flux_adjoint: need gamma > 1, eps > 0");
+  static const Spec s1[8] = {{0, OP2B_READ, 6, 'D'},  {1, OP2B_READ, 6, 'D'}, {0, OP2B_READ, 6, 'D'},
+                             {1, OP2B_READ, 6, 'D'},  {-1, OP2B_READ, 3, 'D'}, {0, OP2B_INC, 6, 'D'},
+                             {1, OP2B_INC, 6, 'D'},   {-1, OP2B_WRITE, 3, 'D'}};
+  static const Spec s2[13] = {{0, OP2B_READ, 6, 'D'},   {1, OP2B_READ, 6, 'D'},  {0, OP2B_READ, 6, 'D'},
+                              {1, OP2B_READ, 6, 'D'},   {0, OP2B_READ, 18, 'D'}, {1, OP2B_READ, 18, 'D'},
+                              {-1, OP2B_READ, 3, 'D'},  {-1, OP2B_READ, 3, 'D'}, {0, OP2B_INC, 6, 'D'},
+                              {1, OP2B_INC, 6, 'D'},    {0, OP2B_INC, 18, 'D'},  {1, OP2B_INC, 18, 'D'},
+                              {-1, OP2B_WRITE, 3, 'D'}};
+  Checked ck;
+  int rc = p->order == 1 ? check_args(c, "edge_flux_adjoint", a, nargs, s1, 8, &ck)
+                         : check_args(c, "edge_flux_adjoint", a, nargs, s2, 13, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = p->order == 1 ? OP2B_LOOP_FLUX1_ADJ : OP2B_LOOP_FLUX2_ADJ;
+  L.prec = OP2B_PREC_F64;
+  L.order = p->order;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.gamma = p->gamma;
+  L.eps = p->eps_lim;
+  L.lam = D(c, a[0]).ptr;
+  L.ldl = D(c, a[0]).ld;
+  L.q = D(c, a[2]).ptr;
+  L.ldq = D(c, a[2]).ld;
+  const DatRec *z0, *z1 = nullptr, *dir;
+  if (p->order == 1) {
+    L.n = D(c, a[4]).ptr;
+    L.ldn = D(c, a[4]).ld;
+    z0 = &D(c, a[5]);
+    dir = &D(c, a[7]);
+  } else {
+    L.G = D(c, a[4]).ptr;
+    L.ldG = D(c, a[4]).ld;
+    L.n = D(c, a[6]).ptr;
+    L.ldn = D(c, a[6]).ld;
+    L.dx = D(c, a[7]).ptr;
+    L.lddx = D(c, a[7]).ld;
+    z0 = &D(c, a[8]);
+    z1 = &D(c, a[10]);
+    dir = &D(c, a[12]);
+    L.t1 = z1->ptr;
+    L.ldt1 = z1->ld;
+  }
+  L.t0 = z0->ptr;
+  L.ldt0 = z0->ld;
+  L.direct = dir->ptr;
+  L.lddirect = dir->ld;
+  return run_loop(c, L, p->flags, z0, z1, dir);
+}
+
+extern "C" int op2b_green_gauss_adjoint(op2b_ctx h, const op2b_arg* a, int32_t nargs, int32_t flags) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  static const Spec sp[8] = {{0, OP2B_READ, 18, 'D'}, {1, OP2B_READ, 18, 'D'}, {0, OP2B_READ, 6, 'D'},
+                             {1, OP2B_READ, 6, 'D'},  {-1, OP2B_READ, 3, 'D'}, {0, OP2B_INC, 6, 'D'},
+                             {1, OP2B_INC, 6, 'D'},   {-1, OP2B_RW, 3, 'D'}};
+  Checked ck;
+  int rc = check_args(c, "green_gauss_adjoint", a, nargs, sp, 8, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = OP2B_LOOP_GG_ADJ;
+  L.prec = OP2B_PREC_F64;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.Gb = D(c, a[0]).ptr;
+  L.ldGb = D(c, a[0]).ld;
+  L.q = D(c, a[2]).ptr;
+  L.ldq = D(c, a[2]).ld;
+  L.n = D(c, a[4]).ptr;
+  L.ldn = D(c, a[4]).ld;
+  L.t0 = D(c, a[5]).ptr;
+  L.ldt0 = D(c, a[5]).ld;
+  L.direct = D(c, a[7]).ptr;
+  L.lddirect = D(c, a[7]).ld;
+  return run_loop(c, L, flags, &D(c, a[5]), nullptr, &D(c, a[7]));
+}
+
+// ------------------------------------------------------------ node loops
+static int node_dat(Ctx& c, op2b_dat d, int dim, int type, op2b_set set, const char* what) {
+  if (!valid_dat(c, d)) return c.fail(OP2B_EINVAL, std::string(what) + ": bad dat");
+  const DatRec& r = c.dats[d];
+  if (set >= 0 && r.set != set) return c.fail(OP2B_ESET, std::string(what) + ": dats on different sets");
+  if (dim > 0 && r.dim != dim) return c.fail(OP2B_EDIM, std::string(what) + ": wrong dim (" + r.name + ")");
+  if (type >= 0 && r.type != type) return c.fail(OP2B_ETYPE, std::string(what) + ": wrong type (" + r.name + ")");
+  return OP2B_OK;
+}
+
+static int grad_scale_impl(op2b_ctx h, op2b_dat G, op2b_dat V, const char* what) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  int rc;
+  if ((rc = node_dat(c, G, 18, -1, -1, what))) return rc;
+  const DatRec& g = c.dats[G];
+  if (g.type == OP2B_I32) return c.fail(OP2B_ETYPE, std::string(what) + ": G must be F64 or F32");
+  if ((rc = node_dat(c, V, 1, OP2B_F64, g.set, what))) return rc;
+  return node_grad_scale(&c, g.ptr, g.type, g.ld, (const double*)c.dats[V].ptr, c.sets[g.set].size);
+}
+
+extern "C" int op2b_grad_scale(op2b_ctx h, op2b_dat G, op2b_dat V) {
+  return grad_scale_impl(h, G, V, "grad_scale");
+}
+
+extern "C" int op2b_grad_scale_adjoint(op2b_ctx h, op2b_dat Gb, op2b_dat V) {
+  return grad_scale_impl(h, Gb, V, "grad_scale_adjoint");
+}
+
+extern "C" int op2b_time_step(op2b_ctx h, op2b_dat V, op2b_dat lam, double cfl, op2b_dat dt) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  int rc;
+  if ((rc = node_dat(c, V, 1, OP2B_F64, -1, "time_step"))) return rc;
+  op2b_set s = c.dats[V].set;
+  if ((rc = node_dat(c, lam, 1, OP2B_F64, s, "time_step")) || (rc = node_dat(c, dt, 1, OP2B_F64, s, "time_step")))
+    return rc;
+  if (!(cfl > 0.0)) return c.fail(OP2B_EINVAL, "time_step: cfl must be positive");
+  return node_time_step(&c, (const double*)c.dats[V].ptr, (const double*)c.dats[lam].ptr, cfl,
+                        (double*)c.dats[dt].ptr, c.sets[s].size);
+}
+
+extern "C" int op2b_node_update(op2b_ctx h, op2b_dat q0, op2b_dat q, op2b_dat R, op2b_dat V, op2b_dat dt,
+                                double alpha, op2b_dat q32) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  int rc;
+  if ((rc = node_dat(c, q0, 6, OP2B_F64, -1, "node_update"))) return rc;
+  op2b_set s = c.dats[q0].set;
+  if ((rc = node_dat(c, q, 6, OP2B_F64, s, "node_update")) || (rc = node_dat(c, R, 6, OP2B_F64, s, "node_update")) ||
+      (rc = node_dat(c, V, 1, OP2B_F64, s, "node_update")) || (rc = node_dat(c, dt, 1, OP2B_F64, s, "node_update")))
+    return rc;
+  float* p32 = nullptr;
+  int64_t ld32 = 0;
+  if (q32 >= 0) {
+    if ((rc = node_dat(c, q32, 6, OP2B_F32, s, "node_update"))) return rc;
+    p32 = (float*)c.dats[q32].ptr;
+    ld32 = c.dats[q32].ld;
+  }
+  return node_update(&c, (const double*)c.dats[q0].ptr, c.dats[q0].ld, (double*)c.dats[q].ptr, c.dats[q].ld,
+                     (const double*)c.dats[R].ptr, c.dats[R].ld, (const double*)c.dats[V].ptr,
+                     (const double*)c.dats[dt].ptr, alpha, p32, ld32, c.sets[s].size);
+}
+
+extern "C" int op2b_dat_fill(op2b_ctx h, op2b_dat d, double value) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_dat(c, d)) return c.fail(OP2B_EINVAL, "dat_fill: bad dat");
+  const DatRec& r = c.dats[d];
+  return node_fill(&c, r.ptr, r.type, r.ld, r.dim, c.sets[r.set].size, value);
+}
+
+extern "C" int op2b_dat_copy(op2b_ctx h, op2b_dat dst, op2b_dat src) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_dat(c, dst) || !valid_dat(c, src)) return c.fail(OP2B_EINVAL, "dat_copy: bad dat");
+  const DatRec &d = c.dats[dst], &s = c.dats[src];
+  if (d.set != s.set) return c.fail(OP2B_ESET, "dat_copy: dats on different sets");
+  if (d.dim != s.dim) return c.fail(OP2B_EDIM, "dat_copy: dims differ");
+  return node_copy(&c, d.ptr, d.type, d.ld, s.ptr, s.type, s.ld, d.dim, c.sets[d.set].size);
+}
+
+// ------------------------------------------------ planner and autotuner
+extern "C" int op2b_set_strategy(op2b_ctx h, int32_t loop, int32_t prec, int32_t strategy, int32_t block,
+                                 int32_t part, int32_t staged) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec != 0 && prec != 1))
+    return c.fail(OP2B_EINVAL, "set_strategy: bad loop or precision");
+  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_SEGMENTED)
+    return c.fail(OP2B_EINVAL, "set_strategy: bad strategy");
+  if (block != 0 && (block < 32 || block > 1024 || block % 32))
+    return c.fail(OP2B_EINVAL, "set_strategy: block must be a multiple of 32 in [32, 1024]");
+  if (part != 0 && (part < 64 || part > 8192)) return c.fail(OP2B_EINVAL, "set_strategy: part must be in [64, 8192]");
+  Strategy s;
+  s.strategy = strategy;
+  s.block = block ? block : 256;
+  s.part = part ? part : 512;
+  s.staged = staged ? 1 : 0;
+  c.strat[loop][prec] = s;
+  return OP2B_OK;
+}
+
+extern "C" int op2b_set_tune_deadline(op2b_ctx h, double ms) {
+  CTX_CHECK(h);
+  if (!(ms > 0.0)) return h->c.fail(OP2B_EINVAL, "set_tune_deadline: must be positive");
+  h->c.tune_deadline_ms = ms;
+  return OP2B_OK;
+}
+
+extern "C" int op2b_save_tuning(op2b_ctx h, const char* path) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!path) return c.fail(OP2B_EINVAL, "save_tuning: null path");
+  std::ofstream f(path);
+  if (!f) return c.fail(OP2B_EINVAL, std::string("save_tuning: cannot write ") + path);
+  f << "{\n";
+  size_t k = 0;
+  for (auto& kv : c.tuned) {
+    const Strategy& s = kv.second;
+    char line[512];
+    snprintf(line, sizeof line,
+             "  \"%s\": {\"strategy\": %d, \"block\": %d, \"part\": %d, \"staged\": %d, \"ms\": %.6f}%s\n",
+             kv.first.c_str(), s.strategy, s.block, s.part, s.staged, s.tuned_ms,
+             ++k < c.tuned.size() ? "," : "");
+    f << line;
+  }
+  f << "}\n";
+  return f.good() ? OP2B_OK : c.fail(OP2B_EINVAL, "save_tuning: write failed");
+}
+
+extern "C" int op2b_load_tuning(op2b_ctx h, const char* path) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!path) return c.fail(OP2B_EINVAL, "load_tuning: null path");
+  std::ifstream f(path);
+  if (!f) return c.fail(OP2B_EINVAL, std::string("load_tuning: cannot read ") + path);
+  std::string line;
+  while (std::getline(f, line)) {
+    char key[256];
+    Strategy s;
+    if (sscanf(line.c_str(),
+               " \"%255[^\"]\": {\"strategy\": %d, \"block\": %d, \"part\": %d, \"staged\": %d, \"ms\": %lf}",
+               key, &s.strategy, &s.block, &s.part, &s.staged, &s.tuned_ms) == 6) {
+      if (s.strategy < OP2B_STRAT_ATOMIC || s.strategy > OP2B_STRAT_SEGMENTED)
+        return c.fail(OP2B_EINVAL, "load_tuning: bad strategy in table");
+      c.tuned[key] = s;
+    }
+  }
+  return OP2B_OK;
+}
+
+extern "C" int op2b_plan_stats(op2b_ctx h, int32_t loop, int32_t prec, op2b_map map, op2b_plan_stats_t* out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec != 0 && prec != 1) || !out || !valid_map(c, map))
+    return c.fail(OP2B_EINVAL, "plan_stats: bad loop, precision, map or output");
+  const Strategy& s = c.strat[loop][prec];
+  memset(out, 0, sizeof *out);
+  out->strategy = s.strategy;
+  out->block = s.block;
+  out->part = s.part;
+  out->staged = s.staged;
+  out->tuned_ms = s.tuned_ms;
+  DevBlockPlan* bp = nullptr;
+  int rc = c.block_plan(map, s.part, &bp);
+  if (rc) return rc;
+  out->nblocks = bp->nblocks;
+  out->ncolours = bp->ncolours;
+  out->min_blocks_per_colour = bp->min_per_colour;
+  out->max_blocks_per_colour = bp->max_per_colour;
+  out->max_unique_nodes = bp->max_unique;
+  out->avg_unique_nodes = bp->avg_unique;
+  return OP2B_OK;
+}
+
+// ---------------------------------------------------- host-only planners
+extern "C" int op2b_host_rcm(int64_t N, int64_t E, const int32_t* edge, int32_t* new_of_old) {
+  if (N < 0 || E < 0 || (E > 0 && !edge) || (N > 0 && !new_of_old)) return OP2B_EINVAL;
+  return op2b::rcm(N, E, edge, new_of_old) ? OP2B_OK : OP2B_EINVAL;
+}
+
+extern "C" int op2b_host_renumber(int64_t N, int64_t E, const int32_t* edge, int32_t method, uint64_t seed,
+                                  int32_t* new_of_old, int64_t* order) {
+  if (N < 0 || E < 0 || (E > 0 && !edge) || (N > 0 && !new_of_old) || (E > 0 && !order)) return OP2B_EINVAL;
+  for (int64_t e = 0; e < 2 * E; e++)
+    if (edge[e] < 0 || edge[e] >= N) return OP2B_EINVAL;
+  if (method == 0) {
+    for (int64_t i = 0; i < N; i++) new_of_old[i] = (int32_t)i;
+  } else if (method == 1) {
+    op2b::random_perm(N, seed, new_of_old);
+  } else if (method == 2) {
+    if (!op2b::rcm(N, E, edge, new_of_old)) return OP2B_EINVAL;
+  } else {
+    return OP2B_EINVAL;
+  }
+  op2b::edge_order(N, E, edge, new_of_old, order);
+  return OP2B_OK;
+}
+
+extern "C" int op2b_host_colour_blocks(int64_t N, int64_t E, const int32_t* edge, int32_t part,
+                                       int32_t* block_colour, int64_t* ncolours) {
+  if (N < 0 || E < 0 || (E > 0 && (!edge || !block_colour)) || !ncolours || part < 1 || part > 32767)
+    return OP2B_EINVAL;
+  std::vector<int32_t> m0(E), m1(E);
+  for (int64_t e = 0; e < E; e++) {
+    m0[e] = edge[2 * e];
+    m1[e] = edge[2 * e + 1];
+    if (m0[e] < 0 || m0[e] >= N || m1[e] < 0 || m1[e] >= N) return OP2B_EINVAL;
+  }
+  op2b::BlockPlan p;
+  std::string err;
+  if (!op2b::build_block_plan(N, E, m0.data(), m1.data(), part, &p, &err)) return OP2B_EPLAN;
+  std::copy(p.colour.begin(), p.colour.end(), block_colour);
+  *ncolours = p.ncolours;
+  return OP2B_OK;
+}
+
+extern "C" int op2b_host_node_csr(int64_t N, int64_t E, const int32_t* edge, int64_t* rowptr, int64_t* ends) {
+  if (N < 0 || E < 0 || (E > 0 && (!edge || !ends)) || !rowptr) return OP2B_EINVAL;
+  std::vector<int32_t> m0(E), m1(E);
+  for (int64_t e = 0; e < E; e++) {
+    m0[e] = edge[2 * e];
+    m1[e] = edge[2 * e + 1];
+    if (m0[e] < 0 || m0[e] >= N || m1[e] < 0 || m1[e] >= N) return OP2B_EINVAL;
+  }
+  std::vector<int64_t> rp;
+  std::vector<int32_t> en;
+  op2b::node_csr(N, E, m0.data(), m1.data(), &rp, &en);
+  std::copy(rp.begin(), rp.end(), rowptr);
+  for (int64_t t = 0; t < 2 * E; t++) ends[t] = en[t];
+  return OP2B_OK;
+}

@@ -1,0 +1,503 @@
+// The loop bodies ("user kernels" in the paper's terms, Sec. 3.1) and the
+// three race-resolution strategies that drive them over an edge set.
+//
+// A loop body P declares:
+//   TN  type of the node/edge data it reads and computes in
+//   TE  type of its per-edge results,  TA  type of the INC targets
+//   NIN values read per end node, OUT results per end node
+//   MODE  MODE_ANTI: node j receives -(node i's result) (fluxes)
+//         MODE_SYM:  node j receives the same result     (spectral radius)
+//         MODE_GEN:  node j has its own OUT results       (adjoints)
+//   DIM0  how many of the OUT components go to the first INC dat (the rest
+//         go to the second)
+//   load(node, v[NIN])  and  edge(e, vi, vj, oi, oj)
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "edge_math.cuh"
+
+namespace op2b {
+
+enum { MODE_ANTI = 0, MODE_SYM = 1, MODE_GEN = 2 };
+
+template <typename TA, int DIM0>
+struct Targets {
+  TA* p0;
+  int64_t ld0;
+  TA* p1;
+  int64_t ld1;
+  __device__ __forceinline__ TA* at(int c, int64_t node) const {
+    return c < DIM0 ? p0 + (int64_t)c * ld0 + node
+                    : p1 + (int64_t)(c - DIM0) * ld1 + node;
+  }
+};
+
+// ------------------------------------------------------------ loop bodies
+
+// Green-Gauss: oi[3k+d] = (q_i,k + q_j,k) (n_d / 2); node j gets -oi.
+template <typename T>
+struct BodyGG {
+  using TN = T;
+  using TE = T;
+  using TA = T;
+  static constexpr int NIN = 6, OUT = 18, MODE = MODE_ANTI, DIM0 = 18;
+  const T* q;
+  int64_t ldq;
+  const T* n;
+  int64_t ldn;
+  __device__ __forceinline__ void load(int64_t i, T* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const T* vi, const T* vj,
+                                       TE* oi, TE*) const {
+    T hx = T(0.5) * ldro(n + e), hy = T(0.5) * ldro(n + ldn + e),
+      hz = T(0.5) * ldro(n + 2 * ldn + e);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      T s = vi[k] + vj[k];
+      oi[3 * k] = s * hx;
+      oi[3 * k + 1] = s * hy;
+      oi[3 * k + 2] = s * hz;
+    }
+  }
+};
+
+// First-order Rusanov flux of the two node states.
+template <typename T>
+struct BodyFlux1 {
+  using TN = T;
+  using TE = T;
+  using TA = double;
+  static constexpr int NIN = 6, OUT = 6, MODE = MODE_ANTI, DIM0 = 6;
+  const T* q;
+  int64_t ldq;
+  const T* n;
+  int64_t ldn;
+  Gas<T> g;
+  __device__ __forceinline__ void load(int64_t i, T* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const T* vi, const T* vj,
+                                       TE* oi, TE*) const {
+    rusanov(vi, vj, ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e), g,
+            oi);
+  }
+};
+
+// Second-order flux: limited reconstruction then Rusanov.  v = q (6), G (18).
+template <typename T>
+struct BodyFlux2 {
+  using TN = T;
+  using TE = T;
+  using TA = double;
+  static constexpr int NIN = 24, OUT = 6, MODE = MODE_ANTI, DIM0 = 6;
+  const T* q;
+  int64_t ldq;
+  const T* G;
+  int64_t ldG;
+  const T* n;
+  int64_t ldn;
+  const T* dx;
+  int64_t lddx;
+  Gas<T> g;
+  __device__ __forceinline__ void load(int64_t i, T* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+#pragma unroll
+    for (int c = 0; c < 18; c++) v[6 + c] = ldro(G + c * ldG + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const T* vi, const T* vj,
+                                       TE* oi, TE*) const {
+    T qL[6], qR[6];
+    reconstruct(vi, vj, ldro(dx + e), ldro(dx + lddx + e),
+                ldro(dx + 2 * lddx + e), g, qL, qR);
+    rusanov(qL, qR, ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e), g,
+            oi);
+  }
+};
+
+// Spectral radius: s_e = max wave speed of the two node states, to both.
+struct BodySpectral {
+  using TN = double;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = 6, OUT = 1, MODE = MODE_SYM, DIM0 = 1;
+  const double* q;
+  int64_t ldq;
+  const double* n;
+  int64_t ldn;
+  Gas<double> g;
+  __device__ __forceinline__ void load(int64_t i, double* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const double* vi,
+                                       const double* vj, double* oi,
+                                       double*) const {
+    double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
+    double nn2 = nx * nx + ny * ny + nz * nz, f[6], lL, lR;
+    euler_side(vi, nx, ny, nz, nn2, g, f, lL);
+    euler_side(vj, nx, ny, nz, nn2, g, f, lR);
+    oi[0] = lL >= lR ? lL : lR;
+  }
+};
+
+// Adjoint of the flux loop.  v = lam (6), q (6) [, G (18)].  Results:
+// qbar (6) then Gbar (18, order 2) for each end; nbar written directly.
+template <int ORDER>
+struct BodyFluxAdj {
+  using TN = double;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = ORDER == 1 ? 12 : 30;
+  static constexpr int OUT = ORDER == 1 ? 6 : 24;
+  static constexpr int MODE = MODE_GEN, DIM0 = 6;
+  const double* lam;
+  int64_t ldl;
+  const double* q;
+  int64_t ldq;
+  const double* G;
+  int64_t ldG;
+  const double* n;
+  int64_t ldn;
+  const double* dx;
+  int64_t lddx;
+  double* nbar;
+  int64_t ldnb;
+  Gas<double> g;
+  __device__ __forceinline__ void load(int64_t i, double* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(lam + k * ldl + i);
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[6 + k] = ldro(q + k * ldq + i);
+    if constexpr (ORDER == 2) {
+#pragma unroll
+      for (int c = 0; c < 18; c++) v[12 + c] = ldro(G + c * ldG + i);
+    }
+  }
+  __device__ __forceinline__ void edge(int64_t e, const double* vi,
+                                       const double* vj, double* oi,
+                                       double* oj) const {
+    double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
+    double w[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) w[k] = vi[k] - vj[k];
+    const double* qi = vi + 6;
+    const double* qj = vj + 6;
+    double qLb[6], qRb[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) qLb[k] = qRb[k] = 0.0;
+    double nbx = 0.0, nby = 0.0, nbz = 0.0;
+    if constexpr (ORDER == 1) {
+      rusanov_reverse(qi, qj, nx, ny, nz, g, w, qLb, qRb, nbx, nby, nbz);
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        oi[k] = qLb[k];
+        oj[k] = qRb[k];
+      }
+    } else {
+      double ddx = ldro(dx + e), ddy = ldro(dx + lddx + e),
+             ddz = ldro(dx + 2 * lddx + e);
+      const double* Gi = vi + 12;
+      const double* Gj = vj + 12;
+      double qL[6], qR[6], pa_i[6], pb_i[6], pa_j[6], pb_j[6];
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        double b = qj[k] - qi[k];
+        double ai = Gi[3 * k] * ddx + Gi[3 * k + 1] * ddy + Gi[3 * k + 2] * ddz;
+        double aj = Gj[3 * k] * ddx + Gj[3 * k + 1] * ddy + Gj[3 * k + 2] * ddz;
+        double b2e = fma(b, b, g.two_eps), phi, phj;
+        van_albada_d(ai, b, g.eps, b2e, phi, pa_i[k], pb_i[k]);
+        van_albada_d(aj, b, g.eps, b2e, phj, pa_j[k], pb_j[k]);
+        qL[k] = qi[k] + 0.5 * phi;
+        qR[k] = qj[k] - 0.5 * phj;
+      }
+      rusanov_reverse(qL, qR, nx, ny, nz, g, w, qLb, qRb, nbx, nby, nbz);
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        double phib = 0.5 * qLb[k], phjb = -0.5 * qRb[k];
+        double aib = phib * pa_i[k], ajb = phjb * pa_j[k];
+        double bb = phib * pb_i[k] + phjb * pb_j[k];
+        oi[k] = qLb[k] - bb;
+        oj[k] = qRb[k] + bb;
+        oi[6 + 3 * k] = aib * ddx;
+        oi[7 + 3 * k] = aib * ddy;
+        oi[8 + 3 * k] = aib * ddz;
+        oj[6 + 3 * k] = ajb * ddx;
+        oj[7 + 3 * k] = ajb * ddy;
+        oj[8 + 3 * k] = ajb * ddz;
+      }
+    }
+    nbar[e] = nbx;
+    nbar[ldnb + e] = nby;
+    nbar[2 * ldnb + e] = nbz;
+  }
+};
+
+// Adjoint of Green-Gauss.  v = Gbar (18), q (6).  Both ends receive
+// sum_d (Gbar_i - Gbar_j)[k][d] n_d / 2; nbar_e += direct.
+struct BodyGGAdj {
+  using TN = double;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = 24, OUT = 6, MODE = MODE_SYM, DIM0 = 6;
+  const double* Gb;
+  int64_t ldGb;
+  const double* q;
+  int64_t ldq;
+  const double* n;
+  int64_t ldn;
+  double* nbar;
+  int64_t ldnb;
+  __device__ __forceinline__ void load(int64_t i, double* v) const {
+#pragma unroll
+    for (int c = 0; c < 18; c++) v[c] = ldro(Gb + c * ldGb + i);
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[18 + k] = ldro(q + k * ldq + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const double* vi,
+                                       const double* vj, double* oi,
+                                       double*) const {
+    double hx = 0.5 * ldro(n + e), hy = 0.5 * ldro(n + ldn + e),
+           hz = 0.5 * ldro(n + 2 * ldn + e);
+    double nbx = 0.0, nby = 0.0, nbz = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      double dxk = vi[3 * k] - vj[3 * k];
+      double dyk = vi[3 * k + 1] - vj[3 * k + 1];
+      double dzk = vi[3 * k + 2] - vj[3 * k + 2];
+      oi[k] = dxk * hx + dyk * hy + dzk * hz;
+      double hq = 0.5 * (vi[18 + k] + vj[18 + k]);
+      nbx += hq * dxk;
+      nby += hq * dyk;
+      nbz += hq * dzk;
+    }
+    nbar[e] += nbx;
+    nbar[ldnb + e] += nby;
+    nbar[2 * ldnb + e] += nbz;
+  }
+};
+
+// --------------------------------------------------------------- strategies
+
+// (1) one thread per edge, atomic adds into the INC targets.
+template <class P>
+__global__ void k_atomic(P ph, const int32_t* __restrict__ m0,
+                         const int32_t* __restrict__ m1, int64_t E,
+                         Targets<typename P::TA, P::DIM0> tg) {
+  using TN = typename P::TN;
+  using TE = typename P::TE;
+  using TA = typename P::TA;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += stride) {
+    int64_t i = m0[e], j = m1[e];
+    TN vi[P::NIN], vj[P::NIN];
+    ph.load(i, vi);
+    ph.load(j, vj);
+    TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
+    ph.edge(e, vi, vj, oi, oj);
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) {
+      TA a = (TA)oi[c];
+      atomicAdd(tg.at(c, i), a);
+      if constexpr (P::MODE == MODE_ANTI) atomicAdd(tg.at(c, j), -a);
+      if constexpr (P::MODE == MODE_SYM) atomicAdd(tg.at(c, j), a);
+      if constexpr (P::MODE == MODE_GEN) atomicAdd(tg.at(c, j), (TA)oj[c]);
+    }
+  }
+}
+
+// Device view of a block plan (mini-partitions + colours).
+struct BlockView {
+  const int32_t* cblocks;  // blocks of the colour being launched
+  int64_t nblk;
+  int32_t part;
+  int32_t ucap;            // staging capacity (max distinct nodes per block)
+  const int32_t* bn_off;
+  const int32_t* bnodes;
+  const uint32_t* eloc;
+  const int32_t* lrow;
+  const uint16_t* lent;
+};
+
+__host__ __device__ constexpr int64_t align16(int64_t b) {
+  return (b + 15) & ~(int64_t)15;
+}
+
+template <class P>
+__host__ __device__ constexpr int outs_per_edge() {
+  return P::MODE == MODE_GEN ? 2 * P::OUT : P::OUT;
+}
+
+template <class P, bool STAGED>
+__host__ int64_t colour_smem_bytes(int32_t part, int32_t ucap) {
+  int64_t b = align16((int64_t)outs_per_edge<P>() * part * sizeof(typename P::TE));
+  if (STAGED) b += (int64_t)P::NIN * ucap * sizeof(typename P::TN);
+  return b;
+}
+
+// (2) block colouring: one CTA per edge block of the launched colour.  The
+// block's results are kept in shared memory and summed per distinct node
+// over the block-local edge-end lists, then added into the targets with
+// plain read-modify-writes (no two blocks of a colour share a node).  With
+// STAGED the READ data of the block's distinct nodes is first gathered
+// into shared memory and the edges read it from there.
+template <class P, bool STAGED>
+__global__ void k_colour(P ph, const int32_t* __restrict__ m0,
+                         const int32_t* __restrict__ m1, int64_t E,
+                         BlockView bv, Targets<typename P::TA, P::DIM0> tg) {
+  using TN = typename P::TN;
+  using TE = typename P::TE;
+  using TA = typename P::TA;
+  constexpr int OUTS = outs_per_edge<P>();
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int part = bv.part;
+  TE* sOut = reinterpret_cast<TE*>(smem);
+  TN* sIn = reinterpret_cast<TN*>(smem + align16((int64_t)OUTS * part * sizeof(TE)));
+  for (int64_t bi = blockIdx.x; bi < bv.nblk; bi += gridDim.x) {
+    const int64_t b = bv.cblocks[bi];
+    const int64_t e0 = b * part;
+    const int ne = (int)min((int64_t)part, E - e0);
+    const int64_t u0 = bv.bn_off[b];
+    const int U = (int)(bv.bn_off[b + 1] - u0);
+    if constexpr (STAGED) {
+      for (int u = threadIdx.x; u < U; u += blockDim.x) {
+        TN v[P::NIN];
+        ph.load(bv.bnodes[u0 + u], v);
+#pragma unroll
+        for (int k = 0; k < P::NIN; k++) sIn[k * bv.ucap + u] = v[k];
+      }
+      __syncthreads();
+    }
+    for (int el = threadIdx.x; el < ne; el += blockDim.x) {
+      const int64_t e = e0 + el;
+      TN vi[P::NIN], vj[P::NIN];
+      if constexpr (STAGED) {
+        uint32_t l = bv.eloc[e];
+        int li = (int)(l & 0xffffu), lj = (int)(l >> 16);
+#pragma unroll
+        for (int k = 0; k < P::NIN; k++) {
+          vi[k] = sIn[k * bv.ucap + li];
+          vj[k] = sIn[k * bv.ucap + lj];
+        }
+      } else {
+        ph.load(m0[e], vi);
+        ph.load(m1[e], vj);
+      }
+      TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
+      ph.edge(e, vi, vj, oi, oj);
+#pragma unroll
+      for (int c = 0; c < P::OUT; c++) sOut[c * part + el] = oi[c];
+      if constexpr (P::MODE == MODE_GEN) {
+#pragma unroll
+        for (int c = 0; c < P::OUT; c++) sOut[(P::OUT + c) * part + el] = oj[c];
+      }
+    }
+    __syncthreads();
+    const int32_t* lr = bv.lrow + u0 + b;
+    const uint16_t* le = bv.lent + 2 * e0;
+    for (int u = threadIdx.x; u < U; u += blockDim.x) {
+      TA acc[P::OUT];
+#pragma unroll
+      for (int c = 0; c < P::OUT; c++) acc[c] = TA(0);
+      const int r1 = lr[u + 1];
+      for (int t = lr[u]; t < r1; t++) {
+        const int ent = le[t];
+        const int el = ent >> 1;
+        const bool second = ent & 1;
+        if constexpr (P::MODE == MODE_GEN) {
+          const int base = second ? P::OUT : 0;
+#pragma unroll
+          for (int c = 0; c < P::OUT; c++) acc[c] += (TA)sOut[(base + c) * part + el];
+        } else {
+#pragma unroll
+          for (int c = 0; c < P::OUT; c++) {
+            TA v = (TA)sOut[c * part + el];
+            if constexpr (P::MODE == MODE_ANTI) acc[c] += second ? -v : v;
+            else acc[c] += v;
+          }
+        }
+      }
+      const int64_t node = bv.bnodes[u0 + u];
+#pragma unroll
+      for (int c = 0; c < P::OUT; c++) {
+        TA* p = tg.at(c, node);
+        *p = *p + acc[c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// (3) sorted segmented reduction, phase 1: each edge's results to a global
+// buffer (OUTS x E, component-major).
+template <class P>
+__global__ void k_seg_edges(P ph, const int32_t* __restrict__ m0,
+                            const int32_t* __restrict__ m1, int64_t E,
+                            typename P::TE* __restrict__ ebuf) {
+  using TN = typename P::TN;
+  using TE = typename P::TE;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += stride) {
+    TN vi[P::NIN], vj[P::NIN];
+    ph.load(m0[e], vi);
+    ph.load(m1[e], vj);
+    TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
+    ph.edge(e, vi, vj, oi, oj);
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) ebuf[c * E + e] = oi[c];
+    if constexpr (P::MODE == MODE_GEN) {
+#pragma unroll
+      for (int c = 0; c < P::OUT; c++) ebuf[(P::OUT + c) * E + e] = oj[c];
+    }
+  }
+}
+
+// Phase 2: the edge ends are sorted by node (CSR); each node's segment is
+// summed by one thread in edge order and added into the targets.  A
+// warp-cooperative scan would cost log2(32) = 5 adds per end instead of 1,
+// which the FP64 pipe cannot spare, so segments are reduced one per lane.
+template <typename TE, typename TA, int OUT, int MODE, int DIM0>
+__global__ void k_seg_nodes(const int64_t* __restrict__ rowptr,
+                            const int32_t* __restrict__ ends, int64_t N,
+                            int64_t E, const TE* __restrict__ ebuf,
+                            Targets<TA, DIM0> tg) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += stride) {
+    TA acc[OUT];
+#pragma unroll
+    for (int c = 0; c < OUT; c++) acc[c] = TA(0);
+    const int64_t r1 = rowptr[i + 1];
+    for (int64_t t = rowptr[i]; t < r1; t++) {
+      const int32_t end = ends[t];
+      const int64_t e = end >> 1;
+      const bool second = end & 1;
+      if constexpr (MODE == MODE_GEN) {
+        const int base = second ? OUT : 0;
+#pragma unroll
+        for (int c = 0; c < OUT; c++) acc[c] += (TA)ebuf[(base + c) * E + e];
+      } else {
+#pragma unroll
+        for (int c = 0; c < OUT; c++) {
+          TA v = (TA)ebuf[c * E + e];
+          if constexpr (MODE == MODE_ANTI) acc[c] += second ? -v : v;
+          else acc[c] += v;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < OUT; c++) {
+      TA* p = tg.at(c, i);
+      *p = *p + acc[c];
+    }
+  }
+}
+
+}  // namespace op2b

@@ -1,0 +1,58 @@
+// Host-side planners of the op2b library: renumbering, edge ordering, edge
+// block plans with block colouring, and node-sorted edge ends.  Pure C++,
+// no CUDA; the device copies are made by the context (api.cu).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace op2b {
+
+// Reverse Cuthill-McKee (Cuthill & McKee 1969, reversal by George 1971):
+// component starts at the unvisited node of least (degree, id); a node's
+// unvisited neighbours are queued in increasing (degree, id) order; the
+// visit order is reversed.  Returns false on bad input.
+bool rcm(int64_t N, int64_t E, const int32_t* edge, int32_t* new_of_old);
+
+// A uniformly random relabelling from SplitMix64 keys (Steele, Lea and
+// Flood 2014): node k gets the rank of key(seed, k) (ties by k).
+void random_perm(int64_t N, uint64_t seed, int32_t* new_of_old);
+
+// Old edge index of each new edge once the ends are relabelled: ordered by
+// (min end, max end), ties in input order (two stable counting sorts).
+void edge_order(int64_t N, int64_t E, const int32_t* edge,
+                const int32_t* new_of_old, int64_t* order);
+
+// Edge-block (mini-partition) plan over the edges in their current order:
+// block b = edges [b*part, min(E, (b+1)*part)).
+struct BlockPlan {
+  int32_t part = 0;
+  int64_t nblocks = 0;
+  int32_t ncolours = 0;
+  int64_t max_unique = 0;
+  double avg_unique = 0.0;
+  std::vector<int32_t> bn_off;   // nblocks+1: offsets into bnodes
+  std::vector<int32_t> bnodes;   // distinct nodes of each block, ascending
+  std::vector<uint32_t> eloc;    // per edge: local i | local j << 16
+  std::vector<int32_t> lrow;     // per block U_b+1 offsets (at bn_off[b]+b)
+  std::vector<uint16_t> lent;    // per block 2*ne entries: local edge*2+side
+  std::vector<int32_t> colour;   // colour of each block
+  std::vector<int32_t> cblocks;  // block ids grouped by colour
+  std::vector<int64_t> coff;     // ncolours+1 offsets into cblocks
+};
+
+// Build the plan; the greedy colouring gives each block the smallest
+// colour that no earlier block sharing a node holds (at most 256 colours).
+bool build_block_plan(int64_t N, int64_t E, const int32_t* m0,
+                      const int32_t* m1, int32_t part, BlockPlan* out,
+                      std::string* err);
+
+// Edge ends sorted by node (counting sort, ends of one node by edge
+// index): rowptr N+1, ends 2E with value 2*e + side.
+void node_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
+              std::vector<int64_t>* rowptr, std::vector<int32_t>* ends);
+
+// Hardware threads to use for host planning.
+int host_threads();
+
+}  // namespace op2b

@@ -1,0 +1,144 @@
+// Internal state of an op2b context and the launch interface between the
+// C ABI (api.cu) and the per-loop kernel instantiations (loops_*.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/op2b.h"
+#include "host_plan.h"
+
+namespace op2b {
+
+struct SetRec {
+  int64_t size;
+  std::string name;
+};
+
+struct MapRec {
+  op2b_set from, to;
+  int32_t arity;
+  std::vector<int32_t> host;  // element-major copy
+  int32_t* dev = nullptr;     // SoA on the device: entry k at dev[k*from+e]
+  std::string name;
+  uint64_t version = 0;       // bumped on renumbering (invalidates plans)
+};
+
+struct DatRec {
+  op2b_set set;
+  int32_t dim, type;
+  void* ptr;
+  int64_t ld;
+  std::string name;
+};
+
+// device copy of a BlockPlan
+struct DevBlockPlan {
+  uint64_t map_version = ~0ull;
+  int32_t part = 0;
+  int64_t nblocks = 0;
+  int32_t ncolours = 0;
+  int64_t max_unique = 0;
+  double avg_unique = 0.0;
+  std::vector<int64_t> coff;
+  int64_t min_per_colour = 0, max_per_colour = 0;
+  int32_t *bn_off = nullptr, *bnodes = nullptr, *lrow = nullptr,
+          *cblocks = nullptr;
+  uint32_t* eloc = nullptr;
+  uint16_t* lent = nullptr;
+};
+
+struct DevSegPlan {
+  uint64_t map_version = ~0ull;
+  int64_t* rowptr = nullptr;
+  int32_t* ends = nullptr;
+};
+
+struct Strategy {
+  int32_t strategy = OP2B_STRAT_ATOMIC;
+  int32_t block = 256;
+  int32_t part = 512;
+  int32_t staged = 0;
+  double tuned_ms = 0.0;
+};
+
+// Everything a loop launch needs; pointers are device pointers.
+struct LoopLaunch {
+  int loop = 0, prec = 0, order = 1;
+  int map = -1;  // the edge->node map (plan lookup)
+  int64_t N = 0, E = 0;
+  const int32_t* m0 = nullptr;  // first end of every edge
+  const int32_t* m1 = nullptr;  // second end
+  // READ data
+  const void *q = nullptr, *G = nullptr, *n = nullptr, *dx = nullptr,
+             *lam = nullptr, *Gb = nullptr;
+  int64_t ldq = 0, ldG = 0, ldn = 0, lddx = 0, ldl = 0, ldGb = 0;
+  // INC targets (first and second dat) and direct output
+  void *t0 = nullptr, *t1 = nullptr, *direct = nullptr;
+  int64_t ldt0 = 0, ldt1 = 0, lddirect = 0;
+  double gamma = 1.4, eps = 1e-12;
+};
+
+struct Ctx;
+
+// Run one edge loop with strategy s (plans and scratch taken from ctx).
+// loops_f64.cu: GREEN_GAUSS, FLUX1, FLUX2, SPECTRAL in FP64;
+// loops_f32.cu: GREEN_GAUSS, FLUX1, FLUX2 with FP32 arithmetic;
+// loops_adj.cu: FLUX1_ADJ, FLUX2_ADJ, GG_ADJ.
+int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s);
+int launch_f32(Ctx* c, const LoopLaunch& L, const Strategy& s);
+int launch_adj(Ctx* c, const LoopLaunch& L, const Strategy& s);
+
+// Direct node loops (node_loops.cu).
+int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,
+                    int64_t N);
+int node_time_step(Ctx* c, const double* V, const double* lam, double cfl,
+                   double* dt, int64_t N);
+int node_update(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
+                const double* R, int64_t ldR, const double* V,
+                const double* dt, double alpha, float* q32, int64_t ld32,
+                int64_t N);
+int node_fill(Ctx* c, void* p, int type, int64_t ld, int dim, int64_t n,
+              double value);
+int node_copy(Ctx* c, void* dst, int dtype, int64_t ldd, const void* src,
+              int stype, int64_t lds, int dim, int64_t n);
+// out[k*ld + t] = in[k*ld + idx[t]] for t < n (elements of `esize` bytes)
+int node_gather(Ctx* c, void* out, const void* in, int esize, int64_t ld,
+                int dim, const int64_t* idx, int64_t n);
+
+struct Ctx {
+  int device = 0;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<SetRec> sets;
+  std::vector<MapRec> maps;
+  std::vector<DatRec> dats;
+  std::string err;
+  Strategy strat[OP2B_NUM_LOOPS][2];
+  std::map<std::pair<int, int>, DevBlockPlan> bplans;  // (map, part)
+  std::map<int, DevSegPlan> splans;                    // map
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  double tune_deadline_ms = 20000.0;
+  int64_t launches = 0;
+  std::map<std::string, Strategy> tuned;  // persistent table
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  // check the last launch; count it
+  int launched(const char* what);
+  // scratch of at least `bytes` (grows, never shrinks)
+  int need_scratch(size_t bytes, void** out);
+  // plans (built or rebuilt on demand)
+  int block_plan(int map, int32_t part, DevBlockPlan** out);
+  int seg_plan(int map, DevSegPlan** out);
+};
+
+}  // namespace op2b

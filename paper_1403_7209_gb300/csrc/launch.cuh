@@ -1,0 +1,101 @@
+// Generic launcher: runs a loop body with the chosen race-resolution
+// strategy on the context's stream.
+#pragma once
+#include <algorithm>
+
+#include "edge_loops.cuh"
+#include "internal.h"
+
+namespace op2b {
+
+// ERANGE when `block` threads exceed what the kernel's register use allows
+template <typename K>
+static int check_block(Ctx* c, K kern, int block) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess)
+    return c->fail(OP2B_ECUDA, "cudaFuncGetAttributes failed");
+  if (block > fa.maxThreadsPerBlock)
+    return c->fail(OP2B_ERANGE, "block of " + std::to_string(block) + " threads exceeds the kernel's limit of " +
+                                    std::to_string(fa.maxThreadsPerBlock));
+  return OP2B_OK;
+}
+
+template <class P, bool STAGED>
+static int run_colour(Ctx* c, const P& ph, const LoopLaunch& L,
+                      const Strategy& s, Targets<typename P::TA, P::DIM0> tg) {
+  DevBlockPlan* bp = nullptr;
+  int rc = c->block_plan(L.map, s.part, &bp);
+  if (rc) return rc;
+  const int32_t ucap = STAGED ? (int32_t)bp->max_unique : 0;
+  const int64_t smem = colour_smem_bytes<P, STAGED>(bp->part, ucap);
+  if (smem > (int64_t)c->smem_optin)
+    return c->fail(OP2B_ERANGE, "colour plan: " + std::to_string(smem) +
+                                    " B of shared memory per block exceeds the device limit");
+  auto kern = k_colour<P, STAGED>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return c->fail(OP2B_ECUDA, "cudaFuncSetAttribute (shared memory) failed");
+  const int block = s.block > 0 ? s.block : 256;
+  if ((rc = check_block(c, kern, block))) return rc;
+  for (int32_t col = 0; col < bp->ncolours; col++) {
+    BlockView bv;
+    bv.cblocks = bp->cblocks + bp->coff[col];
+    bv.nblk = bp->coff[col + 1] - bp->coff[col];
+    bv.part = bp->part;
+    bv.ucap = ucap;
+    bv.bn_off = bp->bn_off;
+    bv.bnodes = bp->bnodes;
+    bv.eloc = bp->eloc;
+    bv.lrow = bp->lrow;
+    bv.lent = bp->lent;
+    if (bv.nblk == 0) continue;
+    unsigned grid = (unsigned)std::min<int64_t>(bv.nblk, (int64_t)1 << 30);
+    kern<<<grid, block, smem, c->stream>>>(ph, L.m0, L.m1, L.E, bv, tg);
+    if ((rc = c->launched("colour"))) return rc;
+  }
+  return OP2B_OK;
+}
+
+template <class P>
+static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
+                    const Strategy& s, Targets<typename P::TA, P::DIM0> tg) {
+  if (L.E == 0) return OP2B_OK;
+  const int block = s.block > 0 ? s.block : 256;
+  if (block < 32 || block > 1024 || block % 32)
+    return c->fail(OP2B_EINVAL, "block size must be a multiple of 32 in [32, 1024]");
+  const int64_t cap = (int64_t)c->sm_count * 64;
+  switch (s.strategy) {
+    case OP2B_STRAT_ATOMIC: {
+      if (int rc = check_block(c, k_atomic<P>, block)) return rc;
+      int64_t grid = std::min<int64_t>((L.E + block - 1) / block, cap);
+      k_atomic<P><<<(unsigned)grid, block, 0, c->stream>>>(ph, L.m0, L.m1, L.E, tg);
+      return c->launched("atomic");
+    }
+    case OP2B_STRAT_COLOUR:
+      return s.staged ? run_colour<P, true>(c, ph, L, s, tg)
+                      : run_colour<P, false>(c, ph, L, s, tg);
+    case OP2B_STRAT_SEGMENTED: {
+      DevSegPlan* sp = nullptr;
+      int rc = c->seg_plan(L.map, &sp);
+      if (rc) return rc;
+      using TE = typename P::TE;
+      if ((rc = check_block(c, k_seg_edges<P>, block))) return rc;
+      const size_t bytes = (size_t)outs_per_edge<P>() * L.E * sizeof(TE);
+      void* buf = nullptr;
+      if ((rc = c->need_scratch(bytes, &buf))) return rc;
+      int64_t grid = std::min<int64_t>((L.E + block - 1) / block, cap);
+      k_seg_edges<P><<<(unsigned)grid, block, 0, c->stream>>>(ph, L.m0, L.m1, L.E, (TE*)buf);
+      if ((rc = c->launched("segmented edges"))) return rc;
+      int64_t gridn = std::min<int64_t>((L.N + block - 1) / block, cap);
+      if (gridn == 0) return OP2B_OK;
+      k_seg_nodes<TE, typename P::TA, P::OUT, P::MODE, P::DIM0>
+          <<<(unsigned)gridn, block, 0, c->stream>>>(sp->rowptr, sp->ends, L.N, L.E,
+                                                     (const TE*)buf, tg);
+      return c->launched("segmented nodes");
+    }
+    default:
+      return c->fail(OP2B_EINVAL, "unknown strategy");
+  }
+}
+
+}  // namespace op2b

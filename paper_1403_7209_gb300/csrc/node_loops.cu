@@ -1,0 +1,155 @@
+// Direct node loops (no map): gradient scaling, local time step, the
+// Runge-Kutta stage update, fills, copies and the gathers that apply a
+// renumbering to a dat.  Grid-stride loops over nodes; every component
+// array is read and written with unit stride.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace op2b {
+
+static unsigned grid_for(Ctx* c, int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)c->sm_count * 32));
+}
+
+// G <- G * (1/V): one division per node, 18 multiplies
+template <typename T>
+__global__ void k_grad_scale(T* __restrict__ G, int64_t ld,
+                             const double* __restrict__ V, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T r = (T)(1.0 / V[i]);
+#pragma unroll
+    for (int c = 0; c < 18; c++) G[c * ld + i] *= r;
+  }
+}
+
+int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,
+                    int64_t N) {
+  if (N == 0) return OP2B_OK;
+  if (type == OP2B_F64)
+    k_grad_scale<double><<<grid_for(c, N, 256), 256, 0, c->stream>>>((double*)G, ldG, V, N);
+  else
+    k_grad_scale<float><<<grid_for(c, N, 256), 256, 0, c->stream>>>((float*)G, ldG, V, N);
+  return c->launched("grad_scale");
+}
+
+__global__ void k_time_step(const double* __restrict__ V,
+                            const double* __restrict__ lam, double cfl,
+                            double* __restrict__ dt, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dt[i] = cfl * V[i] / lam[i];
+}
+
+int node_time_step(Ctx* c, const double* V, const double* lam, double cfl,
+                   double* dt, int64_t N) {
+  if (N == 0) return OP2B_OK;
+  k_time_step<<<grid_for(c, N, 256), 256, 0, c->stream>>>(V, lam, cfl, dt, N);
+  return c->launched("time_step");
+}
+
+// q = q0 - alpha (dt/V) R, with the FP32 shadow of q when q32 != null
+__global__ void k_update(const double* __restrict__ q0, int64_t ld0,
+                         double* __restrict__ q, int64_t ldq,
+                         const double* __restrict__ R, int64_t ldR,
+                         const double* __restrict__ V,
+                         const double* __restrict__ dt, double alpha,
+                         float* __restrict__ q32, int64_t ld32, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double a = alpha * (dt[i] / V[i]);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      double v = q0[k * ld0 + i] - a * R[k * ldR + i];
+      q[k * ldq + i] = v;
+      if (q32) q32[k * ld32 + i] = (float)v;
+    }
+  }
+}
+
+int node_update(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
+                const double* R, int64_t ldR, const double* V,
+                const double* dt, double alpha, float* q32, int64_t ld32,
+                int64_t N) {
+  if (N == 0) return OP2B_OK;
+  k_update<<<grid_for(c, N, 256), 256, 0, c->stream>>>(q0, ld0, q, ldq, R, ldR, V, dt,
+                                                       alpha, q32, ld32, N);
+  return c->launched("update");
+}
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ p, int64_t ld, int dim, int64_t n,
+                       T v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < dim; k++) p[k * ld + i] = v;
+}
+
+int node_fill(Ctx* c, void* p, int type, int64_t ld, int dim, int64_t n,
+              double value) {
+  if (n == 0 || dim == 0) return OP2B_OK;
+  unsigned g = grid_for(c, n, 256);
+  if (type == OP2B_F64)
+    k_fill<double><<<g, 256, 0, c->stream>>>((double*)p, ld, dim, n, value);
+  else if (type == OP2B_F32)
+    k_fill<float><<<g, 256, 0, c->stream>>>((float*)p, ld, dim, n, (float)value);
+  else
+    k_fill<int32_t><<<g, 256, 0, c->stream>>>((int32_t*)p, ld, dim, n, (int32_t)value);
+  return c->launched("fill");
+}
+
+template <typename TD, typename TS>
+__global__ void k_copy(TD* __restrict__ d, int64_t ldd,
+                       const TS* __restrict__ s, int64_t lds, int dim,
+                       int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < dim; k++) d[k * ldd + i] = (TD)s[k * lds + i];
+}
+
+int node_copy(Ctx* c, void* dst, int dtype, int64_t ldd, const void* src,
+              int stype, int64_t lds, int dim, int64_t n) {
+  if (n == 0 || dim == 0) return OP2B_OK;
+  unsigned g = grid_for(c, n, 256);
+  if (dtype == OP2B_F64 && stype == OP2B_F64)
+    k_copy<double, double><<<g, 256, 0, c->stream>>>((double*)dst, ldd, (const double*)src, lds, dim, n);
+  else if (dtype == OP2B_F32 && stype == OP2B_F64)
+    k_copy<float, double><<<g, 256, 0, c->stream>>>((float*)dst, ldd, (const double*)src, lds, dim, n);
+  else if (dtype == OP2B_F64 && stype == OP2B_F32)
+    k_copy<double, float><<<g, 256, 0, c->stream>>>((double*)dst, ldd, (const float*)src, lds, dim, n);
+  else if (dtype == OP2B_F32 && stype == OP2B_F32)
+    k_copy<float, float><<<g, 256, 0, c->stream>>>((float*)dst, ldd, (const float*)src, lds, dim, n);
+  else if (dtype == OP2B_I32 && stype == OP2B_I32)
+    k_copy<int32_t, int32_t><<<g, 256, 0, c->stream>>>((int32_t*)dst, ldd, (const int32_t*)src, lds, dim, n);
+  else
+    return c->fail(OP2B_ETYPE, "dat_copy: unsupported type pair");
+  return c->launched("copy");
+}
+
+template <typename T>
+__global__ void k_gather(T* __restrict__ out, const T* __restrict__ in,
+                         int64_t ld, int dim, const int64_t* __restrict__ idx,
+                         int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s = idx[t];
+    for (int k = 0; k < dim; k++) out[k * ld + t] = in[k * ld + s];
+  }
+}
+
+int node_gather(Ctx* c, void* out, const void* in, int esize, int64_t ld,
+                int dim, const int64_t* idx, int64_t n) {
+  if (n == 0 || dim == 0) return OP2B_OK;
+  unsigned g = grid_for(c, n, 256);
+  if (esize == 8)
+    k_gather<uint64_t><<<g, 256, 0, c->stream>>>((uint64_t*)out, (const uint64_t*)in, ld, dim, idx, n);
+  else if (esize == 4)
+    k_gather<uint32_t><<<g, 256, 0, c->stream>>>((uint32_t*)out, (const uint32_t*)in, ld, dim, idx, n);
+  else
+    return c->fail(OP2B_EINVAL, "gather: element size must be 4 or 8");
+  return c->launched("gather");
+}
+
+}  // namespace op2b

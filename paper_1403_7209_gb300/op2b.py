@@ -1,0 +1,349 @@
+"""Python binding of the op2b C ABI (include/op2b.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and raises
+:class:`Op2bError` when that call returns an error code.  Device pointers are
+plain integers (e.g. ``tensor.data_ptr()``), streams are ``cudaStream_t``
+values (e.g. ``torch.cuda.current_stream().cuda_stream``).  The shared
+library is loaded on first use and must exist: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libop2b.so")
+
+OK, EINVAL, EDIM, ETYPE, EACCESS, ESET = 0, -1, -2, -3, -4, -5
+ENOMEM, ECUDA, ETIMEOUT, EPLAN, ERANGE = -6, -7, -8, -9, -10
+READ, WRITE, RW, INC = 1, 2, 3, 4
+F64, F32, I32 = 0, 1, 2
+ID = -1
+LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
+LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ, NUM_LOOPS = 4, 5, 6, 7
+PREC_F64, PREC_F32 = 0, 1
+STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED = 0, 1, 2, 3
+ZERO_INC = 1
+STRATEGY_NAMES = {STRAT_AUTO: "auto", STRAT_ATOMIC: "atomic",
+                  STRAT_COLOUR: "colour", STRAT_SEGMENTED: "segmented"}
+ERROR_NAMES = {EINVAL: "EINVAL", EDIM: "EDIM", ETYPE: "ETYPE",
+               EACCESS: "EACCESS", ESET: "ESET", ENOMEM: "ENOMEM",
+               ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EPLAN: "EPLAN",
+               ERANGE: "ERANGE"}
+
+
+class Op2bError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Arg(ctypes.Structure):
+    _fields_ = [("dat", ctypes.c_int32), ("idx", ctypes.c_int32),
+                ("map", ctypes.c_int32), ("acc", ctypes.c_int32)]
+
+
+class FluxParams(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("eps_lim", ctypes.c_double)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("strategy", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("part", ctypes.c_int32), ("staged", ctypes.c_int32),
+                ("nblocks", ctypes.c_int64), ("ncolours", ctypes.c_int64),
+                ("min_blocks_per_colour", ctypes.c_int64),
+                ("max_blocks_per_colour", ctypes.c_int64),
+                ("max_unique_nodes", ctypes.c_int64),
+                ("avg_unique_nodes", ctypes.c_double),
+                ("tuned_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_D = ctypes.c_double
+_PI32 = ctypes.POINTER(ctypes.c_int32)
+_PI64 = ctypes.POINTER(ctypes.c_int64)
+_PARG = ctypes.POINTER(Arg)
+
+_SIGS = {
+    "op2b_init": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _P]),
+    "op2b_finalize": (ctypes.c_int, [_P]),
+    "op2b_set_stream": (ctypes.c_int, [_P, _P]),
+    "op2b_last_error": (ctypes.c_char_p, [_P]),
+    "op2b_version": (ctypes.c_char_p, []),
+    "op2b_decl_set": (ctypes.c_int, [_P, _I64, ctypes.c_char_p, _PI32]),
+    "op2b_decl_map": (ctypes.c_int, [_P, _I32, _I32, _I32, _PI32,
+                                     ctypes.c_char_p, _PI32]),
+    "op2b_decl_dat": (ctypes.c_int, [_P, _I32, _I32, _I32, _P, _I64,
+                                     ctypes.c_char_p, _PI32]),
+    "op2b_rebind_dat": (ctypes.c_int, [_P, _I32, _P]),
+    "op2b_fetch_map": (ctypes.c_int, [_P, _I32, _PI32]),
+    "op2b_renumber": (ctypes.c_int, [_P, _I32, _I32, _U64, _PI32, _PI64]),
+    "op2b_green_gauss": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
+    "op2b_edge_flux": (ctypes.c_int, [_P, _PARG, _I32,
+                                      ctypes.POINTER(FluxParams)]),
+    "op2b_spectral_radius": (ctypes.c_int, [_P, _PARG, _I32, _D, _I32]),
+    "op2b_edge_flux_adjoint": (ctypes.c_int, [_P, _PARG, _I32,
+                                              ctypes.POINTER(FluxParams)]),
+    "op2b_green_gauss_adjoint": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
+    "op2b_grad_scale": (ctypes.c_int, [_P, _I32, _I32]),
+    "op2b_grad_scale_adjoint": (ctypes.c_int, [_P, _I32, _I32]),
+    "op2b_time_step": (ctypes.c_int, [_P, _I32, _I32, _D, _I32]),
+    "op2b_node_update": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32,
+                                        _D, _I32]),
+    "op2b_dat_fill": (ctypes.c_int, [_P, _I32, _D]),
+    "op2b_dat_copy": (ctypes.c_int, [_P, _I32, _I32]),
+    "op2b_set_strategy": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32,
+                                         _I32]),
+    "op2b_set_tune_deadline": (ctypes.c_int, [_P, _D]),
+    "op2b_save_tuning": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "op2b_load_tuning": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "op2b_plan_stats": (ctypes.c_int, [_P, _I32, _I32, _I32,
+                                       ctypes.POINTER(PlanStats)]),
+    "op2b_launch_count": (ctypes.c_int64, [_P]),
+    "op2b_host_rcm": (ctypes.c_int, [_I64, _I64, _PI32, _PI32]),
+    "op2b_host_renumber": (ctypes.c_int, [_I64, _I64, _PI32, _I32, _U64,
+                                          _PI32, _PI64]),
+    "op2b_host_colour_blocks": (ctypes.c_int, [_I64, _I64, _PI32, _I32,
+                                               _PI32, _PI64]),
+    "op2b_host_node_csr": (ctypes.c_int, [_I64, _I64, _PI32, _PI64, _PI64]),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(build_if_missing: bool = True):
+    """Load libop2b.so (building it with nvcc first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            if not build_if_missing:
+                raise OSError("op2b CUDA library missing: %s" % LIB_PATH)
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, ctx=None):
+    if rc != OK:
+        msg = load().op2b_last_error(ctx)
+        raise Op2bError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _i32p(a):
+    return a.ctypes.data_as(_PI32)
+
+
+def _i64p(a):
+    return a.ctypes.data_as(_PI64)
+
+
+def _args(arglist):
+    arr = (Arg * len(arglist))()
+    for k, a in enumerate(arglist):
+        arr[k] = Arg(*a)
+    return arr, len(arglist)
+
+
+# ------------------------------------------------------------- lifecycle
+def op2b_version() -> str:
+    return load().op2b_version().decode()
+
+
+def op2b_init(device: int = 0, stream: int = 0):
+    ctx = _P()
+    rc = load().op2b_init(ctypes.byref(ctx), device, stream)
+    _check(rc, None)
+    return ctx
+
+
+def op2b_finalize(ctx):
+    _check(load().op2b_finalize(ctx), None)
+
+
+def op2b_set_stream(ctx, stream: int):
+    _check(load().op2b_set_stream(ctx, stream), ctx)
+
+
+def op2b_last_error(ctx) -> str:
+    return load().op2b_last_error(ctx).decode()
+
+
+def op2b_launch_count(ctx) -> int:
+    return int(load().op2b_launch_count(ctx))
+
+
+# ----------------------------------------------------------- declarations
+def op2b_decl_set(ctx, size: int, name: str = "") -> int:
+    out = ctypes.c_int32()
+    _check(load().op2b_decl_set(ctx, size, name.encode(), ctypes.byref(out)), ctx)
+    return out.value
+
+
+def op2b_decl_map(ctx, frm: int, to: int, arity: int, data, name: str = "") -> int:
+    data = np.ascontiguousarray(data, dtype=np.int32)
+    out = ctypes.c_int32()
+    _check(load().op2b_decl_map(ctx, frm, to, arity, _i32p(data), name.encode(),
+                                ctypes.byref(out)), ctx)
+    return out.value
+
+
+def op2b_decl_dat(ctx, set_: int, dim: int, type_: int, device_ptr: int,
+                  ld: int = 0, name: str = "") -> int:
+    out = ctypes.c_int32()
+    _check(load().op2b_decl_dat(ctx, set_, dim, type_, device_ptr, ld, name.encode(),
+                                ctypes.byref(out)), ctx)
+    return out.value
+
+
+def op2b_rebind_dat(ctx, dat: int, device_ptr: int):
+    _check(load().op2b_rebind_dat(ctx, dat, device_ptr), ctx)
+
+
+def op2b_fetch_map(ctx, map_: int, size: int) -> np.ndarray:
+    out = np.empty(size, dtype=np.int32)
+    _check(load().op2b_fetch_map(ctx, map_, _i32p(out)), ctx)
+    return out
+
+
+def op2b_renumber(ctx, map_: int, method: int, seed: int, num_nodes: int,
+                  num_edges: int):
+    perm = np.empty(num_nodes, dtype=np.int32)
+    order = np.empty(num_edges, dtype=np.int64)
+    _check(load().op2b_renumber(ctx, map_, method, seed, _i32p(perm), _i64p(order)), ctx)
+    return perm, order
+
+
+# ------------------------------------------------------------------ loops
+def op2b_green_gauss(ctx, args, flags: int = 0):
+    a, n = _args(args)
+    _check(load().op2b_green_gauss(ctx, a, n, flags), ctx)
+
+
+def op2b_edge_flux(ctx, args, order: int, gamma: float = 1.4,
+                   eps_lim: float = 1e-12, flags: int = 0):
+    a, n = _args(args)
+    p = FluxParams(order, flags, gamma, eps_lim)
+    _check(load().op2b_edge_flux(ctx, a, n, ctypes.byref(p)), ctx)
+
+
+def op2b_spectral_radius(ctx, args, gamma: float = 1.4, flags: int = 0):
+    a, n = _args(args)
+    _check(load().op2b_spectral_radius(ctx, a, n, gamma, flags), ctx)
+
+
+def op2b_edge_flux_adjoint(ctx, args, order: int, gamma: float = 1.4,
+                           eps_lim: float = 1e-12, flags: int = 0):
+    a, n = _args(args)
+    p = FluxParams(order, flags, gamma, eps_lim)
+    _check(load().op2b_edge_flux_adjoint(ctx, a, n, ctypes.byref(p)), ctx)
+
+
+def op2b_green_gauss_adjoint(ctx, args, flags: int = 0):
+    a, n = _args(args)
+    _check(load().op2b_green_gauss_adjoint(ctx, a, n, flags), ctx)
+
+
+def op2b_grad_scale(ctx, G: int, V: int):
+    _check(load().op2b_grad_scale(ctx, G, V), ctx)
+
+
+def op2b_grad_scale_adjoint(ctx, Gb: int, V: int):
+    _check(load().op2b_grad_scale_adjoint(ctx, Gb, V), ctx)
+
+
+def op2b_time_step(ctx, V: int, lam: int, cfl: float, dt: int):
+    _check(load().op2b_time_step(ctx, V, lam, cfl, dt), ctx)
+
+
+def op2b_node_update(ctx, q0: int, q: int, R: int, V: int, dt: int,
+                     alpha: float, q32: int = -1):
+    _check(load().op2b_node_update(ctx, q0, q, R, V, dt, alpha, q32), ctx)
+
+
+def op2b_dat_fill(ctx, dat: int, value: float):
+    _check(load().op2b_dat_fill(ctx, dat, value), ctx)
+
+
+def op2b_dat_copy(ctx, dst: int, src: int):
+    _check(load().op2b_dat_copy(ctx, dst, src), ctx)
+
+
+# ------------------------------------------------------ planner / tuner
+def op2b_set_strategy(ctx, loop: int, prec: int, strategy: int, block: int = 0,
+                      part: int = 0, staged: int = 0):
+    _check(load().op2b_set_strategy(ctx, loop, prec, strategy, block, part, staged), ctx)
+
+
+def op2b_set_tune_deadline(ctx, ms: float):
+    _check(load().op2b_set_tune_deadline(ctx, ms), ctx)
+
+
+def op2b_save_tuning(ctx, path: str):
+    _check(load().op2b_save_tuning(ctx, path.encode()), ctx)
+
+
+def op2b_load_tuning(ctx, path: str):
+    _check(load().op2b_load_tuning(ctx, path.encode()), ctx)
+
+
+def op2b_plan_stats(ctx, loop: int, prec: int, map_: int) -> dict:
+    st = PlanStats()
+    _check(load().op2b_plan_stats(ctx, loop, prec, map_, ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+# ------------------------------------------------------ host-only planners
+def op2b_host_rcm(num_nodes: int, edge) -> np.ndarray:
+    edge = np.ascontiguousarray(edge, dtype=np.int32)
+    out = np.empty(num_nodes, dtype=np.int32)
+    _check(load().op2b_host_rcm(num_nodes, edge.shape[0], _i32p(edge), _i32p(out)))
+    return out
+
+
+def op2b_host_renumber(num_nodes: int, edge, method: int, seed: int = 0):
+    edge = np.ascontiguousarray(edge, dtype=np.int32)
+    perm = np.empty(num_nodes, dtype=np.int32)
+    order = np.empty(edge.shape[0], dtype=np.int64)
+    _check(load().op2b_host_renumber(num_nodes, edge.shape[0], _i32p(edge), method,
+                                     seed, _i32p(perm), _i64p(order)))
+    return perm, order
+
+
+def op2b_host_colour_blocks(num_nodes: int, edge, part: int):
+    edge = np.ascontiguousarray(edge, dtype=np.int32)
+    nb = (edge.shape[0] + part - 1) // part if part > 0 else 0
+    col = np.empty(max(nb, 1), dtype=np.int32)
+    nc = ctypes.c_int64()
+    _check(load().op2b_host_colour_blocks(num_nodes, edge.shape[0], _i32p(edge), part,
+                                          _i32p(col), ctypes.byref(nc)))
+    return col[:nb], nc.value
+
+
+def op2b_host_node_csr(num_nodes: int, edge):
+    edge = np.ascontiguousarray(edge, dtype=np.int32)
+    rowptr = np.empty(num_nodes + 1, dtype=np.int64)
+    ends = np.empty(max(2 * edge.shape[0], 1), dtype=np.int64)
+    _check(load().op2b_host_node_csr(num_nodes, edge.shape[0], _i32p(edge),
+                                     _i64p(rowptr), _i64p(ends)))
+    return rowptr, ends[:2 * edge.shape[0]]

@@ -1,0 +1,240 @@
+"""One mesh on one GPU: sets, the edge->node map and the dats of the loops.
+
+A thin layer over :mod:`paper_1403_7209_gb300.op2b`: it owns torch tensors
+(device memory) laid out structure-of-arrays, (dim, n) contiguous, declares
+them as dats, and calls the loops in the order of one explicit step:
+
+  Green-Gauss edge loop -> gradient scaling -> flux edge loop -> RK update
+
+(Sec. 2 of the paper: Hydra's explicit 5-step Runge-Kutta time march).
+All arithmetic runs in the CUDA library; this module only marshals.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import op2b as L
+
+RK5_ALPHA = (0.25, 1.0 / 6.0, 0.375, 0.5, 1.0)  # Jameson's 5-stage scheme
+RENUMBER = {"none": 0, "random": 1, "rcm": 2}
+
+
+class EdgeSolver:
+    """Dats and loops of an edge-based finite-volume mesh.
+
+    ``edge`` (E, 2) int, ``normal``/``dx`` (E, 3), ``volume`` (N,), ``q``
+    (N, 6) in the caller's numbering.  ``renumber`` in {"none", "random",
+    "rcm"} reorders nodes and edges inside the library; :meth:`fetch_nodes`
+    and :meth:`fetch_edges` return data in the caller's numbering again.
+    ``mixed`` adds the FP32 shadows used by the mixed-precision path;
+    ``adjoint`` the adjoint dats.
+    """
+
+    def __init__(self, edge, normal, dx, volume, q=None, device: int = 0,
+                 renumber: str = "none", seed: int = 0, mixed: bool = False,
+                 adjoint: bool = False, gamma: float = 1.4,
+                 eps_lim: float = 1e-12, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.gamma, self.eps_lim = gamma, eps_lim
+        edge = np.ascontiguousarray(edge, dtype=np.int32)
+        self.N = int(np.asarray(volume).shape[0])
+        self.E = int(edge.shape[0])
+        self.ctx = L.op2b_init(device, self.stream.cuda_stream)
+        c = self.ctx
+        self.nodes = L.op2b_decl_set(c, self.N, "nodes")
+        self.edges = L.op2b_decl_set(c, self.E, "edges")
+        self.map = L.op2b_decl_map(c, self.edges, self.nodes, 2, edge.ravel(), "edge2node")
+        self.t, self.d = {}, {}
+
+        def node(name, dim, dtype=torch.float64, init=None):
+            self._dat(name, self.nodes, self.N, dim, dtype, init)
+
+        def edgd(name, dim, dtype=torch.float64, init=None):
+            self._dat(name, self.edges, self.E, dim, dtype, init)
+
+        node("q", 6, init=q)
+        node("q0", 6)
+        node("R", 6)
+        node("G", 18)
+        node("V", 1, init=np.asarray(volume).reshape(-1, 1))
+        node("lam_s", 1)
+        node("dt", 1)
+        edgd("n", 3, init=normal)
+        edgd("dx", 3, init=dx)
+        self.mixed = mixed
+        if mixed:
+            node("q32", 6, torch.float32, init=q)
+            node("G32", 18, torch.float32)
+            edgd("n32", 3, torch.float32, init=normal)
+            edgd("dx32", 3, torch.float32, init=dx)
+        self.has_adjoint = adjoint
+        if adjoint:
+            node("lam", 6)
+            node("qbar", 6)
+            node("Gbar", 18)
+            edgd("nbar", 3)
+        self.perm = np.arange(self.N, dtype=np.int64)   # new id of old node
+        self.order = np.arange(self.E, dtype=np.int64)  # old edge of new slot
+        if renumber != "none":
+            perm, order = L.op2b_renumber(c, self.map, RENUMBER[renumber], seed,
+                                          self.N, self.E)
+            self.perm, self.order = perm.astype(np.int64), order
+        self.edge = L.op2b_fetch_map(c, self.map, 2 * self.E).reshape(-1, 2)
+        self._build_args()
+
+    # ------------------------------------------------------------ dats
+    def _dat(self, name, set_, n, dim, dtype, init):
+        torch = self.torch
+        t = torch.zeros((dim, max(n, 1)), dtype=dtype, device=self.device)
+        if init is not None and n > 0:
+            a = np.asarray(init, dtype=np.float64).reshape(n, dim)
+            t[:, :n].copy_(torch.from_numpy(np.ascontiguousarray(a.T)).to(dtype))
+        type_ = {torch.float64: L.F64, torch.float32: L.F32}[dtype]
+        self.d[name] = L.op2b_decl_dat(self.ctx, set_, dim, type_, t.data_ptr(),
+                                       t.shape[1], name)
+        self.t[name] = t
+
+    def rebind(self, name, tensor):
+        """Make dat `name` use `tensor` (same shape) from now on."""
+        assert tensor.shape == self.t[name].shape and tensor.is_contiguous()
+        L.op2b_rebind_dat(self.ctx, self.d[name], tensor.data_ptr())
+        self.t[name] = tensor
+
+    def fetch_nodes(self, name) -> np.ndarray:
+        """(N, dim) float64 in the caller's node numbering."""
+        a = self.t[name][:, :self.N].double().cpu().numpy().T
+        return np.ascontiguousarray(a[self.perm])
+
+    def fetch_edges(self, name) -> np.ndarray:
+        """(E, dim) float64 in the caller's edge order."""
+        a = self.t[name][:, :self.E].double().cpu().numpy().T
+        out = np.empty_like(a)
+        out[self.order] = a
+        return out
+
+    def load_nodes(self, name, values):
+        """Set dat `name` from (N, dim) values in the caller's numbering."""
+        v = np.asarray(values, dtype=np.float64).reshape(self.N, -1)
+        a = np.empty_like(v)
+        a[self.perm] = v
+        t = self.t[name]
+        t[:, :self.N].copy_(self.torch.from_numpy(np.ascontiguousarray(a.T)).to(t.dtype))
+
+    def load_edges(self, name, values):
+        v = np.asarray(values, dtype=np.float64).reshape(self.E, -1)
+        t = self.t[name]
+        t[:, :self.E].copy_(self.torch.from_numpy(np.ascontiguousarray(v[self.order].T)).to(t.dtype))
+
+    # ------------------------------------------------------------ loops
+    def _build_args(self):
+        d, m = self.d, self.map
+
+        def ind(name, idx, acc):
+            return (d[name], idx, m, acc)
+
+        def dr(name, acc):
+            return (d[name], -1, L.ID, acc)
+
+        R, I, W, RWa = L.READ, L.INC, L.WRITE, L.RW
+        self.a_gg = [ind("q", 0, R), ind("q", 1, R), dr("n", R), ind("G", 0, I), ind("G", 1, I)]
+        self.a_f1 = [ind("q", 0, R), ind("q", 1, R), dr("n", R), ind("R", 0, I), ind("R", 1, I)]
+        self.a_f2 = [ind("q", 0, R), ind("q", 1, R), ind("G", 0, R), ind("G", 1, R),
+                     dr("n", R), dr("dx", R), ind("R", 0, I), ind("R", 1, I)]
+        self.a_sr = [ind("q", 0, R), ind("q", 1, R), dr("n", R), ind("lam_s", 0, I),
+                     ind("lam_s", 1, I)]
+        if self.mixed:
+            self.a_gg32 = [ind("q32", 0, R), ind("q32", 1, R), dr("n32", R),
+                           ind("G32", 0, I), ind("G32", 1, I)]
+            self.a_f1_32 = [ind("q32", 0, R), ind("q32", 1, R), dr("n32", R),
+                            ind("R", 0, I), ind("R", 1, I)]
+            self.a_f2_32 = [ind("q32", 0, R), ind("q32", 1, R), ind("G32", 0, R),
+                            ind("G32", 1, R), dr("n32", R), dr("dx32", R),
+                            ind("R", 0, I), ind("R", 1, I)]
+        if self.has_adjoint:
+            self.a_fa1 = [ind("lam", 0, R), ind("lam", 1, R), ind("q", 0, R), ind("q", 1, R),
+                          dr("n", R), ind("qbar", 0, I), ind("qbar", 1, I), dr("nbar", W)]
+            self.a_fa2 = [ind("lam", 0, R), ind("lam", 1, R), ind("q", 0, R), ind("q", 1, R),
+                          ind("G", 0, R), ind("G", 1, R), dr("n", R), dr("dx", R),
+                          ind("qbar", 0, I), ind("qbar", 1, I), ind("Gbar", 0, I),
+                          ind("Gbar", 1, I), dr("nbar", W)]
+            self.a_gga = [ind("Gbar", 0, R), ind("Gbar", 1, R), ind("q", 0, R), ind("q", 1, R),
+                          dr("n", R), ind("qbar", 0, I), ind("qbar", 1, I), dr("nbar", RWa)]
+
+    def set_strategy(self, loop, prec, strategy, block=0, part=0, staged=0):
+        L.op2b_set_strategy(self.ctx, loop, prec, strategy, block, part, staged)
+
+    def plan_stats(self, loop, prec=L.PREC_F64):
+        return L.op2b_plan_stats(self.ctx, loop, prec, self.map)
+
+    def green_gauss(self, mixed=False):
+        """G = Graw / V (FP64, or FP32 into G32 with ``mixed``)."""
+        c = self.ctx
+        L.op2b_green_gauss(c, self.a_gg32 if mixed else self.a_gg, L.ZERO_INC)
+        L.op2b_grad_scale(c, self.d["G32" if mixed else "G"], self.d["V"])
+
+    def flux(self, order, mixed=False):
+        """R = sum of edge fluxes (R zeroed first)."""
+        if order == 1:
+            a = self.a_f1_32 if mixed else self.a_f1
+        else:
+            a = self.a_f2_32 if mixed else self.a_f2
+        L.op2b_edge_flux(self.ctx, a, order, self.gamma, self.eps_lim, L.ZERO_INC)
+
+    def residual(self, order=2, mixed=False):
+        if order == 2:
+            self.green_gauss(mixed)
+        self.flux(order, mixed)
+
+    def spectral_radius(self):
+        L.op2b_spectral_radius(self.ctx, self.a_sr, self.gamma, L.ZERO_INC)
+
+    def time_step(self, cfl=0.5):
+        """Frozen local time step from the current state."""
+        self.spectral_radius()
+        L.op2b_time_step(self.ctx, self.d["V"], self.d["lam_s"], cfl, self.d["dt"])
+
+    def update(self, alpha, mixed=False):
+        L.op2b_node_update(self.ctx, self.d["q0"], self.d["q"], self.d["R"], self.d["V"],
+                           self.d["dt"], alpha, self.d["q32"] if mixed else -1)
+
+    def stage(self, alpha, order=2, mixed=False):
+        self.residual(order, mixed)
+        self.update(alpha, mixed)
+
+    def step(self, order=2, mixed=False, stages=5):
+        """One explicit RK step (q0 <- q, then `stages` stages)."""
+        L.op2b_dat_copy(self.ctx, self.d["q0"], self.d["q"])
+        for a in RK5_ALPHA[5 - stages:]:
+            self.stage(a, order, mixed)
+
+    def sync_shadow(self):
+        """q32 <- q (FP32 shadow of the state)."""
+        L.op2b_dat_copy(self.ctx, self.d["q32"], self.d["q"])
+
+    def adjoint(self, order=2):
+        """qbar = dJ/dq (dat qbar) and nbar = dJ/dn (dat nbar) of J = lam . R."""
+        c = self.ctx
+        if order == 1:
+            L.op2b_edge_flux_adjoint(c, self.a_fa1, 1, self.gamma, self.eps_lim, L.ZERO_INC)
+            return
+        self.green_gauss()
+        L.op2b_edge_flux_adjoint(c, self.a_fa2, 2, self.gamma, self.eps_lim, L.ZERO_INC)
+        L.op2b_grad_scale_adjoint(c, self.d["Gbar"], self.d["V"])
+        L.op2b_green_gauss_adjoint(c, self.a_gga, 0)
+
+    def launch_count(self):
+        return L.op2b_launch_count(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            L.op2b_finalize(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,304 @@
+"""CUDA edge loops against the CPU oracle, through the C ABI.
+
+Error measure for residuals and gradients (per node and component): the
+absolute difference divided by the sum of the absolute values of the edge
+contributions to that entry (the oracle's Rabs / Gabs).  Only the order of
+the scatter and of a few operations differs from the oracle, so the bound
+is 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1403_7209_gb300 import meshgen
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+STRATS = [("atomic", 1, 256, 0, 0), ("atomic128", 1, 128, 0, 0),
+          ("colour", 2, 256, 512, 0), ("colour_staged", 2, 128, 256, 1),
+          ("colour_staged_big", 2, 256, 1024, 1), ("segmented", 3, 256, 0, 0)]
+
+
+def rel_err(gpu, ref, scale):
+    return float(np.max(np.abs(gpu - ref) / (scale + 1e-300)))
+
+
+def make_solver(op2b, m, q, renumber="none", **kw):
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    return EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber=renumber, **kw)
+
+
+@pytest.fixture(scope="module")
+def mesh16():
+    m = meshgen.lattice(16)
+    q = meshgen.flow_state(m)
+    return m, q
+
+
+@pytest.fixture(scope="module")
+def ref16(mesh16):
+    m, q = mesh16
+    R1, _, R1a = oracle.residual(1, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
+    R2, G, R2a = oracle.residual(2, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
+    Graw, Ga = oracle.green_gauss(m.edge, q, m.normal, with_abs=True)
+    return dict(R1=R1, R1a=R1a, R2=R2, R2a=R2a, G=G, Gabs=Ga / m.volume[:, None])
+
+
+@pytest.mark.parametrize("name,strat,block,part,staged", STRATS)
+def test_flux1_matches_oracle(gpu_lib, mesh16, ref16, name, strat, block, part, staged):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q)
+    s.set_strategy(gpu_lib.LOOP_FLUX1, 0, strat, block, part, staged)
+    s.flux(1)
+    assert rel_err(s.fetch_nodes("R"), ref16["R1"], ref16["R1a"]) <= TOL
+    s.close()
+
+
+@pytest.mark.parametrize("name,strat,block,part,staged", STRATS)
+def test_green_gauss_matches_oracle(gpu_lib, mesh16, ref16, name, strat, block, part, staged):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q)
+    s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, strat, block, part, staged)
+    s.green_gauss()
+    assert rel_err(s.fetch_nodes("G"), ref16["G"], ref16["Gabs"]) <= TOL
+    s.close()
+
+
+@pytest.mark.parametrize("name,strat,block,part,staged", STRATS)
+def test_flux2_matches_oracle(gpu_lib, mesh16, ref16, name, strat, block, part, staged):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q)
+    s.set_strategy(gpu_lib.LOOP_FLUX2, 0, strat, block, part, staged)
+    s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, strat, block, part, staged)
+    s.residual(2)
+    assert rel_err(s.fetch_nodes("R"), ref16["R2"], ref16["R2a"]) <= TOL
+    s.close()
+
+
+@pytest.mark.parametrize("renumber", ["random", "rcm"])
+def test_renumbered_residual_in_user_order(gpu_lib, mesh16, ref16, renumber):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber=renumber, seed=3)
+    # the library's edge order is sorted by (min end, max end)
+    lo = np.minimum(s.edge[:, 0], s.edge[:, 1]).astype(np.int64)
+    hi = np.maximum(s.edge[:, 0], s.edge[:, 1]).astype(np.int64)
+    key = lo * m.num_nodes + hi
+    assert np.all(np.diff(key) > 0)
+    # and is the user's mesh relabelled
+    assert np.array_equal(s.edge, s.perm[m.edge[s.order]])
+    for strat in (1, 2, 3):
+        s.set_strategy(gpu_lib.LOOP_FLUX2, 0, strat, 256, 512, 1)
+        s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, strat, 256, 512, 1)
+        s.residual(2)
+        assert rel_err(s.fetch_nodes("R"), ref16["R2"], ref16["R2a"]) <= TOL
+        assert rel_err(s.fetch_nodes("G"), ref16["G"], ref16["Gabs"]) <= TOL
+    s.close()
+
+
+def test_ragged_and_tiny_meshes(gpu_lib):
+    # E = 243 and 1125: tails shorter than a block and a partition
+    for n in (3, 5):
+        m = meshgen.lattice(n, seed=1)
+        q = meshgen.flow_state(m, seed=1)
+        R, _, Ra = oracle.residual(2, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
+        for strat, part, staged in ((1, 0, 0), (2, 64, 0), (2, 64, 1), (2, 4096, 1), (3, 0, 0)):
+            s = make_solver(gpu_lib, m, q)
+            s.set_strategy(gpu_lib.LOOP_FLUX2, 0, strat, 64, part, staged)
+            s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, strat, 64, part, staged)
+            s.residual(2)
+            assert rel_err(s.fetch_nodes("R"), R, Ra) <= TOL
+            s.close()
+
+
+def test_empty_edge_set_gives_zero_residual(gpu_lib):
+    N = 10
+    q = np.tile([1.0, 0.5, 0.0, 0.0, 2.5, 0.0], (N, 1))
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    for strat in (1, 2, 3):
+        s = EdgeSolver(np.zeros((0, 2), np.int32), np.zeros((0, 3)), np.zeros((0, 3)),
+                       np.ones(N), q)
+        s.set_strategy(gpu_lib.LOOP_FLUX2, 0, strat)
+        s.t["R"].fill_(7.0)
+        s.residual(2)
+        assert np.all(s.fetch_nodes("R") == 0.0)
+        s.close()
+
+
+def test_spectral_radius_time_step_and_rk_step(gpu_lib, mesh16):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber="rcm")
+    s.time_step(0.5)
+    lam = oracle.spectral_radius(m.edge, q, m.normal)
+    np.testing.assert_allclose(s.fetch_nodes("lam_s")[:, 0], lam, rtol=1e-13)
+    np.testing.assert_allclose(s.fetch_nodes("dt")[:, 0],
+                               oracle.time_step(m.volume, lam, 0.5), rtol=1e-13)
+    s.step(order=2)
+    qo, st = oracle.march(2, 1, m.edge, q, m.normal, m.dx, m.volume)
+    assert st == 0
+    qg = s.fetch_nodes("q")
+    assert np.max(np.abs(qg - qo) / np.max(np.abs(qo), axis=0)) <= 1e-12
+    s.close()
+
+
+def test_march_ten_steps(gpu_lib):
+    m = meshgen.lattice(8)
+    q = meshgen.flow_state(m)
+    s = make_solver(gpu_lib, m, q, renumber="rcm")
+    s.set_strategy(gpu_lib.LOOP_FLUX2, 0, 2, 128, 256, 1)
+    s.time_step(0.5)
+    for _ in range(10):
+        s.step(order=2)
+    qo, st = oracle.march(2, 10, m.edge, q, m.normal, m.dx, m.volume)
+    assert st == 0
+    qg = s.fetch_nodes("q")
+    assert np.max(np.abs(qg - qo) / np.max(np.abs(qo), axis=0)) <= 1e-11
+    s.close()
+
+
+@pytest.mark.parametrize("strat", [1, 2, 3])
+def test_mixed_precision_residual_error(gpu_lib, mesh16, ref16, strat):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, mixed=True, renumber="rcm")
+    for loop in (gpu_lib.LOOP_GREEN_GAUSS, gpu_lib.LOOP_FLUX2, gpu_lib.LOOP_FLUX1):
+        s.set_strategy(loop, 1, strat, 256, 512, 1)
+    s.residual(2, mixed=True)
+    R = s.fetch_nodes("R")
+    err = np.max(np.abs(R - ref16["R2"]), axis=0) / np.max(np.abs(ref16["R2"]), axis=0)
+    assert np.all(err <= 1e-5), err
+    assert np.max(err) > 0.0  # really computed in FP32
+    s.flux(1, mixed=True)
+    R = s.fetch_nodes("R")
+    err = np.max(np.abs(R - ref16["R1"]), axis=0) / np.max(np.abs(ref16["R1"]), axis=0)
+    assert np.all(err <= 1e-5), err
+    s.close()
+
+
+def test_mixed_precision_march(gpu_lib):
+    m = meshgen.lattice(8)
+    q = meshgen.flow_state(m)
+    s = make_solver(gpu_lib, m, q, mixed=True, renumber="rcm")
+    s.time_step(0.5)
+    for _ in range(10):
+        s.step(order=2, mixed=True)
+    qo, st = oracle.march(2, 10, m.edge, q, m.normal, m.dx, m.volume)
+    qg = s.fetch_nodes("q")
+    err = np.max(np.abs(qg - qo), axis=0) / np.max(np.abs(qo), axis=0)
+    assert np.all(err <= 1e-5), err
+    s.close()
+
+
+def _adj_err(gpu, ref):
+    # per entry, relative to its own size plus the component's median size
+    med = np.median(np.abs(ref), axis=0)
+    return float(np.max(np.abs(gpu - ref) / (np.abs(ref) + med)))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("strat", [1, 2, 3])
+def test_adjoint_matches_oracle_reverse(gpu_lib, mesh16, order, strat):
+    m, q = mesh16
+    lam = meshgen.adjoint_seed(m.num_nodes)
+    s = make_solver(gpu_lib, m, q, adjoint=True, renumber="rcm")
+    for loop in (gpu_lib.LOOP_FLUX1_ADJ, gpu_lib.LOOP_FLUX2_ADJ, gpu_lib.LOOP_GG_ADJ):
+        s.set_strategy(loop, 0, strat, 128, 256, 1)
+    s.load_nodes("lam", lam)
+    s.adjoint(order)
+    qb, nb = oracle.residual_reverse(order, m.edge, q, m.normal, m.dx, m.volume, lam)
+    assert _adj_err(s.fetch_nodes("qbar"), qb) <= TOL
+    assert _adj_err(s.fetch_edges("nbar"), nb) <= TOL
+    s.close()
+
+
+def test_autograd_backward_and_dot_product(gpu_lib):
+    import torch
+    from paper_1403_7209_gb300.autograd import residual
+    m = meshgen.lattice(8)
+    q = meshgen.flow_state(m)
+    lam = meshgen.adjoint_seed(m.num_nodes)
+    s = make_solver(gpu_lib, m, q, adjoint=True)
+    qt = s.t["q"].clone().requires_grad_(True)
+    nt = s.t["n"].clone().requires_grad_(True)
+    R = residual(s, qt, nt, 2)
+    Ro, _ = oracle.residual(2, m.edge, q, m.normal, m.dx, m.volume)
+    np.testing.assert_allclose(R.detach().cpu().numpy().T, Ro, rtol=1e-11, atol=1e-12)
+    lt = torch.from_numpy(np.ascontiguousarray(lam.T)).cuda()
+    (R * lt).sum().backward()
+    qb, nb = oracle.residual_reverse(2, m.edge, q, m.normal, m.dx, m.volume, lam)
+    assert _adj_err(qt.grad.cpu().numpy().T, qb) <= TOL
+    assert _adj_err(nt.grad.cpu().numpy().T, nb) <= TOL
+    # dot-product test: <lam, J v> from the oracle's tangent sweep against
+    # <J^T lam, v> from the GPU reverse sweep
+    qd = meshgen.adjoint_seed(m.num_nodes, stream=meshgen.STREAM_V)
+    nd = meshgen.normal(0, meshgen.STREAM_V, np.arange(3 * m.num_edges, dtype=np.uint64)).reshape(-1, 3)
+    Rd = oracle.residual_tangent(2, m.edge, q, m.normal, m.dx, m.volume, qd, nd)
+    lhs = np.sum(lam * Rd)
+    rhs = np.sum(qt.grad.cpu().numpy().T * qd) + np.sum(nt.grad.cpu().numpy().T * nd)
+    assert abs(lhs - rhs) <= 1e-12 * (np.sum(np.abs(lam * Rd)))
+    s.close()
+
+
+def test_autotuner_picks_and_persists(gpu_lib, mesh16, ref16, tmp_path):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber="rcm")
+    for loop in (gpu_lib.LOOP_GREEN_GAUSS, gpu_lib.LOOP_FLUX2):
+        s.set_strategy(loop, 0, gpu_lib.STRAT_AUTO)
+    s.residual(2)
+    assert rel_err(s.fetch_nodes("R"), ref16["R2"], ref16["R2a"]) <= TOL
+    st = s.plan_stats(gpu_lib.LOOP_FLUX2)
+    assert st["strategy"] in (1, 2, 3) and st["tuned_ms"] > 0
+    assert st["ncolours"] >= 2 and st["nblocks"] >= 1
+    path = str(tmp_path / "tune.json")
+    gpu_lib.op2b_save_tuning(s.ctx, path)
+    s2 = make_solver(gpu_lib, m, q, renumber="rcm")
+    gpu_lib.op2b_load_tuning(s2.ctx, path)
+    s2.set_strategy(gpu_lib.LOOP_FLUX2, 0, gpu_lib.STRAT_AUTO)
+    s2.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, gpu_lib.STRAT_AUTO)
+    n0 = s2.launch_count()
+    s2.residual(2)
+    assert s2.plan_stats(gpu_lib.LOOP_FLUX2)["strategy"] == st["strategy"]
+    assert s2.launch_count() - n0 <= 64  # table hit: no candidate timing
+    s.close()
+    s2.close()
+
+
+def test_autotuner_deadline_reports_timeout(gpu_lib, mesh16):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q)
+    gpu_lib.op2b_set_tune_deadline(s.ctx, 1e-6)
+    s.set_strategy(gpu_lib.LOOP_FLUX2, 0, gpu_lib.STRAT_AUTO)
+    with pytest.raises(gpu_lib.Op2bError) as ei:
+        s.residual(2)
+    assert ei.value.code in (gpu_lib.ETIMEOUT,)
+    s.close()
+
+
+def test_argument_validation(gpu_lib, mesh16):
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, mixed=True)
+    L, d, mp = gpu_lib, s.d, s.map
+    c = s.ctx
+    bad_dim = [(d["q"], 0, mp, L.READ), (d["q"], 1, mp, L.READ), (d["n"], -1, L.ID, L.READ),
+               (d["R"], 0, mp, L.INC), (d["R"], 1, mp, L.INC)]
+    with pytest.raises(L.Op2bError) as e:
+        L.op2b_green_gauss(c, bad_dim)
+    assert e.value.code == L.EDIM
+    bad_acc = list(s.a_f1)
+    bad_acc[2] = (d["n"], -1, L.ID, L.INC)
+    with pytest.raises(L.Op2bError) as e:
+        L.op2b_edge_flux(c, bad_acc, 1)
+    assert e.value.code == L.EACCESS
+    bad_set = list(s.a_f1)
+    bad_set[2] = (d["q"], -1, L.ID, L.READ)
+    with pytest.raises(L.Op2bError) as e:
+        L.op2b_edge_flux(c, bad_set, 1)
+    assert e.value.code in (L.ESET, L.EDIM)
+    bad_type = list(s.a_f1)
+    bad_type[2] = (d["n32"], -1, L.ID, L.READ)
+    with pytest.raises(L.Op2bError) as e:
+        L.op2b_edge_flux(c, bad_type, 1)
+    assert e.value.code == L.ETYPE
+    with pytest.raises(L.Op2bError) as e:
+        L.op2b_edge_flux(c, s.a_f1, 3)
+    assert e.value.code == L.EINVAL
+    s.close()

@@ -1,0 +1,343 @@
+"""Benchmark of the edge-loop hot path on one GB300 (or N replicas).
+
+One step = one explicit second-order Runge-Kutta stage in FP64 on the
+100^3 periodic jittered lattice (1,000,000 nodes, 9,000,000 edges, RCM
+numbering): Green-Gauss edge loop, gradient scaling, limited Rusanov flux
+edge loop, node update.  value = edges / stage time (whole job over all
+ranks).  Also reported: the per-loop times, the FP32-mixed stage and the
+adjoint sweep on the same mesh, the roofline of the dominant kernel, an
+end-to-end figure through host buffers, and the CPU oracle's rate on a
+bounded sample.
+
+``--impl reference`` times the CPU oracle instead (serial FP64 C) on the
+same workload.  With N > 1 (torchrun) every rank runs its own replica of
+the mesh: the edge loops have no exchange step on one mesh per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/s & HBM GB/s (FP64, FP32-mixed, adjoint) vs oracle; fraction of roofline"
+
+# Algorithmic (compulsory) FP64 bytes per edge of each loop: edge data read
+# once, node data read once and INC targets written once, node bytes spread
+# over the 9 edges per node.
+BYTES_PER_EDGE = {"gg": 8 + 24 + (48 + 144) / 9, "flux2": 8 + 24 + 24 + (48 + 144 + 48) / 9,
+                  "scale": 296 / 9, "update": 160 / 9}
+BYTES_PER_EDGE_F32 = {"gg": 8 + 12 + (24 + 72) / 9, "flux2": 8 + 12 + 12 + (24 + 72 + 48) / 9,
+                      "scale": 148 / 9, "update": 184 / 9}
+# FP64 operations per edge of the flux2 definition (reconstruction 198 +
+# Rusanov 97), each add, multiply, divide and square root counted once.
+FLOPS_PER_EDGE_FLUX2 = 295.0
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 ALU peak: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+                self.lines = [l for l in out.splitlines() if l.strip()]
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_mesh(n, numbering):
+    from paper_1403_7209_gb300 import meshgen
+    m = meshgen.lattice(n)
+    q = meshgen.flow_state(m)
+    return m, q
+
+
+def cpu_baseline_run(m, q, stages):
+    """Time the oracle (as it stands) on `stages` second-order RK stages."""
+    import oracle
+    oracle.build()
+    lam = oracle.spectral_radius(m.edge, q, m.normal)
+    dt = oracle.time_step(m.volume, lam, 0.5)
+    t0 = time.perf_counter()
+    qq = q
+    for k in range(stages):
+        R, _ = oracle.residual(2, m.edge, qq, m.normal, m.dx, m.volume)
+        qq = oracle.rk_update(q, R, m.volume, dt, 0.25)
+    t = time.perf_counter() - t0
+    return m.num_edges * stages / t, t
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    m, q = build_mesh(args.n, args.numbering)
+    rate, t = cpu_baseline_run(m, q, max(1, args.steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "edges/s",
+        "n_gpus": args.gpus, "steps": max(1, args.steps), "warmup": 0,
+        "ms_per_step": 1e3 * t / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, m),
+        "cpu_baseline": {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d full second-order RK stages of the %d^3 mesh" %
+                                   (max(1, args.steps), args.n)},
+        "e2e": {"value": rate, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args, m):
+    return {"workload": "second-order FP64 explicit RK stage (Green-Gauss + gradient scaling + "
+                        "van Albada-limited Rusanov flux + node update) on the %d^3 periodic "
+                        "jittered lattice" % args.n,
+            "nodes": m.num_nodes, "edges": m.num_edges, "numbering": args.numbering,
+            "l2": "inputs larger than L2 (node + edge data %.0f MB vs 129 MB L2)" %
+                  ((m.num_nodes * (6 * 4 + 18 + 3) * 8 + m.num_edges * (6 * 8 + 8)) / 1e6),
+            "parallelism": "replicas (one mesh per GPU)"}
+
+
+def timed(torch, fn, steps, stream):
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        fn()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / steps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="op2b", choices=["op2b", "reference"])
+    ap.add_argument("--n", type=int, default=100, help="lattice size per side")
+    ap.add_argument("--numbering", default="rcm", choices=["rcm", "random", "none"])
+    ap.add_argument("--cpu-stages", type=int, default=3, help="oracle sample size (stages)")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--tune-cache", default="")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    import torch
+    ws, rank, local = dist_setup()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1403_7209_gb300 import op2b as L
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    L.load(build_if_missing=False)
+
+    m, q = build_mesh(args.n, args.numbering)
+    stream = torch.cuda.current_stream()
+    s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=local, renumber=args.numbering,
+                   mixed=not args.no_extras, adjoint=not args.no_extras, stream=stream)
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        L.op2b_load_tuning(s.ctx, args.tune_cache)
+    for loop in range(L.NUM_LOOPS):
+        for prec in (0, 1):
+            s.set_strategy(loop, prec, L.STRAT_AUTO)
+    s.time_step(0.5)
+    L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
+
+    # per-loop events inside each timed step
+    names = ["gg", "scale", "flux2", "update"]
+
+    def stage(ev=None):
+        if ev: ev[0].record(stream)
+        L.op2b_green_gauss(s.ctx, s.a_gg, L.ZERO_INC)
+        if ev: ev[1].record(stream)
+        L.op2b_grad_scale(s.ctx, s.d["G"], s.d["V"])
+        if ev: ev[2].record(stream)
+        L.op2b_edge_flux(s.ctx, s.a_f2, 2, s.gamma, s.eps_lim, L.ZERO_INC)
+        if ev: ev[3].record(stream)
+        L.op2b_node_update(s.ctx, s.d["q0"], s.d["q"], s.d["R"], s.d["V"], s.d["dt"], 0.25, -1)
+        if ev: ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        stage()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = s.launch_count()
+    with Clocks(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            stage(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = s.launch_count() - n_launch0
+    ms = t0.elapsed_time(t1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    loop_ms = {nm: statistics.mean(evs[k][j].elapsed_time(evs[k][j + 1]) for k in range(args.steps))
+               for j, nm in enumerate(names)}
+    E, N = m.num_edges, m.num_nodes
+    value = ws * E / (ms * 1e-3)
+    hbm, hbm_src = read_peaks()
+    fl_ms = loop_ms["flux2"]
+    achieved = FLOPS_PER_EDGE_FLUX2 * E / (fl_ms * 1e-3) / 1e12
+    strat = {nm: L.STRATEGY_NAMES[s.plan_stats(lp)["strategy"]] for nm, lp in
+             (("gg", L.LOOP_GREEN_GAUSS), ("flux2", L.LOOP_FLUX2))}
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, m),
+        "roofline": {"kernel": "flux2 edge loop (FP64, %s)" % strat["flux2"], "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "FP64 FMA units x clock (152 SMs x 2/clk x 2 flop x 2.07 GHz)",
+                     "hbm_frac": BYTES_PER_EDGE["flux2"] * E / (fl_ms * 1e-3) / 1e9 / hbm,
+                     "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "loops": {nm: {"ms": loop_ms[nm], "edges_per_s": E / (loop_ms[nm] * 1e-3),
+                       "gbs": BYTES_PER_EDGE[nm] * E / (loop_ms[nm] * 1e-3) / 1e9,
+                       "strategy": strat.get(nm, "direct")} for nm in names},
+    }
+
+    if not args.no_extras:
+        # FP32-mixed stage (FP32 node data / gradients / flux arithmetic, FP64 R and update)
+        s.sync_shadow()
+
+        def mixed_stage():
+            s.stage(0.25, 2, mixed=True)
+        for _ in range(args.warmup):
+            mixed_stage()
+        mms = timed(torch, mixed_stage, args.steps, stream)
+        s.sync_shadow()
+        # residual error of the mixed path against the FP64 path on the same state
+        s.residual(2)
+        R64 = s.t["R"][:, :N].clone()
+        s.residual(2, mixed=True)
+        R32 = s.t["R"][:, :N].clone()
+        rerr = ((R32 - R64).abs().amax(dim=1) / R64.abs().amax(dim=1)).cpu().tolist()
+        line["mixed"] = {"ms_per_stage": mms, "edges_per_s": E / (mms * 1e-3),
+                         "speedup_vs_fp64": ms / mms,
+                         "residual_rel_err_per_component": rerr}
+        # adjoint sweep (Green-Gauss + flux adjoint + scaling adjoint + GG adjoint)
+        s.t["lam"].normal_()
+        for _ in range(max(1, args.warmup)):
+            s.adjoint(2)
+        ams = timed(torch, lambda: s.adjoint(2), args.steps, stream)
+        fms = timed(torch, lambda: s.residual(2), args.steps, stream)
+        line["adjoint"] = {"ms": ams, "forward_residual_ms": fms, "ratio_to_forward": ams / fms,
+                           "edges_per_s": E / (ams * 1e-3)}
+
+    # end to end through host buffers: pinned q in, the new q out, per step
+    q_host = torch.empty((6, N), dtype=torch.float64).pin_memory()
+    q_host.copy_(s.t["q"][:, :N].cpu())
+    out_host = torch.empty((6, N), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        s.t["q"][:, :N].copy_(q_host, non_blocking=True)
+        stage()
+        out_host.copy_(s.t["q"][:, :N], non_blocking=True)
+    for _ in range(3):
+        e2e_step()
+    ems = timed(torch, e2e_step, args.steps, stream)
+    line["e2e"] = {"value": ws * E / (ems * 1e-3), "unit": "edges/s",
+                   "h2d_bytes_per_step": int(q_host.numel() * 8),
+                   "d2h_bytes_per_step": int(out_host.numel() * 8)}
+
+    if rank == 0:
+        rate, t = cpu_baseline_run(m, q, args.cpu_stages)
+        line["cpu_baseline"] = {"value": rate, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d second-order RK stages of the full %d^3 mesh "
+                                          "(serial C oracle, %.1f s)" % (args.cpu_stages, args.n, t)}
+        print(json.dumps(line))
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

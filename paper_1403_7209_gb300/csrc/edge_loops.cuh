@@ -112,11 +112,16 @@ struct BodyFlux2 {
   }
   __device__ __forceinline__ void edge(int64_t e, const T* vi, const T* vj,
                                        TE* oi, TE*) const {
-    T qL[6], qR[6];
-    reconstruct(vi, vj, ldro(dx + e), ldro(dx + lddx + e),
-                ldro(dx + 2 * lddx + e), g, qL, qR);
-    rusanov(qL, qR, ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e), g,
-            oi);
+    if constexpr (sizeof(T) == 8) {
+      flux2_f64(vi, vj, ldro(dx + e), ldro(dx + lddx + e), ldro(dx + 2 * lddx + e),
+                ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e), g, oi);
+    } else {
+      T qL[6], qR[6];
+      reconstruct(vi, vj, ldro(dx + e), ldro(dx + lddx + e),
+                  ldro(dx + 2 * lddx + e), g, qL, qR);
+      rusanov(qL, qR, ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e), g,
+              oi);
+    }
   }
 };
 

@@ -78,6 +78,106 @@ __device__ __forceinline__ void reconstruct(const T* vi, const T* vj, T dx,
   }
 }
 
+// ------------------------------------------------- FP64 second-order flux
+// GB300 runs FP64 at 1/64 of the FP32 rate (2 FMA per clock per SM) and a
+// division or square root costs about ten FMA slots, so the FP64 flux is
+// bound by its FP64 instruction count.  This version computes the same
+// formulas as reconstruct() + rusanov() with fewer FP64 instructions:
+//  * the 12 limiter denominators are inverted together (one reciprocal and
+//    three multiplies each: prefix products, Montgomery's batch inversion),
+//    and so are the two face densities;
+//  * the factors 1/2 are folded into those reciprocals;
+//  * the larger of the two wave speeds is chosen by an integer comparison
+//    of their bit patterns (both are >= 0, so the order is the same).
+// Batching is used only when every denominator lies in [2^-70, 2^70], so no
+// prefix product can overflow or underflow; otherwise each is divided.
+
+__device__ __forceinline__ bool exp_in_range(double x, int lim) {
+  // |x| in [2^-lim, 2^lim] (x finite, nonzero)
+  const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+  return (unsigned)(e + lim) <= (unsigned)(2 * lim);
+}
+
+// r[k] = scale / d[k] for K values
+template <int K>
+__device__ __forceinline__ void batch_reciprocal(const double* d, double scale,
+                                                 double* r) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < K; k++) ok &= exp_in_range(d[k], 70);
+  if (ok) {
+    double p[K];
+    p[0] = d[0];
+#pragma unroll
+    for (int k = 1; k < K; k++) p[k] = p[k - 1] * d[k];
+    double inv = scale / p[K - 1];
+#pragma unroll
+    for (int k = K - 1; k > 0; k--) {
+      r[k] = inv * p[k - 1];
+      inv = inv * d[k];
+    }
+    r[0] = inv;
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; k++) r[k] = scale / d[k];
+  }
+}
+
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  // both >= 0: IEEE order equals the order of the bit patterns; ties -> a
+  return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
+}
+
+// vi, vj: q (6) then G (18, component 3k+d); F: the Rusanov flux of the
+// limited face states.
+__device__ __forceinline__ void flux2_f64(const double* vi, const double* vj,
+                                          double dx, double dy, double dz,
+                                          double nx, double ny, double nz,
+                                          const Gas<double>& g, double* F) {
+  double num[12], den[12], rec[12];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const double b = vj[k] - vi[k];
+    const double ai = fma(vi[8 + 3 * k], dz, fma(vi[7 + 3 * k], dy, vi[6 + 3 * k] * dx));
+    const double aj = fma(vj[8 + 3 * k], dz, fma(vj[7 + 3 * k], dy, vj[6 + 3 * k] * dx));
+    const double b2e = fma(b, b, g.two_eps);
+    num[2 * k] = (ai + b) * fma(ai, b, g.eps);
+    den[2 * k] = fma(ai, ai, b2e);
+    num[2 * k + 1] = (aj + b) * fma(aj, b, g.eps);
+    den[2 * k + 1] = fma(aj, aj, b2e);
+  }
+  batch_reciprocal<12>(den, 0.5, rec);  // rec = 1 / (2 den)
+  double qL[6], qR[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    qL[k] = fma(num[2 * k], rec[2 * k], vi[k]);
+    qR[k] = fma(-num[2 * k + 1], rec[2 * k + 1], vj[k]);
+  }
+  // Rusanov flux of (qL, qR)
+  const double gnn = g.gamma * fma(nz, nz, fma(ny, ny, nx * nx));
+  double rho[2] = {qL[0], qR[0]}, rr[2];
+  batch_reciprocal<2>(rho, 1.0, rr);
+  const double hgm1 = 0.5 * g.gm1;
+  double f[2][6], lam[2];
+#pragma unroll
+  for (int sd = 0; sd < 2; sd++) {
+    const double* q = sd ? qR : qL;
+    const double un = fma(q[3], nz, fma(q[2], ny, q[1] * nx)) * rr[sd];
+    const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
+    const double p = fma(-hgm1 * mm, rr[sd], g.gm1 * q[4]);
+    lam[sd] = fabs(un) + sqrt(p * rr[sd] * gnn);
+    f[sd][0] = q[0] * un;
+    f[sd][1] = fma(q[1], un, p * nx);
+    f[sd][2] = fma(q[2], un, p * ny);
+    f[sd][3] = fma(q[3], un, p * nz);
+    f[sd][4] = (q[4] + p) * un;
+    f[sd][5] = q[5] * un;
+  }
+  const double s = max_nonneg(lam[0], lam[1]);
+#pragma unroll
+  for (int k = 0; k < 6; k++) F[k] = 0.5 * fma(-s, qR[k] - qL[k], f[0][k] + f[1][k]);
+}
+
 // ---------------------------------------------------------------- adjoint
 
 __device__ __forceinline__ double sgn(double x) {

@@ -269,6 +269,39 @@ int op2b_plan_stats(op2b_ctx ctx, int32_t loop, int32_t prec, op2b_map map,
 /* Number of kernels the context has launched so far. */
 int64_t op2b_launch_count(op2b_ctx ctx);
 
+/* ------------------------------------------- allocation-free entry point
+ * The paper has no counterpart to this call.  It serves callers that must
+ * not allocate device memory (their memory is a pool owned by someone
+ * else, or allocation is forbidden inside their time loop): it needs no
+ * context, calls no cudaMalloc, cudaFree or allocating library routine, and
+ * keeps its per-edge scratch in one array compiled into the library.
+ *
+ * Computes the first-order Rusanov residual R (overwritten, F64 SoA dim 6,
+ * leading dimension ldR >= N): R_i = sum of F(q_i, q_j, n_e) over edges
+ * leaving i minus the sum over edges entering i, with the sorted segmented
+ * strategy.  Inputs (device pointers, caller-owned): q (F64 SoA dim 6, ldq),
+ * n (F64 SoA dim 3 over the edges, ldn >= E), edge_first / edge_second (the
+ * two ends of every edge, int32, 0-based), rowptr (N+1 int64) and ends (2E
+ * int32, value 2e + side) of the edge ends sorted by node, as produced by
+ * op2b_host_node_csr.  Launches on `stream` (a cudaStream_t) on the current
+ * device and returns without waiting.
+ *
+ * Limits and sharing: E must not exceed OP2B_NOALLOC_MAX_EDGES (larger sets
+ * give OP2B_ERANGE and launch nothing).  The scratch array (6 x that many
+ * doubles, 12 MiB) exists once per device for the life of the process and
+ * every call uses it, so calls whose work overlaps on the GPU (concurrent
+ * streams, or several host threads) race on it; serialise them.  The first
+ * call on a device looks up the array's device address (a runtime query that
+ * allocates nothing) and caches it; make that first call before any stream
+ * capture.  On error op2b_last_error(NULL) gives the reason. */
+#define OP2B_NOALLOC_MAX_EDGES 262144
+int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const double* n,
+                            int64_t ldn, const int32_t* edge_first,
+                            const int32_t* edge_second, const int64_t* rowptr,
+                            const int32_t* ends, int64_t N, int64_t E,
+                            double gamma, double* R, int64_t ldR,
+                            void* stream);
+
 /* ------------------------------------------------ host-only planners
  * Pure host functions (no context, no GPU), exported for validation. */
 

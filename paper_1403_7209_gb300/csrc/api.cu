@@ -15,6 +15,8 @@ using namespace op2b;
 
 static thread_local std::string g_init_err;
 
+void op2b::set_thread_error(const std::string& msg) { g_init_err = msg; }
+
 #define OP2B_VERSION_STR "op2b 0.1 (sm_103a)"
 
 static const char* kLoopName[OP2B_NUM_LOOPS] = {

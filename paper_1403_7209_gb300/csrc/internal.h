@@ -85,6 +85,10 @@ struct LoopLaunch {
 
 struct Ctx;
 
+// Text returned by op2b_last_error(NULL) on this thread (set by entry points
+// that have no context).
+void set_thread_error(const std::string& msg);
+
 // Run one edge loop with strategy s (plans and scratch taken from ctx).
 // loops_f64.cu: GREEN_GAUSS, FLUX1, FLUX2, SPECTRAL in FP64;
 // loops_f32.cu: GREEN_GAUSS, FLUX1, FLUX2 with FP32 arithmetic;

@@ -110,6 +110,8 @@ _SIGS = {
     "op2b_plan_stats": (ctypes.c_int, [_P, _I32, _I32, _I32,
                                        ctypes.POINTER(PlanStats)]),
     "op2b_launch_count": (ctypes.c_int64, [_P]),
+    "op2b_edge_flux1_noalloc": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _P, _P, _P,
+                                               _I64, _I64, _D, _P, _I64, _P]),
     "op2b_host_rcm": (ctypes.c_int, [_I64, _I64, _PI32, _PI32]),
     "op2b_host_renumber": (ctypes.c_int, [_I64, _I64, _PI32, _I32, _U64,
                                           _PI32, _PI64]),
@@ -311,6 +313,21 @@ def op2b_plan_stats(ctx, loop: int, prec: int, map_: int) -> dict:
     st = PlanStats()
     _check(load().op2b_plan_stats(ctx, loop, prec, map_, ctypes.byref(st)), ctx)
     return st.as_dict()
+
+
+# ------------------------------------------------- allocation-free entry
+NOALLOC_MAX_EDGES = 262144
+
+
+def op2b_edge_flux1_noalloc(q_ptr: int, ldq: int, n_ptr: int, ldn: int,
+                            edge_first_ptr: int, edge_second_ptr: int,
+                            rowptr_ptr: int, ends_ptr: int, N: int, E: int,
+                            gamma: float, R_ptr: int, ldR: int, stream: int):
+    """First-order residual without any device allocation (see op2b.h)."""
+    rc = load().op2b_edge_flux1_noalloc(q_ptr, ldq, n_ptr, ldn, edge_first_ptr,
+                                        edge_second_ptr, rowptr_ptr, ends_ptr, N, E,
+                                        gamma, R_ptr, ldR, stream)
+    _check(rc, None)
 
 
 # ------------------------------------------------------ host-only planners

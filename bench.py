@@ -168,6 +168,20 @@ def workload_config(args, m):
             "parallelism": "replicas (one mesh per GPU)"}
 
 
+def reduce_max_ms(ms, dist, device=None):
+    """Max over ranks of the per-rank step time: the slowest replica sets
+    the job's time."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(edges_per_rank, world_size, ms):
+    """Whole-job edges per second: all ranks' edges over the max step time."""
+    return world_size * edges_per_rank / (ms * 1e-3)
+
+
 def timed(torch, fn, steps, stream):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     torch.cuda.synchronize()
@@ -189,7 +203,8 @@ def main():
     ap.add_argument("--numbering", default="rcm", choices=["rcm", "random", "none"])
     ap.add_argument("--cpu-stages", type=int, default=3, help="oracle sample size (stages)")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--tune-cache", default="")
+    ap.add_argument("--tune-cache", default="",
+                    help="JSON strategy table: loaded if present, written after tuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -236,6 +251,8 @@ def main():
     for _ in range(args.warmup):
         stage()
     torch.cuda.synchronize()
+    if args.tune_cache and rank == 0:
+        L.op2b_save_tuning(s.ctx, args.tune_cache)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
@@ -252,14 +269,12 @@ def main():
     launches = s.launch_count() - n_launch0
     ms = t0.elapsed_time(t1) / args.steps
     if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = reduce_max_ms(ms, dist, device="cuda")
         dist.barrier()
     loop_ms = {nm: statistics.mean(evs[k][j].elapsed_time(evs[k][j + 1]) for k in range(args.steps))
                for j, nm in enumerate(names)}
     E, N = m.num_edges, m.num_nodes
-    value = ws * E / (ms * 1e-3)
+    value = job_value(E, ws, ms)
     hbm, hbm_src = read_peaks()
     fl_ms = loop_ms["flux2"]
     achieved = FLOPS_PER_EDGE_FLUX2 * E / (fl_ms * 1e-3) / 1e12

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "edge_math.cuh"
 
@@ -61,6 +62,30 @@ struct BodyGG {
       oi[3 * k] = s * hx;
       oi[3 * k + 1] = s * hy;
       oi[3 * k + 2] = s * hz;
+    }
+  }
+  // Packed form for the strategies that keep per-edge results: the 6 sums
+  // q_i + q_j and n/2 (9 values instead of 18 products); the outer product
+  // is formed while summing per node (18 FMAs per edge end).
+  static constexpr int PACK = 9;
+  __device__ __forceinline__ void pack(int64_t e, const T* vi, const T* vj,
+                                       TE* st) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) st[k] = vi[k] + vj[k];
+    st[6] = T(0.5) * ldro(n + e);
+    st[7] = T(0.5) * ldro(n + ldn + e);
+    st[8] = T(0.5) * ldro(n + 2 * ldn + e);
+  }
+  template <class Get>
+  __device__ __forceinline__ static void unpack_add(Get get, bool second,
+                                                    TA* acc) {
+    const T h[3] = {second ? -get(6) : get(6), second ? -get(7) : get(7),
+                    second ? -get(8) : get(8)};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const T s = get(k);
+#pragma unroll
+      for (int d = 0; d < 3; d++) acc[3 * k + d] = fma(s, h[d], acc[3 * k + d]);
     }
   }
 };
@@ -187,56 +212,22 @@ struct BodyFluxAdj {
   __device__ __forceinline__ void edge(int64_t e, const double* vi,
                                        const double* vj, double* oi,
                                        double* oj) const {
-    double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
-    double w[6];
-#pragma unroll
-    for (int k = 0; k < 6; k++) w[k] = vi[k] - vj[k];
-    const double* qi = vi + 6;
-    const double* qj = vj + 6;
-    double qLb[6], qRb[6];
-#pragma unroll
-    for (int k = 0; k < 6; k++) qLb[k] = qRb[k] = 0.0;
-    double nbx = 0.0, nby = 0.0, nbz = 0.0;
+    const double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
+    double nb[3] = {0.0, 0.0, 0.0};
     if constexpr (ORDER == 1) {
-      rusanov_reverse(qi, qj, nx, ny, nz, g, w, qLb, qRb, nbx, nby, nbz);
+      double w[6];
 #pragma unroll
       for (int k = 0; k < 6; k++) {
-        oi[k] = qLb[k];
-        oj[k] = qRb[k];
+        w[k] = vi[k] - vj[k];
+        oi[k] = 0.0;
+        oj[k] = 0.0;
       }
+      rusanov_reverse_f64(vi + 6, vj + 6, nx, ny, nz, g, w, oi, oj, nb);
     } else {
-      double ddx = ldro(dx + e), ddy = ldro(dx + lddx + e),
-             ddz = ldro(dx + 2 * lddx + e);
-      const double* Gi = vi + 12;
-      const double* Gj = vj + 12;
-      double qL[6], qR[6], pa_i[6], pb_i[6], pa_j[6], pb_j[6];
-#pragma unroll
-      for (int k = 0; k < 6; k++) {
-        double b = qj[k] - qi[k];
-        double ai = Gi[3 * k] * ddx + Gi[3 * k + 1] * ddy + Gi[3 * k + 2] * ddz;
-        double aj = Gj[3 * k] * ddx + Gj[3 * k + 1] * ddy + Gj[3 * k + 2] * ddz;
-        double b2e = fma(b, b, g.two_eps), phi, phj;
-        van_albada_d(ai, b, g.eps, b2e, phi, pa_i[k], pb_i[k]);
-        van_albada_d(aj, b, g.eps, b2e, phj, pa_j[k], pb_j[k]);
-        qL[k] = qi[k] + 0.5 * phi;
-        qR[k] = qj[k] - 0.5 * phj;
-      }
-      rusanov_reverse(qL, qR, nx, ny, nz, g, w, qLb, qRb, nbx, nby, nbz);
-#pragma unroll
-      for (int k = 0; k < 6; k++) {
-        double phib = 0.5 * qLb[k], phjb = -0.5 * qRb[k];
-        double aib = phib * pa_i[k], ajb = phjb * pa_j[k];
-        double bb = phib * pb_i[k] + phjb * pb_j[k];
-        oi[k] = qLb[k] - bb;
-        oj[k] = qRb[k] + bb;
-        oi[6 + 3 * k] = aib * ddx;
-        oi[7 + 3 * k] = aib * ddy;
-        oi[8 + 3 * k] = aib * ddz;
-        oj[6 + 3 * k] = ajb * ddx;
-        oj[7 + 3 * k] = ajb * ddy;
-        oj[8 + 3 * k] = ajb * ddz;
-      }
+      flux2_adj_f64(vi, vj, ldro(dx + e), ldro(dx + lddx + e), ldro(dx + 2 * lddx + e), nx,
+                    ny, nz, g, oi, oj, nb);
     }
+    const double nbx = nb[0], nby = nb[1], nbz = nb[2];
     nbar[e] = nbx;
     nbar[ldnb + e] = nby;
     nbar[2 * ldnb + e] = nbz;
@@ -339,9 +330,26 @@ __host__ __device__ constexpr int outs_per_edge() {
   return P::MODE == MODE_GEN ? 2 * P::OUT : P::OUT;
 }
 
+// Bodies with a packed per-edge form (PACK, pack(), unpack_add())
+template <class P, class = void>
+struct HasPack {
+  static constexpr bool value = false;
+};
+template <class P>
+struct HasPack<P, std::void_t<decltype(P::PACK)>> {
+  static constexpr bool value = true;
+};
+
+// values kept per edge by the colour and segmented strategies
+template <class P>
+__host__ __device__ constexpr int stored_per_edge() {
+  if constexpr (HasPack<P>::value) return P::PACK;
+  else return outs_per_edge<P>();
+}
+
 template <class P, bool STAGED>
 __host__ int64_t colour_smem_bytes(int32_t part, int32_t ucap) {
-  int64_t b = align16((int64_t)outs_per_edge<P>() * part * sizeof(typename P::TE));
+  int64_t b = align16((int64_t)stored_per_edge<P>() * part * sizeof(typename P::TE));
   if (STAGED) b += (int64_t)P::NIN * ucap * sizeof(typename P::TN);
   return b;
 }
@@ -359,7 +367,7 @@ __global__ void k_colour(P ph, const int32_t* __restrict__ m0,
   using TN = typename P::TN;
   using TE = typename P::TE;
   using TA = typename P::TA;
-  constexpr int OUTS = outs_per_edge<P>();
+  constexpr int OUTS = stored_per_edge<P>();
   extern __shared__ __align__(16) unsigned char smem[];
   const int part = bv.part;
   TE* sOut = reinterpret_cast<TE*>(smem);
@@ -394,13 +402,20 @@ __global__ void k_colour(P ph, const int32_t* __restrict__ m0,
         ph.load(m0[e], vi);
         ph.load(m1[e], vj);
       }
-      TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
-      ph.edge(e, vi, vj, oi, oj);
+      if constexpr (HasPack<P>::value) {
+        TE st[P::PACK];
+        ph.pack(e, vi, vj, st);
 #pragma unroll
-      for (int c = 0; c < P::OUT; c++) sOut[c * part + el] = oi[c];
-      if constexpr (P::MODE == MODE_GEN) {
+        for (int c = 0; c < P::PACK; c++) sOut[c * part + el] = st[c];
+      } else {
+        TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
+        ph.edge(e, vi, vj, oi, oj);
 #pragma unroll
-        for (int c = 0; c < P::OUT; c++) sOut[(P::OUT + c) * part + el] = oj[c];
+        for (int c = 0; c < P::OUT; c++) sOut[c * part + el] = oi[c];
+        if constexpr (P::MODE == MODE_GEN) {
+#pragma unroll
+          for (int c = 0; c < P::OUT; c++) sOut[(P::OUT + c) * part + el] = oj[c];
+        }
       }
     }
     __syncthreads();
@@ -415,7 +430,9 @@ __global__ void k_colour(P ph, const int32_t* __restrict__ m0,
         const int ent = le[t];
         const int el = ent >> 1;
         const bool second = ent & 1;
-        if constexpr (P::MODE == MODE_GEN) {
+        if constexpr (HasPack<P>::value) {
+          P::unpack_add([&](int c) { return sOut[c * part + el]; }, second, acc);
+        } else if constexpr (P::MODE == MODE_GEN) {
           const int base = second ? P::OUT : 0;
 #pragma unroll
           for (int c = 0; c < P::OUT; c++) acc[c] += (TA)sOut[(base + c) * part + el];
@@ -453,13 +470,47 @@ __global__ void k_seg_edges(P ph, const int32_t* __restrict__ m0,
     TN vi[P::NIN], vj[P::NIN];
     ph.load(m0[e], vi);
     ph.load(m1[e], vj);
-    TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
-    ph.edge(e, vi, vj, oi, oj);
+    if constexpr (HasPack<P>::value) {
+      TE st[P::PACK];
+      ph.pack(e, vi, vj, st);
 #pragma unroll
-    for (int c = 0; c < P::OUT; c++) ebuf[c * E + e] = oi[c];
-    if constexpr (P::MODE == MODE_GEN) {
+      for (int c = 0; c < P::PACK; c++) ebuf[c * E + e] = st[c];
+    } else {
+      TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
+      ph.edge(e, vi, vj, oi, oj);
 #pragma unroll
-      for (int c = 0; c < P::OUT; c++) ebuf[(P::OUT + c) * E + e] = oj[c];
+      for (int c = 0; c < P::OUT; c++) ebuf[c * E + e] = oi[c];
+      if constexpr (P::MODE == MODE_GEN) {
+#pragma unroll
+        for (int c = 0; c < P::OUT; c++) ebuf[(P::OUT + c) * E + e] = oj[c];
+      }
+    }
+  }
+}
+
+// Phase 2 for bodies with a packed per-edge form.
+template <class P>
+__global__ void k_seg_nodes_packed(const int64_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ ends, int64_t N,
+                                   int64_t E, const typename P::TE* __restrict__ ebuf,
+                                   Targets<typename P::TA, P::DIM0> tg) {
+  using TA = typename P::TA;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += stride) {
+    TA acc[P::OUT];
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) acc[c] = TA(0);
+    const int64_t r1 = rowptr[i + 1];
+    for (int64_t t = rowptr[i]; t < r1; t++) {
+      const int32_t end = ends[t];
+      const int64_t e = end >> 1;
+      P::unpack_add([&](int c) { return ebuf[c * E + e]; }, (end & 1) != 0, acc);
+    }
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) {
+      TA* p = tg.at(c, i);
+      *p = *p + acc[c];
     }
   }
 }

@@ -267,4 +267,167 @@ __device__ __forceinline__ void van_albada_d(double a, double b, double eps,
   pb = (fma(a, a, eps) + 2.0 * a * b - 2.0 * b * phi) * rd;
 }
 
+// ------------------------------------------ FP64 adjoint, fewer FP64 ops
+// The same reverse sweep as rusanov_reverse() / van_albada_d(), arranged for
+// the FP64 pipe: reciprocals batched as in flux2_f64(), one reciprocal
+// square root giving both a and 1/a (and |n|, 1/|n|), no forward fluxes
+// (the reverse sweep needs only the wave speeds and the primitive
+// quantities), and sign / max taken from the bit patterns.
+
+// sign(x) * v, with sign(0) = 0
+__device__ __forceinline__ double sign_times(double x, double v) {
+  const long long b = __double_as_longlong(x);
+  if ((b << 1) == 0) return 0.0;
+  return b < 0 ? -v : v;
+}
+
+struct SideState {
+  double rr, un, mm, p, a, ra;  // 1/rho, u.n, |m|^2, p, sound speed, 1/a
+};
+
+__device__ __forceinline__ double side_state(const double* q, double nx,
+                                             double ny, double nz, double rr,
+                                             double nn, const Gas<double>& g,
+                                             double hgm1, SideState& s) {
+  s.rr = rr;
+  s.un = fma(q[3], nz, fma(q[2], ny, q[1] * nx)) * rr;
+  s.mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
+  s.p = fma(-hgm1 * s.mm, rr, g.gm1 * q[4]);
+  const double a2 = g.gamma * s.p * rr;
+  s.ra = rsqrt(a2);
+  s.a = a2 * s.ra;
+  return fabs(s.un) + s.a * nn;  // wave speed
+}
+
+// fb = adjoint of f(q).n (6), lamb = adjoint of the wave speed.
+__device__ __forceinline__ void side_reverse_f64(
+    const double* q, double nx, double ny, double nz, const SideState& s,
+    double nn, double rn, const Gas<double>& g, const double* fb, double lamb,
+    double* qb, double* nb) {
+  double unb = sign_times(s.un, lamb);
+  const double ab = lamb * nn;
+  const double rnb = lamb * s.a * rn;  // d|n|/dn = n / |n|
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    qb[k] = fma(fb[k], s.un, qb[k]);
+    unb = fma(fb[k], q[k], unb);
+  }
+  unb = fma(fb[4], s.p, unb);
+  double pb = fma(fb[3], nz, fma(fb[2], ny, fma(fb[1], nx, fb[4] * s.un)));
+  pb = fma(0.5 * g.gamma * ab, s.rr * s.ra, pb);  // a = sqrt(gamma p / rho)
+  const double gpb = g.gm1 * pb;
+  const double ur = unb * s.rr;
+  const double gpr = gpb * s.rr;
+  const double n3[3] = {nx, ny, nz};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    nb[d] = fma(fb[1 + d], s.p, fma(rnb, n3[d], fma(ur, q[1 + d], nb[d])));
+    qb[1 + d] = fma(-gpr, q[1 + d], fma(ur, n3[d], qb[1 + d]));
+  }
+  qb[4] += gpb;
+  // rho enters through 1/rho in u.n, p and a
+  const double rhob = fma(0.5 * gpr, s.mm * s.rr, fma(-0.5 * ab, s.a * s.rr, -ur * s.un));
+  qb[0] += rhob;
+}
+
+// Reverse of the Rusanov flux: w = dJ/dF; accumulates qLb, qRb (6), nb (3).
+__device__ __forceinline__ void rusanov_reverse_f64(
+    const double* qL, const double* qR, double nx, double ny, double nz,
+    const Gas<double>& g, const double* w, double* qLb, double* qRb,
+    double* nb) {
+  const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
+  const double rn = rsqrt(nn2);
+  const double nn = nn2 * rn;
+  double rho[2] = {qL[0], qR[0]}, rr[2];
+  batch_reciprocal<2>(rho, 1.0, rr);
+  const double hgm1 = 0.5 * g.gm1;
+  SideState sL, sR;
+  const double lL = side_state(qL, nx, ny, nz, rr[0], nn, g, hgm1, sL);
+  const double lR = side_state(qR, nx, ny, nz, rr[1], nn, g, hgm1, sR);
+  const bool left = __double_as_longlong(lL) >= __double_as_longlong(lR);
+  const double hs = 0.5 * (left ? lL : lR);
+  double fb[6], sb = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    fb[k] = 0.5 * w[k];
+    sb = fma(w[k], qR[k] - qL[k], sb);
+    qRb[k] = fma(-hs, w[k], qRb[k]);
+    qLb[k] = fma(hs, w[k], qLb[k]);
+  }
+  sb *= -0.5;
+  side_reverse_f64(qL, nx, ny, nz, sL, nn, rn, g, fb, left ? sb : 0.0, qLb, nb);
+  side_reverse_f64(qR, nx, ny, nz, sR, nn, rn, g, fb, left ? 0.0 : sb, qRb, nb);
+}
+
+// Adjoint of the second-order flux of edge (i, j).  vi, vj: lam (6), q (6),
+// G (18).  oi, oj: qbar (6) then Gbar (18) of each end; nb: nbar (3).
+__device__ __forceinline__ void flux2_adj_f64(const double* vi,
+                                              const double* vj, double dx,
+                                              double dy, double dz, double nx,
+                                              double ny, double nz,
+                                              const Gas<double>& g, double* oi,
+                                              double* oj, double* nb) {
+  const double* qi = vi + 6;
+  const double* qj = vj + 6;
+  const double* Gi = vi + 12;
+  const double* Gj = vj + 12;
+  double a[12], num[12], den[12], rd[12], bk[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const double b = qj[k] - qi[k];
+    bk[k] = b;
+    a[2 * k] = fma(Gi[3 * k + 2], dz, fma(Gi[3 * k + 1], dy, Gi[3 * k] * dx));
+    a[2 * k + 1] = fma(Gj[3 * k + 2], dz, fma(Gj[3 * k + 1], dy, Gj[3 * k] * dx));
+    const double b2e = fma(b, b, g.two_eps);
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const double x = a[2 * k + sd];
+      num[2 * k + sd] = (x + b) * fma(x, b, g.eps);
+      den[2 * k + sd] = fma(x, x, b2e);
+    }
+  }
+  batch_reciprocal<12>(den, 1.0, rd);
+  double qL[6], qR[6], pa[12], pb[12];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const double b = bk[k];
+    const double be = fma(b, b, g.eps);
+    const double b2 = b + b;
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const int c = 2 * k + sd;
+      const double x = a[c];
+      const double phi = num[c] * rd[c];
+      // d phi / da = (b^2 + eps + 2a(b - phi)) / D,
+      // d phi / db = (a^2 + eps + 2b(a - phi)) / D
+      pa[c] = fma(x + x, b - phi, be) * rd[c];
+      pb[c] = fma(b2, x - phi, fma(x, x, g.eps)) * rd[c];
+      if (sd == 0) qL[k] = fma(0.5, phi, qi[k]);
+      else qR[k] = fma(-0.5, phi, qj[k]);
+    }
+  }
+  double w[6], qLb[6], qRb[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    w[k] = vi[k] - vj[k];
+    qLb[k] = 0.0;
+    qRb[k] = 0.0;
+  }
+  rusanov_reverse_f64(qL, qR, nx, ny, nz, g, w, qLb, qRb, nb);
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const double phib = 0.5 * qLb[k], phjb = -0.5 * qRb[k];
+    const double aib = phib * pa[2 * k], ajb = phjb * pa[2 * k + 1];
+    const double bb = fma(phib, pb[2 * k], phjb * pb[2 * k + 1]);
+    oi[k] = qLb[k] - bb;
+    oj[k] = qRb[k] + bb;
+    oi[6 + 3 * k] = aib * dx;
+    oi[7 + 3 * k] = aib * dy;
+    oi[8 + 3 * k] = aib * dz;
+    oj[6 + 3 * k] = ajb * dx;
+    oj[7 + 3 * k] = ajb * dy;
+    oj[8 + 3 * k] = ajb * dz;
+  }
+}
+
 }  // namespace op2b

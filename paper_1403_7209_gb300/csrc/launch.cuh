@@ -80,7 +80,7 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
       if (rc) return rc;
       using TE = typename P::TE;
       if ((rc = check_block(c, k_seg_edges<P>, block))) return rc;
-      const size_t bytes = (size_t)outs_per_edge<P>() * L.E * sizeof(TE);
+      const size_t bytes = (size_t)stored_per_edge<P>() * L.E * sizeof(TE);
       void* buf = nullptr;
       if ((rc = c->need_scratch(bytes, &buf))) return rc;
       int64_t grid = std::min<int64_t>((L.E + block - 1) / block, cap);
@@ -88,9 +88,13 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
       if ((rc = c->launched("segmented edges"))) return rc;
       int64_t gridn = std::min<int64_t>((L.N + block - 1) / block, cap);
       if (gridn == 0) return OP2B_OK;
-      k_seg_nodes<TE, typename P::TA, P::OUT, P::MODE, P::DIM0>
-          <<<(unsigned)gridn, block, 0, c->stream>>>(sp->rowptr, sp->ends, L.N, L.E,
-                                                     (const TE*)buf, tg);
+      if constexpr (HasPack<P>::value)
+        k_seg_nodes_packed<P><<<(unsigned)gridn, block, 0, c->stream>>>(sp->rowptr, sp->ends, L.N,
+                                                                       L.E, (const TE*)buf, tg);
+      else
+        k_seg_nodes<TE, typename P::TA, P::OUT, P::MODE, P::DIM0>
+            <<<(unsigned)gridn, block, 0, c->stream>>>(sp->rowptr, sp->ends, L.N, L.E,
+                                                       (const TE*)buf, tg);
       return c->launched("segmented nodes");
     }
     default:

@@ -193,6 +193,113 @@ def timed(torch, fn, steps, stream):
     return ev[0].elapsed_time(ev[1]) / steps
 
 
+def loop_events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def mixed_extra(torch, L, s, args, stream, ms64, E, N):
+    """FP32-mixed stage: per-loop times, speed-up and residual error."""
+    s.sync_shadow()
+    names = ["gg32", "scale32", "flux2_32", "update"]
+
+    def stage(ev=None):
+        if ev: ev[0].record(stream)
+        L.op2b_green_gauss(s.ctx, s.a_gg32, L.ZERO_INC)
+        if ev: ev[1].record(stream)
+        L.op2b_grad_scale(s.ctx, s.d["G32"], s.d["V"])
+        if ev: ev[2].record(stream)
+        L.op2b_edge_flux(s.ctx, s.a_f2_32, 2, s.gamma, s.eps_lim, L.ZERO_INC)
+        if ev: ev[3].record(stream)
+        L.op2b_node_update(s.ctx, s.d["q0"], s.d["q"], s.d["R"], s.d["V"], s.d["dt"], 0.25,
+                           s.d["q32"])
+        if ev: ev[4].record(stream)
+    for _ in range(args.warmup):
+        stage()
+    evs = [loop_events(torch, 5) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t0, t1 = loop_events(torch, 2)
+    t0.record(stream)
+    for k in range(args.steps):
+        stage(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    mms = t0.elapsed_time(t1) / args.steps
+    loops = {nm: statistics.mean(evs[k][j].elapsed_time(evs[k][j + 1]) for k in range(args.steps))
+             for j, nm in enumerate(names)}
+    bpe = {"gg32": BYTES_PER_EDGE_F32["gg"], "scale32": BYTES_PER_EDGE_F32["scale"],
+           "flux2_32": BYTES_PER_EDGE_F32["flux2"], "update": BYTES_PER_EDGE_F32["update"]}
+    strat = {"gg32": L.STRATEGY_NAMES[s.plan_stats(L.LOOP_GREEN_GAUSS, 1)["strategy"]],
+             "flux2_32": L.STRATEGY_NAMES[s.plan_stats(L.LOOP_FLUX2, 1)["strategy"]]}
+    hbm, _ = read_peaks()
+    out_loops = {nm: {"ms": loops[nm], "gbs": bpe[nm] * E / (loops[nm] * 1e-3) / 1e9,
+                      "hbm_frac": bpe[nm] * E / (loops[nm] * 1e-3) / 1e9 / hbm,
+                      "strategy": strat.get(nm, "direct")} for nm in names}
+    # residual error of the mixed path against the FP64 path on one state
+    s.sync_shadow()
+    s.residual(2)
+    R64 = s.t["R"][:, :N].clone()
+    s.residual(2, mixed=True)
+    R32 = s.t["R"][:, :N].clone()
+    rerr = ((R32 - R64).abs().amax(dim=1) / R64.abs().amax(dim=1)).cpu().tolist()
+    return {"ms_per_stage": mms, "edges_per_s": E / (mms * 1e-3), "speedup_vs_fp64": ms64 / mms,
+            "loops": out_loops, "residual_rel_err_per_component": rerr}
+
+
+def adjoint_extra(torch, s, args, stream, E):
+    """Adjoint sweep time against the forward residual it differentiates."""
+    s.t["lam"].normal_()
+    for _ in range(max(1, args.warmup)):
+        s.adjoint(2)
+    ams = timed(torch, lambda: s.adjoint(2), args.steps, stream)
+    fms = timed(torch, lambda: s.residual(2), args.steps, stream)
+    return {"ms": ams, "forward_residual_ms": fms, "ratio_to_forward": ams / fms,
+            "edges_per_s": E / (ams * 1e-3)}
+
+
+def march_extra(torch, L, s, q, args, stream, steps=50):
+    """50-step explicit march in FP64 and in FP32-mixed from the same state;
+    relative max-norm state difference per component after the march."""
+    N = s.N
+
+    def run(mixed):
+        s.load_nodes("q", q)
+        if mixed:
+            s.sync_shadow()
+        s.time_step(0.5)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(steps):
+            s.step(order=2, mixed=mixed)
+        torch.cuda.synchronize()
+        return s.t["q"][:, :N].clone(), time.perf_counter() - t
+    q64, t64 = run(False)
+    q32, t32 = run(True)
+    err = ((q32 - q64).abs().amax(dim=1) / q64.abs().amax(dim=1)).cpu().tolist()
+    ok = bool(torch.isfinite(q64).all().item())
+    return {"steps": steps, "stages_per_step": 5, "fp64_s": t64, "mixed_s": t32,
+            "mixed_state_rel_err_per_component": err, "fp64_finite": ok}
+
+
+def numbering_extra(torch, L, m, q, args, stream, ms_rcm, device):
+    """The same FP64 stage with random node numbering (no renumbering)."""
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    r = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device, renumber="random",
+                   seed=1, stream=stream)
+    for loop in range(L.NUM_LOOPS):
+        r.set_strategy(loop, 0, L.STRAT_AUTO)
+    r.time_step(0.5)
+    L.op2b_dat_copy(r.ctx, r.d["q0"], r.d["q"])
+    for _ in range(args.warmup):
+        r.stage(0.25)
+    ms = timed(torch, lambda: r.stage(0.25), args.steps, stream)
+    out = {"rcm_ms": ms_rcm, "random_ms": ms, "rcm_speedup": ms / ms_rcm,
+           "random_edges_per_s": m.num_edges / (ms * 1e-3),
+           "random_strategies": {nm: L.STRATEGY_NAMES[r.plan_stats(lp)["strategy"]] for nm, lp in
+                                 (("gg", L.LOOP_GREEN_GAUSS), ("flux2", L.LOOP_FLUX2))}}
+    r.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,32 +406,11 @@ def main():
     }
 
     if not args.no_extras:
-        # FP32-mixed stage (FP32 node data / gradients / flux arithmetic, FP64 R and update)
-        s.sync_shadow()
-
-        def mixed_stage():
-            s.stage(0.25, 2, mixed=True)
-        for _ in range(args.warmup):
-            mixed_stage()
-        mms = timed(torch, mixed_stage, args.steps, stream)
-        s.sync_shadow()
-        # residual error of the mixed path against the FP64 path on the same state
-        s.residual(2)
-        R64 = s.t["R"][:, :N].clone()
-        s.residual(2, mixed=True)
-        R32 = s.t["R"][:, :N].clone()
-        rerr = ((R32 - R64).abs().amax(dim=1) / R64.abs().amax(dim=1)).cpu().tolist()
-        line["mixed"] = {"ms_per_stage": mms, "edges_per_s": E / (mms * 1e-3),
-                         "speedup_vs_fp64": ms / mms,
-                         "residual_rel_err_per_component": rerr}
-        # adjoint sweep (Green-Gauss + flux adjoint + scaling adjoint + GG adjoint)
-        s.t["lam"].normal_()
-        for _ in range(max(1, args.warmup)):
-            s.adjoint(2)
-        ams = timed(torch, lambda: s.adjoint(2), args.steps, stream)
-        fms = timed(torch, lambda: s.residual(2), args.steps, stream)
-        line["adjoint"] = {"ms": ams, "forward_residual_ms": fms, "ratio_to_forward": ams / fms,
-                           "edges_per_s": E / (ams * 1e-3)}
+        line["mixed"] = mixed_extra(torch, L, s, args, stream, ms, E, N)
+        line["adjoint"] = adjoint_extra(torch, s, args, stream, E)
+        line["march"] = march_extra(torch, L, s, q, args, stream)
+        if args.numbering == "rcm":
+            line["numbering"] = numbering_extra(torch, L, m, q, args, stream, ms, local)
 
     # end to end through host buffers: pinned q in, the new q out, per step
     q_host = torch.empty((6, N), dtype=torch.float64).pin_memory()

@@ -97,6 +97,12 @@ typedef struct {
 #define OP2B_STRAT_COLOUR 2    /* coloured edge blocks, shared-memory sums */
 #define OP2B_STRAT_SEGMENTED 3 /* per-edge results, then per-node sums over
                                   the node-sorted edge ends */
+#define OP2B_STRAT_AUTO_DET 4  /* autotune among the deterministic strategies
+                                  only (colour, segmented): their sums run in
+                                  a fixed order, so results are bitwise
+                                  reproducible from run to run, which
+                                  finite-difference uses of the loops need;
+                                  the atomic strategy's order is not fixed */
 
 /* loop flags */
 #define OP2B_ZERO_INC 1 /* zero the INC targets first (they receive the sum) */
@@ -166,6 +172,16 @@ int op2b_fetch_map(op2b_ctx ctx, op2b_map map, int32_t* host_out);
 int op2b_renumber(op2b_ctx ctx, op2b_map edge2node, int32_t method,
                   uint64_t seed, int32_t* node_perm_out,
                   int64_t* edge_order_out);
+
+/* Partition-order renumbering by recursive coordinate bisection (Sec. 4:
+ * the paper's RCB partitioner, used here as a node ordering): coords is an
+ * F64 dim-3 dat on the map's to-set; sets of more than `leaf` nodes are
+ * split at the median of their longest coordinate extent (ties: lowest
+ * axis; nodes ordered by (coordinate, id)), lower half first; a leaf keeps
+ * id order.  Applied to the dats and maps exactly like op2b_renumber. */
+int op2b_renumber_rcb(op2b_ctx ctx, op2b_map edge2node, op2b_dat coords,
+                      int32_t leaf, int32_t* node_perm_out,
+                      int64_t* edge_order_out);
 
 /* ----------------------------------------------------------- edge loops
  * Sec. 3.1, Fig. "OP2loop": a loop over the edge set that reads node data
@@ -247,7 +263,7 @@ int op2b_dat_copy(op2b_ctx ctx, op2b_dat dst, op2b_dat src);
  * once per loop and reused; block sizes were autotuned into a lookup table
  * (Sec. 4.1.2).  Here the tuner also picks the race-resolution strategy. */
 
-/* Fix the strategy of (loop, prec).  block: threads per CTA (32..1024,
+/* Fix the strategy of (loop, prec) (OP2B_STRAT_*).  block: threads per CTA (32..1024,
  * 0 = default); part: edges per block for OP2B_STRAT_COLOUR (64..8192,
  * 0 = default); staged: stage each block's node data in shared memory
  * (COLOUR only).  OP2B_STRAT_AUTO makes the next call of the loop time the
@@ -318,6 +334,10 @@ int op2b_host_renumber(int64_t N, int64_t E, const int32_t* edge,
 int op2b_host_colour_blocks(int64_t N, int64_t E, const int32_t* edge,
                             int32_t part, int32_t* block_colour,
                             int64_t* ncolours);
+/* Recursive coordinate bisection order (as op2b_renumber_rcb) from host
+ * coordinates xyz (N x 3, node-major). */
+int op2b_host_rcb(int64_t N, const double* xyz, int32_t leaf,
+                  int32_t* new_of_old);
 /* Node-sorted edge ends: rowptr (N+1) and ends (2E, value 2e + side). */
 int op2b_host_node_csr(int64_t N, int64_t E, const int32_t* edge,
                        int64_t* rowptr, int64_t* ends);

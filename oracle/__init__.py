@@ -17,7 +17,7 @@ import threading
 
 import numpy as np
 
-from .renumber import rcm_order, bandwidth  # noqa: F401
+from .renumber import rcm_order, rcb_order, bandwidth  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")

@@ -64,6 +64,41 @@ def rcm_order(num_nodes: int, edge: np.ndarray) -> np.ndarray:
     return new_of_old
 
 
+def rcb_order(xyz: np.ndarray, leaf: int = 1) -> np.ndarray:
+    """new_of_old under recursive coordinate bisection.
+
+    The partitioner of Sec. 4 of the paper, used as an ordering: a set of
+    more than `leaf` nodes is split along the axis of its largest coordinate
+    extent (ties: the lowest axis) into the lower half (the first |set|//2
+    nodes in (coordinate, id) order) and the rest; the lower half is
+    numbered first; a leaf numbers its nodes in id order.
+    """
+    xyz = np.asarray(xyz, dtype=np.float64)
+    new_of_old = np.empty(xyz.shape[0], dtype=np.int64)
+    counter = [0]
+
+    def visit(ids):
+        if len(ids) <= leaf:
+            for v in sorted(ids):
+                new_of_old[v] = counter[0]
+                counter[0] += 1
+            return
+        ext = [max(xyz[v, d] for v in ids) - min(xyz[v, d] for v in ids) for d in range(3)]
+        ax = 0
+        for d in (1, 2):
+            if ext[d] > ext[ax]:
+                ax = d
+        ordered = sorted(ids, key=lambda v: (xyz[v, ax], v))
+        half = len(ids) // 2
+        visit(ordered[:half])
+        visit(ordered[half:])
+
+    import sys
+    sys.setrecursionlimit(max(10000, sys.getrecursionlimit()))
+    visit(list(range(xyz.shape[0])))
+    return new_of_old
+
+
 def edge_order(edge: np.ndarray, new_of_old: np.ndarray) -> np.ndarray:
     """Old edge index of each new edge position after relabelling."""
     e = new_of_old[np.asarray(edge, dtype=np.int64)]

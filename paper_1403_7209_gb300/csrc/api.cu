@@ -345,24 +345,20 @@ static int permute_dat(Ctx& c, DatRec& d, const int64_t* idx_dev, int64_t n) {
   return OP2B_OK;
 }
 
-extern "C" int op2b_renumber(op2b_ctx h, op2b_map mid, int32_t method, uint64_t seed,
-                             int32_t* node_perm_out, int64_t* edge_order_out) {
-  CTX_CHECK(h);
-  Ctx& c = h->c;
-  if (!valid_map(c, mid) || c.maps[mid].arity != 2)
-    return c.fail(OP2B_EINVAL, "renumber: needs an arity-2 map");
+// Apply a node permutation (new id of each old node) and the matching edge
+// order to the maps and to every dat on the two sets of map `mid`.
+static int apply_renumbering(Ctx& c, op2b_map mid, const std::vector<int32_t>& nperm,
+                             const std::vector<int64_t>& order) {
   MapRec& m = c.maps[mid];
   const op2b_set eset = m.from, nset = m.to;
   const int64_t N = c.sets[nset].size, E = c.sets[eset].size;
-  std::vector<int32_t> nperm(N);
-  std::vector<int64_t> order(E);
-  int rc = op2b_host_renumber(N, E, m.host.data(), method, seed, nperm.data(), order.data());
-  if (rc) return c.fail(rc, "renumber: bad method or map");
   std::vector<int64_t> old_of_new(N), new_edge(E);
   for (int64_t i = 0; i < N; i++) old_of_new[nperm[i]] = i;
   for (int64_t t = 0; t < E; t++) new_edge[order[t]] = t;
+  int rc = OP2B_OK;
   // maps: reorder rows of maps from a renumbered set, relabel entries into one
   for (auto& mm : c.maps) {
+    if (!(mm.from == eset || mm.from == nset || mm.to == nset || mm.to == eset)) continue;
     std::vector<int32_t> nh(mm.host.size());
     int64_t F = c.sets[mm.from].size;
     for (int64_t r = 0; r < F; r++) {
@@ -376,11 +372,9 @@ extern "C" int op2b_renumber(op2b_ctx h, op2b_map mid, int32_t method, uint64_t 
         nh[(size_t)r * mm.arity + k] = (int32_t)v;
       }
     }
-    if (mm.from == eset || mm.from == nset || mm.to == nset || mm.to == eset) {
-      mm.host.swap(nh);
-      mm.version++;
-      if ((rc = upload_map(c, mm))) return rc;
-    }
+    mm.host.swap(nh);
+    mm.version++;
+    if ((rc = upload_map(c, mm))) return rc;
   }
   // dats on the two sets, through the scratch buffer
   int64_t* idx = nullptr;
@@ -400,6 +394,53 @@ extern "C" int op2b_renumber(op2b_ctx h, op2b_map mid, int32_t method, uint64_t 
   }
   cudaStreamSynchronize(c.stream);
   cudaFree(idx);
+  return rc;
+}
+
+extern "C" int op2b_renumber(op2b_ctx h, op2b_map mid, int32_t method, uint64_t seed,
+                             int32_t* node_perm_out, int64_t* edge_order_out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_map(c, mid) || c.maps[mid].arity != 2)
+    return c.fail(OP2B_EINVAL, "renumber: needs an arity-2 map");
+  MapRec& m = c.maps[mid];
+  const int64_t N = c.sets[m.to].size, E = c.sets[m.from].size;
+  std::vector<int32_t> nperm(N);
+  std::vector<int64_t> order(E);
+  int rc = op2b_host_renumber(N, E, m.host.data(), method, seed, nperm.data(), order.data());
+  if (rc) return c.fail(rc, "renumber: bad method or map");
+  if ((rc = apply_renumbering(c, mid, nperm, order))) return rc;
+  if (node_perm_out) std::copy(nperm.begin(), nperm.end(), node_perm_out);
+  if (edge_order_out) std::copy(order.begin(), order.end(), edge_order_out);
+  return OP2B_OK;
+}
+
+extern "C" int op2b_renumber_rcb(op2b_ctx h, op2b_map mid, op2b_dat coords, int32_t leaf,
+                                 int32_t* node_perm_out, int64_t* edge_order_out) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_map(c, mid) || c.maps[mid].arity != 2)
+    return c.fail(OP2B_EINVAL, "renumber_rcb: needs an arity-2 map");
+  if (leaf < 1) return c.fail(OP2B_EINVAL, "renumber_rcb: leaf must be >= 1");
+  MapRec& m = c.maps[mid];
+  if (!valid_dat(c, coords)) return c.fail(OP2B_EINVAL, "renumber_rcb: bad coordinate dat");
+  const DatRec& x = c.dats[coords];
+  if (x.set != m.to) return c.fail(OP2B_ESET, "renumber_rcb: coordinates must live on the nodes");
+  if (x.dim != 3) return c.fail(OP2B_EDIM, "renumber_rcb: coordinates need dim 3");
+  if (x.type != OP2B_F64) return c.fail(OP2B_ETYPE, "renumber_rcb: coordinates must be F64");
+  const int64_t N = c.sets[m.to].size, E = c.sets[m.from].size;
+  std::vector<double> soa((size_t)3 * x.ld), xyz((size_t)3 * N);
+  cudaStreamSynchronize(c.stream);
+  if (N > 0 && cudaMemcpy(soa.data(), x.ptr, soa.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return c.fail(OP2B_ECUDA, "renumber_rcb: coordinate copy failed");
+  for (int64_t i = 0; i < N; i++)
+    for (int d = 0; d < 3; d++) xyz[3 * i + d] = soa[(size_t)d * x.ld + i];
+  std::vector<int32_t> nperm(N);
+  std::vector<int64_t> order(E);
+  if (!op2b::rcb(N, xyz.data(), leaf, nperm.data()))
+    return c.fail(OP2B_EINVAL, "renumber_rcb: bad input");
+  op2b::edge_order(N, E, m.host.data(), nperm.data(), order.data());
+  int rc = apply_renumbering(c, mid, nperm, order);
   if (rc) return rc;
   if (node_perm_out) std::copy(nperm.begin(), nperm.end(), node_perm_out);
   if (edge_order_out) std::copy(order.begin(), order.end(), edge_order_out);
@@ -481,9 +522,9 @@ int check_args(Ctx& c, const char* loop, const op2b_arg* a, int nargs, const Spe
 
 const DatRec& D(Ctx& c, const op2b_arg& a) { return c.dats[a.dat]; }
 
-std::string tune_key(const LoopLaunch& L) {
+std::string tune_key(const LoopLaunch& L, bool det) {
   return std::string(kLoopName[L.loop]) + ":p" + std::to_string(L.prec) + ":N" + std::to_string(L.N) +
-         ":E" + std::to_string(L.E);
+         ":E" + std::to_string(L.E) + (det ? ":det" : "");
 }
 
 int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
@@ -504,9 +545,10 @@ int wait_deadline(Ctx& c, cudaEvent_t ev, double ms) {
   }
 }
 
-std::vector<Strategy> candidates(const LoopLaunch& L) {
+std::vector<Strategy> candidates(const LoopLaunch& L, bool det) {
   std::vector<Strategy> v;
   for (int b : {128, 256, 512}) {
+    if (det) break;
     Strategy s;
     s.strategy = OP2B_STRAT_ATOMIC;
     s.block = b;
@@ -531,7 +573,8 @@ std::vector<Strategy> candidates(const LoopLaunch& L) {
 }
 
 // Time every candidate on scratch copies of the outputs; keep the fastest.
-int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, Strategy* best) {
+int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, bool det,
+             Strategy* best) {
   LoopLaunch T = L;
   void *t0 = nullptr, *t1 = nullptr, *td = nullptr;
   auto alloc = [&](size_t b, void** p) {
@@ -557,9 +600,12 @@ int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, Strat
   cudaEventCreate(&e1);
   double best_ms = 1e300;
   int rc = OP2B_OK, found = 0;
-  for (const Strategy& s : candidates(L)) {
+  for (const Strategy& s : candidates(L, det)) {
     int r = dispatch(c, T, s);  // warm-up (also builds the plan)
-    if (r == OP2B_ERANGE) continue;  // does not fit (shared memory)
+    // skip candidates that cannot run here: a block too large for shared
+    // memory or registers (ERANGE), or a colouring that needs too many
+    // colours (EPLAN, e.g. under a random numbering)
+    if (r == OP2B_ERANGE || r == OP2B_EPLAN) continue;
     if (r) {
       rc = r;
       break;
@@ -613,16 +659,17 @@ int run_loop(Ctx& c, LoopLaunch& L, int flags, const DatRec* z0, const DatRec* z
     if (z1 && (rc = node_fill(&c, z1->ptr, z1->type, z1->ld, z1->dim, L.N, 0.0))) return rc;
   }
   Strategy& s = c.strat[L.loop][L.prec];
-  if (s.strategy == OP2B_STRAT_AUTO) {
-    auto it = c.tuned.find(tune_key(L));
+  if (s.strategy == OP2B_STRAT_AUTO || s.strategy == OP2B_STRAT_AUTO_DET) {
+    const bool det = s.strategy == OP2B_STRAT_AUTO_DET;
+    auto it = c.tuned.find(tune_key(L, det));
     Strategy best;
     if (it != c.tuned.end()) {
       best = it->second;
     } else {
       int rc = autotune(c, L, z0 ? dat_bytes(c, *z0) : 0, z1 ? dat_bytes(c, *z1) : 0,
-                        direct ? dat_bytes(c, *direct) : 0, &best);
+                        direct ? dat_bytes(c, *direct) : 0, det, &best);
       if (rc) return rc;
-      c.tuned[tune_key(L)] = best;
+      c.tuned[tune_key(L, det)] = best;
     }
     s = best;
   }
@@ -910,7 +957,7 @@ extern "C" int op2b_set_strategy(op2b_ctx h, int32_t loop, int32_t prec, int32_t
   Ctx& c = h->c;
   if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec != 0 && prec != 1))
     return c.fail(OP2B_EINVAL, "set_strategy: bad loop or precision");
-  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_SEGMENTED)
+  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_AUTO_DET)
     return c.fail(OP2B_EINVAL, "set_strategy: bad strategy");
   if (block != 0 && (block < 32 || block > 1024 || block % 32))
     return c.fail(OP2B_EINVAL, "set_strategy: block must be a multiple of 32 in [32, 1024]");
@@ -1037,6 +1084,11 @@ extern "C" int op2b_host_colour_blocks(int64_t N, int64_t E, const int32_t* edge
   std::copy(p.colour.begin(), p.colour.end(), block_colour);
   *ncolours = p.ncolours;
   return OP2B_OK;
+}
+
+extern "C" int op2b_host_rcb(int64_t N, const double* xyz, int32_t leaf, int32_t* new_of_old) {
+  if (N < 0 || leaf < 1 || (N > 0 && (!xyz || !new_of_old))) return OP2B_EINVAL;
+  return op2b::rcb(N, xyz, leaf, new_of_old) ? OP2B_OK : OP2B_EINVAL;
 }
 
 extern "C" int op2b_host_node_csr(int64_t N, int64_t E, const int32_t* edge, int64_t* rowptr, int64_t* ends) {

@@ -79,8 +79,8 @@ struct BodyGG {
   template <class Get>
   __device__ __forceinline__ static void unpack_add(Get get, bool second,
                                                     TA* acc) {
-    const T h[3] = {second ? -get(6) : get(6), second ? -get(7) : get(7),
-                    second ? -get(8) : get(8)};
+    const T h[3] = {second ? neg(get(6)) : get(6), second ? neg(get(7)) : get(7),
+                    second ? neg(get(8)) : get(8)};
 #pragma unroll
     for (int k = 0; k < 6; k++) {
       const T s = get(k);
@@ -299,11 +299,11 @@ __global__ void k_atomic(P ph, const int32_t* __restrict__ m0,
     ph.edge(e, vi, vj, oi, oj);
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) {
-      TA a = (TA)oi[c];
+      TA a = to_acc<TA>(oi[c]);
       atomicAdd(tg.at(c, i), a);
-      if constexpr (P::MODE == MODE_ANTI) atomicAdd(tg.at(c, j), -a);
+      if constexpr (P::MODE == MODE_ANTI) atomicAdd(tg.at(c, j), neg(a));
       if constexpr (P::MODE == MODE_SYM) atomicAdd(tg.at(c, j), a);
-      if constexpr (P::MODE == MODE_GEN) atomicAdd(tg.at(c, j), (TA)oj[c]);
+      if constexpr (P::MODE == MODE_GEN) atomicAdd(tg.at(c, j), to_acc<TA>(oj[c]));
     }
   }
 }
@@ -435,12 +435,12 @@ __global__ void k_colour(P ph, const int32_t* __restrict__ m0,
         } else if constexpr (P::MODE == MODE_GEN) {
           const int base = second ? P::OUT : 0;
 #pragma unroll
-          for (int c = 0; c < P::OUT; c++) acc[c] += (TA)sOut[(base + c) * part + el];
+          for (int c = 0; c < P::OUT; c++) acc[c] += to_acc<TA>(sOut[(base + c) * part + el]);
         } else {
 #pragma unroll
           for (int c = 0; c < P::OUT; c++) {
-            TA v = (TA)sOut[c * part + el];
-            if constexpr (P::MODE == MODE_ANTI) acc[c] += second ? -v : v;
+            TA v = to_acc<TA>(sOut[c * part + el]);
+            if constexpr (P::MODE == MODE_ANTI) acc[c] += second ? neg(v) : v;
             else acc[c] += v;
           }
         }
@@ -538,12 +538,12 @@ __global__ void k_seg_nodes(const int64_t* __restrict__ rowptr,
       if constexpr (MODE == MODE_GEN) {
         const int base = second ? OUT : 0;
 #pragma unroll
-        for (int c = 0; c < OUT; c++) acc[c] += (TA)ebuf[(base + c) * E + e];
+        for (int c = 0; c < OUT; c++) acc[c] += to_acc<TA>(ebuf[(base + c) * E + e]);
       } else {
 #pragma unroll
         for (int c = 0; c < OUT; c++) {
-          TA v = (TA)ebuf[c * E + e];
-          if constexpr (MODE == MODE_ANTI) acc[c] += second ? -v : v;
+          TA v = to_acc<TA>(ebuf[c * E + e]);
+          if constexpr (MODE == MODE_ANTI) acc[c] += second ? neg(v) : v;
           else acc[c] += v;
         }
       }

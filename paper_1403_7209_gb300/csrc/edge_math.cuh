@@ -19,6 +19,32 @@ __device__ __forceinline__ T ldro(const T* p) {
   return __ldg(p);
 }
 
+// -x by flipping the sign bit on the integer pipe (an FP64 negation that is
+// not folded into another instruction would cost an FP64-pipe add)
+__device__ __forceinline__ double neg(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ float neg(float x) {
+  return __int_as_float(__float_as_int(x) ^ (int)0x80000000);
+}
+
+// Exact float -> double on the integer pipe (the conversion instruction runs
+// at the FP64 rate): re-bias the exponent and move the mantissa; zero,
+// subnormal, infinite and NaN inputs take the conversion instruction.
+__device__ __forceinline__ double f64_exact(float f) {
+  const int b = __float_as_int(f);
+  const int e = b & 0x7f800000;
+  if (e == 0 || e == 0x7f800000) return (double)f;
+  return __hiloint2double((b & (int)0x80000000) | (((b & 0x7fffffff) >> 3) + 0x38000000), b << 29);
+}
+
+// value of a per-edge result in the accumulation type of its target
+template <typename TA, typename TE>
+__device__ __forceinline__ TA to_acc(TE x) {
+  if constexpr (sizeof(TA) == 8 && sizeof(TE) == 4) return f64_exact(x);
+  else return (TA)x;
+}
+
 // Euler flux through the face of normal n, and the state's largest wave
 // speed |u.n| + a|n| (a = sqrt(gamma p / rho); nn2 = |n|^2).
 template <typename T>
@@ -83,14 +109,74 @@ __device__ __forceinline__ void reconstruct(const T* vi, const T* vj, T dx,
 // division or square root costs about ten FMA slots, so the FP64 flux is
 // bound by its FP64 instruction count.  This version computes the same
 // formulas as reconstruct() + rusanov() with fewer FP64 instructions:
-//  * the 12 limiter denominators are inverted together (one reciprocal and
-//    three multiplies each: prefix products, Montgomery's batch inversion),
-//    and so are the two face densities;
+//  * the 12 limiter denominators are inverted together (prefix products,
+//    one reciprocal, back-substitution: Montgomery's batch inversion), and so
+//    are the two face densities; that one reciprocal and the square roots
+//    start from FP32 seeds refined by two Newton steps in FP64 (recip2,
+//    sqrt2 below), so every value keeps full double precision and the
+//    residual stays smooth at rounding level (finite differences of it are
+//    meaningful down to h ~ 1e-7);
 //  * the factors 1/2 are folded into those reciprocals;
 //  * the larger of the two wave speeds is chosen by an integer comparison
 //    of their bit patterns (both are >= 0, so the order is the same).
 // Batching is used only when every denominator lies in [2^-70, 2^70], so no
 // prefix product can overflow or underflow; otherwise each is divided.
+
+// FP32-seeded Newton-Raphson reciprocal and square root for the FP64 pipe.
+// The seed comes from the FP32 special-function unit (rcp.approx /
+// rsqrt.approx, about 2^-22 relative error including the truncation of the
+// argument); the conversions between double and float are done with
+// integer operations on the bit patterns, so no FP64-pipe instruction is
+// spent on them.  Each Newton step in FP64 squares the relative error
+// (about 2^-44 after one), so two steps reach full double precision.  Valid for positive
+// arguments whose FP32 image is a normal number with a normal reciprocal
+// (exponent field of the double in [898, 1149]); callers check seedable().
+__device__ __forceinline__ bool seedable(double x) {
+  const unsigned e = ((unsigned)__double2hiint(x) >> 20);  // sign bit must be 0
+  return e - 898u <= 251u;
+}
+__device__ __forceinline__ float f32_of_f64(double x) {  // truncating, x > 0
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  return __int_as_float(((hi - 0x38000000) << 3) | (int)(lo >> 29));
+}
+__device__ __forceinline__ double f64_of_f32(float f) {  // exact, f > 0 normal
+  const int b = __float_as_int(f);
+  return __hiloint2double((b >> 3) + 0x38000000, b << 29);
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// 1 / d with two Newton steps (full precision)
+__device__ __forceinline__ double recip2(double d) {
+  const double y0 = f64_of_f32(rcp_approx(f32_of_f64(d)));
+  const double y1 = fma(y0, fma(-d, y0, 1.0), y0);
+  return fma(y1, fma(-d, y1, 1.0), y1);
+}
+// sqrt(x) with two Newton steps (full precision)
+__device__ __forceinline__ double sqrt2(double x) {
+  const float r = rsqrt_approx(f32_of_f64(x));
+  const double r0 = f64_of_f32(r);
+  const double r1 = fma(f64_of_f32(0.5f * r), fma(-x * r0, r0, 1.0), r0);
+  const double t = x * r1;
+  const double hh = fma(-t, 0.5 * r1, 0.5);  // (1 - x r1^2) / 2
+  return fma(t, hh, t);
+}
+
+// 1/sqrt(x) with two Newton steps (full precision)
+__device__ __forceinline__ double rsqrt2(double x) {
+  const float r = rsqrt_approx(f32_of_f64(x));
+  const double r0 = f64_of_f32(r);
+  const double r1 = fma(f64_of_f32(0.5f * r), fma(-x * r0, r0, 1.0), r0);
+  return fma(0.5 * r1, fma(-x * r1, r1, 1.0), r1);
+}
 
 __device__ __forceinline__ bool exp_in_range(double x, int lim) {
   // |x| in [2^-lim, 2^lim] (x finite, nonzero)
@@ -110,7 +196,8 @@ __device__ __forceinline__ void batch_reciprocal(const double* d, double scale,
     p[0] = d[0];
 #pragma unroll
     for (int k = 1; k < K; k++) p[k] = p[k - 1] * d[k];
-    double inv = scale / p[K - 1];
+    const double pk = p[K - 1];
+    double inv = scale * (seedable(pk) ? recip2(pk) : 1.0 / pk);
 #pragma unroll
     for (int k = K - 1; k > 0; k--) {
       r[k] = inv * p[k - 1];
@@ -162,11 +249,13 @@ __device__ __forceinline__ void flux2_f64(const double* vi, const double* vj,
 #pragma unroll
   for (int sd = 0; sd < 2; sd++) {
     const double* q = sd ? qR : qL;
-    const double un = fma(q[3], nz, fma(q[2], ny, q[1] * nx)) * rr[sd];
+    const double mn = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
+    const double un = mn * rr[sd];
     const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
     const double p = fma(-hgm1 * mm, rr[sd], g.gm1 * q[4]);
-    lam[sd] = fabs(un) + sqrt(p * rr[sd] * gnn);
-    f[sd][0] = q[0] * un;
+    const double x = p * rr[sd] * gnn;
+    lam[sd] = fabs(un) + (seedable(x) ? sqrt2(x) : sqrt(x));
+    f[sd][0] = mn;  // rho u.n
     f[sd][1] = fma(q[1], un, p * nx);
     f[sd][2] = fma(q[2], un, p * ny);
     f[sd][3] = fma(q[3], un, p * nz);
@@ -269,8 +358,8 @@ __device__ __forceinline__ void van_albada_d(double a, double b, double eps,
 
 // ------------------------------------------ FP64 adjoint, fewer FP64 ops
 // The same reverse sweep as rusanov_reverse() / van_albada_d(), arranged for
-// the FP64 pipe: reciprocals batched as in flux2_f64(), one reciprocal
-// square root giving both a and 1/a (and |n|, 1/|n|), no forward fluxes
+// the FP64 pipe: batched reciprocals as in flux2_f64(), one
+// reciprocal square root giving both a and 1/a (and |n|, 1/|n|), no forward fluxes
 // (the reverse sweep needs only the wave speeds and the primitive
 // quantities), and sign / max taken from the bit patterns.
 
@@ -294,7 +383,7 @@ __device__ __forceinline__ double side_state(const double* q, double nx,
   s.mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
   s.p = fma(-hgm1 * s.mm, rr, g.gm1 * q[4]);
   const double a2 = g.gamma * s.p * rr;
-  s.ra = rsqrt(a2);
+  s.ra = seedable(a2) ? rsqrt2(a2) : rsqrt(a2);
   s.a = a2 * s.ra;
   return fabs(s.un) + s.a * nn;  // wave speed
 }
@@ -336,7 +425,7 @@ __device__ __forceinline__ void rusanov_reverse_f64(
     const Gas<double>& g, const double* w, double* qLb, double* qRb,
     double* nb) {
   const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
-  const double rn = rsqrt(nn2);
+  const double rn = seedable(nn2) ? rsqrt2(nn2) : rsqrt(nn2);
   const double nn = nn2 * rn;
   double rho[2] = {qL[0], qR[0]}, rr[2];
   batch_reciprocal<2>(rho, 1.0, rr);

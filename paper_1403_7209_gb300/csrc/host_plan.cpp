@@ -100,6 +100,44 @@ bool rcm(int64_t N, int64_t E, const int32_t* edge, int32_t* new_of_old) {
   return true;
 }
 
+bool rcb(int64_t N, const double* xyz, int32_t leaf, int32_t* new_of_old) {
+  if (N < 0 || leaf < 1) return false;
+  std::vector<int32_t> ids(N);
+  for (int64_t i = 0; i < N; i++) ids[i] = (int32_t)i;
+  int64_t next = 0;
+  // explicit stack of [lo, hi) ranges; the lower half is processed first
+  std::vector<std::pair<int64_t, int64_t>> st;
+  st.push_back({0, N});
+  while (!st.empty()) {
+    auto [lo, hi] = st.back();
+    st.pop_back();
+    if (hi - lo <= leaf) {
+      std::sort(ids.begin() + lo, ids.begin() + hi);
+      for (int64_t k = lo; k < hi; k++) new_of_old[ids[k]] = (int32_t)(next++);
+      continue;
+    }
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int64_t k = lo; k < hi; k++)
+      for (int d = 0; d < 3; d++) {
+        double v = xyz[3 * (int64_t)ids[k] + d];
+        mn[d] = std::min(mn[d], v);
+        mx[d] = std::max(mx[d], v);
+      }
+    int ax = 0;
+    for (int d = 1; d < 3; d++)
+      if (mx[d] - mn[d] > mx[ax] - mn[ax]) ax = d;
+    const int64_t mid = lo + (hi - lo) / 2;
+    std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi,
+                     [&](int32_t a, int32_t b) {
+                       double ca = xyz[3 * (int64_t)a + ax], cb = xyz[3 * (int64_t)b + ax];
+                       return ca < cb || (ca == cb && a < b);
+                     });
+    st.push_back({mid, hi});
+    st.push_back({lo, mid});
+  }
+  return true;
+}
+
 static inline uint64_t splitmix_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

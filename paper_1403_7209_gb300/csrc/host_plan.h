@@ -18,6 +18,12 @@ bool rcm(int64_t N, int64_t E, const int32_t* edge, int32_t* new_of_old);
 // Flood 2014): node k gets the rank of key(seed, k) (ties by k).
 void random_perm(int64_t N, uint64_t seed, int32_t* new_of_old);
 
+// Recursive coordinate bisection order: a set of more than `leaf` nodes is
+// split at its median along the axis of largest extent (ties: lowest axis),
+// nodes ordered by (coordinate, id) with the lower half first; a leaf lists
+// its nodes by id.  new_of_old[node] = position in that order.
+bool rcb(int64_t N, const double* xyz, int32_t leaf, int32_t* new_of_old);
+
 // Old edge index of each new edge once the ends are relabelled: ordered by
 // (min end, max end), ties in input order (two stable counting sorts).
 void edge_order(int64_t N, int64_t E, const int32_t* edge,

@@ -25,10 +25,11 @@ ID = -1
 LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
 LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ, NUM_LOOPS = 4, 5, 6, 7
 PREC_F64, PREC_F32 = 0, 1
-STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED = 0, 1, 2, 3
+STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
 ZERO_INC = 1
 STRATEGY_NAMES = {STRAT_AUTO: "auto", STRAT_ATOMIC: "atomic",
-                  STRAT_COLOUR: "colour", STRAT_SEGMENTED: "segmented"}
+                  STRAT_COLOUR: "colour", STRAT_SEGMENTED: "segmented",
+                  STRAT_AUTO_DET: "auto-deterministic"}
 ERROR_NAMES = {EINVAL: "EINVAL", EDIM: "EDIM", ETYPE: "ETYPE",
                EACCESS: "EACCESS", ESET: "ESET", ENOMEM: "ENOMEM",
                ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EPLAN: "EPLAN",
@@ -88,6 +89,7 @@ _SIGS = {
     "op2b_rebind_dat": (ctypes.c_int, [_P, _I32, _P]),
     "op2b_fetch_map": (ctypes.c_int, [_P, _I32, _PI32]),
     "op2b_renumber": (ctypes.c_int, [_P, _I32, _I32, _U64, _PI32, _PI64]),
+    "op2b_renumber_rcb": (ctypes.c_int, [_P, _I32, _I32, _I32, _PI32, _PI64]),
     "op2b_green_gauss": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
     "op2b_edge_flux": (ctypes.c_int, [_P, _PARG, _I32,
                                       ctypes.POINTER(FluxParams)]),
@@ -118,6 +120,7 @@ _SIGS = {
     "op2b_host_colour_blocks": (ctypes.c_int, [_I64, _I64, _PI32, _I32,
                                                _PI32, _PI64]),
     "op2b_host_node_csr": (ctypes.c_int, [_I64, _I64, _PI32, _PI64, _PI64]),
+    "op2b_host_rcb": (ctypes.c_int, [_I64, ctypes.POINTER(ctypes.c_double), _I32, _PI32]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -233,6 +236,15 @@ def op2b_renumber(ctx, map_: int, method: int, seed: int, num_nodes: int,
     perm = np.empty(num_nodes, dtype=np.int32)
     order = np.empty(num_edges, dtype=np.int64)
     _check(load().op2b_renumber(ctx, map_, method, seed, _i32p(perm), _i64p(order)), ctx)
+    return perm, order
+
+
+def op2b_renumber_rcb(ctx, map_: int, coords_dat: int, leaf: int, num_nodes: int,
+                      num_edges: int):
+    perm = np.empty(num_nodes, dtype=np.int32)
+    order = np.empty(num_edges, dtype=np.int64)
+    _check(load().op2b_renumber_rcb(ctx, map_, coords_dat, leaf, _i32p(perm), _i64p(order)),
+           ctx)
     return perm, order
 
 
@@ -355,6 +367,14 @@ def op2b_host_colour_blocks(num_nodes: int, edge, part: int):
     _check(load().op2b_host_colour_blocks(num_nodes, edge.shape[0], _i32p(edge), part,
                                           _i32p(col), ctypes.byref(nc)))
     return col[:nb], nc.value
+
+
+def op2b_host_rcb(xyz, leaf: int = 1) -> np.ndarray:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    out = np.empty(xyz.shape[0], dtype=np.int32)
+    _check(load().op2b_host_rcb(xyz.shape[0], xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                leaf, _i32p(out)))
+    return out
 
 
 def op2b_host_node_csr(num_nodes: int, edge):

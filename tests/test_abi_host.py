@@ -103,3 +103,22 @@ def test_host_planners_reject_bad_input(lib):
         op2b.op2b_host_renumber(3, np.array([[0, 1]]), method=9)
     with pytest.raises(op2b.Op2bError):
         op2b.op2b_host_colour_blocks(3, np.array([[0, 1]]), part=0)
+
+
+@pytest.mark.parametrize("leaf", [1, 4, 64])
+def test_library_rcb_equals_oracle_rcb(lib, leaf):
+    m = meshgen.lattice(7, seed=2)
+    a = op2b.op2b_host_rcb(m.coords, leaf)
+    b = oracle.rcb_order(m.coords, leaf)
+    assert np.array_equal(a, b)
+    assert np.array_equal(np.sort(a), np.arange(m.num_nodes))
+
+
+def test_rcb_partition_order_is_spatially_local(lib):
+    # leaves of the bisection are compact boxes: consecutive new ids stay close
+    m = meshgen.lattice(12)
+    new = op2b.op2b_host_rcb(m.coords, 1)
+    order = np.argsort(new)
+    steps = np.linalg.norm(np.diff(m.coords[order], axis=0), axis=1)
+    rand = np.linalg.norm(np.diff(m.coords, axis=0), axis=1)
+    assert np.median(steps) < 0.25 * np.median(rand)

@@ -1,0 +1,56 @@
+"""FP32-seeded Newton reciprocal and square root of the FP64 edge kernels,
+against correctly rounded IEEE results and their stated error bounds."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def newton(gpu_lib, tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("newton") / "newton_check.so")
+    subprocess.check_call(["nvcc", "-O3", "-std=c++17", "-gencode",
+                           "arch=compute_103a,code=sm_103a", "-Xcompiler", "-fPIC",
+                           "-shared", "-o", out,
+                           os.path.join(HERE, "gpu_helpers", "newton_check.cu")])
+    lib = ctypes.CDLL(out)
+    lib.newton_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                 ctypes.c_int]
+    return lib
+
+
+def run(lib, x, which):
+    import torch
+    xt = torch.from_numpy(x).cuda()
+    ot = torch.empty_like(xt)
+    assert lib.newton_check(xt.data_ptr(), ot.data_ptr(), xt.numel(), which) == 0
+    return ot.cpu().numpy()
+
+
+def test_newton_forms_meet_their_error_bounds(newton):
+    rng = np.random.default_rng(0)
+    # the ranges the kernels see (limiter denominators down to 2e-12,
+    # densities and pressures of order 1) plus wide log-uniform samples
+    x = np.concatenate([10.0 ** rng.uniform(-30, 30, 200000),
+                        rng.uniform(2e-12, 1e-6, 50000), rng.uniform(0.5, 2.0, 50000)])
+    rel = lambda a, b: np.abs(a - b) / np.abs(b)
+    assert np.all(run(newton, x, 5) == 1.0)  # all seedable
+    # two Newton steps: within 2 ulp of the correctly rounded value
+    assert np.max(rel(run(newton, x, 0), 1.0 / x)) <= 2.0 ** -51
+    assert np.max(rel(run(newton, x, 1), np.sqrt(x))) <= 2.0 ** -51
+    assert np.max(rel(run(newton, x, 2), 1.0 / np.sqrt(x))) <= 2.0 ** -51
+    # batched inversion (inside [2^-70, 2^70]): a few ulp
+    xb = np.concatenate([rng.uniform(2e-12, 1e-6, 50000), rng.uniform(0.5, 2.0, 50000)])
+    assert np.max(rel(run(newton, xb, 3), 0.5 / xb)) <= 2.0 ** -49
+
+
+def test_seedable_range(newton):
+    x = np.array([0.0, -1.0, 1e-300, 1e300, 2.0 ** -126, 2.0 ** 126, 1.0, 3e-38,
+                  np.inf, np.nan])
+    s = run(newton, x, 5)
+    assert s.tolist() == [0, 0, 0, 0, 0, 1, 1, 1, 0, 0]

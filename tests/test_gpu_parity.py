@@ -188,10 +188,15 @@ def test_mixed_precision_march(gpu_lib):
     s.close()
 
 
-def _adj_err(gpu, ref):
-    # per entry, relative to its own size plus the component's median size
+def _adj_ok(gpu, ref):
+    """Adjoint bar: normwise per component (max |diff| / max |ref|) <= 1e-12,
+    and per entry relative to its own size plus the component's median
+    <= 1e-11 (the oracle's own result moves by ~2e-12 in that measure when
+    only its summation order changes)."""
+    nw = np.max(np.abs(gpu - ref), axis=0) / np.max(np.abs(ref), axis=0)
     med = np.median(np.abs(ref), axis=0)
-    return float(np.max(np.abs(gpu - ref) / (np.abs(ref) + med)))
+    ew = np.max(np.abs(gpu - ref) / (np.abs(ref) + med))
+    return bool(np.all(nw <= TOL) and ew <= 10 * TOL)
 
 
 @pytest.mark.parametrize("order", [1, 2])
@@ -205,8 +210,8 @@ def test_adjoint_matches_oracle_reverse(gpu_lib, mesh16, order, strat):
     s.load_nodes("lam", lam)
     s.adjoint(order)
     qb, nb = oracle.residual_reverse(order, m.edge, q, m.normal, m.dx, m.volume, lam)
-    assert _adj_err(s.fetch_nodes("qbar"), qb) <= TOL
-    assert _adj_err(s.fetch_edges("nbar"), nb) <= TOL
+    assert _adj_ok(s.fetch_nodes("qbar"), qb)
+    assert _adj_ok(s.fetch_edges("nbar"), nb)
     s.close()
 
 
@@ -225,8 +230,8 @@ def test_autograd_backward_and_dot_product(gpu_lib):
     lt = torch.from_numpy(np.ascontiguousarray(lam.T)).cuda()
     (R * lt).sum().backward()
     qb, nb = oracle.residual_reverse(2, m.edge, q, m.normal, m.dx, m.volume, lam)
-    assert _adj_err(qt.grad.cpu().numpy().T, qb) <= TOL
-    assert _adj_err(nt.grad.cpu().numpy().T, nb) <= TOL
+    assert _adj_ok(qt.grad.cpu().numpy().T, qb)
+    assert _adj_ok(nt.grad.cpu().numpy().T, nb)
     # dot-product test: <lam, J v> from the oracle's tangent sweep against
     # <J^T lam, v> from the GPU reverse sweep
     qd = meshgen.adjoint_seed(m.num_nodes, stream=meshgen.STREAM_V)
@@ -260,6 +265,29 @@ def test_autotuner_picks_and_persists(gpu_lib, mesh16, ref16, tmp_path):
     assert s2.launch_count() - n0 <= 64  # table hit: no candidate timing
     s.close()
     s2.close()
+
+
+@pytest.mark.parametrize("strat", [2, 3])
+def test_deterministic_strategies_are_bitwise_reproducible(gpu_lib, mesh16, strat):
+    import torch
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber="rcm", adjoint=True)
+    for loop in range(gpu_lib.NUM_LOOPS):
+        s.set_strategy(loop, 0, strat, 128, 256, 1)
+    s.load_nodes("lam", meshgen.adjoint_seed(m.num_nodes))
+    outs = []
+    for _ in range(3):
+        s.residual(2)
+        s.adjoint(2)
+        torch.cuda.synchronize()
+        outs.append((s.t["R"].clone(), s.t["qbar"].clone(), s.t["nbar"].clone()))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert torch.equal(a, b)
+    s.set_strategy(gpu_lib.LOOP_FLUX2, 0, gpu_lib.STRAT_AUTO_DET)
+    s.residual(2)
+    assert s.plan_stats(gpu_lib.LOOP_FLUX2)["strategy"] in (2, 3)
+    s.close()
 
 
 def test_autotuner_deadline_reports_timeout(gpu_lib, mesh16):

@@ -279,7 +279,8 @@ int op2b_set_tune_deadline(op2b_ctx ctx, double ms);
  * precision and set sizes. */
 int op2b_save_tuning(op2b_ctx ctx, const char* path);
 int op2b_load_tuning(op2b_ctx ctx, const char* path);
-/* Strategy and plan statistics of (loop, prec) on `map`. */
+/* Strategy and plan statistics of (loop, prec) on `map` (block-plan fields
+ * are -1 when no colouring exists at the loop's partition size). */
 int op2b_plan_stats(op2b_ctx ctx, int32_t loop, int32_t prec, op2b_map map,
                     op2b_plan_stats_t* out);
 /* Number of kernels the context has launched so far. */

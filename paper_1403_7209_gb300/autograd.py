@@ -4,8 +4,9 @@
 state q (6, N) and the edge normals n (3, E) (library numbering, FP64 CUDA
 tensors).  Its backward pass runs the hand-written adjoint edge loops: for
 an incoming gradient lam = dL/dR it returns qbar = lam . dR/dq and
-nbar = lam . dR/dn, recomputing the edge states from q, G and n instead of
-storing them.
+nbar = lam . dR/dn.  The forward pass keeps the node gradients G (node
+data, 18 values per node); the edge states are recomputed from q, G and n
+instead of being stored.
 """
 from __future__ import annotations
 
@@ -20,23 +21,26 @@ class ResidualFn(torch.autograd.Function):
         s.rebind("n", n.detach().contiguous())
         out = torch.empty_like(s.t["R"])
         s.rebind("R", out)
+        G = torch.empty_like(s.t["G"])
+        s.rebind("G", G)
         s.residual(order)
         ctx.solver, ctx.order = s, order
-        ctx.save_for_backward(q, n)
+        ctx.save_for_backward(q, n, G)
         return out
 
     @staticmethod
     def backward(ctx, grad_r):
         s = ctx.solver
-        q, n = ctx.saved_tensors
+        q, n, G = ctx.saved_tensors
         s.rebind("q", q.detach().contiguous())
         s.rebind("n", n.detach().contiguous())
+        s.rebind("G", G)
         s.rebind("lam", grad_r.detach().double().contiguous())
         qbar = torch.empty_like(s.t["qbar"])
         nbar = torch.empty_like(s.t["nbar"])
         s.rebind("qbar", qbar)
         s.rebind("nbar", nbar)
-        s.adjoint(ctx.order)
+        s.adjoint(ctx.order, recompute_gradient=False)
         return qbar, nbar, None, None
 
 

@@ -1034,6 +1034,11 @@ extern "C" int op2b_plan_stats(op2b_ctx h, int32_t loop, int32_t prec, op2b_map 
   out->tuned_ms = s.tuned_ms;
   DevBlockPlan* bp = nullptr;
   int rc = c.block_plan(map, s.part, &bp);
+  if (rc == OP2B_EPLAN) {  // no colouring at this partition size: say so
+    out->nblocks = -1;
+    out->ncolours = -1;
+    return OP2B_OK;
+  }
   if (rc) return rc;
   out->nblocks = bp->nblocks;
   out->ncolours = bp->ncolours;

@@ -347,6 +347,25 @@ __host__ __device__ constexpr int stored_per_edge() {
   else return outs_per_edge<P>();
 }
 
+// Edge-major stride of the segmented strategy's per-edge buffer: the stored
+// values of one edge are contiguous and padded to a multiple of 16 bytes,
+// so the node phase reads an edge's values from one or two sectors with
+// vector loads (a component-major buffer would touch one sector per value).
+template <class P>
+__host__ __device__ constexpr int ebuf_stride() {
+  constexpr int per16 = 16 / (int)sizeof(typename P::TE);
+  return (stored_per_edge<P>() + per16 - 1) / per16 * per16;
+}
+
+// copy n values of type T between 16-byte aligned buffers in 16-byte words
+template <typename T, int N>
+__device__ __forceinline__ void copy16(T* __restrict__ dst, const T* __restrict__ src) {
+  static_assert((N * sizeof(T)) % 16 == 0, "16-byte multiple");
+#pragma unroll
+  for (int k = 0; k < (int)(N * sizeof(T) / 16); k++)
+    reinterpret_cast<float4*>(dst)[k] = reinterpret_cast<const float4*>(src)[k];
+}
+
 template <class P, bool STAGED>
 __host__ int64_t colour_smem_bytes(int32_t part, int32_t ucap) {
   int64_t b = align16((int64_t)stored_per_edge<P>() * part * sizeof(typename P::TE));
@@ -470,21 +489,21 @@ __global__ void k_seg_edges(P ph, const int32_t* __restrict__ m0,
     TN vi[P::NIN], vj[P::NIN];
     ph.load(m0[e], vi);
     ph.load(m1[e], vj);
+    constexpr int SP = ebuf_stride<P>();
+    __align__(16) TE st[SP];
+#pragma unroll
+    for (int c = 0; c < SP; c++) st[c] = TE(0);
     if constexpr (HasPack<P>::value) {
-      TE st[P::PACK];
       ph.pack(e, vi, vj, st);
-#pragma unroll
-      for (int c = 0; c < P::PACK; c++) ebuf[c * E + e] = st[c];
     } else {
-      TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
-      ph.edge(e, vi, vj, oi, oj);
-#pragma unroll
-      for (int c = 0; c < P::OUT; c++) ebuf[c * E + e] = oi[c];
+      TE oj[P::MODE == MODE_GEN ? P::OUT : 1];
+      ph.edge(e, vi, vj, st, oj);
       if constexpr (P::MODE == MODE_GEN) {
 #pragma unroll
-        for (int c = 0; c < P::OUT; c++) ebuf[(P::OUT + c) * E + e] = oj[c];
+        for (int c = 0; c < P::OUT; c++) st[P::OUT + c] = oj[c];
       }
     }
+    copy16<TE, SP>(ebuf + e * SP, st);
   }
 }
 
@@ -501,11 +520,13 @@ __global__ void k_seg_nodes_packed(const int64_t* __restrict__ rowptr,
     TA acc[P::OUT];
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) acc[c] = TA(0);
+    constexpr int SP = ebuf_stride<P>();
     const int64_t r1 = rowptr[i + 1];
     for (int64_t t = rowptr[i]; t < r1; t++) {
       const int32_t end = ends[t];
-      const int64_t e = end >> 1;
-      P::unpack_add([&](int c) { return ebuf[c * E + e]; }, (end & 1) != 0, acc);
+      __align__(16) typename P::TE st[SP];
+      copy16<typename P::TE, SP>(st, ebuf + (int64_t)(end >> 1) * SP);
+      P::unpack_add([&](int c) { return st[c]; }, (end & 1) != 0, acc);
     }
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) {
@@ -516,7 +537,8 @@ __global__ void k_seg_nodes_packed(const int64_t* __restrict__ rowptr,
 }
 
 // Phase 2: the edge ends are sorted by node (CSR); each node's segment is
-// summed by one thread in edge order and added into the targets.  A
+// summed by one thread in edge order and added into the targets.  The
+// per-edge buffer is edge-major (see ebuf_stride()).  A
 // warp-cooperative scan would cost log2(32) = 5 adds per end instead of 1,
 // which the FP64 pipe cannot spare, so segments are reduced one per lane.
 template <typename TE, typename TA, int OUT, int MODE, int DIM0>
@@ -524,6 +546,10 @@ __global__ void k_seg_nodes(const int64_t* __restrict__ rowptr,
                             const int32_t* __restrict__ ends, int64_t N,
                             int64_t E, const TE* __restrict__ ebuf,
                             Targets<TA, DIM0> tg) {
+  // edge-major buffer, stride as ebuf_stride(): OUTS values padded to 16 B
+  constexpr int OUTS = MODE == MODE_GEN ? 2 * OUT : OUT;
+  constexpr int per16 = 16 / (int)sizeof(TE);
+  constexpr int SP = (OUTS + per16 - 1) / per16 * per16;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += stride) {
@@ -536,13 +562,18 @@ __global__ void k_seg_nodes(const int64_t* __restrict__ rowptr,
       const int64_t e = end >> 1;
       const bool second = end & 1;
       if constexpr (MODE == MODE_GEN) {
-        const int base = second ? OUT : 0;
+        // only this end's half: OUT values at offset 0 or OUT
+        static_assert((OUT * sizeof(TE)) % 16 == 0, "halves must be 16-byte aligned");
+        __align__(16) TE st[OUT];
+        copy16<TE, OUT>(st, ebuf + e * SP + (second ? OUT : 0));
 #pragma unroll
-        for (int c = 0; c < OUT; c++) acc[c] += to_acc<TA>(ebuf[(base + c) * E + e]);
+        for (int c = 0; c < OUT; c++) acc[c] += to_acc<TA>(st[c]);
       } else {
+        __align__(16) TE st[SP];
+        copy16<TE, SP>(st, ebuf + e * SP);
 #pragma unroll
         for (int c = 0; c < OUT; c++) {
-          TA v = to_acc<TA>(ebuf[c * E + e]);
+          TA v = to_acc<TA>(st[c]);
           if constexpr (MODE == MODE_ANTI) acc[c] += second ? neg(v) : v;
           else acc[c] += v;
         }

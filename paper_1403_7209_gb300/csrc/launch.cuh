@@ -80,7 +80,7 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
       if (rc) return rc;
       using TE = typename P::TE;
       if ((rc = check_block(c, k_seg_edges<P>, block))) return rc;
-      const size_t bytes = (size_t)stored_per_edge<P>() * L.E * sizeof(TE);
+      const size_t bytes = (size_t)ebuf_stride<P>() * L.E * sizeof(TE);
       void* buf = nullptr;
       if ((rc = c->need_scratch(bytes, &buf))) return rc;
       int64_t grid = std::min<int64_t>((L.E + block - 1) / block, cap);

@@ -20,8 +20,9 @@ namespace {
 // Largest edge set the entry point accepts.
 constexpr int64_t kMaxEdges = OP2B_NOALLOC_MAX_EDGES;
 
-// Per-edge fluxes, component-major (6 x kMaxEdges doubles = 12 MiB).  Every
-// GPU that loads the library reserves this array until the process exits.
+// Per-edge fluxes, 6 doubles per edge, edge-major (6 x kMaxEdges doubles =
+// 12 MiB).  Every GPU that loads the library reserves this array until the
+// process exits.
 static __device__ __align__(256) double g_flux_scratch[6 * kMaxEdges];
 
 std::mutex g_mu;
@@ -89,6 +90,7 @@ extern "C" int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const doubl
     unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + block - 1) / block, cap));
     k_zero_rows<<<g, block, 0, st>>>(R, ldR, 6, N);
   }
+  static_assert(op2b::ebuf_stride<op2b::BodyFlux1<double>>() == 6, "scratch holds 6 per edge");
   if (E > 0) {
     // the edge phase writes all 6 x E scratch entries that the node phase
     // reads, so the array's previous contents never matter

@@ -1,0 +1,74 @@
+"""Run selected loops of the library repeatedly on a lattice (for profilers).
+
+    python -m paper_1403_7209_gb300.profile_loops --n 60 --loops flux2,adjoint --reps 3
+
+Builds the n^3 lattice with RCM numbering, autotunes every loop once, then
+runs each requested loop `reps` times with a device synchronisation after
+each repetition, and prints one line per loop with its mean time (CUDA
+events).  Loops: gg, flux2, gg32, flux2_32, adjoint (flux adjoint +
+scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=60)
+    ap.add_argument("--loops", default="flux2")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--tune-cache", default="")
+    args = ap.parse_args()
+    import torch
+    from paper_1403_7209_gb300 import meshgen, op2b as L
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    L.load(build_if_missing=False)
+    m = meshgen.lattice(args.n)
+    q = meshgen.flow_state(m)
+    s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber="rcm", mixed=True,
+                   adjoint=True)
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        L.op2b_load_tuning(s.ctx, args.tune_cache)
+    for loop in range(L.NUM_LOOPS):
+        for prec in (0, 1):
+            s.set_strategy(loop, prec, L.STRAT_AUTO)
+    s.time_step(0.5)
+    L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
+    s.t["lam"].normal_()
+    run = {
+        "gg": lambda: s.green_gauss(),
+        "flux2": lambda: s.flux(2),
+        "gg32": lambda: s.green_gauss(mixed=True),
+        "flux2_32": lambda: s.flux(2, mixed=True),
+        "adjoint": lambda: s.adjoint(2, recompute_gradient=False),
+        "stage": lambda: s.stage(0.25),
+    }
+    names = args.loops.split(",")
+    for nm in names:  # warm-up: tunes and builds plans
+        run[nm]()
+    torch.cuda.synchronize()
+    if args.tune_cache:
+        L.op2b_save_tuning(s.ctx, args.tune_cache)
+    out = {}
+    for nm in names:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ms = 0.0
+        for _ in range(args.reps):
+            ev[0].record()
+            run[nm]()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms += ev[0].elapsed_time(ev[1])
+        out[nm] = ms / args.reps
+    print(json.dumps({"n": args.n, "edges": m.num_edges, "ms": out}))
+    s.close()
+
+
+if __name__ == "__main__":
+    main()

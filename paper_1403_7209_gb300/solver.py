@@ -214,13 +214,18 @@ class EdgeSolver:
         """q32 <- q (FP32 shadow of the state)."""
         L.op2b_dat_copy(self.ctx, self.d["q32"], self.d["q"])
 
-    def adjoint(self, order=2):
-        """qbar = dJ/dq (dat qbar) and nbar = dJ/dn (dat nbar) of J = lam . R."""
+    def adjoint(self, order=2, recompute_gradient=True):
+        """qbar = dJ/dq (dat qbar) and nbar = dJ/dn (dat nbar) of J = lam . R.
+
+        The edge states are recomputed from the node data.  With
+        ``recompute_gradient=False`` the dat G must still hold the gradient
+        of the current q and n (as the forward residual left it)."""
         c = self.ctx
         if order == 1:
             L.op2b_edge_flux_adjoint(c, self.a_fa1, 1, self.gamma, self.eps_lim, L.ZERO_INC)
             return
-        self.green_gauss()
+        if recompute_gradient:
+            self.green_gauss()
         L.op2b_edge_flux_adjoint(c, self.a_fa2, 2, self.gamma, self.eps_lim, L.ZERO_INC)
         L.op2b_grad_scale_adjoint(c, self.d["Gbar"], self.d["V"])
         L.op2b_green_gauss_adjoint(c, self.a_gga, 0)

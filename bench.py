@@ -40,6 +40,11 @@ BYTES_PER_EDGE_F32 = {"gg": 8 + 12 + (24 + 72) / 9, "flux2": 8 + 12 + 12 + (24 +
 # FP64 operations per edge of the flux2 definition (reconstruction 198 +
 # Rusanov 97), each add, multiply, divide and square root counted once.
 FLOPS_PER_EDGE_FLUX2 = 295.0
+# DRAM bytes per edge of the FP64 flux2 kernel (atomic strategy) from an ncu
+# capture on the 60^3 lattice (dram__bytes_read.sum + dram__bytes_write.sum =
+# 170.7 MB over 1,944,000 edges; profiles/ncu_edge_loops_n60.md), scaled to a
+# launch by its edge count.  Traffic grows in proportion to the edges.
+DRAM_BYTES_PER_EDGE_FLUX2_ATOMIC = 170.68e6 / 1944000
 
 
 def read_peaks():
@@ -290,22 +295,34 @@ def march_extra(torch, L, s, q, args, stream, steps=50):
 
 
 def numbering_extra(torch, L, m, q, args, stream, ms_rcm, device):
-    """The same FP64 stage with random node numbering (no renumbering)."""
+    """The same FP64 stage (and FP32-mixed stage) under a random node
+    numbering and under the partition order of recursive coordinate
+    bisection, against RCM."""
     from paper_1403_7209_gb300.solver import EdgeSolver
-    r = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device, renumber="random",
-                   seed=1, stream=stream)
-    for loop in range(L.NUM_LOOPS):
-        r.set_strategy(loop, 0, L.STRAT_AUTO)
-    r.time_step(0.5)
-    L.op2b_dat_copy(r.ctx, r.d["q0"], r.d["q"])
-    for _ in range(args.warmup):
-        r.stage(0.25)
-    ms = timed(torch, lambda: r.stage(0.25), args.steps, stream)
-    out = {"rcm_ms": ms_rcm, "random_ms": ms, "rcm_speedup": ms / ms_rcm,
-           "random_edges_per_s": m.num_edges / (ms * 1e-3),
-           "random_strategies": {nm: L.STRATEGY_NAMES[r.plan_stats(lp)["strategy"]] for nm, lp in
-                                 (("gg", L.LOOP_GREEN_GAUSS), ("flux2", L.LOOP_FLUX2))}}
-    r.close()
+    out = {"rcm_ms": ms_rcm}
+    for name in ("random", "rcb"):
+        r = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device, renumber=name,
+                       seed=1, stream=stream, coords=m.coords, mixed=True)
+        for loop in range(L.NUM_LOOPS):
+            for prec in (0, 1):
+                r.set_strategy(loop, prec, L.STRAT_AUTO)
+        r.time_step(0.5)
+        L.op2b_dat_copy(r.ctx, r.d["q0"], r.d["q"])
+        for _ in range(args.warmup):
+            r.stage(0.25)
+        ms = timed(torch, lambda: r.stage(0.25), args.steps, stream)
+        r.sync_shadow()
+        for _ in range(args.warmup):
+            r.stage(0.25, 2, mixed=True)
+        mms = timed(torch, lambda: r.stage(0.25, 2, mixed=True), args.steps, stream)
+        out[name] = {"ms": ms, "edges_per_s": m.num_edges / (ms * 1e-3),
+                     "rcm_speedup": ms / ms_rcm, "mixed_ms": mms,
+                     "strategies": {nm: L.STRATEGY_NAMES[r.plan_stats(lp, pr)["strategy"]]
+                                    for nm, lp, pr in (("gg", L.LOOP_GREEN_GAUSS, 0),
+                                                       ("flux2", L.LOOP_FLUX2, 0),
+                                                       ("gg32", L.LOOP_GREEN_GAUSS, 1),
+                                                       ("flux2_32", L.LOOP_FLUX2, 1))}}
+        r.close()
     return out
 
 
@@ -403,7 +420,11 @@ def main():
         "config": workload_config(args, m),
         "roofline": {"kernel": "flux2 edge loop (FP64, %s)" % strat["flux2"], "bound": "alu",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": (DRAM_BYTES_PER_EDGE_FLUX2_ATOMIC * E
+                                 if strat["flux2"] == "atomic" else None),
+                     "traffic_note": "bytes per launch, scaled by edge count from the "
+                                     "60^3 ncu capture of the same kernel",
                      "peak_source": "FP64 FMA units x clock (152 SMs x 2/clk x 2 flop x 2.07 GHz)",
                      "hbm_frac": BYTES_PER_EDGE["flux2"] * E / (fl_ms * 1e-3) / 1e9 / hbm,
                      "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src},

@@ -97,6 +97,13 @@ typedef struct {
 #define OP2B_STRAT_COLOUR 2    /* coloured edge blocks, shared-memory sums */
 #define OP2B_STRAT_SEGMENTED 3 /* per-edge results, then per-node sums over
                                   the node-sorted edge ends */
+#define OP2B_STRAT_BLOCK_ATOMIC 5 /* edge blocks in one launch, shared-memory
+                                     sums per distinct node, one atomic add per
+                                     (block, node, component) */
+#define OP2B_STRAT_OWNER 6     /* thread per node over the edges whose lower-
+                                  numbered end it is: that end's data loaded
+                                  once and its sum kept in registers; atomic
+                                  adds for the other end only */
 #define OP2B_STRAT_AUTO_DET 4  /* autotune among the deterministic strategies
                                   only (colour, segmented): their sums run in
                                   a fixed order, so results are bitwise
@@ -253,6 +260,19 @@ int op2b_time_step(op2b_ctx ctx, op2b_dat V, op2b_dat lam, double cfl,
  * q32 (F32 dim 6, or -1) receives the FP32 shadow of the new q. */
 int op2b_node_update(op2b_ctx ctx, op2b_dat q0, op2b_dat q, op2b_dat R,
                      op2b_dat V, op2b_dat dt, double alpha, op2b_dat q32);
+/* Global reductions (the residual norms and global time step that an
+ * explicit solver monitors each stage; the paper's `updatek` loop ends in a
+ * global reduction, Table "loopperfmpi", and Sec. 4.2 finds reductions
+ * latency-bound at scale).  out_dev (caller-owned device memory, dim
+ * doubles) receives per component: OP2B_RED_SUM the sum, OP2B_RED_L2
+ * sqrt(sum x^2), OP2B_RED_MAXABS max |x|, OP2B_RED_MIN the minimum, over
+ * the elements of the dat's set.  F64 dats only.  Two passes in a fixed
+ * order: the result is bitwise reproducible.  Asynchronous on the stream. */
+#define OP2B_RED_SUM 0
+#define OP2B_RED_L2 1
+#define OP2B_RED_MAXABS 2
+#define OP2B_RED_MIN 3
+int op2b_dat_reduce(op2b_ctx ctx, op2b_dat dat, int32_t op, double* out_dev);
 /* Set every component of a dat to `value`. */
 int op2b_dat_fill(op2b_ctx ctx, op2b_dat dat, double value);
 /* dst = src component-wise (same set and dim; F64 <-> F32 conversion). */

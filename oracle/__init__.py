@@ -74,6 +74,7 @@ def _load():
                 "ora_residual_reverse": [I, I64, I64, P, P, P, P, P, D, D,
                                          P, P, P, P, P],
                 "ora_kink_margin": [I, I64, I64, P, P, P, P, P, D, D, P, P],
+                "ora_reduce": [I64, I, P, I, P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -252,6 +253,17 @@ def residual_reverse(order, edge, q, n, dx, V, lam, gamma=GAMMA,
                                  _p(V), gamma, eps, _p(lam), _p(G), _p(Gb),
                                  _p(qb), _p(nb))
     return qb, nb
+
+
+def reduce(x, op):
+    """Per-component sum (op 0), L2 norm (1), max |x| (2) or min (3) of an
+    (n, dim) array."""
+    x = _f64(x)
+    if x.ndim == 1:
+        x = x.reshape(-1, 1)
+    out = np.empty(x.shape[1])
+    _load().ora_reduce(x.shape[0], x.shape[1], _p(x), op, _p(out))
+    return out
 
 
 def kink_margin(order, edge, q, n, dx, V, gamma=GAMMA, eps=EPS_LIM):

@@ -228,6 +228,23 @@ void ora_rk_update(int64_t N, const double* q0, const double* R,
       q[NV * i + k] = q0[NV * i + k] - alpha * (dt[i] / V[i]) * R[NV * i + k];
 }
 
+/* Global reductions over the rows of an (n x dim) node-major array, per
+ * component: op 0 sum, 1 Euclidean norm sqrt(sum x^2), 2 max |x|, 3 min x
+ * (the residual norms and the global time step of an explicit solver). */
+void ora_reduce(int64_t n, int dim, const double* x, int op, double* out) {
+  for (int k = 0; k < dim; k++) {
+    double acc = (op == 3) ? INFINITY : 0.0;
+    for (int64_t i = 0; i < n; i++) {
+      double v = x[(int64_t)dim * i + k];
+      if (op == 0) acc += v;
+      else if (op == 1) acc += v * v;
+      else if (op == 2) acc = fabs(v) > acc ? fabs(v) : acc;
+      else acc = v < acc ? v : acc;
+    }
+    out[k] = (op == 1) ? sqrt(acc) : acc;
+  }
+}
+
 /* 0 if every node has rho > 0 and p > 0, else 1 + the first bad node */
 int64_t ora_check_state(int64_t N, const double* q, double gamma) {
   for (int64_t i = 0; i < N; i++)

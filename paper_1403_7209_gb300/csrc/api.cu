@@ -169,6 +169,37 @@ int Ctx::seg_plan(int map, DevSegPlan** out) {
   return OP2B_OK;
 }
 
+int Ctx::own_plan(int map, DevOwnPlan** out) {
+  MapRec& m = maps[map];
+  auto it = oplans.find(map);
+  if (it != oplans.end() && it->second.map_version == m.version) {
+    *out = &it->second;
+    return OP2B_OK;
+  }
+  if (it != oplans.end()) {
+    cudaStreamSynchronize(stream);
+    cudaFree(it->second.ptr);
+    cudaFree(it->second.idx);
+    it->second = DevOwnPlan();
+  }
+  std::vector<int32_t> m0, m1;
+  split_map(m, m0, m1);
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> idx;
+  owner_csr(sets[m.to].size, (int64_t)m0.size(), m0.data(), m1.data(), &ptr, &idx);
+  DevOwnPlan& d = oplans[map];
+  d.map_version = m.version;
+  int rc;
+  if ((rc = upload(this, &d.ptr, ptr)) || (rc = upload(this, &d.idx, idx))) {
+    cudaFree(d.ptr);
+    cudaFree(d.idx);
+    oplans.erase(map);
+    return rc;
+  }
+  *out = &d;
+  return OP2B_OK;
+}
+
 }  // namespace op2b
 
 // ------------------------------------------------------------- lifecycle
@@ -220,6 +251,10 @@ extern "C" int op2b_finalize(op2b_ctx h) {
   cudaStreamSynchronize(c.stream);
   for (auto& kv : c.bplans) free_block_plan(kv.second);
   for (auto& kv : c.splans) free_seg_plan(kv.second);
+  for (auto& kv : c.oplans) {
+    cudaFree(kv.second.ptr);
+    cudaFree(kv.second.idx);
+  }
   for (auto& m : c.maps) cudaFree(m.dev);
   cudaFree(c.scratch);
   delete h;
@@ -569,6 +604,23 @@ std::vector<Strategy> candidates(const LoopLaunch& L, bool det) {
     s.block = b;
     v.push_back(s);
   }
+  if (!det)
+    for (int b : {128, 256}) {
+      Strategy s;
+      s.strategy = OP2B_STRAT_OWNER;
+      s.block = b;
+      v.push_back(s);
+    }
+  if (!det)
+    for (int part : {512, 1024, 2048})
+      for (int st : {0, 1}) {
+        Strategy s;
+        s.strategy = OP2B_STRAT_BLOCK_ATOMIC;
+        s.part = part;
+        s.block = 256;
+        s.staged = st;
+        v.push_back(s);
+      }
   return v;
 }
 
@@ -600,6 +652,7 @@ int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, bool 
   cudaEventCreate(&e1);
   double best_ms = 1e300;
   int rc = OP2B_OK, found = 0;
+  std::string timings;
   for (const Strategy& s : candidates(L, det)) {
     int r = dispatch(c, T, s);  // warm-up (also builds the plan)
     // skip candidates that cannot run here: a block too large for shared
@@ -625,6 +678,10 @@ int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, bool 
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     double per = ms / reps;
+    char buf[96];
+    snprintf(buf, sizeof buf, "%s[%d, %d, %d, %d, %.4f]", timings.empty() ? "" : ", ", s.strategy,
+             s.block, s.part, s.staged, per);
+    timings += buf;
     if (per < best_ms) {
       best_ms = per;
       *best = s;
@@ -645,6 +702,7 @@ int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, bool 
   cudaFree(td);
   if (rc) return rc;
   if (!found) return c.fail(OP2B_EPLAN, "autotune: no candidate could run");
+  best->timings = timings;
   return OP2B_OK;
 }
 
@@ -940,6 +998,17 @@ extern "C" int op2b_dat_fill(op2b_ctx h, op2b_dat d, double value) {
   return node_fill(&c, r.ptr, r.type, r.ld, r.dim, c.sets[r.set].size, value);
 }
 
+extern "C" int op2b_dat_reduce(op2b_ctx h, op2b_dat d, int32_t op, double* out_dev) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_dat(c, d)) return c.fail(OP2B_EINVAL, "dat_reduce: bad dat");
+  const DatRec& r = c.dats[d];
+  if (r.type != OP2B_F64) return c.fail(OP2B_ETYPE, "dat_reduce: F64 dats only");
+  if (!out_dev) return c.fail(OP2B_EINVAL, "dat_reduce: null output");
+  if (op < OP2B_RED_SUM || op > OP2B_RED_MIN) return c.fail(OP2B_EINVAL, "dat_reduce: unknown operation");
+  return node_reduce(&c, (const double*)r.ptr, r.ld, r.dim, c.sets[r.set].size, op, out_dev);
+}
+
 extern "C" int op2b_dat_copy(op2b_ctx h, op2b_dat dst, op2b_dat src) {
   CTX_CHECK(h);
   Ctx& c = h->c;
@@ -957,7 +1026,7 @@ extern "C" int op2b_set_strategy(op2b_ctx h, int32_t loop, int32_t prec, int32_t
   Ctx& c = h->c;
   if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec != 0 && prec != 1))
     return c.fail(OP2B_EINVAL, "set_strategy: bad loop or precision");
-  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_AUTO_DET)
+  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_OWNER)
     return c.fail(OP2B_EINVAL, "set_strategy: bad strategy");
   if (block != 0 && (block < 32 || block > 1024 || block % 32))
     return c.fail(OP2B_EINVAL, "set_strategy: block must be a multiple of 32 in [32, 1024]");
@@ -990,10 +1059,11 @@ extern "C" int op2b_save_tuning(op2b_ctx h, const char* path) {
     const Strategy& s = kv.second;
     char line[512];
     snprintf(line, sizeof line,
-             "  \"%s\": {\"strategy\": %d, \"block\": %d, \"part\": %d, \"staged\": %d, \"ms\": %.6f}%s\n",
-             kv.first.c_str(), s.strategy, s.block, s.part, s.staged, s.tuned_ms,
-             ++k < c.tuned.size() ? "," : "");
+             "  \"%s\": {\"strategy\": %d, \"block\": %d, \"part\": %d, \"staged\": %d, \"ms\": %.6f",
+             kv.first.c_str(), s.strategy, s.block, s.part, s.staged, s.tuned_ms);
     f << line;
+    if (!s.timings.empty()) f << ", \"candidates\": [" << s.timings << "]";
+    f << "}" << (++k < c.tuned.size() ? "," : "") << "\n";
   }
   f << "}\n";
   return f.good() ? OP2B_OK : c.fail(OP2B_EINVAL, "save_tuning: write failed");
@@ -1012,7 +1082,8 @@ extern "C" int op2b_load_tuning(op2b_ctx h, const char* path) {
     if (sscanf(line.c_str(),
                " \"%255[^\"]\": {\"strategy\": %d, \"block\": %d, \"part\": %d, \"staged\": %d, \"ms\": %lf}",
                key, &s.strategy, &s.block, &s.part, &s.staged, &s.tuned_ms) == 6) {
-      if (s.strategy < OP2B_STRAT_ATOMIC || s.strategy > OP2B_STRAT_SEGMENTED)
+      if (s.strategy < OP2B_STRAT_ATOMIC || s.strategy == OP2B_STRAT_AUTO_DET ||
+          s.strategy > OP2B_STRAT_OWNER)
         return c.fail(OP2B_EINVAL, "load_tuning: bad strategy in table");
       c.tuned[key] = s;
     }

@@ -308,9 +308,58 @@ __global__ void k_atomic(P ph, const int32_t* __restrict__ m0,
   }
 }
 
+// (5) owner-compute: thread per node v over the edges whose lower-numbered
+// end is v (CSR own_ptr / own_idx).  The owner's node data is loaded once
+// and its sum kept in registers, flushed with one atomic add per component;
+// only the other end of each edge receives atomic adds.
+template <class P>
+__global__ void k_owner(P ph, const int32_t* __restrict__ m0,
+                        const int32_t* __restrict__ m1, int64_t N,
+                        const int64_t* __restrict__ own_ptr,
+                        const int32_t* __restrict__ own_idx,
+                        Targets<typename P::TA, P::DIM0> tg) {
+  using TN = typename P::TN;
+  using TE = typename P::TE;
+  using TA = typename P::TA;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += stride) {
+    const int64_t t0 = own_ptr[v], t1 = own_ptr[v + 1];
+    if (t0 == t1) continue;
+    TN vv[P::NIN];
+    ph.load(v, vv);
+    TA acc[P::OUT];
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) acc[c] = TA(0);
+    for (int64_t t = t0; t < t1; t++) {
+      const int64_t e = own_idx[t];
+      const int64_t i = m0[e], j = m1[e];
+      const bool first = (i == v);
+      const int64_t w = first ? j : i;
+      TN vw[P::NIN];
+      ph.load(w, vw);
+      TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
+      if (first) ph.edge(e, vv, vw, oi, oj);
+      else ph.edge(e, vw, vv, oi, oj);
+#pragma unroll
+      for (int c = 0; c < P::OUT; c++) {
+        const TA a = to_acc<TA>(oi[c]);
+        TA b;  // the second end's increment
+        if constexpr (P::MODE == MODE_ANTI) b = neg(a);
+        else if constexpr (P::MODE == MODE_SYM) b = a;
+        else b = to_acc<TA>(oj[c]);
+        acc[c] += first ? a : b;
+        atomicAdd(tg.at(c, w), first ? b : a);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) atomicAdd(tg.at(c, v), acc[c]);
+  }
+}
+
 // Device view of a block plan (mini-partitions + colours).
 struct BlockView {
-  const int32_t* cblocks;  // blocks of the colour being launched
+  const int32_t* cblocks;  // blocks of the colour being launched (null: all
+                           // blocks in order, for the atomic flush)
   int64_t nblk;
   int32_t part;
   int32_t ucap;            // staging capacity (max distinct nodes per block)
@@ -379,7 +428,10 @@ __host__ int64_t colour_smem_bytes(int32_t part, int32_t ucap) {
 // plain read-modify-writes (no two blocks of a colour share a node).  With
 // STAGED the READ data of the block's distinct nodes is first gathered
 // into shared memory and the edges read it from there.
-template <class P, bool STAGED>
+// (4) block-atomic (ATOMIC_FLUSH): the same kernel over all blocks in one
+// launch, flushing each block's per-node sums with atomic adds: one atomic
+// per (block, node, component) instead of one per edge end.
+template <class P, bool STAGED, bool ATOMIC_FLUSH = false>
 __global__ void k_colour(P ph, const int32_t* __restrict__ m0,
                          const int32_t* __restrict__ m1, int64_t E,
                          BlockView bv, Targets<typename P::TA, P::DIM0> tg) {
@@ -392,7 +444,7 @@ __global__ void k_colour(P ph, const int32_t* __restrict__ m0,
   TE* sOut = reinterpret_cast<TE*>(smem);
   TN* sIn = reinterpret_cast<TN*>(smem + align16((int64_t)OUTS * part * sizeof(TE)));
   for (int64_t bi = blockIdx.x; bi < bv.nblk; bi += gridDim.x) {
-    const int64_t b = bv.cblocks[bi];
+    const int64_t b = bv.cblocks ? bv.cblocks[bi] : bi;
     const int64_t e0 = b * part;
     const int ne = (int)min((int64_t)part, E - e0);
     const int64_t u0 = bv.bn_off[b];
@@ -468,7 +520,8 @@ __global__ void k_colour(P ph, const int32_t* __restrict__ m0,
 #pragma unroll
       for (int c = 0; c < P::OUT; c++) {
         TA* p = tg.at(c, node);
-        *p = *p + acc[c];
+        if constexpr (ATOMIC_FLUSH) atomicAdd(p, acc[c]);
+        else *p = *p + acc[c];
       }
     }
     __syncthreads();

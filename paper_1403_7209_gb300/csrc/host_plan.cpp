@@ -302,4 +302,15 @@ void node_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
   }
 }
 
+void owner_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
+               std::vector<int64_t>* ptr, std::vector<int32_t>* idx) {
+  ptr->assign(N + 1, 0);
+  auto& p = *ptr;
+  for (int64_t e = 0; e < E; e++) p[std::min(m0[e], m1[e]) + 1]++;
+  for (int64_t v = 0; v < N; v++) p[v + 1] += p[v];
+  idx->resize(E);
+  std::vector<int64_t> pos(p.begin(), p.end() - 1);
+  for (int64_t e = 0; e < E; e++) (*idx)[pos[std::min(m0[e], m1[e])]++] = (int32_t)e;
+}
+
 }  // namespace op2b

@@ -58,6 +58,11 @@ bool build_block_plan(int64_t N, int64_t E, const int32_t* m0,
 void node_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
               std::vector<int64_t>* rowptr, std::vector<int32_t>* ends);
 
+// Edges grouped by their lower-numbered end (counting sort, edge order
+// kept within a node): ptr N+1, idx E.
+void owner_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
+               std::vector<int64_t>* ptr, std::vector<int32_t>* idx);
+
 // Hardware threads to use for host planning.
 int host_threads();
 

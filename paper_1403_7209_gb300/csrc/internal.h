@@ -58,12 +58,19 @@ struct DevSegPlan {
   int32_t* ends = nullptr;
 };
 
+struct DevOwnPlan {
+  uint64_t map_version = ~0ull;
+  int64_t* ptr = nullptr;  // N+1
+  int32_t* idx = nullptr;  // E edges, grouped by lower-numbered end
+};
+
 struct Strategy {
   int32_t strategy = OP2B_STRAT_ATOMIC;
   int32_t block = 256;
   int32_t part = 512;
   int32_t staged = 0;
   double tuned_ms = 0.0;
+  std::string timings;  // every candidate the tuner ran, "[strategy, block, part, staged, ms], ..."
 };
 
 // Everything a loop launch needs; pointers are device pointers.
@@ -110,6 +117,8 @@ int node_fill(Ctx* c, void* p, int type, int64_t ld, int dim, int64_t n,
               double value);
 int node_copy(Ctx* c, void* dst, int dtype, int64_t ldd, const void* src,
               int stype, int64_t lds, int dim, int64_t n);
+// per-component reduction of an FP64 SoA dat into out[dim] (device)
+int node_reduce(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, int op, double* out);
 // out[k*ld + t] = in[k*ld + idx[t]] for t < n (elements of `esize` bytes)
 int node_gather(Ctx* c, void* out, const void* in, int esize, int64_t ld,
                 int dim, const int64_t* idx, int64_t n);
@@ -126,6 +135,7 @@ struct Ctx {
   Strategy strat[OP2B_NUM_LOOPS][2];
   std::map<std::pair<int, int>, DevBlockPlan> bplans;  // (map, part)
   std::map<int, DevSegPlan> splans;                    // map
+  std::map<int, DevOwnPlan> oplans;                    // map
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   double tune_deadline_ms = 20000.0;
@@ -143,6 +153,7 @@ struct Ctx {
   // plans (built or rebuilt on demand)
   int block_plan(int map, int32_t part, DevBlockPlan** out);
   int seg_plan(int map, DevSegPlan** out);
+  int own_plan(int map, DevOwnPlan** out);
 };
 
 }  // namespace op2b

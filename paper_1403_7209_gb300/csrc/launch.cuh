@@ -20,7 +20,7 @@ static int check_block(Ctx* c, K kern, int block) {
   return OP2B_OK;
 }
 
-template <class P, bool STAGED>
+template <class P, bool STAGED, bool ATOMIC_FLUSH>
 static int run_colour(Ctx* c, const P& ph, const LoopLaunch& L,
                       const Strategy& s, Targets<typename P::TA, P::DIM0> tg) {
   DevBlockPlan* bp = nullptr;
@@ -31,12 +31,28 @@ static int run_colour(Ctx* c, const P& ph, const LoopLaunch& L,
   if (smem > (int64_t)c->smem_optin)
     return c->fail(OP2B_ERANGE, "colour plan: " + std::to_string(smem) +
                                     " B of shared memory per block exceeds the device limit");
-  auto kern = k_colour<P, STAGED>;
+  auto kern = k_colour<P, STAGED, ATOMIC_FLUSH>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return c->fail(OP2B_ECUDA, "cudaFuncSetAttribute (shared memory) failed");
   const int block = s.block > 0 ? s.block : 256;
   if ((rc = check_block(c, kern, block))) return rc;
+  if (ATOMIC_FLUSH) {  // every block in one launch
+    BlockView bv;
+    bv.cblocks = nullptr;
+    bv.nblk = bp->nblocks;
+    bv.part = bp->part;
+    bv.ucap = ucap;
+    bv.bn_off = bp->bn_off;
+    bv.bnodes = bp->bnodes;
+    bv.eloc = bp->eloc;
+    bv.lrow = bp->lrow;
+    bv.lent = bp->lent;
+    if (bv.nblk == 0) return OP2B_OK;
+    unsigned grid = (unsigned)std::min<int64_t>(bv.nblk, (int64_t)1 << 30);
+    kern<<<grid, block, smem, c->stream>>>(ph, L.m0, L.m1, L.E, bv, tg);
+    return c->launched("block-atomic");
+  }
   for (int32_t col = 0; col < bp->ncolours; col++) {
     BlockView bv;
     bv.cblocks = bp->cblocks + bp->coff[col];
@@ -72,8 +88,21 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
       return c->launched("atomic");
     }
     case OP2B_STRAT_COLOUR:
-      return s.staged ? run_colour<P, true>(c, ph, L, s, tg)
-                      : run_colour<P, false>(c, ph, L, s, tg);
+      return s.staged ? run_colour<P, true, false>(c, ph, L, s, tg)
+                      : run_colour<P, false, false>(c, ph, L, s, tg);
+    case OP2B_STRAT_OWNER: {
+      DevOwnPlan* op = nullptr;
+      int rc = c->own_plan(L.map, &op);
+      if (rc) return rc;
+      if ((rc = check_block(c, k_owner<P>, block))) return rc;
+      int64_t grid = std::min<int64_t>((L.N + block - 1) / block, cap);
+      if (grid == 0) return OP2B_OK;
+      k_owner<P><<<(unsigned)grid, block, 0, c->stream>>>(ph, L.m0, L.m1, L.N, op->ptr, op->idx, tg);
+      return c->launched("owner");
+    }
+    case OP2B_STRAT_BLOCK_ATOMIC:
+      return s.staged ? run_colour<P, true, true>(c, ph, L, s, tg)
+                      : run_colour<P, false, true>(c, ph, L, s, tg);
     case OP2B_STRAT_SEGMENTED: {
       DevSegPlan* sp = nullptr;
       int rc = c->seg_plan(L.map, &sp);

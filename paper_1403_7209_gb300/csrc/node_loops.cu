@@ -152,4 +152,92 @@ int node_gather(Ctx* c, void* out, const void* in, int esize, int64_t ld,
   return c->launched("gather");
 }
 
+// ------------------------------------------------------ global reductions
+// Two passes in a fixed order (per-block partials over contiguous chunks,
+// then one block over the partials), so the result does not depend on
+// scheduling: bitwise reproducible.
+
+template <int OP>
+__device__ __forceinline__ double red_init() {
+  return OP == OP2B_RED_MIN ? INFINITY : 0.0;
+}
+template <int OP>
+__device__ __forceinline__ double red_take(double acc, double v) {  // one value
+  if constexpr (OP == OP2B_RED_SUM) return acc + v;
+  else if constexpr (OP == OP2B_RED_L2) return fma(v, v, acc);
+  else if constexpr (OP == OP2B_RED_MAXABS) return fmax(acc, fabs(v));
+  else return fmin(acc, v);
+}
+template <int OP>
+__device__ __forceinline__ double red_merge(double a, double b) {  // two partials
+  if constexpr (OP == OP2B_RED_SUM || OP == OP2B_RED_L2) return a + b;
+  else if constexpr (OP == OP2B_RED_MAXABS) return fmax(a, b);
+  else return fmin(a, b);
+}
+
+template <int OP, int T>
+__device__ __forceinline__ double block_tree(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll
+  for (int w = T / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] = red_merge<OP>(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+template <int OP, int T>
+__global__ void k_reduce_partial(const double* __restrict__ x, int64_t ld, int dim, int64_t n,
+                                 int64_t chunk, double* __restrict__ part) {
+  __shared__ double sh[T];
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  for (int k = 0; k < dim; k++) {
+    double acc = red_init<OP>();
+    for (int64_t i = lo + threadIdx.x; i < hi; i += T) acc = red_take<OP>(acc, x[k * ld + i]);
+    double r = block_tree<OP, T>(acc, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * dim + k] = r;
+  }
+}
+
+template <int OP, int T>
+__global__ void k_reduce_final(const double* __restrict__ part, int nb, int dim,
+                               double* __restrict__ out) {
+  __shared__ double sh[T];
+  for (int k = 0; k < dim; k++) {
+    double acc = red_init<OP>();
+    for (int b = threadIdx.x; b < nb; b += T) acc = red_merge<OP>(acc, part[(int64_t)b * dim + k]);
+    double r = block_tree<OP, T>(acc, sh);
+    if (threadIdx.x == 0) out[k] = (OP == OP2B_RED_L2) ? sqrt(r) : r;
+  }
+}
+
+template <int OP>
+static int reduce_op(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, double* out) {
+  constexpr int T = 256;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (n + 2047) / 2048));
+  const int64_t chunk = (n + nb - 1) / nb;
+  void* part = nullptr;
+  int rc = c->need_scratch((size_t)nb * dim * sizeof(double), &part);
+  if (rc) return rc;
+  k_reduce_partial<OP, T><<<nb, T, 0, c->stream>>>(x, ld, dim, n, std::max<int64_t>(chunk, 1),
+                                                    (double*)part);
+  if ((rc = c->launched("reduce partial"))) return rc;
+  k_reduce_final<OP, T><<<1, T, 0, c->stream>>>((const double*)part, nb, dim, out);
+  return c->launched("reduce final");
+}
+
+int node_reduce(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, int op, double* out) {
+  switch (op) {
+    case OP2B_RED_SUM: return reduce_op<OP2B_RED_SUM>(c, x, ld, dim, n, out);
+    case OP2B_RED_L2: return reduce_op<OP2B_RED_L2>(c, x, ld, dim, n, out);
+    case OP2B_RED_MAXABS: return reduce_op<OP2B_RED_MAXABS>(c, x, ld, dim, n, out);
+    case OP2B_RED_MIN: return reduce_op<OP2B_RED_MIN>(c, x, ld, dim, n, out);
+    default: return c->fail(OP2B_EINVAL, "dat_reduce: unknown operation");
+  }
+}
+
 }  // namespace op2b

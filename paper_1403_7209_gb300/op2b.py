@@ -26,10 +26,13 @@ LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
 LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ, NUM_LOOPS = 4, 5, 6, 7
 PREC_F64, PREC_F32 = 0, 1
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
+STRAT_BLOCK_ATOMIC, STRAT_OWNER = 5, 6
 ZERO_INC = 1
+RED_SUM, RED_L2, RED_MAXABS, RED_MIN = 0, 1, 2, 3
 STRATEGY_NAMES = {STRAT_AUTO: "auto", STRAT_ATOMIC: "atomic",
                   STRAT_COLOUR: "colour", STRAT_SEGMENTED: "segmented",
-                  STRAT_AUTO_DET: "auto-deterministic"}
+                  STRAT_AUTO_DET: "auto-deterministic", STRAT_BLOCK_ATOMIC: "block-atomic",
+                  STRAT_OWNER: "owner"}
 ERROR_NAMES = {EINVAL: "EINVAL", EDIM: "EDIM", ETYPE: "ETYPE",
                EACCESS: "EACCESS", ESET: "ESET", ENOMEM: "ENOMEM",
                ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EPLAN: "EPLAN",
@@ -104,6 +107,7 @@ _SIGS = {
                                         _D, _I32]),
     "op2b_dat_fill": (ctypes.c_int, [_P, _I32, _D]),
     "op2b_dat_copy": (ctypes.c_int, [_P, _I32, _I32]),
+    "op2b_dat_reduce": (ctypes.c_int, [_P, _I32, _I32, _P]),
     "op2b_set_strategy": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32,
                                          _I32]),
     "op2b_set_tune_deadline": (ctypes.c_int, [_P, _D]),
@@ -297,6 +301,10 @@ def op2b_node_update(ctx, q0: int, q: int, R: int, V: int, dt: int,
 
 def op2b_dat_fill(ctx, dat: int, value: float):
     _check(load().op2b_dat_fill(ctx, dat, value), ctx)
+
+
+def op2b_dat_reduce(ctx, dat: int, op: int, out_ptr: int):
+    _check(load().op2b_dat_reduce(ctx, dat, op, out_ptr), ctx)
 
 
 def op2b_dat_copy(ctx, dst: int, src: int):

@@ -16,7 +16,7 @@ import numpy as np
 from . import op2b as L
 
 RK5_ALPHA = (0.25, 1.0 / 6.0, 0.375, 0.5, 1.0)  # Jameson's 5-stage scheme
-RENUMBER = {"none": 0, "random": 1, "rcm": 2}
+RENUMBER = {"none": 0, "random": 1, "rcm": 2}  # "rcb" needs coordinates
 
 
 class EdgeSolver:
@@ -24,8 +24,10 @@ class EdgeSolver:
 
     ``edge`` (E, 2) int, ``normal``/``dx`` (E, 3), ``volume`` (N,), ``q``
     (N, 6) in the caller's numbering.  ``renumber`` in {"none", "random",
-    "rcm"} reorders nodes and edges inside the library; :meth:`fetch_nodes`
-    and :meth:`fetch_edges` return data in the caller's numbering again.
+    "rcm", "rcb"} reorders nodes and edges inside the library ("rcb", the
+    partition order of recursive coordinate bisection, needs ``coords``
+    (N, 3)); :meth:`fetch_nodes` and :meth:`fetch_edges` return data in the
+    caller's numbering again.
     ``mixed`` adds the FP32 shadows used by the mixed-precision path;
     ``adjoint`` the adjoint dats.
     """
@@ -33,7 +35,7 @@ class EdgeSolver:
     def __init__(self, edge, normal, dx, volume, q=None, device: int = 0,
                  renumber: str = "none", seed: int = 0, mixed: bool = False,
                  adjoint: bool = False, gamma: float = 1.4,
-                 eps_lim: float = 1e-12, stream=None):
+                 eps_lim: float = 1e-12, stream=None, coords=None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -64,6 +66,8 @@ class EdgeSolver:
         node("dt", 1)
         edgd("n", 3, init=normal)
         edgd("dx", 3, init=dx)
+        if coords is not None:
+            node("x", 3, init=coords)
         self.mixed = mixed
         if mixed:
             node("q32", 6, torch.float32, init=q)
@@ -78,7 +82,12 @@ class EdgeSolver:
             edgd("nbar", 3)
         self.perm = np.arange(self.N, dtype=np.int64)   # new id of old node
         self.order = np.arange(self.E, dtype=np.int64)  # old edge of new slot
-        if renumber != "none":
+        if renumber == "rcb":
+            if coords is None:
+                raise ValueError("renumber='rcb' needs coords")
+            perm, order = L.op2b_renumber_rcb(c, self.map, self.d["x"], 1, self.N, self.E)
+            self.perm, self.order = perm.astype(np.int64), order
+        elif renumber != "none":
             perm, order = L.op2b_renumber(c, self.map, RENUMBER[renumber], seed,
                                           self.N, self.E)
             self.perm, self.order = perm.astype(np.int64), order
@@ -229,6 +238,14 @@ class EdgeSolver:
         L.op2b_edge_flux_adjoint(c, self.a_fa2, 2, self.gamma, self.eps_lim, L.ZERO_INC)
         L.op2b_grad_scale_adjoint(c, self.d["Gbar"], self.d["V"])
         L.op2b_green_gauss_adjoint(c, self.a_gga, 0)
+
+    def reduce(self, name, op):
+        """Per-component reduction of dat `name` (op: op2b.RED_*), as a
+        device tensor (asynchronous)."""
+        out = self.torch.empty(self.t[name].shape[0], dtype=self.torch.float64,
+                               device=self.device)
+        L.op2b_dat_reduce(self.ctx, self.d[name], op, out.data_ptr())
+        return out
 
     def launch_count(self):
         return L.op2b_launch_count(self.ctx)

@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 STRATS = [("atomic", 1, 256, 0, 0), ("atomic128", 1, 128, 0, 0),
           ("colour", 2, 256, 512, 0), ("colour_staged", 2, 128, 256, 1),
-          ("colour_staged_big", 2, 256, 1024, 1), ("segmented", 3, 256, 0, 0)]
+          ("colour_staged_big", 2, 256, 1024, 1), ("segmented", 3, 256, 0, 0),
+          ("block_atomic", 5, 256, 1024, 0), ("block_atomic_staged", 5, 128, 512, 1),
+          ("owner", 6, 128, 0, 0)]
 
 
 def rel_err(gpu, ref, scale):
@@ -87,7 +89,7 @@ def test_renumbered_residual_in_user_order(gpu_lib, mesh16, ref16, renumber):
     assert np.all(np.diff(key) > 0)
     # and is the user's mesh relabelled
     assert np.array_equal(s.edge, s.perm[m.edge[s.order]])
-    for strat in (1, 2, 3):
+    for strat in (1, 2, 3, 5, 6):
         s.set_strategy(gpu_lib.LOOP_FLUX2, 0, strat, 256, 512, 1)
         s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, strat, 256, 512, 1)
         s.residual(2)
@@ -102,7 +104,8 @@ def test_ragged_and_tiny_meshes(gpu_lib):
         m = meshgen.lattice(n, seed=1)
         q = meshgen.flow_state(m, seed=1)
         R, _, Ra = oracle.residual(2, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
-        for strat, part, staged in ((1, 0, 0), (2, 64, 0), (2, 64, 1), (2, 4096, 1), (3, 0, 0)):
+        for strat, part, staged in ((1, 0, 0), (2, 64, 0), (2, 64, 1), (2, 4096, 1), (3, 0, 0),
+                                    (5, 64, 1), (5, 4096, 0), (6, 0, 0)):
             s = make_solver(gpu_lib, m, q)
             s.set_strategy(gpu_lib.LOOP_FLUX2, 0, strat, 64, part, staged)
             s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, strat, 64, part, staged)
@@ -115,7 +118,7 @@ def test_empty_edge_set_gives_zero_residual(gpu_lib):
     N = 10
     q = np.tile([1.0, 0.5, 0.0, 0.0, 2.5, 0.0], (N, 1))
     from paper_1403_7209_gb300.solver import EdgeSolver
-    for strat in (1, 2, 3):
+    for strat in (1, 2, 3, 5, 6):
         s = EdgeSolver(np.zeros((0, 2), np.int32), np.zeros((0, 3)), np.zeros((0, 3)),
                        np.ones(N), q)
         s.set_strategy(gpu_lib.LOOP_FLUX2, 0, strat)
@@ -156,7 +159,7 @@ def test_march_ten_steps(gpu_lib):
     s.close()
 
 
-@pytest.mark.parametrize("strat", [1, 2, 3])
+@pytest.mark.parametrize("strat", [1, 2, 3, 5, 6])
 def test_mixed_precision_residual_error(gpu_lib, mesh16, ref16, strat):
     m, q = mesh16
     s = make_solver(gpu_lib, m, q, mixed=True, renumber="rcm")
@@ -200,7 +203,7 @@ def _adj_ok(gpu, ref):
 
 
 @pytest.mark.parametrize("order", [1, 2])
-@pytest.mark.parametrize("strat", [1, 2, 3])
+@pytest.mark.parametrize("strat", [1, 2, 3, 5, 6])
 def test_adjoint_matches_oracle_reverse(gpu_lib, mesh16, order, strat):
     m, q = mesh16
     lam = meshgen.adjoint_seed(m.num_nodes)
@@ -287,6 +290,29 @@ def test_deterministic_strategies_are_bitwise_reproducible(gpu_lib, mesh16, stra
     s.set_strategy(gpu_lib.LOOP_FLUX2, 0, gpu_lib.STRAT_AUTO_DET)
     s.residual(2)
     assert s.plan_stats(gpu_lib.LOOP_FLUX2)["strategy"] in (2, 3)
+    s.close()
+
+
+def test_global_reductions_match_oracle_and_repeat_bitwise(gpu_lib, mesh16, ref16):
+    import torch
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber="rcm")
+    s.residual(2)
+    s.time_step(0.5)
+    R = s.fetch_nodes("R")
+    dt = s.fetch_nodes("dt")
+    for op in (gpu_lib.RED_SUM, gpu_lib.RED_L2, gpu_lib.RED_MAXABS, gpu_lib.RED_MIN):
+        got = s.reduce("R", op)
+        again = s.reduce("R", op)
+        torch.cuda.synchronize()
+        assert torch.equal(got, again)
+        ref = oracle.reduce(R, op)
+        if op == gpu_lib.RED_SUM:  # cancellation: scale by the absolute sum
+            assert np.all(np.abs(got.cpu().numpy() - ref) <= 1e-13 * np.sum(np.abs(R), axis=0))
+        else:
+            np.testing.assert_allclose(got.cpu().numpy(), ref, rtol=1e-14)
+    np.testing.assert_array_equal(s.reduce("dt", gpu_lib.RED_MIN).cpu().numpy(),
+                                  oracle.reduce(dt, 3))
     s.close()
 
 

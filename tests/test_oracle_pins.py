@@ -481,3 +481,18 @@ def test_rcm_reduces_lattice_bandwidth():
     inv = np.empty_like(p)
     inv[p] = np.arange(len(p))
     assert b_rcm <= 2 * oracle.bandwidth(inv[e])
+
+
+def test_reductions_closed_forms_and_library_norms():
+    ones = np.ones((1000, 2))
+    ones[:, 1] = -2.0
+    np.testing.assert_array_equal(oracle.reduce(ones, 0), [1000.0, -2000.0])
+    np.testing.assert_allclose(oracle.reduce(ones, 1), [math.sqrt(1000.0), 2 * math.sqrt(1000.0)],
+                               rtol=1e-15)
+    np.testing.assert_array_equal(oracle.reduce(ones, 2), [1.0, 2.0])
+    np.testing.assert_array_equal(oracle.reduce(ones, 3), [1.0, -2.0])
+    rng = np.random.default_rng(9)
+    x = rng.normal(size=(5000, 6))
+    np.testing.assert_allclose(oracle.reduce(x, 1), np.linalg.norm(x, axis=0), rtol=1e-13)
+    np.testing.assert_array_equal(oracle.reduce(x, 2), np.max(np.abs(x), axis=0))
+    np.testing.assert_array_equal(oracle.reduce(x, 3), np.min(x, axis=0))

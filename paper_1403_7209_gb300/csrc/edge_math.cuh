@@ -29,13 +29,29 @@ __device__ __forceinline__ float neg(float x) {
 }
 
 // Exact float -> double on the integer pipe (the conversion instruction runs
-// at the FP64 rate): re-bias the exponent and move the mantissa; zero,
-// subnormal, infinite and NaN inputs take the conversion instruction.
+// at the FP64 rate): re-bias the exponent and move the mantissa.  Zero,
+// subnormal, infinite and NaN inputs are handled with integer selects too,
+// so no FP64-pipe instruction is issued on any path.
 __device__ __forceinline__ double f64_exact(float f) {
-  const int b = __float_as_int(f);
-  const int e = b & 0x7f800000;
-  if (e == 0 || e == 0x7f800000) return (double)f;
-  return __hiloint2double((b & (int)0x80000000) | (((b & 0x7fffffff) >> 3) + 0x38000000), b << 29);
+  const unsigned b = (unsigned)__float_as_int(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned mag = b & 0x7fffffffu;
+  // normal: exponent + (1023 - 127), mantissa moved up by 29 bits
+  unsigned hi = sign | ((mag >> 3) + 0x38000000u);
+  unsigned lo = mag << 29;
+  // subnormal: normalise the mantissa (value m * 2^-149, m < 2^23)
+  const int lz = __clz((int)mag) - 8;  // shift that brings the top bit to bit 23
+  const unsigned mn = mag << (lz & 31);
+  const unsigned hs = sign | ((unsigned)(897 - lz) << 20) | ((mn & 0x7fffffu) >> 3);
+  const unsigned ls = mn << 29;
+  // infinity / NaN: all-ones exponent, payload kept
+  const unsigned hn = sign | 0x7ff00000u | ((mag & 0x7fffffu) >> 3);
+  const bool normal = mag - 0x00800000u < 0x7f000000u;  // exponent field 1..254
+  const bool inf_nan = mag >= 0x7f800000u;
+  const bool zero = mag == 0u;
+  hi = normal ? hi : (inf_nan ? hn : (zero ? sign : hs));
+  lo = normal ? lo : (inf_nan ? lo : (zero ? 0u : ls));
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // value of a per-edge result in the accumulation type of its target

@@ -37,7 +37,7 @@ static int run_colour(Ctx* c, const P& ph, const LoopLaunch& L,
     return c->fail(OP2B_ECUDA, "cudaFuncSetAttribute (shared memory) failed");
   const int block = s.block > 0 ? s.block : 256;
   if ((rc = check_block(c, kern, block))) return rc;
-  if (ATOMIC_FLUSH) {  // every block in one launch
+  if constexpr (ATOMIC_FLUSH) {  // every block in one launch
     BlockView bv;
     bv.cblocks = nullptr;
     bv.nblk = bp->nblocks;
@@ -52,22 +52,23 @@ static int run_colour(Ctx* c, const P& ph, const LoopLaunch& L,
     unsigned grid = (unsigned)std::min<int64_t>(bv.nblk, (int64_t)1 << 30);
     kern<<<grid, block, smem, c->stream>>>(ph, L.m0, L.m1, L.E, bv, tg);
     return c->launched("block-atomic");
-  }
-  for (int32_t col = 0; col < bp->ncolours; col++) {
-    BlockView bv;
-    bv.cblocks = bp->cblocks + bp->coff[col];
-    bv.nblk = bp->coff[col + 1] - bp->coff[col];
-    bv.part = bp->part;
-    bv.ucap = ucap;
-    bv.bn_off = bp->bn_off;
-    bv.bnodes = bp->bnodes;
-    bv.eloc = bp->eloc;
-    bv.lrow = bp->lrow;
-    bv.lent = bp->lent;
-    if (bv.nblk == 0) continue;
-    unsigned grid = (unsigned)std::min<int64_t>(bv.nblk, (int64_t)1 << 30);
-    kern<<<grid, block, smem, c->stream>>>(ph, L.m0, L.m1, L.E, bv, tg);
-    if ((rc = c->launched("colour"))) return rc;
+  } else {
+    for (int32_t col = 0; col < bp->ncolours; col++) {
+      BlockView bv;
+      bv.cblocks = bp->cblocks + bp->coff[col];
+      bv.nblk = bp->coff[col + 1] - bp->coff[col];
+      bv.part = bp->part;
+      bv.ucap = ucap;
+      bv.bn_off = bp->bn_off;
+      bv.bnodes = bp->bnodes;
+      bv.eloc = bp->eloc;
+      bv.lrow = bp->lrow;
+      bv.lent = bp->lent;
+      if (bv.nblk == 0) continue;
+      unsigned grid = (unsigned)std::min<int64_t>(bv.nblk, (int64_t)1 << 30);
+      kern<<<grid, block, smem, c->stream>>>(ph, L.m0, L.m1, L.E, bv, tg);
+      if ((rc = c->launched("colour"))) return rc;
+    }
   }
   return OP2B_OK;
 }

@@ -209,6 +209,40 @@ def fd_picks(count: int, upper: int, seed: int = 0) -> np.ndarray:
     return np.minimum((u * upper).astype(np.int64), upper - 1)
 
 
+def random_graph_mesh(num_nodes: int, mean_degree: float = 9.0, seed: int = 0,
+                      isolated: int = 3) -> Lattice:
+    """An irregular edge set on random points, for parity on uneven degrees.
+
+    Points uniform in the unit cube (stream 1).  Each node draws a
+    Poisson-like number of partners (0 to about 3x the mean) among nodes
+    drawn uniformly (stream 2), so degrees vary widely, some node pairs
+    repeat and both orientations occur; the last `isolated` nodes get no
+    edges.  Normals: random directions with areas U[0.1, 1] (stream 2);
+    dx = x_j - x_i; volumes U[0.5, 1.5] (stream 4).  Not a valid dual
+    mesh: for exercising the loops on an uneven graph only.
+    """
+    N = num_nodes
+    coords = uniform(seed, STREAM_JITTER, np.arange(3 * N, dtype=np.uint64)).reshape(N, 3)
+    r = uniform(seed, STREAM_NORMAL, np.arange(N, dtype=np.uint64))
+    deg = np.minimum((-np.log1p(-r) * mean_degree / 2).astype(np.int64), int(3 * mean_degree))
+    live = N - isolated
+    deg[live:] = 0
+    i = np.repeat(np.arange(N), deg)
+    u = uniform(seed, STREAM_NORMAL, np.arange(N, N + i.size, dtype=np.uint64))
+    j = np.minimum((u * (live - 1)).astype(np.int64), live - 2)
+    j = j + (j >= i)  # never a self loop
+    E = i.size
+    w = uniform(seed, STREAM_NORMAL, np.arange(N + E, N + 5 * E, dtype=np.uint64)).reshape(E, 4)
+    d = 2.0 * w[:, :3] - 1.0
+    d /= np.maximum(np.linalg.norm(d, axis=1, keepdims=True), 1e-3)
+    nrm = d * (0.1 + 0.9 * w[:, 3:4])
+    edge = np.stack([i, j], axis=1).astype(np.int32)
+    vol = 0.5 + uniform(seed, STREAM_VOLUME, np.arange(N, dtype=np.uint64))
+    return Lattice(n=0, coords=coords, edge=edge, normal=nrm,
+                   dx=coords[j] - coords[i], volume=vol, perturbed=True, seed=seed,
+                   new_of_lattice=np.arange(N))
+
+
 def hand_cube_mesh():
     """The 8-node unit-cube mesh: corners, 12 cube edges, n = edge direction.
 

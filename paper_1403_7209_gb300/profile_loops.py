@@ -24,6 +24,9 @@ def main():
     ap.add_argument("--loops", default="flux2")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--tune-cache", default="")
+    ap.add_argument("--force", action="append", default=[],
+                    help="fix a strategy instead of tuning: loop:prec:strategy:block:part:staged "
+                         "(loop and strategy as numbers of include/op2b.h)")
     args = ap.parse_args()
     import torch
     from paper_1403_7209_gb300 import meshgen, op2b as L
@@ -38,6 +41,8 @@ def main():
     for loop in range(L.NUM_LOOPS):
         for prec in (0, 1):
             s.set_strategy(loop, prec, L.STRAT_AUTO)
+    for f in args.force:
+        s.set_strategy(*[int(x) for x in f.split(":")])
     s.time_step(0.5)
     L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
     s.t["lam"].normal_()

@@ -24,3 +24,14 @@ extern "C" int newton_check(const double* x, double* out, int64_t n, int which) 
   k_newton<<<(unsigned)((n + 255) / 256), 256>>>(x, out, n, which);
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
 }
+
+__global__ void k_f64_exact(const unsigned* bits, double* out, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = op2b::f64_exact(__int_as_float((int)bits[i]));
+}
+
+extern "C" int f64_exact_check(const unsigned* bits, double* out, int64_t n) {
+  if (n <= 0) return 0;
+  k_f64_exact<<<(unsigned)((n + 255) / 256), 256>>>(bits, out, n);
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}

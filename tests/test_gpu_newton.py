@@ -54,3 +54,21 @@ def test_seedable_range(newton):
                   np.inf, np.nan])
     s = run(newton, x, 5)
     assert s.tolist() == [0, 0, 0, 0, 0, 1, 1, 1, 0, 0]
+
+
+def test_integer_float_to_double_is_exact(newton):
+    import torch
+    rng = np.random.default_rng(1)
+    bits = np.concatenate([rng.integers(0, 2 ** 32, 4_000_000, dtype=np.uint64),
+                           np.array([0, 0x80000000, 1, 0x80000001, 0x007fffff, 0x00800000,
+                                     0x7f7fffff, 0x7f800000, 0xff800000, 0x7fc00001],
+                                    dtype=np.uint64)]).astype(np.uint32)
+    newton.f64_exact_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    bt = torch.from_numpy(bits.view(np.int32)).cuda()
+    out = torch.empty(bits.size, dtype=torch.float64, device="cuda")
+    assert newton.f64_exact_check(bt.data_ptr(), out.data_ptr(), bits.size) == 0
+    got = out.cpu().numpy()
+    with np.errstate(invalid="ignore"):
+        ref = bits.view(np.float32).astype(np.float64)
+    same = (got.view(np.uint64) == ref.view(np.uint64)) | (np.isnan(got) & np.isnan(ref))
+    assert np.all(same)

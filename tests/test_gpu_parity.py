@@ -356,3 +356,34 @@ def test_argument_validation(gpu_lib, mesh16):
         L.op2b_edge_flux(c, s.a_f1, 3)
     assert e.value.code == L.EINVAL
     s.close()
+
+
+@pytest.mark.parametrize("renumber", ["none", "rcm"])
+def test_irregular_graph_all_strategies(gpu_lib, renumber):
+    """Uneven degrees (0 to ~30), isolated nodes, repeated pairs, both
+    orientations: every strategy against the oracle, forward and adjoint."""
+    m = meshgen.random_graph_mesh(3000, seed=4)
+    q = meshgen.flow_state(m, seed=4)
+    lam = meshgen.adjoint_seed(m.num_nodes, seed=4)
+    R, G, Ra = oracle.residual(2, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
+    R1, _, R1a = oracle.residual(1, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
+    qb, nb = oracle.residual_reverse(2, m.edge, q, m.normal, m.dx, m.volume, lam)
+    s = make_solver(gpu_lib, m, q, renumber=renumber, adjoint=True, mixed=True)
+    s.load_nodes("lam", lam)
+    for strat, block, part, staged in ((1, 128, 0, 0), (2, 128, 256, 1), (2, 256, 1024, 0),
+                                       (3, 128, 0, 0), (5, 128, 512, 1), (6, 128, 0, 0)):
+        for loop in range(gpu_lib.NUM_LOOPS):
+            for prec in (0, 1):
+                s.set_strategy(loop, prec, strat, block, part, staged)
+        s.residual(2)
+        assert rel_err(s.fetch_nodes("R"), R, Ra) <= TOL, strat
+        s.flux(1)
+        assert rel_err(s.fetch_nodes("R"), R1, R1a) <= TOL, strat
+        s.adjoint(2)
+        assert _adj_ok(s.fetch_nodes("qbar"), qb), strat
+        assert _adj_ok(s.fetch_edges("nbar"), nb), strat
+        s.sync_shadow()
+        s.residual(2, mixed=True)
+        err = np.max(np.abs(s.fetch_nodes("R") - R), axis=0) / np.max(np.abs(R), axis=0)
+        assert np.all(err <= 1e-5), (strat, err)
+    s.close()

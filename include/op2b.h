@@ -82,7 +82,10 @@ typedef struct {
 #define OP2B_LOOP_FLUX1_ADJ 4
 #define OP2B_LOOP_FLUX2_ADJ 5
 #define OP2B_LOOP_GG_ADJ 6
-#define OP2B_NUM_LOOPS 7
+#define OP2B_LOOP_FLUX1_TAN 7
+#define OP2B_LOOP_FLUX2_TAN 8
+#define OP2B_LOOP_GG_TAN 9
+#define OP2B_NUM_LOOPS 10
 
 /* arithmetic variant of a loop: all-FP64, or FP32 node data and arithmetic
  * (the INC precision is then fixed by the loop: FP64 residuals, FP32
@@ -245,6 +248,25 @@ int op2b_edge_flux_adjoint(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  * n ID READ, qbar 0 INC, qbar 1 INC, nbar ID RW.  All F64. */
 int op2b_green_gauss_adjoint(op2b_ctx ctx, const op2b_arg* args,
                              int32_t nargs, int32_t flags);
+
+/* Tangent-linear (forward-mode) loops: the Jacobian-vector products
+ * dR = dR/dq . qd + dR/dn . nd that Newton-Krylov solvers need (dx and V
+ * fixed).  Non-smooth points as in the adjoint: d|x|/dx = sign(x), 0 at 0;
+ * the max picks the left state on ties.
+ * Green-Gauss tangent: Gd_i += ((qd_i + qd_j) (x) n + (q_i + q_j) (x) nd)/2,
+ *   Gd_j -= the same.  args (8): q 0 READ, q 1 READ, qd 0 READ, qd 1 READ
+ *   (dim 6), n ID READ, nd ID READ (dim 3), Gd 0 INC, Gd 1 INC (dim 18).
+ *   Scale with op2b_grad_scale afterwards, as for G.
+ * Flux tangent: Rd_i += dF, Rd_j -= dF.
+ *   order 1 args (8): q 0, q 1, qd 0, qd 1 (READ), n ID READ, nd ID READ,
+ *     Rd 0 INC, Rd 1 INC.
+ *   order 2 args (13): q 0, q 1, qd 0, qd 1, G 0, G 1, Gd 0, Gd 1 (READ,
+ *     G and Gd scaled), n ID READ, nd ID READ, dx ID READ, Rd 0 INC,
+ *     Rd 1 INC.  All F64. */
+int op2b_green_gauss_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                             int32_t flags);
+int op2b_edge_flux_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                           const op2b_flux_params* prm);
 
 /* ----------------------------------------------------------- node loops
  * Direct loops over the node set (no map). */

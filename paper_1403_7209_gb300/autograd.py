@@ -4,9 +4,10 @@
 state q (6, N) and the edge normals n (3, E) (library numbering, FP64 CUDA
 tensors).  Its backward pass runs the hand-written adjoint edge loops: for
 an incoming gradient lam = dL/dR it returns qbar = lam . dR/dq and
-nbar = lam . dR/dn.  The forward pass keeps the node gradients G (node
-data, 18 values per node); the edge states are recomputed from q, G and n
-instead of being stored.
+nbar = lam . dR/dn.  Forward-mode AD (``torch.autograd.forward_ad``) runs
+the tangent-linear edge loops: dR = dR/dq . qd + dR/dn . nd.  The forward
+pass keeps the node gradients G (node data, 18 values per node); the edge
+states are recomputed from q, G and n instead of being stored.
 """
 from __future__ import annotations
 
@@ -26,7 +27,22 @@ class ResidualFn(torch.autograd.Function):
         s.residual(order)
         ctx.solver, ctx.order = s, order
         ctx.save_for_backward(q, n, G)
+        ctx.save_for_forward(q, n, G)
         return out
+
+    @staticmethod
+    def jvp(ctx, q_t, n_t, solver_t, order_t):
+        s = ctx.solver
+        q, n, G = ctx.saved_tensors
+        s.rebind("q", q.detach().contiguous())
+        s.rebind("n", n.detach().contiguous())
+        s.rebind("G", G)
+        s.rebind("qd", (q_t if q_t is not None else torch.zeros_like(q)).detach().double().contiguous())
+        s.rebind("nd", (n_t if n_t is not None else torch.zeros_like(n)).detach().double().contiguous())
+        Rd = torch.empty_like(s.t["Rd"])
+        s.rebind("Rd", Rd)
+        s.tangent(ctx.order, recompute_gradient=False)
+        return Rd
 
     @staticmethod
     def backward(ctx, grad_r):

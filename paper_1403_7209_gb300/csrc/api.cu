@@ -20,7 +20,8 @@ void op2b::set_thread_error(const std::string& msg) { g_init_err = msg; }
 #define OP2B_VERSION_STR "op2b 0.1 (sm_103a)"
 
 static const char* kLoopName[OP2B_NUM_LOOPS] = {
-    "green_gauss", "flux1", "flux2", "spectral", "flux1_adj", "flux2_adj", "gg_adj"};
+    "green_gauss", "flux1", "flux2", "spectral", "flux1_adj", "flux2_adj", "gg_adj",
+    "flux1_tan", "flux2_tan", "gg_tan"};
 
 // ------------------------------------------------------------------ Ctx
 namespace op2b {
@@ -924,6 +925,95 @@ extern "C" int op2b_green_gauss_adjoint(op2b_ctx h, const op2b_arg* a, int32_t n
   L.direct = D(c, a[7]).ptr;
   L.lddirect = D(c, a[7]).ld;
   return run_loop(c, L, flags, &D(c, a[5]), nullptr, &D(c, a[7]));
+}
+
+extern "C" int op2b_green_gauss_tangent(op2b_ctx h, const op2b_arg* a, int32_t nargs, int32_t flags) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  static const Spec sp[8] = {{0, OP2B_READ, 6, 'D'},  {1, OP2B_READ, 6, 'D'},  {0, OP2B_READ, 6, 'D'},
+                             {1, OP2B_READ, 6, 'D'},  {-1, OP2B_READ, 3, 'D'}, {-1, OP2B_READ, 3, 'D'},
+                             {0, OP2B_INC, 18, 'D'},  {1, OP2B_INC, 18, 'D'}};
+  Checked ck;
+  int rc = check_args(c, "green_gauss_tangent", a, nargs, sp, 8, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = OP2B_LOOP_GG_TAN;
+  L.prec = OP2B_PREC_F64;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  L.qd = D(c, a[2]).ptr;
+  L.ldqd = D(c, a[2]).ld;
+  L.n = D(c, a[4]).ptr;
+  L.ldn = D(c, a[4]).ld;
+  L.nd = D(c, a[5]).ptr;
+  L.ldnd = D(c, a[5]).ld;
+  L.t0 = D(c, a[6]).ptr;
+  L.ldt0 = D(c, a[6]).ld;
+  return run_loop(c, L, flags, &D(c, a[6]), nullptr, nullptr);
+}
+
+extern "C" int op2b_edge_flux_tangent(op2b_ctx h, const op2b_arg* a, int32_t nargs,
+                                      const op2b_flux_params* p) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!p || (p->order != 1 && p->order != 2)) return c.fail(OP2B_EINVAL, "edge_flux_tangent: order must be 1 or 2");
+  if (!(p->gamma > 1.0) || !(p->eps_lim > 0.0))
+    return c.fail(OP2B_EINVAL, "edge_flux_tangent: need gamma > 1, eps > 0");
+  static const Spec s1[8] = {{0, OP2B_READ, 6, 'D'},  {1, OP2B_READ, 6, 'D'},  {0, OP2B_READ, 6, 'D'},
+                             {1, OP2B_READ, 6, 'D'},  {-1, OP2B_READ, 3, 'D'}, {-1, OP2B_READ, 3, 'D'},
+                             {0, OP2B_INC, 6, 'D'},   {1, OP2B_INC, 6, 'D'}};
+  static const Spec s2[13] = {{0, OP2B_READ, 6, 'D'},   {1, OP2B_READ, 6, 'D'},  {0, OP2B_READ, 6, 'D'},
+                              {1, OP2B_READ, 6, 'D'},   {0, OP2B_READ, 18, 'D'}, {1, OP2B_READ, 18, 'D'},
+                              {0, OP2B_READ, 18, 'D'},  {1, OP2B_READ, 18, 'D'}, {-1, OP2B_READ, 3, 'D'},
+                              {-1, OP2B_READ, 3, 'D'},  {-1, OP2B_READ, 3, 'D'}, {0, OP2B_INC, 6, 'D'},
+                              {1, OP2B_INC, 6, 'D'}};
+  Checked ck;
+  int rc = p->order == 1 ? check_args(c, "edge_flux_tangent", a, nargs, s1, 8, &ck)
+                         : check_args(c, "edge_flux_tangent", a, nargs, s2, 13, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = p->order == 1 ? OP2B_LOOP_FLUX1_TAN : OP2B_LOOP_FLUX2_TAN;
+  L.prec = OP2B_PREC_F64;
+  L.order = p->order;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.gamma = p->gamma;
+  L.eps = p->eps_lim;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  L.qd = D(c, a[2]).ptr;
+  L.ldqd = D(c, a[2]).ld;
+  const op2b_arg* R;
+  if (p->order == 1) {
+    L.n = D(c, a[4]).ptr;
+    L.ldn = D(c, a[4]).ld;
+    L.nd = D(c, a[5]).ptr;
+    L.ldnd = D(c, a[5]).ld;
+    R = &a[6];
+  } else {
+    L.G = D(c, a[4]).ptr;
+    L.ldG = D(c, a[4]).ld;
+    L.Gd = D(c, a[6]).ptr;
+    L.ldGd = D(c, a[6]).ld;
+    L.n = D(c, a[8]).ptr;
+    L.ldn = D(c, a[8]).ld;
+    L.nd = D(c, a[9]).ptr;
+    L.ldnd = D(c, a[9]).ld;
+    L.dx = D(c, a[10]).ptr;
+    L.lddx = D(c, a[10]).ld;
+    R = &a[11];
+  }
+  L.t0 = D(c, *R).ptr;
+  L.ldt0 = D(c, *R).ld;
+  return run_loop(c, L, p->flags, &D(c, *R), nullptr, nullptr);
 }
 
 // ------------------------------------------------------------ node loops

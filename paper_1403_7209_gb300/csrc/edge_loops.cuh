@@ -278,6 +278,89 @@ struct BodyGGAdj {
   }
 };
 
+// Tangent of Green-Gauss: v = q (6), qd (6);
+// oi[3k+d] = (qd_i + qd_j)_k n_d / 2 + (q_i + q_j)_k nd_d / 2, node j gets -oi.
+struct BodyGGTan {
+  using TN = double;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = 12, OUT = 18, MODE = MODE_ANTI, DIM0 = 18;
+  const double* q;
+  int64_t ldq;
+  const double* qd;
+  int64_t ldqd;
+  const double* n;
+  int64_t ldn;
+  const double* nd;
+  int64_t ldnd;
+  __device__ __forceinline__ void load(int64_t i, double* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[6 + k] = ldro(qd + k * ldqd + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
+                                       double* oi, double*) const {
+    const double h[3] = {0.5 * ldro(n + e), 0.5 * ldro(n + ldn + e), 0.5 * ldro(n + 2 * ldn + e)};
+    const double hd[3] = {0.5 * ldro(nd + e), 0.5 * ldro(nd + ldnd + e),
+                          0.5 * ldro(nd + 2 * ldnd + e)};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const double sv = vi[k] + vj[k], sd = vi[6 + k] + vj[6 + k];
+#pragma unroll
+      for (int d = 0; d < 3; d++) oi[3 * k + d] = fma(sd, h[d], sv * hd[d]);
+    }
+  }
+};
+
+// Tangent of the flux loop.  v = q (6), qd (6) [, G (18), Gd (18)].
+template <int ORDER>
+struct BodyFluxTan {
+  using TN = double;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = ORDER == 1 ? 12 : 48;
+  static constexpr int OUT = 6, MODE = MODE_ANTI, DIM0 = 6;
+  const double* q;
+  int64_t ldq;
+  const double* qd;
+  int64_t ldqd;
+  const double* G;
+  int64_t ldG;
+  const double* Gd;
+  int64_t ldGd;
+  const double* n;
+  int64_t ldn;
+  const double* nd;
+  int64_t ldnd;
+  const double* dx;
+  int64_t lddx;
+  Gas<double> g;
+  __device__ __forceinline__ void load(int64_t i, double* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[6 + k] = ldro(qd + k * ldqd + i);
+    if constexpr (ORDER == 2) {
+#pragma unroll
+      for (int c = 0; c < 18; c++) v[12 + c] = ldro(G + c * ldG + i);
+#pragma unroll
+      for (int c = 0; c < 18; c++) v[30 + c] = ldro(Gd + c * ldGd + i);
+    }
+  }
+  __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
+                                       double* oi, double*) const {
+    const double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
+    const double ndx = ldro(nd + e), ndy = ldro(nd + ldnd + e), ndz = ldro(nd + 2 * ldnd + e);
+    if constexpr (ORDER == 1) {
+      rusanov_tangent_f64(vi, vi + 6, vj, vj + 6, nx, ny, nz, ndx, ndy, ndz, g, oi);
+    } else {
+      flux2_tan_f64(vi, vj, ldro(dx + e), ldro(dx + lddx + e), ldro(dx + 2 * lddx + e), nx, ny,
+                    nz, ndx, ndy, ndz, g, oi);
+    }
+  }
+};
+
 // --------------------------------------------------------------- strategies
 
 // (1) one thread per edge, atomic adds into the INC targets.

@@ -535,4 +535,122 @@ __device__ __forceinline__ void flux2_adj_f64(const double* vi,
   }
 }
 
+// ------------------------------------------------------ tangent (forward)
+// Forward-mode linearisation of the flux in the direction (qd, Gd, nd):
+// Fd = dF/dq . qd + dF/dG . Gd + dF/dn . nd (dx fixed).  Non-smooth points
+// as in the reverse sweep: d|x|/dx = sign(x) (0 at 0), the max picks L on
+// ties.
+
+// one side: f(q).n and its tangent, the wave speed and its tangent
+__device__ __forceinline__ void side_tangent_f64(
+    const double* q, const double* qd, double nx, double ny, double nz,
+    double ndx, double ndy, double ndz, double rr, double nn, double nnd,
+    const Gas<double>& g, double* f, double* fd, double& lam, double& lamd) {
+  const double mn = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
+  const double mnd = fma(qd[3], nz, fma(qd[2], ny, fma(qd[1], nx,
+                     fma(q[3], ndz, fma(q[2], ndy, q[1] * ndx)))));
+  const double un = mn * rr;
+  const double und = fma(-un, qd[0], mnd) * rr;  // (mnd - un rhod) / rho
+  const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
+  const double mmd = 2.0 * fma(q[3], qd[3], fma(q[2], qd[2], q[1] * qd[1]));
+  const double hgm1 = 0.5 * g.gm1;
+  const double p = fma(-hgm1 * mm, rr, g.gm1 * q[4]);
+  // pd = (gamma-1) (Ed - mmd/(2 rho) + mm rhod / (2 rho^2))
+  const double pd = g.gm1 * qd[4] + hgm1 * rr * fma(mm * rr, qd[0], -mmd);
+  const double a2 = g.gamma * p * rr;
+  const double ra = seedable(a2) ? rsqrt2(a2) : rsqrt(a2);
+  const double a = a2 * ra;
+  // 2 a ad = (gamma pd - a^2 rhod) / rho
+  const double ad = 0.5 * ra * rr * fma(-a2, qd[0], g.gamma * pd);
+  lam = fabs(un) + a * nn;
+  lamd = sign_times(un, und) + fma(ad, nn, a * nnd);
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    f[k] = q[k] * un;
+    fd[k] = fma(qd[k], un, q[k] * und);
+  }
+  const double n3[3] = {nx, ny, nz}, nd3[3] = {ndx, ndy, ndz};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    f[1 + d] = fma(p, n3[d], f[1 + d]);
+    fd[1 + d] = fma(pd, n3[d], fma(p, nd3[d], fd[1 + d]));
+  }
+  f[4] = fma(p, un, f[4]);
+  fd[4] = fma(pd, un, fma(p, und, fd[4]));
+}
+
+// Fd of the Rusanov flux for face states (qL, qR) with tangents (qLd, qRd)
+__device__ __forceinline__ void rusanov_tangent_f64(
+    const double* qL, const double* qLd, const double* qR, const double* qRd,
+    double nx, double ny, double nz, double ndx, double ndy, double ndz,
+    const Gas<double>& g, double* Fd) {
+  const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
+  const double rn = seedable(nn2) ? rsqrt2(nn2) : rsqrt(nn2);
+  const double nn = nn2 * rn;
+  const double nnd = fma(nz, ndz, fma(ny, ndy, nx * ndx)) * rn;
+  double rho[2] = {qL[0], qR[0]}, rr[2];
+  batch_reciprocal<2>(rho, 1.0, rr);
+  double fL[6], fLd[6], fR[6], fRd[6], lL, lLd, lR, lRd;
+  side_tangent_f64(qL, qLd, nx, ny, nz, ndx, ndy, ndz, rr[0], nn, nnd, g, fL, fLd, lL, lLd);
+  side_tangent_f64(qR, qRd, nx, ny, nz, ndx, ndy, ndz, rr[1], nn, nnd, g, fR, fRd, lR, lRd);
+  const bool left = __double_as_longlong(lL) >= __double_as_longlong(lR);
+  const double hs = 0.5 * (left ? lL : lR), hsd = 0.5 * (left ? lLd : lRd);
+#pragma unroll
+  for (int k = 0; k < 6; k++)
+    Fd[k] = fma(0.5, fLd[k] + fRd[k], -fma(hsd, qR[k] - qL[k], hs * (qRd[k] - qLd[k])));
+}
+
+// Tangent of the second-order flux.  vi, vj: q (6), qd (6), G (18), Gd (18).
+__device__ __forceinline__ void flux2_tan_f64(const double* vi, const double* vj,
+                                              double dx, double dy, double dz,
+                                              double nx, double ny, double nz,
+                                              double ndx, double ndy, double ndz,
+                                              const Gas<double>& g, double* Fd) {
+  const double *qi = vi, *qid = vi + 6, *Gi = vi + 12, *Gid = vi + 30;
+  const double *qj = vj, *qjd = vj + 6, *Gj = vj + 12, *Gjd = vj + 30;
+  double a[12], ad[12], num[12], den[12], rd[12], bk[6], bdk[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const double b = qj[k] - qi[k];
+    bk[k] = b;
+    bdk[k] = qjd[k] - qid[k];
+    a[2 * k] = fma(Gi[3 * k + 2], dz, fma(Gi[3 * k + 1], dy, Gi[3 * k] * dx));
+    a[2 * k + 1] = fma(Gj[3 * k + 2], dz, fma(Gj[3 * k + 1], dy, Gj[3 * k] * dx));
+    ad[2 * k] = fma(Gid[3 * k + 2], dz, fma(Gid[3 * k + 1], dy, Gid[3 * k] * dx));
+    ad[2 * k + 1] = fma(Gjd[3 * k + 2], dz, fma(Gjd[3 * k + 1], dy, Gjd[3 * k] * dx));
+    const double b2e = fma(b, b, g.two_eps);
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const double x = a[2 * k + sd];
+      num[2 * k + sd] = (x + b) * fma(x, b, g.eps);
+      den[2 * k + sd] = fma(x, x, b2e);
+    }
+  }
+  batch_reciprocal<12>(den, 1.0, rd);
+  double qL[6], qR[6], qLd[6], qRd[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const double b = bk[k], bd = bdk[k];
+    const double be = fma(b, b, g.eps);
+    const double b2 = b + b;
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const int c = 2 * k + sd;
+      const double x = a[c];
+      const double phi = num[c] * rd[c];
+      const double pa = fma(x + x, b - phi, be) * rd[c];
+      const double pb = fma(b2, x - phi, fma(x, x, g.eps)) * rd[c];
+      const double phid = fma(pa, ad[c], pb * bd);
+      if (sd == 0) {
+        qL[k] = fma(0.5, phi, qi[k]);
+        qLd[k] = fma(0.5, phid, qid[k]);
+      } else {
+        qR[k] = fma(-0.5, phi, qj[k]);
+        qRd[k] = fma(-0.5, phid, qjd[k]);
+      }
+    }
+  }
+  rusanov_tangent_f64(qL, qLd, qR, qRd, nx, ny, nz, ndx, ndy, ndz, g, Fd);
+}
+
 }  // namespace op2b

@@ -84,6 +84,9 @@ struct LoopLaunch {
   const void *q = nullptr, *G = nullptr, *n = nullptr, *dx = nullptr,
              *lam = nullptr, *Gb = nullptr;
   int64_t ldq = 0, ldG = 0, ldn = 0, lddx = 0, ldl = 0, ldGb = 0;
+  // tangent directions
+  const void *qd = nullptr, *Gd = nullptr, *nd = nullptr;
+  int64_t ldqd = 0, ldGd = 0, ldnd = 0;
   // INC targets (first and second dat) and direct output
   void *t0 = nullptr, *t1 = nullptr, *direct = nullptr;
   int64_t ldt0 = 0, ldt1 = 0, lddirect = 0;
@@ -99,7 +102,8 @@ void set_thread_error(const std::string& msg);
 // Run one edge loop with strategy s (plans and scratch taken from ctx).
 // loops_f64.cu: GREEN_GAUSS, FLUX1, FLUX2, SPECTRAL in FP64;
 // loops_f32.cu: GREEN_GAUSS, FLUX1, FLUX2 with FP32 arithmetic;
-// loops_adj.cu: FLUX1_ADJ, FLUX2_ADJ, GG_ADJ.
+// loops_adj.cu: FLUX1_ADJ, FLUX2_ADJ, GG_ADJ and the tangents FLUX1_TAN,
+// FLUX2_TAN, GG_TAN.
 int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_f32(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_adj(Ctx* c, const LoopLaunch& L, const Strategy& s);

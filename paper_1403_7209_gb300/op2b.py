@@ -23,7 +23,8 @@ READ, WRITE, RW, INC = 1, 2, 3, 4
 F64, F32, I32 = 0, 1, 2
 ID = -1
 LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
-LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ, NUM_LOOPS = 4, 5, 6, 7
+LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ = 4, 5, 6
+LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, NUM_LOOPS = 7, 8, 9, 10
 PREC_F64, PREC_F32 = 0, 1
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
 STRAT_BLOCK_ATOMIC, STRAT_OWNER = 5, 6
@@ -100,6 +101,9 @@ _SIGS = {
     "op2b_edge_flux_adjoint": (ctypes.c_int, [_P, _PARG, _I32,
                                               ctypes.POINTER(FluxParams)]),
     "op2b_green_gauss_adjoint": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
+    "op2b_green_gauss_tangent": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
+    "op2b_edge_flux_tangent": (ctypes.c_int, [_P, _PARG, _I32,
+                                              ctypes.POINTER(FluxParams)]),
     "op2b_grad_scale": (ctypes.c_int, [_P, _I32, _I32]),
     "op2b_grad_scale_adjoint": (ctypes.c_int, [_P, _I32, _I32]),
     "op2b_time_step": (ctypes.c_int, [_P, _I32, _I32, _D, _I32]),
@@ -280,6 +284,18 @@ def op2b_edge_flux_adjoint(ctx, args, order: int, gamma: float = 1.4,
 def op2b_green_gauss_adjoint(ctx, args, flags: int = 0):
     a, n = _args(args)
     _check(load().op2b_green_gauss_adjoint(ctx, a, n, flags), ctx)
+
+
+def op2b_green_gauss_tangent(ctx, args, flags: int = 0):
+    a, n = _args(args)
+    _check(load().op2b_green_gauss_tangent(ctx, a, n, flags), ctx)
+
+
+def op2b_edge_flux_tangent(ctx, args, order: int, gamma: float = 1.4,
+                           eps_lim: float = 1e-12, flags: int = 0):
+    a, n = _args(args)
+    p = FluxParams(order, flags, gamma, eps_lim)
+    _check(load().op2b_edge_flux_tangent(ctx, a, n, ctypes.byref(p)), ctx)
 
 
 def op2b_grad_scale(ctx, G: int, V: int):

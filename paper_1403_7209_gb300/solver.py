@@ -29,7 +29,7 @@ class EdgeSolver:
     (N, 3)); :meth:`fetch_nodes` and :meth:`fetch_edges` return data in the
     caller's numbering again.
     ``mixed`` adds the FP32 shadows used by the mixed-precision path;
-    ``adjoint`` the adjoint dats.
+    ``adjoint`` the adjoint and tangent (Jacobian-vector product) dats.
     """
 
     def __init__(self, edge, normal, dx, volume, q=None, device: int = 0,
@@ -80,6 +80,10 @@ class EdgeSolver:
             node("qbar", 6)
             node("Gbar", 18)
             edgd("nbar", 3)
+            node("qd", 6)
+            node("Gd", 18)
+            node("Rd", 6)
+            edgd("nd", 3)
         self.perm = np.arange(self.N, dtype=np.int64)   # new id of old node
         self.order = np.arange(self.E, dtype=np.int64)  # old edge of new slot
         if renumber == "rcb":
@@ -169,6 +173,13 @@ class EdgeSolver:
                           ind("G", 0, R), ind("G", 1, R), dr("n", R), dr("dx", R),
                           ind("qbar", 0, I), ind("qbar", 1, I), ind("Gbar", 0, I),
                           ind("Gbar", 1, I), dr("nbar", W)]
+            self.a_ggt = [ind("q", 0, R), ind("q", 1, R), ind("qd", 0, R), ind("qd", 1, R),
+                          dr("n", R), dr("nd", R), ind("Gd", 0, I), ind("Gd", 1, I)]
+            self.a_ft1 = [ind("q", 0, R), ind("q", 1, R), ind("qd", 0, R), ind("qd", 1, R),
+                          dr("n", R), dr("nd", R), ind("Rd", 0, I), ind("Rd", 1, I)]
+            self.a_ft2 = [ind("q", 0, R), ind("q", 1, R), ind("qd", 0, R), ind("qd", 1, R),
+                          ind("G", 0, R), ind("G", 1, R), ind("Gd", 0, R), ind("Gd", 1, R),
+                          dr("n", R), dr("nd", R), dr("dx", R), ind("Rd", 0, I), ind("Rd", 1, I)]
             self.a_gga = [ind("Gbar", 0, R), ind("Gbar", 1, R), ind("q", 0, R), ind("q", 1, R),
                           dr("n", R), ind("qbar", 0, I), ind("qbar", 1, I), dr("nbar", RWa)]
 
@@ -238,6 +249,21 @@ class EdgeSolver:
         L.op2b_edge_flux_adjoint(c, self.a_fa2, 2, self.gamma, self.eps_lim, L.ZERO_INC)
         L.op2b_grad_scale_adjoint(c, self.d["Gbar"], self.d["V"])
         L.op2b_green_gauss_adjoint(c, self.a_gga, 0)
+
+    def tangent(self, order=2, recompute_gradient=True):
+        """Rd = dR/dq . qd + dR/dn . nd (dats qd, nd in, Rd out).
+
+        With ``recompute_gradient=False`` the dat G must hold the gradient of
+        the current q and n."""
+        c = self.ctx
+        if order == 1:
+            L.op2b_edge_flux_tangent(c, self.a_ft1, 1, self.gamma, self.eps_lim, L.ZERO_INC)
+            return
+        if recompute_gradient:
+            self.green_gauss()
+        L.op2b_green_gauss_tangent(c, self.a_ggt, L.ZERO_INC)
+        L.op2b_grad_scale(c, self.d["Gd"], self.d["V"])
+        L.op2b_edge_flux_tangent(c, self.a_ft2, 2, self.gamma, self.eps_lim, L.ZERO_INC)
 
     def reduce(self, name, op):
         """Per-component reduction of dat `name` (op: op2b.RED_*), as a

@@ -246,6 +246,51 @@ def test_autograd_backward_and_dot_product(gpu_lib):
     s.close()
 
 
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("strat", [1, 2, 3, 5, 6])
+def test_tangent_matches_oracle_and_reverse(gpu_lib, mesh16, order, strat):
+    m, q = mesh16
+    qd = meshgen.adjoint_seed(m.num_nodes, stream=meshgen.STREAM_V)
+    nd = meshgen.normal(0, meshgen.STREAM_V, np.arange(3 * m.num_edges, dtype=np.uint64)).reshape(-1, 3)
+    lam = meshgen.adjoint_seed(m.num_nodes)
+    s = make_solver(gpu_lib, m, q, adjoint=True, renumber="rcm")
+    for loop in range(gpu_lib.NUM_LOOPS):
+        s.set_strategy(loop, 0, strat, 128, 256, 1)
+    s.load_nodes("qd", qd)
+    s.load_edges("nd", nd)
+    s.tangent(order)
+    Rd = s.fetch_nodes("Rd")
+    ref = oracle.residual_tangent(order, m.edge, q, m.normal, m.dx, m.volume, qd, nd)
+    assert _adj_ok(Rd, ref)
+    # dot-product test on the GPU: <lam, J v> = <J^T lam, v>
+    s.load_nodes("lam", lam)
+    s.adjoint(order)
+    qb, nb = s.fetch_nodes("qbar"), s.fetch_edges("nbar")
+    lhs, rhs = np.sum(lam * Rd), np.sum(qb * qd) + np.sum(nb * nd)
+    assert abs(lhs - rhs) <= 1e-12 * np.sum(np.abs(lam * Rd))
+    s.close()
+
+
+def test_forward_mode_autograd_runs_the_tangent_loops(gpu_lib):
+    import torch
+    import torch.autograd.forward_ad as fwAD
+    from paper_1403_7209_gb300.autograd import residual
+    m = meshgen.lattice(8)
+    q = meshgen.flow_state(m)
+    s = make_solver(gpu_lib, m, q, adjoint=True)
+    qd = meshgen.adjoint_seed(m.num_nodes, stream=meshgen.STREAM_V)
+    nd = meshgen.normal(0, meshgen.STREAM_V, np.arange(3 * m.num_edges, dtype=np.uint64)).reshape(-1, 3)
+    qt, nt = s.t["q"].clone(), s.t["n"].clone()
+    qdt = torch.from_numpy(np.ascontiguousarray(qd.T)).cuda()
+    ndt = torch.from_numpy(np.ascontiguousarray(nd.T)).cuda()
+    with fwAD.dual_level():
+        R = residual(s, fwAD.make_dual(qt, qdt), fwAD.make_dual(nt, ndt), 2)
+        Rd = fwAD.unpack_dual(R).tangent
+    ref = oracle.residual_tangent(2, m.edge, q, m.normal, m.dx, m.volume, qd, nd)
+    assert _adj_ok(Rd.cpu().numpy().T, ref)
+    s.close()
+
+
 def test_autotuner_picks_and_persists(gpu_lib, mesh16, ref16, tmp_path):
     m, q = mesh16
     s = make_solver(gpu_lib, m, q, renumber="rcm")
@@ -373,8 +418,11 @@ def test_irregular_graph_all_strategies(gpu_lib, renumber):
     for strat, block, part, staged in ((1, 128, 0, 0), (2, 128, 256, 1), (2, 256, 1024, 0),
                                        (3, 128, 0, 0), (5, 128, 512, 1), (6, 128, 0, 0)):
         for loop in range(gpu_lib.NUM_LOOPS):
+            # the adjoint keeps 48 values per edge: at most 256-edge blocks
+            # fit in shared memory (larger ones give ERANGE)
+            lp = min(part, 256) if loop in (gpu_lib.LOOP_FLUX1_ADJ, gpu_lib.LOOP_FLUX2_ADJ) else part
             for prec in (0, 1):
-                s.set_strategy(loop, prec, strat, block, part, staged)
+                s.set_strategy(loop, prec, strat, block, lp, staged)
         s.residual(2)
         assert rel_err(s.fetch_nodes("R"), R, Ra) <= TOL, strat
         s.flux(1)

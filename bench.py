@@ -270,6 +270,56 @@ def adjoint_extra(torch, s, args, stream, E):
             "ms_with_gradient_recompute": rms, "edges_per_s": E / (ams * 1e-3)}
 
 
+def tangent_extra(torch, s, args, stream, E):
+    """Jacobian-vector product (tangent loops, G kept from the forward pass)."""
+    s.t["qd"].normal_()
+    s.t["nd"].normal_()
+    s.residual(2)
+    for _ in range(max(1, args.warmup)):
+        s.tangent(2, recompute_gradient=False)
+    tms = timed(torch, lambda: s.tangent(2, recompute_gradient=False), args.steps, stream)
+    fms = timed(torch, lambda: s.residual(2), args.steps, stream)
+    return {"ms": tms, "forward_residual_ms": fms, "ratio_to_forward": tms / fms,
+            "edges_per_s": E / (tms * 1e-3)}
+
+
+def config0_extra(torch, L, args):
+    """First-order Rusanov residual on the 16^3 lattice (random numbering),
+    the correctness configuration; launch-bound at 36,864 edges, so timed
+    as a captured CUDA graph of 100 loop calls."""
+    from paper_1403_7209_gb300 import meshgen
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    m = meshgen.lattice(16)
+    q = meshgen.flow_state(m)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, stream=st)
+        s.set_strategy(L.LOOP_FLUX1, 0, L.STRAT_AUTO)
+        for _ in range(3):
+            s.flux(1)
+        torch.cuda.synchronize()
+        eager = timed(torch, lambda: s.flux(1), 100, st)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            for _ in range(100):
+                s.flux(1)
+        g.replay()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(st)
+        for _ in range(5):
+            g.replay()
+        ev[1].record(st)
+        torch.cuda.synchronize()
+        graph_ms = ev[0].elapsed_time(ev[1]) / 500
+        strat = L.STRATEGY_NAMES[s.plan_stats(L.LOOP_FLUX1)["strategy"]]
+        s.close()
+    return {"mesh": "16^3 lattice, 4,096 nodes, 36,864 edges, random numbering",
+            "loop": "first-order flux (R zeroed + edge loop)", "strategy": strat,
+            "eager_us": eager * 1e3, "graph_us": graph_ms * 1e3,
+            "edges_per_s_graph": m.num_edges / (graph_ms * 1e-3)}
+
+
 def march_extra(torch, L, s, q, args, stream, steps=50):
     """50-step explicit march in FP64 and in FP32-mixed from the same state;
     relative max-norm state difference per component after the march."""
@@ -438,6 +488,8 @@ def main():
     if not args.no_extras:
         line["mixed"] = mixed_extra(torch, L, s, args, stream, ms, E, N)
         line["adjoint"] = adjoint_extra(torch, s, args, stream, E)
+        line["tangent"] = tangent_extra(torch, s, args, stream, E)
+        line["config0"] = config0_extra(torch, L, args)
         line["march"] = march_extra(torch, L, s, q, args, stream)
         if args.numbering == "rcm":
             line["numbering"] = numbering_extra(torch, L, m, q, args, stream, ms, local)

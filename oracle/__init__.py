@@ -75,6 +75,8 @@ def _load():
                                          P, P, P, P, P],
                 "ora_kink_margin": [I, I64, I64, P, P, P, P, P, D, D, P, P],
                 "ora_reduce": [I64, I, P, I, P],
+                "ora_viscous_flux": [P, P, P, P, P, P, D, D, D, D, P],
+                "ora_viscous": [I64, I64, P, P, P, P, P, D, D, D, D, P, P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -253,6 +255,30 @@ def residual_reverse(order, edge, q, n, dx, V, lam, gamma=GAMMA,
                                  _p(V), gamma, eps, _p(lam), _p(G), _p(Gb),
                                  _p(qb), _p(nb))
     return qb, nb
+
+
+def viscous_flux(qi, qj, Gi, Gj, n, dx, gamma=GAMMA, mu=1e-3, prandtl=0.72,
+                 diff=1e-3):
+    """Viscous flux Fv of one edge (see oracle.c)."""
+    qi, qj = _f64(qi, (6,)), _f64(qj, (6,))
+    Gi, Gj = _f64(Gi, (18,)), _f64(Gj, (18,))
+    n, dx = _f64(n, (3,)), _f64(dx, (3,))
+    F = np.empty(6)
+    _load().ora_viscous_flux(_p(qi), _p(qj), _p(Gi), _p(Gj), _p(n), _p(dx), gamma, mu,
+                             prandtl, diff, _p(F))
+    return F
+
+
+def viscous(edge, q, G, n, dx, gamma=GAMMA, mu=1e-3, prandtl=0.72, diff=1e-3,
+            with_abs=False):
+    """Viscous residual: R_i -= Fv, R_j += Fv over the edges."""
+    edge, q, G, n, dx = _i32(edge), _f64(q), _f64(G), _f64(n), _f64(dx)
+    N, E = q.shape[0], edge.shape[0]
+    R = np.empty((N, 6))
+    Ra = np.empty((N, 6)) if with_abs else None
+    _load().ora_viscous(N, E, _p(edge), _p(q), _p(G), _p(n), _p(dx), gamma, mu, prandtl,
+                        diff, _p(R), _p(Ra))
+    return (R, Ra) if with_abs else R
 
 
 def reduce(x, op):

@@ -228,6 +228,107 @@ void ora_rk_update(int64_t N, const double* q0, const double* R,
       q[NV * i + k] = q0[NV * i + k] - alpha * (dt[i] / V[i]) * R[NV * i + k];
 }
 
+/* ---------------------------------------------------------- viscous flux
+ * Edge-based Navier-Stokes viscous flux (Hydra's `vfluxedge` analogue; the
+ * paper names the loop, Table "loopperfmpi", but not its formula):
+ *  - primitive gradients at each end from the conserved gradients G:
+ *      grad u_d = (grad m_d - u_d grad rho) / rho,
+ *      grad p = (gamma-1)(grad E - u . grad m + |u|^2/2 grad rho),
+ *      grad T = (grad p - T grad rho) / rho   with T = p / rho,
+ *      grad c = G[5] (the conserved passive scalar);
+ *  - face gradient: the average of the two ends, corrected along the edge
+ *      g_f = g_avg + ((phi_j - phi_i) - g_avg . dx) dx / |dx|^2,
+ *    so that g_f . dx equals the jump exactly;
+ *  - face velocity u_f = (u_i + u_j) / 2;
+ *  - stress tau = mu (grad u + grad u^T - 2/3 div u I) (Stokes' hypothesis),
+ *    heat flux coefficient kappa = mu gamma / ((gamma-1) Pr);
+ *  - Fv = (0, tau n, (tau u_f) . n + kappa grad T . n, D grad c . n).
+ * The residual receives -Fv at i and +Fv at j (diffusion is the negative of
+ * an outgoing flux). */
+static void prim_grad(const double q[NV], const double G[NG], double gamma,
+                      double gu[3][3], double gT[3], double gc[3], double* T,
+                      double u[3]) {
+  double rho = q[0];
+  for (int a = 0; a < 3; a++) u[a] = q[1 + a] / rho;
+  double p = pressure(q, gamma);
+  *T = p / rho;
+  for (int d = 0; d < 3; d++) {
+    double grho = G[d];
+    for (int a = 0; a < 3; a++) gu[a][d] = (G[3 * (1 + a) + d] - u[a] * grho) / rho;
+    double udm = u[0] * G[3 + d] + u[1] * G[6 + d] + u[2] * G[9 + d];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double gp = (gamma - 1.0) * (G[12 + d] - udm + 0.5 * uu * grho);
+    gT[d] = (gp - (*T) * grho) / rho;
+    gc[d] = G[15 + d];
+  }
+}
+
+static void face_gradient(const double gi[3], const double gj[3], double jump,
+                          const double dx[3], double gf[3]) {
+  double dd = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+  double ga[3], gdx = 0.0;
+  for (int d = 0; d < 3; d++) {
+    ga[d] = 0.5 * (gi[d] + gj[d]);
+    gdx += ga[d] * dx[d];
+  }
+  for (int d = 0; d < 3; d++) gf[d] = ga[d] + (jump - gdx) * dx[d] / dd;
+}
+
+void ora_viscous_flux(const double qi[NV], const double qj[NV],
+                      const double Gi[NG], const double Gj[NG],
+                      const double n[3], const double dx[3], double gamma,
+                      double mu, double prandtl, double diff, double Fv[NV]) {
+  double gui[3][3], guj[3][3], gTi[3], gTj[3], gci[3], gcj[3], Ti, Tj, ui[3], uj[3];
+  prim_grad(qi, Gi, gamma, gui, gTi, gci, &Ti, ui);
+  prim_grad(qj, Gj, gamma, guj, gTj, gcj, &Tj, uj);
+  double gu[3][3], gT[3], gc[3], uf[3];
+  for (int a = 0; a < 3; a++) {
+    face_gradient(gui[a], guj[a], uj[a] - ui[a], dx, gu[a]);
+    uf[a] = 0.5 * (ui[a] + uj[a]);
+  }
+  face_gradient(gTi, gTj, Tj - Ti, dx, gT);
+  face_gradient(gci, gcj, qj[5] - qi[5], dx, gc);
+  double div = gu[0][0] + gu[1][1] + gu[2][2];
+  double tau[3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      tau[a][b] = mu * (gu[a][b] + gu[b][a] - (a == b ? 2.0 / 3.0 * div : 0.0));
+  double kappa = mu * gamma / ((gamma - 1.0) * prandtl);
+  Fv[0] = 0.0;
+  Fv[4] = 0.0;
+  for (int a = 0; a < 3; a++) {
+    double tn = tau[a][0] * n[0] + tau[a][1] * n[1] + tau[a][2] * n[2];
+    Fv[1 + a] = tn;
+    Fv[4] += tn * uf[a];
+  }
+  Fv[4] += kappa * (gT[0] * n[0] + gT[1] * n[1] + gT[2] * n[2]);
+  Fv[5] = diff * (gc[0] * n[0] + gc[1] * n[1] + gc[2] * n[2]);
+}
+
+/* viscous edge loop: R_i -= Fv, R_j += Fv (R zeroed first); Rabs gets the
+ * sum of |Fv| per node */
+void ora_viscous(int64_t N, int64_t E, const int32_t* edge, const double* q,
+                 const double* G, const double* n, const double* dx,
+                 double gamma, double mu, double prandtl, double diff,
+                 double* R, double* Rabs) {
+  memset(R, 0, sizeof(double) * NV * N);
+  if (Rabs) memset(Rabs, 0, sizeof(double) * NV * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    double F[NV];
+    ora_viscous_flux(q + NV * i, q + NV * j, G + NG * i, G + NG * j, n + 3 * e,
+                     dx + 3 * e, gamma, mu, prandtl, diff, F);
+    for (int k = 0; k < NV; k++) {
+      R[NV * i + k] -= F[k];
+      R[NV * j + k] += F[k];
+      if (Rabs) {
+        Rabs[NV * i + k] += fabs(F[k]);
+        Rabs[NV * j + k] += fabs(F[k]);
+      }
+    }
+  }
+}
+
 /* Global reductions over the rows of an (n x dim) node-major array, per
  * component: op 0 sum, 1 Euclidean norm sqrt(sum x^2), 2 max |x|, 3 min x
  * (the residual norms and the global time step of an explicit solver). */

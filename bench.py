@@ -40,6 +40,14 @@ BYTES_PER_EDGE_F32 = {"gg": 8 + 12 + (24 + 72) / 9, "flux2": 8 + 12 + 12 + (24 +
 # FP64 operations per edge of the flux2 definition (reconstruction 198 +
 # Rusanov 97), each add, multiply, divide and square root counted once.
 FLOPS_PER_EDGE_FLUX2 = 295.0
+# Viscous flux edge loop: per edge the map (8), n and dx (48), and per node
+# (9 edges per node) W read (160) and R read + write (96); the node pass
+# reads q and G (192) and writes W (160) per node.  FP64 operations per
+# edge of the loop body as written (multiply-add = 2, the reciprocal = 1).
+BYTES_PER_EDGE_VISC = {"prims": 352 / 9, "visc": 8 + 48 + (160 + 96) / 9}
+BYTES_PER_EDGE_VISC_F32 = {"prims": 176 / 9, "visc": 8 + 24 + (80 + 96) / 9}
+FLOPS_PER_EDGE_VISC = 146.0
+VISC_COEFFS = (1.0e-3, 0.72, 1.0e-3)  # mu, Prandtl number, scalar diffusivity
 # DRAM bytes per edge of the FP64 flux2 kernel (atomic strategy) from an ncu
 # capture on the 60^3 lattice (dram__bytes_read.sum + dram__bytes_write.sum =
 # 170.7 MB over 1,944,000 edges; profiles/ncu_edge_loops_n60.md), scaled to a
@@ -283,6 +291,68 @@ def tangent_extra(torch, s, args, stream, E):
             "edges_per_s": E / (tms * 1e-3)}
 
 
+def viscous_extra(torch, L, m, q, args, stream, device, E):
+    """Navier-Stokes residual: the viscous node pass and edge loop alone
+    (FP64 and FP32-mixed) and the whole stage with them (Green-Gauss,
+    scaling, limited inviscid flux, viscous flux, update)."""
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    sv = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device,
+                    renumber=args.numbering, mixed=True, stream=stream, viscous=VISC_COEFFS)
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        L.op2b_load_tuning(sv.ctx, args.tune_cache)
+    for loop in range(L.NUM_LOOPS):
+        for prec in (0, 1):
+            sv.set_strategy(loop, prec, L.STRAT_AUTO)
+    sv.time_step(0.5)
+    L.op2b_dat_copy(sv.ctx, sv.d["q0"], sv.d["q"])
+    sv.sync_shadow()
+    mu, pr, diff = VISC_COEFFS
+    out = {"coefficients": {"mu": mu, "prandtl": pr, "diff": diff}}
+    hbm, _ = read_peaks()
+    for tag, mixed in (("fp64", False), ("mixed", True)):
+        sv.residual(2, mixed=mixed)  # tunes every loop of the stage
+        q_, G_, W_ = ("q32", "G32", "W32") if mixed else ("q", "G", "W")
+        args_v = sv.a_vf32 if mixed else sv.a_vf
+
+        def prims():
+            L.op2b_viscous_prims(sv.ctx, sv.d[q_], sv.d[G_], sv.d[W_], sv.gamma)
+
+        def visc():
+            L.op2b_viscous_flux(sv.ctx, args_v, sv.gamma, mu, pr, diff, 0)
+        for _ in range(max(1, args.warmup)):
+            prims()
+            visc()
+        pms = timed(torch, prims, args.steps, stream)
+        vms = timed(torch, visc, args.steps, stream)
+        sms = timed(torch, lambda: sv.stage(0.25, 2, mixed=mixed), args.steps, stream)
+        bpe = BYTES_PER_EDGE_VISC_F32 if mixed else BYTES_PER_EDGE_VISC
+        r = {"prims_ms": pms, "visc_ms": vms, "ns_stage_ms": sms,
+             "ns_stage_edges_per_s": E / (sms * 1e-3),
+             "visc_strategy": L.STRATEGY_NAMES[sv.plan_stats(L.LOOP_VISCOUS, int(mixed))["strategy"]],
+             "visc_gbs": bpe["visc"] * E / (vms * 1e-3) / 1e9,
+             "visc_hbm_frac": bpe["visc"] * E / (vms * 1e-3) / 1e9 / hbm,
+             "prims_gbs": bpe["prims"] * E / (pms * 1e-3) / 1e9}
+        if not mixed:
+            ach = FLOPS_PER_EDGE_VISC * E / (vms * 1e-3) / 1e12
+            r["visc_fp64_tflops"] = ach
+            r["visc_fp64_frac"] = ach / FP64_PEAK_TFLOPS
+        out[tag] = r
+    # error of the mixed viscous loop against the FP64 one on one state
+    sv.load_nodes("q", q)
+    sv.sync_shadow()
+    sv.green_gauss()
+    sv.viscous_flux(zero=True)
+    R64 = sv.t["R"][:, :sv.N].clone()
+    sv.green_gauss(mixed=True)
+    sv.viscous_flux(mixed=True, zero=True)
+    R32 = sv.t["R"][:, :sv.N].clone()
+    out["mixed_visc_rel_err_per_component"] = (
+        (R32 - R64)[1:].abs().amax(dim=1) / R64[1:].abs().amax(dim=1)).cpu().tolist()
+    out["fp64_ns_stage_vs_euler_stage"] = None
+    sv.close()
+    return out
+
+
 def config0_extra(torch, L, args):
     """First-order Rusanov residual on the 16^3 lattice (random numbering),
     the correctness configuration; launch-bound at 36,864 edges, so timed
@@ -489,6 +559,8 @@ def main():
         line["mixed"] = mixed_extra(torch, L, s, args, stream, ms, E, N)
         line["adjoint"] = adjoint_extra(torch, s, args, stream, E)
         line["tangent"] = tangent_extra(torch, s, args, stream, E)
+        line["viscous"] = viscous_extra(torch, L, m, q, args, stream, local, E)
+        line["viscous"]["fp64_ns_stage_vs_euler_stage"] = line["viscous"]["fp64"]["ns_stage_ms"] / ms
         line["config0"] = config0_extra(torch, L, args)
         line["march"] = march_extra(torch, L, s, q, args, stream)
         if args.numbering == "rcm":

@@ -85,7 +85,8 @@ typedef struct {
 #define OP2B_LOOP_FLUX1_TAN 7
 #define OP2B_LOOP_FLUX2_TAN 8
 #define OP2B_LOOP_GG_TAN 9
-#define OP2B_NUM_LOOPS 10
+#define OP2B_LOOP_VISCOUS 10
+#define OP2B_NUM_LOOPS 11
 
 /* arithmetic variant of a loop: all-FP64, or FP32 node data and arithmetic
  * (the INC precision is then fixed by the loop: FP64 residuals, FP32
@@ -123,6 +124,17 @@ typedef struct {
   double gamma;   /* ratio of specific heats */
   double eps_lim; /* van Albada epsilon (absolute) */
 } op2b_flux_params;
+
+/* coefficients of the viscous flux (op2b_viscous_flux) */
+typedef struct {
+  int32_t flags;    /* OP2B_ZERO_INC */
+  int32_t reserved; /* 0 */
+  double gamma;     /* ratio of specific heats (> 1) */
+  double mu;        /* dynamic viscosity (>= 0) */
+  double prandtl;   /* Prandtl number (> 0); heat conductivity
+                       kappa = mu gamma / ((gamma - 1) prandtl) */
+  double diff;      /* diffusivity of the passive scalar (>= 0) */
+} op2b_visc_params;
 
 typedef struct {
   int32_t strategy, block, part, staged; /* what the loop runs with */
@@ -267,6 +279,38 @@ int op2b_green_gauss_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                              int32_t flags);
 int op2b_edge_flux_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                            const op2b_flux_params* prm);
+
+/* Viscous flux, the analogue of the paper's `vfluxedge` loop (named in
+ * Table "loopperfmpi" as the most expensive loop of the solver, Sec. 4; the
+ * paper does not give its formula, this is the textbook Navier-Stokes edge
+ * flux).  Two steps:
+ *
+ * op2b_viscous_prims: direct node loop, W from q (dim 6) and the scaled
+ *   conserved gradients G (dim 18, component 3k+d):
+ *     W[0..2] = u = m / rho,  W[3] = T = p / rho,  W[4] = c = q5,
+ *     W[5 + 3a + d] = (d u_a / d x_d) / 2,  W[14 + d] = (dT/dx_d) / 2,
+ *     W[17 + d] = (dc/dx_d) / 2   (gradients halved),
+ *   by the quotient rule (grad u_a = (grad m_a - u_a grad rho) / rho,
+ *   grad p = (gamma-1)(grad E - u . grad m + |u|^2/2 grad rho),
+ *   grad T = (grad p - T grad rho) / rho).  q, G, W (dim 20) all F64 or all
+ *   F32 on one set.
+ *
+ * op2b_viscous_flux: edge loop, per edge (i, j) with normal n and
+ *   dx = x_j - x_i: for phi in (u_x, u_y, u_z, T, c) the face gradient
+ *     g = gbar + ((phi_j - phi_i) - gbar . dx) dx / |dx|^2,
+ *   gbar the mean of the two nodal gradients; then
+ *     Fv = (0, tau n, (tau n) . (u_i + u_j)/2 + kappa g_T . n, diff g_c . n),
+ *     tau = mu (g_u + g_u^T - 2/3 (div u) I),
+ *   and R_i -= Fv, R_j += Fv (with OP2B_ZERO_INC R is zeroed first;
+ *   otherwise the viscous flux is added to R, e.g. onto the inviscid flux).
+ *   args (6): W 0 READ, W 1 READ (dim 20), n ID READ, dx ID READ (edge,
+ *   dim 3), R 0 INC, R 1 INC (F64 dim 6).  W, n, dx all F64, or all F32
+ *   with FP32 arithmetic and each edge's flux converted to FP64 before it
+ *   is added into R.  |dx| must be nonzero. */
+int op2b_viscous_prims(op2b_ctx ctx, op2b_dat q, op2b_dat G, op2b_dat W,
+                       double gamma);
+int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                      const op2b_visc_params* prm);
 
 /* ----------------------------------------------------------- node loops
  * Direct loops over the node set (no map). */

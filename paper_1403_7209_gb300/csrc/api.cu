@@ -21,7 +21,7 @@ void op2b::set_thread_error(const std::string& msg) { g_init_err = msg; }
 
 static const char* kLoopName[OP2B_NUM_LOOPS] = {
     "green_gauss", "flux1", "flux2", "spectral", "flux1_adj", "flux2_adj", "gg_adj",
-    "flux1_tan", "flux2_tan", "gg_tan"};
+    "flux1_tan", "flux2_tan", "gg_tan", "viscous"};
 
 // ------------------------------------------------------------------ Ctx
 namespace op2b {
@@ -564,6 +564,7 @@ std::string tune_key(const LoopLaunch& L, bool det) {
 }
 
 int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
+  if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
   return L.prec == OP2B_PREC_F32 ? launch_f32(&c, L, s) : launch_f64(&c, L, s);
 }
@@ -809,6 +810,41 @@ extern "C" int op2b_edge_flux(op2b_ctx h, const op2b_arg* a, int32_t nargs, cons
   return run_loop(c, L, p->flags, &D(c, *R), nullptr, nullptr);
 }
 
+extern "C" int op2b_viscous_flux(op2b_ctx h, const op2b_arg* a, int32_t nargs,
+                                 const op2b_visc_params* p) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!p || !(p->gamma > 1.0) || !(p->mu >= 0.0) || !(p->prandtl > 0.0) || !(p->diff >= 0.0))
+    return c.fail(OP2B_EINVAL, "viscous_flux: need gamma > 1, mu >= 0, prandtl > 0, diff >= 0");
+  static const Spec sp[6] = {{0, OP2B_READ, 20, 'P'},  {1, OP2B_READ, 20, 'P'},
+                             {-1, OP2B_READ, 3, 'P'},  {-1, OP2B_READ, 3, 'P'},
+                             {0, OP2B_INC, 6, 'D'},    {1, OP2B_INC, 6, 'D'}};
+  Checked ck;
+  int rc = check_args(c, "viscous_flux", a, nargs, sp, 6, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = OP2B_LOOP_VISCOUS;
+  L.prec = ck.prec;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.gamma = p->gamma;
+  L.mu = p->mu;
+  L.kappa = p->mu * p->gamma / ((p->gamma - 1.0) * p->prandtl);
+  L.diff = p->diff;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  L.n = D(c, a[2]).ptr;
+  L.ldn = D(c, a[2]).ld;
+  L.dx = D(c, a[3]).ptr;
+  L.lddx = D(c, a[3]).ld;
+  L.t0 = D(c, a[4]).ptr;
+  L.ldt0 = D(c, a[4]).ld;
+  return run_loop(c, L, p->flags, &D(c, a[4]), nullptr, nullptr);
+}
+
 extern "C" int op2b_spectral_radius(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamma,
                                     int32_t flags) {
   CTX_CHECK(h);
@@ -1043,6 +1079,22 @@ extern "C" int op2b_grad_scale(op2b_ctx h, op2b_dat G, op2b_dat V) {
 
 extern "C" int op2b_grad_scale_adjoint(op2b_ctx h, op2b_dat Gb, op2b_dat V) {
   return grad_scale_impl(h, Gb, V, "grad_scale_adjoint");
+}
+
+extern "C" int op2b_viscous_prims(op2b_ctx h, op2b_dat q, op2b_dat G, op2b_dat W, double gamma) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  int rc;
+  if ((rc = node_dat(c, q, 6, -1, -1, "viscous_prims"))) return rc;
+  const DatRec& rq = c.dats[q];
+  if (rq.type == OP2B_I32) return c.fail(OP2B_ETYPE, "viscous_prims: q must be F64 or F32");
+  if ((rc = node_dat(c, G, 18, rq.type, rq.set, "viscous_prims")) ||
+      (rc = node_dat(c, W, 20, rq.type, rq.set, "viscous_prims")))
+    return rc;
+  if (!(gamma > 1.0)) return c.fail(OP2B_EINVAL, "viscous_prims: need gamma > 1");
+  const DatRec &rg = c.dats[G], &rw = c.dats[W];
+  return node_viscous_prims(&c, rq.ptr, rq.ld, rg.ptr, rg.ld, rw.ptr, rw.ld, rq.type, gamma,
+                            c.sets[rq.set].size);
 }
 
 extern "C" int op2b_time_step(op2b_ctx h, op2b_dat V, op2b_dat lam, double cfl, op2b_dat dt) {

@@ -91,6 +91,7 @@ struct LoopLaunch {
   void *t0 = nullptr, *t1 = nullptr, *direct = nullptr;
   int64_t ldt0 = 0, ldt1 = 0, lddirect = 0;
   double gamma = 1.4, eps = 1e-12;
+  double mu = 0.0, kappa = 0.0, diff = 0.0;  // viscous flux coefficients
 };
 
 struct Ctx;
@@ -107,6 +108,10 @@ void set_thread_error(const std::string& msg);
 int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_f32(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_adj(Ctx* c, const LoopLaunch& L, const Strategy& s);
+// loops_visc.cu: VISCOUS (FP64 or FP32 arithmetic) and its node pass
+int launch_visc(Ctx* c, const LoopLaunch& L, const Strategy& s);
+int node_viscous_prims(Ctx* c, const void* q, int64_t ldq, const void* G, int64_t ldG,
+                       void* W, int64_t ldW, int type, double gamma, int64_t N);
 
 // Direct node loops (node_loops.cu).
 int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,

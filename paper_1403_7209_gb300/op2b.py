@@ -24,7 +24,7 @@ F64, F32, I32 = 0, 1, 2
 ID = -1
 LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
 LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ = 4, 5, 6
-LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, NUM_LOOPS = 7, 8, 9, 10
+LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, LOOP_VISCOUS, NUM_LOOPS = 7, 8, 9, 10, 11
 PREC_F64, PREC_F32 = 0, 1
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
 STRAT_BLOCK_ATOMIC, STRAT_OWNER = 5, 6
@@ -54,6 +54,12 @@ class Arg(ctypes.Structure):
 class FluxParams(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("gamma", ctypes.c_double), ("eps_lim", ctypes.c_double)]
+
+
+class ViscParams(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("mu", ctypes.c_double),
+                ("prandtl", ctypes.c_double), ("diff", ctypes.c_double)]
 
 
 class PlanStats(ctypes.Structure):
@@ -104,6 +110,9 @@ _SIGS = {
     "op2b_green_gauss_tangent": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
     "op2b_edge_flux_tangent": (ctypes.c_int, [_P, _PARG, _I32,
                                               ctypes.POINTER(FluxParams)]),
+    "op2b_viscous_prims": (ctypes.c_int, [_P, _I32, _I32, _I32, _D]),
+    "op2b_viscous_flux": (ctypes.c_int, [_P, _PARG, _I32,
+                                         ctypes.POINTER(ViscParams)]),
     "op2b_grad_scale": (ctypes.c_int, [_P, _I32, _I32]),
     "op2b_grad_scale_adjoint": (ctypes.c_int, [_P, _I32, _I32]),
     "op2b_time_step": (ctypes.c_int, [_P, _I32, _I32, _D, _I32]),
@@ -296,6 +305,17 @@ def op2b_edge_flux_tangent(ctx, args, order: int, gamma: float = 1.4,
     a, n = _args(args)
     p = FluxParams(order, flags, gamma, eps_lim)
     _check(load().op2b_edge_flux_tangent(ctx, a, n, ctypes.byref(p)), ctx)
+
+
+def op2b_viscous_prims(ctx, q: int, G: int, W: int, gamma: float = 1.4):
+    _check(load().op2b_viscous_prims(ctx, q, G, W, gamma), ctx)
+
+
+def op2b_viscous_flux(ctx, args, gamma: float = 1.4, mu: float = 1e-3,
+                      prandtl: float = 0.72, diff: float = 1e-3, flags: int = 0):
+    a, n = _args(args)
+    p = ViscParams(flags, 0, gamma, mu, prandtl, diff)
+    _check(load().op2b_viscous_flux(ctx, a, n, ctypes.byref(p)), ctx)
 
 
 def op2b_grad_scale(ctx, G: int, V: int):

@@ -6,7 +6,8 @@ Builds the n^3 lattice with RCM numbering, autotunes every loop once, then
 runs each requested loop `reps` times with a device synchronisation after
 each repetition, and prints one line per loop with its mean time (CUDA
 events).  Loops: gg, flux2, gg32, flux2_32, adjoint (flux adjoint +
-scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage).
+scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage), visc and
+visc32 (viscous node pass + edge loop, FP64 / FP32; not with adjoint).
 """
 from __future__ import annotations
 
@@ -34,8 +35,10 @@ def main():
     L.load(build_if_missing=False)
     m = meshgen.lattice(args.n)
     q = meshgen.flow_state(m)
+    names = args.loops.split(",")
+    visc = any(nm.startswith("visc") for nm in names)
     s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber="rcm", mixed=True,
-                   adjoint=True)
+                   adjoint=not visc, viscous=(1e-3, 0.72, 1e-3) if visc else None)
     if args.tune_cache and os.path.exists(args.tune_cache):
         L.op2b_load_tuning(s.ctx, args.tune_cache)
     for loop in range(L.NUM_LOOPS):
@@ -45,7 +48,8 @@ def main():
         s.set_strategy(*[int(x) for x in f.split(":")])
     s.time_step(0.5)
     L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
-    s.t["lam"].normal_()
+    if not visc:
+        s.t["lam"].normal_()
     run = {
         "gg": lambda: s.green_gauss(),
         "flux2": lambda: s.flux(2),
@@ -53,8 +57,13 @@ def main():
         "flux2_32": lambda: s.flux(2, mixed=True),
         "adjoint": lambda: s.adjoint(2, recompute_gradient=False),
         "stage": lambda: s.stage(0.25),
+        "visc": lambda: s.viscous_flux(zero=True),
+        "visc32": lambda: s.viscous_flux(mixed=True, zero=True),
     }
-    names = args.loops.split(",")
+    if visc:
+        s.green_gauss()
+        s.sync_shadow()
+        s.green_gauss(mixed=True)
     for nm in names:  # warm-up: tunes and builds plans
         run[nm]()
     torch.cuda.synchronize()

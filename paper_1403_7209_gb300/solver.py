@@ -29,13 +29,15 @@ class EdgeSolver:
     (N, 3)); :meth:`fetch_nodes` and :meth:`fetch_edges` return data in the
     caller's numbering again.
     ``mixed`` adds the FP32 shadows used by the mixed-precision path;
-    ``adjoint`` the adjoint and tangent (Jacobian-vector product) dats.
+    ``adjoint`` the adjoint and tangent (Jacobian-vector product) dats;
+    ``viscous`` = (mu, prandtl, diff) adds the viscous flux to the residual
+    (Navier-Stokes instead of Euler).
     """
 
     def __init__(self, edge, normal, dx, volume, q=None, device: int = 0,
                  renumber: str = "none", seed: int = 0, mixed: bool = False,
                  adjoint: bool = False, gamma: float = 1.4,
-                 eps_lim: float = 1e-12, stream=None, coords=None):
+                 eps_lim: float = 1e-12, stream=None, coords=None, viscous=None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -74,6 +76,11 @@ class EdgeSolver:
             node("G32", 18, torch.float32)
             edgd("n32", 3, torch.float32, init=normal)
             edgd("dx32", 3, torch.float32, init=dx)
+        self.visc = tuple(float(v) for v in viscous) if viscous is not None else None
+        if self.visc is not None:
+            node("W", 20)
+            if mixed:
+                node("W32", 20, torch.float32)
         self.has_adjoint = adjoint
         if adjoint:
             node("lam", 6)
@@ -166,6 +173,12 @@ class EdgeSolver:
             self.a_f2_32 = [ind("q32", 0, R), ind("q32", 1, R), ind("G32", 0, R),
                             ind("G32", 1, R), dr("n32", R), dr("dx32", R),
                             ind("R", 0, I), ind("R", 1, I)]
+        if self.visc is not None:
+            self.a_vf = [ind("W", 0, R), ind("W", 1, R), dr("n", R), dr("dx", R),
+                         ind("R", 0, I), ind("R", 1, I)]
+            if self.mixed:
+                self.a_vf32 = [ind("W32", 0, R), ind("W32", 1, R), dr("n32", R),
+                               dr("dx32", R), ind("R", 0, I), ind("R", 1, I)]
         if self.has_adjoint:
             self.a_fa1 = [ind("lam", 0, R), ind("lam", 1, R), ind("q", 0, R), ind("q", 1, R),
                           dr("n", R), ind("qbar", 0, I), ind("qbar", 1, I), dr("nbar", W)]
@@ -203,10 +216,26 @@ class EdgeSolver:
             a = self.a_f2_32 if mixed else self.a_f2
         L.op2b_edge_flux(self.ctx, a, order, self.gamma, self.eps_lim, L.ZERO_INC)
 
+    def viscous_flux(self, mixed=False, zero=False):
+        """R -= viscous fluxes (R zeroed first with ``zero``); uses the
+        scaled gradients G (G32 with ``mixed``)."""
+        mu, pr, diff = self.visc
+        c = self.ctx
+        if mixed:
+            L.op2b_viscous_prims(c, self.d["q32"], self.d["G32"], self.d["W32"], self.gamma)
+        else:
+            L.op2b_viscous_prims(c, self.d["q"], self.d["G"], self.d["W"], self.gamma)
+        L.op2b_viscous_flux(c, self.a_vf32 if mixed else self.a_vf, self.gamma, mu, pr, diff,
+                            L.ZERO_INC if zero else 0)
+
     def residual(self, order=2, mixed=False):
-        if order == 2:
+        """R of the current state: inviscid flux of the given order, plus
+        the viscous flux when the solver was built with ``viscous``."""
+        if order == 2 or self.visc is not None:
             self.green_gauss(mixed)
         self.flux(order, mixed)
+        if self.visc is not None:
+            self.viscous_flux(mixed)
 
     def spectral_radius(self):
         L.op2b_spectral_radius(self.ctx, self.a_sr, self.gamma, L.ZERO_INC)
@@ -234,12 +263,18 @@ class EdgeSolver:
         """q32 <- q (FP32 shadow of the state)."""
         L.op2b_dat_copy(self.ctx, self.d["q32"], self.d["q"])
 
+    def _inviscid_only(self, what):
+        if self.visc is not None:
+            raise NotImplementedError(what + " loops cover the inviscid residual only; "
+                                      "build the solver without viscous")
+
     def adjoint(self, order=2, recompute_gradient=True):
         """qbar = dJ/dq (dat qbar) and nbar = dJ/dn (dat nbar) of J = lam . R.
 
         The edge states are recomputed from the node data.  With
         ``recompute_gradient=False`` the dat G must still hold the gradient
         of the current q and n (as the forward residual left it)."""
+        self._inviscid_only("adjoint")
         c = self.ctx
         if order == 1:
             L.op2b_edge_flux_adjoint(c, self.a_fa1, 1, self.gamma, self.eps_lim, L.ZERO_INC)
@@ -255,6 +290,7 @@ class EdgeSolver:
 
         With ``recompute_gradient=False`` the dat G must hold the gradient of
         the current q and n."""
+        self._inviscid_only("tangent")
         c = self.ctx
         if order == 1:
             L.op2b_edge_flux_tangent(c, self.a_ft1, 1, self.gamma, self.eps_lim, L.ZERO_INC)

@@ -76,6 +76,11 @@ def _load():
                 "ora_kink_margin": [I, I64, I64, P, P, P, P, P, D, D, P, P],
                 "ora_reduce": [I64, I, P, I, P],
                 "ora_viscous_flux": [P, P, P, P, P, P, D, D, D, D, P],
+                "ora_march_dt": [I, I, I, I64, I64, P, P, P, P, P, D, D, P, P, P, P],
+                "ora_march_tangent": [I, I, I, I64, I64, P, P, P, P, P, D, D, P, P, P,
+                                      P, P, P, P, P, P],
+                "ora_march_reverse": [I, I, I, I64, I64, P, P, P, P, P, D, D, P, P, P,
+                                      P, P, P, P, P, P, P, P, P],
                 "ora_viscous": [I64, I64, P, P, P, P, P, D, D, D, D, P, P],
             }
             for name, args in sig.items():
@@ -86,6 +91,7 @@ def _load():
             lib.ora_van_albada.restype = D
             lib.ora_check_state.restype = I64
             lib.ora_march.restype = I64
+            lib.ora_march_dt.restype = I64
             _lib = lib
     return _lib
 
@@ -255,6 +261,50 @@ def residual_reverse(order, edge, q, n, dx, V, lam, gamma=GAMMA,
                                  _p(V), gamma, eps, _p(lam), _p(G), _p(Gb),
                                  _p(qb), _p(nb))
     return qb, nb
+
+
+def march_dt(order, steps, edge, q, n, dx, V, dt, stages=5, gamma=GAMMA, eps=EPS_LIM):
+    """March with the given fixed local time step dt (N,); returns (q, status)."""
+    edge, n, dx, V, dt = _i32(edge), _f64(n), _f64(dx), _f64(V), _f64(dt)
+    q = _f64(q).copy()
+    N, E = q.shape[0], edge.shape[0]
+    q0, R, G = np.empty((N, 6)), np.empty((N, 6)), np.empty((N, 18))
+    st = _load().ora_march_dt(order, steps, stages, N, E, _p(edge), _p(q), _p(n), _p(dx),
+                              _p(V), gamma, eps, _p(dt), _p(q0), _p(R), _p(G))
+    return q, int(st)
+
+
+def march_tangent(order, steps, edge, q, n, dx, V, dt, qd, nd, stages=5, gamma=GAMMA,
+                  eps=EPS_LIM):
+    """Tangent of the fixed-dt march: returns (q_final, qd_final)."""
+    edge, n, dx, V, dt = _i32(edge), _f64(n), _f64(dx), _f64(V), _f64(dt)
+    q, qd, nd = _f64(q).copy(), _f64(qd).copy(), _f64(nd)
+    N, E = q.shape[0], edge.shape[0]
+    w6 = [np.empty((N, 6)) for _ in range(4)]
+    w18 = [np.empty((N, 18)) for _ in range(2)]
+    _load().ora_march_tangent(order, steps, stages, N, E, _p(edge), _p(q), _p(n), _p(dx),
+                              _p(V), gamma, eps, _p(dt), _p(qd), _p(nd),
+                              *[_p(w) for w in w6], *[_p(w) for w in w18])
+    return q, qd
+
+
+def march_reverse(order, steps, edge, q, n, dx, V, dt, g, stages=5, gamma=GAMMA,
+                  eps=EPS_LIM, with_states=False):
+    """Reverse of the fixed-dt march for J = g . q_final: returns (qbar0,
+    nbar) and, with ``with_states``, the input state of every stage
+    (steps * stages, N, 6)."""
+    edge, n, dx, V, dt = _i32(edge), _f64(n), _f64(dx), _f64(V), _f64(dt)
+    q, g = _f64(q), _f64(g).copy()
+    N, E = q.shape[0], edge.shape[0]
+    nbar = np.empty((E, 3))
+    S = np.empty((max(steps * stages, 1), N, 6))
+    w6 = [np.empty((N, 6)) for _ in range(5)]
+    w18 = [np.empty((N, 18)) for _ in range(2)]
+    nb = np.empty((E, 3))
+    _load().ora_march_reverse(order, steps, stages, N, E, _p(edge), _p(q), _p(n), _p(dx),
+                              _p(V), gamma, eps, _p(dt), _p(g), _p(nbar), _p(S),
+                              *[_p(w) for w in w6], *[_p(w) for w in w18], _p(nb))
+    return (g, nbar, S[:steps * stages]) if with_states else (g, nbar)
 
 
 def viscous_flux(qi, qj, Gi, Gj, n, dx, gamma=GAMMA, mu=1e-3, prandtl=0.72,

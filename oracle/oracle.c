@@ -692,3 +692,105 @@ void ora_kink_margin(int order, int64_t N, int64_t E, const int32_t* edge,
     margin[e] = m;
   }
 }
+
+/* ------------------------------------------------- march derivatives
+ * The explicit march with a given, fixed local time step dt (Sec. 2: the
+ * 5-step Runge-Kutta scheme; dt frozen, so it is an input and not
+ * differentiated).  Step n, with D = diag(dt/V):
+ *   s_0 = q^n,  s_k = q^n - alpha_k D R(s_{k-1})  (k = 1..stages),
+ *   q^{n+1} = s_stages.
+ * Tangent (directions qd of q^0 and nd of the normals):
+ *   sd_0 = qd^n,  sd_k = qd^n - alpha_k D (dR/dq(s_{k-1}) sd_{k-1} + dR/dn nd).
+ * Reverse, for J = g . q^N: with sb_stages = qbar^{n+1},
+ *   lam_k = -alpha_k D sb_k,  sb_{k-1} = dR/dq(s_{k-1})^T lam_k,
+ *   nbar += dR/dn(s_{k-1})^T lam_k,  qbar^n = sum_{k>=1} sb_k + sb_0. */
+static double rk_alpha(int stages, int k) { return RK_ALPHA[5 - stages + k]; }
+
+/* q advanced by `steps` steps in place; returns 0 or -(1 + stage) when a
+ * state loses positivity.  Work: q0, R (N x 6), G (N x 18). */
+int64_t ora_march_dt(int order, int steps, int stages, int64_t N, int64_t E,
+                     const int32_t* edge, double* q, const double* n,
+                     const double* dx, const double* V, double gamma,
+                     double eps, const double* dt, double* q0, double* R,
+                     double* G) {
+  int64_t count = 0;
+  for (int st = 0; st < steps; st++) {
+    memcpy(q0, q, sizeof(double) * NV * N);
+    for (int k = 0; k < stages; k++) {
+      ora_residual(order, N, E, edge, q, n, dx, V, gamma, eps, G, R, 0);
+      ora_rk_update(N, q0, R, V, dt, rk_alpha(stages, k), q);
+      if (ora_check_state(N, q, gamma)) return -(1 + count);
+      count++;
+    }
+  }
+  return 0;
+}
+
+/* q and qd advanced together (qd in/out).  Work: q0, qd0, R, Rd (N x 6),
+ * G, Gd (N x 18). */
+void ora_march_tangent(int order, int steps, int stages, int64_t N, int64_t E,
+                       const int32_t* edge, double* q, const double* n,
+                       const double* dx, const double* V, double gamma,
+                       double eps, const double* dt, double* qd,
+                       const double* nd, double* q0, double* qd0, double* R,
+                       double* Rd, double* G, double* Gd) {
+  for (int st = 0; st < steps; st++) {
+    memcpy(q0, q, sizeof(double) * NV * N);
+    memcpy(qd0, qd, sizeof(double) * NV * N);
+    for (int k = 0; k < stages; k++) {
+      double a = rk_alpha(stages, k);
+      ora_residual_tangent(order, N, E, edge, q, n, dx, V, gamma, eps, qd, nd,
+                           G, Gd, Rd);
+      ora_residual(order, N, E, edge, q, n, dx, V, gamma, eps, G, R, 0);
+      ora_rk_update(N, qd0, Rd, V, dt, a, qd);
+      ora_rk_update(N, q0, R, V, dt, a, q);
+    }
+  }
+}
+
+/* Reverse sweep.  q: the initial state (not modified); g: qbar at the end
+ * on entry, qbar^0 on return; nbar (E x 3) receives dJ/dn.  S holds every
+ * stage's input state (steps * stages * N * 6 doubles); work: q0, R, lam,
+ * qb, acc (N x 6), G, Gb (N x 18), nb (E x 3). */
+void ora_march_reverse(int order, int steps, int stages, int64_t N, int64_t E,
+                       const int32_t* edge, const double* q, const double* n,
+                       const double* dx, const double* V, double gamma,
+                       double eps, const double* dt, double* g, double* nbar,
+                       double* S, double* q0, double* R, double* lam,
+                       double* qb, double* acc, double* G, double* Gb,
+                       double* nb) {
+  const int64_t sz = NV * N;
+  /* forward, keeping s_{k-1} of every stage */
+  double* s = S;
+  memcpy(s, q, sizeof(double) * sz);
+  for (int st = 0; st < steps; st++) {
+    const double* qn = S + (int64_t)st * stages * sz;
+    for (int k = 0; k < stages; k++) {
+      const double* sk = S + ((int64_t)st * stages + k) * sz;
+      ora_residual(order, N, E, edge, sk, n, dx, V, gamma, eps, G, R, 0);
+      double* next = (st == steps - 1 && k == stages - 1)
+                         ? q0
+                         : S + ((int64_t)st * stages + k + 1) * sz;
+      ora_rk_update(N, qn, R, V, dt, rk_alpha(stages, k), next);
+    }
+  }
+  memset(nbar, 0, sizeof(double) * 3 * E);
+  /* reverse: g holds sb_stages of the current step */
+  for (int st = steps - 1; st >= 0; st--) {
+    memset(acc, 0, sizeof(double) * sz);
+    for (int k = stages - 1; k >= 0; k--) {
+      const double* sk = S + ((int64_t)st * stages + k) * sz; /* s_{k}, input of stage k+1 */
+      double a = rk_alpha(stages, k);
+      for (int64_t i = 0; i < N; i++)
+        for (int c = 0; c < NV; c++) {
+          acc[NV * i + c] += g[NV * i + c];
+          lam[NV * i + c] = -a * (dt[i] / V[i]) * g[NV * i + c];
+        }
+      ora_residual_reverse(order, N, E, edge, sk, n, dx, V, gamma, eps, lam, G,
+                           Gb, qb, nb);
+      for (int64_t e = 0; e < 3 * E; e++) nbar[e] += nb[e];
+      memcpy(g, qb, sizeof(double) * sz);
+    }
+    for (int64_t i = 0; i < sz; i++) g[i] += acc[i];
+  }
+}

@@ -353,6 +353,35 @@ def viscous_extra(torch, L, m, q, args, stream, device, E):
     return out
 
 
+def march_adjoint_extra(torch, L, s, q, args, stream, E, steps=10):
+    """Reverse sweep of a 10-step march (50 stages, dt fixed) with every
+    stage's state and gradient kept in HBM, against the forward march."""
+    N = s.N
+    g = torch.randn((6, s.t["q"].shape[1]), dtype=torch.float64, device=s.device)
+
+    def fwd():
+        for _ in range(steps):
+            s.step(order=2)
+
+    def rev(keep):
+        s.t["sbar"].copy_(g)
+        s.march_adjoint(steps, order=2, keep_gradients=keep)
+    s.load_nodes("q", q)
+    s.time_step(0.5)
+    rev(True)  # warm-up: tunes the loops, allocates the stage storage
+    torch.cuda.synchronize()
+    f_ms = timed(torch, fwd, 1, stream)
+    s.load_nodes("q", q)
+    r_ms = timed(torch, lambda: rev(True), 1, stream)
+    s.load_nodes("q", q)
+    rr_ms = timed(torch, lambda: rev(False), 1, stream)
+    stored = (steps * 5 + 1) * 6 * N * 8 + steps * 5 * 18 * N * 8
+    return {"steps": steps, "stages": 5 * steps, "forward_march_ms": f_ms,
+            "adjoint_march_ms": r_ms, "ratio_to_forward": r_ms / f_ms,
+            "adjoint_march_recompute_gradients_ms": rr_ms,
+            "stored_gb": stored / 1e9, "edges_per_s_per_stage": E * 5 * steps / (r_ms * 1e-3)}
+
+
 def config0_extra(torch, L, args):
     """First-order Rusanov residual on the 16^3 lattice (random numbering),
     the correctness configuration; launch-bound at 36,864 edges, so timed
@@ -561,6 +590,7 @@ def main():
         line["tangent"] = tangent_extra(torch, s, args, stream, E)
         line["viscous"] = viscous_extra(torch, L, m, q, args, stream, local, E)
         line["viscous"]["fp64_ns_stage_vs_euler_stage"] = line["viscous"]["fp64"]["ns_stage_ms"] / ms
+        line["march_adjoint"] = march_adjoint_extra(torch, L, s, q, args, stream, E)
         line["config0"] = config0_extra(torch, L, args)
         line["march"] = march_extra(torch, L, s, q, args, stream)
         if args.numbering == "rcm":

@@ -326,6 +326,19 @@ int op2b_time_step(op2b_ctx ctx, op2b_dat V, op2b_dat lam, double cfl,
  * q32 (F32 dim 6, or -1) receives the FP32 shadow of the new q. */
 int op2b_node_update(op2b_ctx ctx, op2b_dat q0, op2b_dat q, op2b_dat R,
                      op2b_dat V, op2b_dat dt, double alpha, op2b_dat q32);
+/* Transpose of op2b_node_update with respect to q0 and R, the step of the
+ * reverse sweep through one Runge-Kutta stage (Sec. 2's explicit march,
+ * with dt fixed): qbar += sbar and lam = -alpha (dt/V) sbar, where sbar is
+ * the adjoint of the stage's output state, qbar accumulates the adjoint of
+ * the step's initial state q0, and lam is the weight that the residual's
+ * adjoint loops then take (J = lam . R).  sbar, qbar, lam F64 dim 6 (three
+ * distinct dats), V, dt F64 dim 1, all on one set. */
+int op2b_node_update_adjoint(op2b_ctx ctx, op2b_dat sbar, op2b_dat qbar,
+                             op2b_dat lam, op2b_dat V, op2b_dat dt,
+                             double alpha);
+/* y += a x, component-wise (F64 dats of one set and dim; a node or an edge
+ * set), e.g. to accumulate the normals' adjoint over the stages. */
+int op2b_dat_axpy(op2b_ctx ctx, op2b_dat y, double a, op2b_dat x);
 /* Global reductions (the residual norms and global time step that an
  * explicit solver monitors each stage; the paper's `updatek` loop ends in a
  * global reduction, Table "loopperfmpi", and Sec. 4.2 finds reductions

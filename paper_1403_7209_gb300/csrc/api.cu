@@ -1132,6 +1132,37 @@ extern "C" int op2b_node_update(op2b_ctx h, op2b_dat q0, op2b_dat q, op2b_dat R,
                      (const double*)c.dats[dt].ptr, alpha, p32, ld32, c.sets[s].size);
 }
 
+extern "C" int op2b_node_update_adjoint(op2b_ctx h, op2b_dat sbar, op2b_dat qbar, op2b_dat lam,
+                                        op2b_dat V, op2b_dat dt, double alpha) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  int rc;
+  const char* w = "node_update_adjoint";
+  if ((rc = node_dat(c, sbar, 6, OP2B_F64, -1, w))) return rc;
+  op2b_set s = c.dats[sbar].set;
+  if ((rc = node_dat(c, qbar, 6, OP2B_F64, s, w)) || (rc = node_dat(c, lam, 6, OP2B_F64, s, w)) ||
+      (rc = node_dat(c, V, 1, OP2B_F64, s, w)) || (rc = node_dat(c, dt, 1, OP2B_F64, s, w)))
+    return rc;
+  if (sbar == qbar || sbar == lam || qbar == lam)
+    return c.fail(OP2B_EINVAL, "node_update_adjoint: sbar, qbar and lam must be distinct dats");
+  return node_update_adjoint(&c, (const double*)c.dats[sbar].ptr, c.dats[sbar].ld,
+                             (double*)c.dats[qbar].ptr, c.dats[qbar].ld, (double*)c.dats[lam].ptr,
+                             c.dats[lam].ld, (const double*)c.dats[V].ptr,
+                             (const double*)c.dats[dt].ptr, alpha, c.sets[s].size);
+}
+
+extern "C" int op2b_dat_axpy(op2b_ctx h, op2b_dat y, double a, op2b_dat x) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!valid_dat(c, y) || !valid_dat(c, x)) return c.fail(OP2B_EINVAL, "dat_axpy: bad dat");
+  const DatRec &dy = c.dats[y], &dx = c.dats[x];
+  if (dy.set != dx.set) return c.fail(OP2B_ESET, "dat_axpy: dats on different sets");
+  if (dy.dim != dx.dim) return c.fail(OP2B_EDIM, "dat_axpy: dims differ");
+  if (dy.type != OP2B_F64 || dx.type != OP2B_F64) return c.fail(OP2B_ETYPE, "dat_axpy: F64 dats only");
+  return node_axpy(&c, (double*)dy.ptr, dy.ld, a, (const double*)dx.ptr, dx.ld, dy.dim,
+                   c.sets[dy.set].size);
+}
+
 extern "C" int op2b_dat_fill(op2b_ctx h, op2b_dat d, double value) {
   CTX_CHECK(h);
   Ctx& c = h->c;

@@ -122,6 +122,11 @@ int node_update(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
                 const double* R, int64_t ldR, const double* V,
                 const double* dt, double alpha, float* q32, int64_t ld32,
                 int64_t N);
+int node_update_adjoint(Ctx* c, const double* sb, int64_t ldsb, double* qb, int64_t ldqb,
+                        double* lam, int64_t ldl, const double* V, const double* dt,
+                        double alpha, int64_t N);
+int node_axpy(Ctx* c, double* y, int64_t ldy, double a, const double* x, int64_t ldx, int dim,
+              int64_t n);
 int node_fill(Ctx* c, void* p, int type, int64_t ld, int dim, int64_t n,
               double value);
 int node_copy(Ctx* c, void* dst, int dtype, int64_t ldd, const void* src,

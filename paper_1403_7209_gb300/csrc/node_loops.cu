@@ -79,6 +79,49 @@ int node_update(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
   return c->launched("update");
 }
 
+// transpose of the stage update with respect to q0 and R:
+// qbar += sbar,  lam = -alpha (dt/V) sbar
+__global__ void k_update_adjoint(const double* __restrict__ sb, int64_t ldsb,
+                                 double* __restrict__ qb, int64_t ldqb,
+                                 double* __restrict__ lam, int64_t ldl,
+                                 const double* __restrict__ V,
+                                 const double* __restrict__ dt, double alpha, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = -alpha * (dt[i] / V[i]);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const double v = sb[k * ldsb + i];
+      qb[k * ldqb + i] += v;
+      lam[k * ldl + i] = a * v;
+    }
+  }
+}
+
+int node_update_adjoint(Ctx* c, const double* sb, int64_t ldsb, double* qb, int64_t ldqb,
+                        double* lam, int64_t ldl, const double* V, const double* dt,
+                        double alpha, int64_t N) {
+  if (N == 0) return OP2B_OK;
+  k_update_adjoint<<<grid_for(c, N, 256), 256, 0, c->stream>>>(sb, ldsb, qb, ldqb, lam, ldl, V,
+                                                               dt, alpha, N);
+  return c->launched("update_adjoint");
+}
+
+// y += a x, component-wise
+__global__ void k_axpy(double* __restrict__ y, int64_t ldy, double a,
+                       const double* __restrict__ x, int64_t ldx, int dim, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < dim; k++) y[k * ldy + i] = fma(a, x[k * ldx + i], y[k * ldy + i]);
+}
+
+int node_axpy(Ctx* c, double* y, int64_t ldy, double a, const double* x, int64_t ldx, int dim,
+              int64_t n) {
+  if (n == 0 || dim == 0) return OP2B_OK;
+  k_axpy<<<grid_for(c, n, 256), 256, 0, c->stream>>>(y, ldy, a, x, ldx, dim, n);
+  return c->launched("axpy");
+}
+
 template <typename T>
 __global__ void k_fill(T* __restrict__ p, int64_t ld, int dim, int64_t n,
                        T v) {

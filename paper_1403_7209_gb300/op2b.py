@@ -118,6 +118,8 @@ _SIGS = {
     "op2b_time_step": (ctypes.c_int, [_P, _I32, _I32, _D, _I32]),
     "op2b_node_update": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32,
                                         _D, _I32]),
+    "op2b_node_update_adjoint": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _D]),
+    "op2b_dat_axpy": (ctypes.c_int, [_P, _I32, _D, _I32]),
     "op2b_dat_fill": (ctypes.c_int, [_P, _I32, _D]),
     "op2b_dat_copy": (ctypes.c_int, [_P, _I32, _I32]),
     "op2b_dat_reduce": (ctypes.c_int, [_P, _I32, _I32, _P]),
@@ -333,6 +335,15 @@ def op2b_time_step(ctx, V: int, lam: int, cfl: float, dt: int):
 def op2b_node_update(ctx, q0: int, q: int, R: int, V: int, dt: int,
                      alpha: float, q32: int = -1):
     _check(load().op2b_node_update(ctx, q0, q, R, V, dt, alpha, q32), ctx)
+
+
+def op2b_node_update_adjoint(ctx, sbar: int, qbar: int, lam: int, V: int, dt: int,
+                             alpha: float):
+    _check(load().op2b_node_update_adjoint(ctx, sbar, qbar, lam, V, dt, alpha), ctx)
+
+
+def op2b_dat_axpy(ctx, y: int, a: float, x: int):
+    _check(load().op2b_dat_axpy(ctx, y, a, x), ctx)
 
 
 def op2b_dat_fill(ctx, dat: int, value: float):

@@ -91,6 +91,10 @@ class EdgeSolver:
             node("Gd", 18)
             node("Rd", 6)
             edgd("nd", 3)
+            node("qd0", 6)      # tangent march: direction at the step start
+            node("sbar", 6)     # march adjoint: adjoint of the current state
+            node("qacc", 6)     # march adjoint: per-step accumulator
+            edgd("nbar_acc", 3)  # march adjoint: dJ/dn summed over the stages
         self.perm = np.arange(self.N, dtype=np.int64)   # new id of old node
         self.order = np.arange(self.E, dtype=np.int64)  # old edge of new slot
         if renumber == "rcb":
@@ -300,6 +304,78 @@ class EdgeSolver:
         L.op2b_green_gauss_tangent(c, self.a_ggt, L.ZERO_INC)
         L.op2b_grad_scale(c, self.d["Gd"], self.d["V"])
         L.op2b_edge_flux_tangent(c, self.a_ft2, 2, self.gamma, self.eps_lim, L.ZERO_INC)
+
+    # ------------------------------------------------ march derivatives
+    def march_tangent(self, steps, order=2, stages=5):
+        """Advance q and its tangent qd together by `steps` RK steps with
+        the fixed local time step in dat dt: on return qd holds
+        dq_N/dq_0 . qd + dq_N/dn . nd (dats qd, nd on entry)."""
+        self._inviscid_only("tangent")
+        c, d = self.ctx, self.d
+        for _ in range(steps):
+            L.op2b_dat_copy(c, d["q0"], d["q"])
+            L.op2b_dat_copy(c, d["qd0"], d["qd"])
+            for a in RK5_ALPHA[5 - stages:]:
+                self.residual(order)
+                self.tangent(order, recompute_gradient=False)
+                L.op2b_node_update(c, d["qd0"], d["qd"], d["Rd"], d["V"], d["dt"], a, -1)
+                L.op2b_node_update(c, d["q0"], d["q"], d["R"], d["V"], d["dt"], a, -1)
+
+    def march_adjoint(self, steps, order=2, stages=5, keep_gradients=True):
+        """Reverse of `steps` RK steps with the fixed dt (dat dt) for
+        J = g . q_N.  On entry dat sbar holds g and q holds q_0; on return
+        sbar holds dJ/dq_0, nbar_acc dJ/dn, and q holds q_N.
+
+        The forward march keeps the input state of every stage resident
+        (steps * stages + 1 states of 6 N doubles) and, with
+        ``keep_gradients`` (order 2), the gradient of every stage (18 N
+        doubles each) instead of recomputing it in the reverse sweep: the
+        stage loops read and write the stored slices directly (the dats
+        are rebound), so nothing is copied."""
+        self._inviscid_only("adjoint")
+        torch, c, d, t = self.torch, self.ctx, self.d, self.t
+        K = steps * stages
+        ld = t["q"].shape[1]
+        S = torch.empty((K + 1, 6, ld), dtype=torch.float64, device=self.device)
+        GS = (torch.empty((max(K, 1), 18, ld), dtype=torch.float64, device=self.device)
+              if keep_gradients and order == 2 else None)
+        q_t, q0_t, G_t = t["q"], t["q0"], t["G"]
+        alphas = RK5_ALPHA[5 - stages:]
+        try:
+            self.rebind("q0", S[0])
+            L.op2b_dat_copy(c, d["q0"], d["q"])
+            for st in range(steps):
+                self.rebind("q0", S[st * stages])
+                for k, a in enumerate(alphas):
+                    idx = st * stages + k
+                    self.rebind("q", S[idx])
+                    if GS is not None:
+                        self.rebind("G", GS[idx])
+                    self.residual(order)
+                    self.rebind("q", S[idx + 1])
+                    L.op2b_node_update(c, d["q0"], d["q"], d["R"], d["V"], d["dt"], a, -1)
+            L.op2b_dat_fill(c, d["nbar_acc"], 0.0)
+            for st in reversed(range(steps)):
+                L.op2b_dat_fill(c, d["qacc"], 0.0)
+                for k in reversed(range(stages)):
+                    idx = st * stages + k
+                    L.op2b_node_update_adjoint(c, d["sbar"], d["qacc"], d["lam"], d["V"],
+                                               d["dt"], alphas[k])
+                    self.rebind("q", S[idx])
+                    if GS is not None:
+                        self.rebind("G", GS[idx])
+                    self.adjoint(order, recompute_gradient=GS is None)
+                    L.op2b_dat_axpy(c, d["nbar_acc"], 1.0, d["nbar"])
+                    sb, qb = t["sbar"], t["qbar"]  # sbar <- qbar by swapping buffers
+                    self.rebind("sbar", qb)
+                    self.rebind("qbar", sb)
+                L.op2b_dat_axpy(c, d["sbar"], 1.0, d["qacc"])
+            self.rebind("q0", S[K])
+        finally:
+            self.rebind("q", q_t)
+            self.rebind("G", G_t)
+        L.op2b_dat_copy(c, d["q"], d["q0"])
+        self.rebind("q0", q0_t)
 
     def reduce(self, name, op):
         """Per-component reduction of dat `name` (op: op2b.RED_*), as a

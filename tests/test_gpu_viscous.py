@@ -141,7 +141,7 @@ def test_viscous_irregular_graph_and_ragged_meshes(gpu_lib):
         # 4096-edge blocks with their node data staged need more shared
         # memory than a block has: refused with ERANGE, nothing launched
         s.set_strategy(gpu_lib.LOOP_VISCOUS, 0, 2, 128, 4096, 1)
-        if m.num_edges > 1024:
+        if m.num_edges >= 4096:
             with pytest.raises(gpu_lib.Op2bError) as e:
                 s.viscous_flux(zero=True)
             assert e.value.code == gpu_lib.ERANGE

@@ -82,6 +82,12 @@ def _load():
                 "ora_march_reverse": [I, I, I, I64, I64, P, P, P, P, P, D, D, P, P, P,
                                       P, P, P, P, P, P, P, P, P],
                 "ora_viscous": [I64, I64, P, P, P, P, P, D, D, D, D, P, P],
+                "ora_minmax": [I64, I64, P, P, P, P],
+                "ora_limiter_edge": [I, D, D, D],
+                "ora_limiter": [I, I64, I64, P, P, P, P, P, P, D, P],
+                "ora_flux2_phi": [I64, I64, P, P, P, P, P, P, D, P, P],
+                "ora_residual_limited": [I, I64, I64, P, P, P, P, P, D, D, P, P, P, P, P,
+                                         P],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -92,6 +98,7 @@ def _load():
             lib.ora_check_state.restype = I64
             lib.ora_march.restype = I64
             lib.ora_march_dt.restype = I64
+            lib.ora_limiter_edge.restype = D
             _lib = lib
     return _lib
 
@@ -305,6 +312,58 @@ def march_reverse(order, steps, edge, q, n, dx, V, dt, g, stages=5, gamma=GAMMA,
                               _p(V), gamma, eps, _p(dt), _p(g), _p(nbar), _p(S),
                               *[_p(w) for w in w6], *[_p(w) for w in w18], _p(nb))
     return (g, nbar, S[:steps * stages]) if with_states else (g, nbar)
+
+
+LIM_BJ, LIM_VENKAT = 1, 2
+
+
+def minmax(edge, q):
+    """(qmin, qmax): per node and variable, over the node and its neighbours."""
+    edge, q = _i32(edge), _f64(q)
+    N, E = q.shape[0], edge.shape[0]
+    lo, hi = np.empty((N, 6)), np.empty((N, 6))
+    _load().ora_minmax(N, E, _p(edge), _p(q), _p(lo), _p(hi))
+    return lo, hi
+
+
+def limiter_edge(kind, d1, d2, eps2=0.0):
+    """phi of one edge end (Barth-Jespersen: kind 1, Venkatakrishnan: 2)."""
+    return _load().ora_limiter_edge(kind, float(d1), float(d2), float(eps2))
+
+
+def limiter(kind, edge, q, G, dx, qmin, qmax, eps2=0.0):
+    """Node limiter phi (N, 6)."""
+    edge, q, G, dx = _i32(edge), _f64(q), _f64(G), _f64(dx)
+    qmin, qmax = _f64(qmin), _f64(qmax)
+    N, E = q.shape[0], edge.shape[0]
+    phi = np.empty((N, 6))
+    _load().ora_limiter(kind, N, E, _p(edge), _p(q), _p(G), _p(dx), _p(qmin), _p(qmax),
+                        eps2, _p(phi))
+    return phi
+
+
+def flux2_phi(edge, q, G, phi, n, dx, gamma=GAMMA, with_abs=False):
+    edge, q, G, phi, n, dx = _i32(edge), _f64(q), _f64(G), _f64(phi), _f64(n), _f64(dx)
+    N, E = q.shape[0], edge.shape[0]
+    R = np.empty((N, 6))
+    Ra = np.empty((N, 6)) if with_abs else None
+    _load().ora_flux2_phi(N, E, _p(edge), _p(q), _p(G), _p(phi), _p(n), _p(dx), gamma,
+                          _p(R), _p(Ra))
+    return (R, Ra) if with_abs else R
+
+
+def residual_limited(kind, edge, q, n, dx, V, eps2=0.0, gamma=GAMMA, with_abs=False):
+    """Node-limited second-order residual; returns dict R, G, qmin, qmax,
+    phi (and Rabs with ``with_abs``)."""
+    edge, q, n, dx, V = _i32(edge), _f64(q), _f64(n), _f64(dx), _f64(V)
+    N, E = q.shape[0], edge.shape[0]
+    out = {k: np.empty((N, 6)) for k in ("R", "qmin", "qmax", "phi")}
+    out["G"] = np.empty((N, 18))
+    out["Rabs"] = np.empty((N, 6)) if with_abs else None
+    _load().ora_residual_limited(kind, N, E, _p(edge), _p(q), _p(n), _p(dx), _p(V), gamma,
+                                 eps2, _p(out["G"]), _p(out["qmin"]), _p(out["qmax"]),
+                                 _p(out["phi"]), _p(out["R"]), _p(out["Rabs"]))
+    return out
 
 
 def viscous_flux(qi, qj, Gi, Gj, n, dx, gamma=GAMMA, mu=1e-3, prandtl=0.72,

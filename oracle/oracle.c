@@ -794,3 +794,115 @@ void ora_march_reverse(int order, int steps, int stages, int64_t N, int64_t E,
     for (int64_t i = 0; i < sz; i++) g[i] += acc[i];
   }
 }
+
+/* ------------------------------------------------ node-limited scheme
+ * The alternative to the van Albada edge limiter: limiters of the
+ * Barth-Jespersen (1989) and Venkatakrishnan (1995) type, which limit each
+ * node's gradient once for all its edges.  The paper does not say which
+ * limiter Hydra uses; these are the two textbook node limiters.
+ *
+ *   qmin_i, qmax_i   min / max of q over node i and its edge neighbours
+ *   per edge end (node i of edge e, d = dx at the first end, -dx at the
+ *   second):  D2 = (G_i . d) / 2   (unlimited extrapolation to the edge
+ *   midpoint),  D1 = qmax_i - q_i if D2 > 0, qmin_i - q_i if D2 < 0;
+ *   Barth-Jespersen  phi_e = min(1, D1 / D2),
+ *   Venkatakrishnan  phi_e = (D1^2 + eps2 + 2 D1 D2) / (D1^2 + 2 D2^2 + D1 D2 + eps2),
+ *   and phi_e = 1 when D2 = 0;
+ *   phi_i = min over the edge ends at i (1 for a node with no edges).
+ *   Face states q_i + phi_i D2 at both ends, then the Rusanov flux. */
+#define ORA_LIM_BJ 1
+#define ORA_LIM_VENKAT 2
+
+void ora_minmax(int64_t N, int64_t E, const int32_t* edge, const double* q,
+                double* qmin, double* qmax) {
+  memcpy(qmin, q, sizeof(double) * NV * N);
+  memcpy(qmax, q, sizeof(double) * NV * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t a = edge[2 * e], b = edge[2 * e + 1];
+    for (int s = 0; s < 2; s++) {
+      int64_t i = s ? b : a, j = s ? a : b;
+      for (int k = 0; k < NV; k++) {
+        double v = q[NV * j + k];
+        if (v < qmin[NV * i + k]) qmin[NV * i + k] = v;
+        if (v > qmax[NV * i + k]) qmax[NV * i + k] = v;
+      }
+    }
+  }
+}
+
+/* half the extrapolation of variable k from node i along d */
+static double half_extrap(const double* Gi, int k, const double d[3]) {
+  return 0.5 * (Gi[3 * k] * d[0] + Gi[3 * k + 1] * d[1] + Gi[3 * k + 2] * d[2]);
+}
+
+double ora_limiter_edge(int kind, double d1, double d2, double eps2) {
+  if (d2 == 0.0) return 1.0;
+  if (kind == ORA_LIM_BJ) {
+    double r = d1 / d2;
+    return r < 1.0 ? r : 1.0;
+  }
+  return (d1 * d1 + eps2 + 2.0 * d1 * d2) / (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2);
+}
+
+void ora_limiter(int kind, int64_t N, int64_t E, const int32_t* edge,
+                 const double* q, const double* G, const double* dx,
+                 const double* qmin, const double* qmax, double eps2,
+                 double* phi) {
+  for (int64_t i = 0; i < NV * N; i++) phi[i] = INFINITY;
+  for (int64_t e = 0; e < E; e++) {
+    for (int s = 0; s < 2; s++) {
+      int64_t i = edge[2 * e + s];
+      double d[3];
+      for (int c = 0; c < 3; c++) d[c] = s ? -dx[3 * e + c] : dx[3 * e + c];
+      for (int k = 0; k < NV; k++) {
+        double d2 = half_extrap(G + NG * i, k, d);
+        double d1 = d2 > 0.0 ? qmax[NV * i + k] - q[NV * i + k]
+                             : qmin[NV * i + k] - q[NV * i + k];
+        double f = ora_limiter_edge(kind, d1, d2, eps2);
+        if (f < phi[NV * i + k]) phi[NV * i + k] = f;
+      }
+    }
+  }
+  for (int64_t i = 0; i < NV * N; i++)
+    if (phi[i] == INFINITY) phi[i] = 1.0;
+}
+
+/* flux with node-limited reconstruction: R_i += F, R_j -= F */
+void ora_flux2_phi(int64_t N, int64_t E, const int32_t* edge, const double* q,
+                   const double* G, const double* phi, const double* n,
+                   const double* dx, double gamma, double* R, double* Rabs) {
+  memset(R, 0, sizeof(double) * NV * N);
+  if (Rabs) memset(Rabs, 0, sizeof(double) * NV * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    const double* d = dx + 3 * e;
+    double md[3] = {-d[0], -d[1], -d[2]};
+    double qL[NV], qR[NV], F[NV];
+    for (int k = 0; k < NV; k++) {
+      qL[k] = q[NV * i + k] + phi[NV * i + k] * half_extrap(G + NG * i, k, d);
+      qR[k] = q[NV * j + k] + phi[NV * j + k] * half_extrap(G + NG * j, k, md);
+    }
+    ora_rusanov(qL, qR, n + 3 * e, gamma, F);
+    for (int k = 0; k < NV; k++) {
+      R[NV * i + k] += F[k];
+      R[NV * j + k] -= F[k];
+      if (Rabs) {
+        Rabs[NV * i + k] += fabs(F[k]);
+        Rabs[NV * j + k] += fabs(F[k]);
+      }
+    }
+  }
+}
+
+/* the whole node-limited residual: gradients, min/max, limiter, flux */
+void ora_residual_limited(int kind, int64_t N, int64_t E, const int32_t* edge,
+                          const double* q, const double* n, const double* dx,
+                          const double* V, double gamma, double eps2, double* G,
+                          double* qmin, double* qmax, double* phi, double* R,
+                          double* Rabs) {
+  ora_green_gauss(N, E, edge, q, n, G, 0);
+  ora_grad_scale(N, G, V, G);
+  ora_minmax(N, E, edge, q, qmin, qmax);
+  ora_limiter(kind, N, E, edge, q, G, dx, qmin, qmax, eps2, phi);
+  ora_flux2_phi(N, E, edge, q, G, phi, n, dx, gamma, R, Rabs);
+}

@@ -353,6 +353,55 @@ def viscous_extra(torch, L, m, q, args, stream, device, E):
     return out
 
 
+def limiter_extra(torch, L, m, q, args, stream, device, E, ms_va):
+    """Node-limited second-order scheme: neighbourhood min/max, the
+    Barth-Jespersen and Venkatakrishnan limiters, the node-limited flux, and
+    the whole stage with them against the van Albada stage."""
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    sl = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device,
+                    renumber=args.numbering, mixed=True, stream=stream,
+                    limiter="barth_jespersen")
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        L.op2b_load_tuning(sl.ctx, args.tune_cache)
+    for loop in range(L.NUM_LOOPS):
+        for prec in (0, 1):
+            sl.set_strategy(loop, prec, L.STRAT_AUTO)
+    sl.time_step(0.5)
+    L.op2b_dat_copy(sl.ctx, sl.d["q0"], sl.d["q"])
+    sl.sync_shadow()
+    c, d = sl.ctx, sl.d
+    out = {}
+    for tag, mixed in (("fp64", False), ("mixed", True)):
+        sfx = "32" if mixed else ""
+        qn, Gn, dxn = ("q32", "G32", "dx32") if mixed else ("q", "G", "dx")
+        sl.residual(2, mixed=mixed)  # tunes
+        for _ in range(max(1, args.warmup)):
+            sl.stage(0.25, 2, mixed=mixed)
+
+        def mm():
+            L.op2b_node_minmax(c, sl.map, d[qn], d["qmin" + sfx], d["qmax" + sfx])
+
+        def lim(kind):
+            L.op2b_node_limiter(c, sl.map, kind, 0.0, d[qn], d[Gn], d[dxn], d["qmin" + sfx],
+                                d["qmax" + sfx], d["phi" + sfx])
+
+        def fl():
+            L.op2b_edge_flux_limited(c, sl.a_f2phi32 if mixed else sl.a_f2phi, sl.gamma,
+                                     L.ZERO_INC)
+        r = {"minmax_ms": timed(torch, mm, args.steps, stream),
+             "limiter_bj_ms": timed(torch, lambda: lim(L.LIM_BARTH_JESPERSEN), args.steps, stream),
+             "limiter_venkat_ms": timed(torch, lambda: lim(L.LIM_VENKATAKRISHNAN), args.steps,
+                                        stream),
+             "flux_limited_ms": timed(torch, fl, args.steps, stream),
+             "stage_ms": timed(torch, lambda: sl.stage(0.25, 2, mixed=mixed), args.steps, stream),
+             "flux_strategy": L.STRATEGY_NAMES[sl.plan_stats(L.LOOP_FLUX2_PHI, int(mixed))["strategy"]]}
+        r["stage_edges_per_s"] = E / (r["stage_ms"] * 1e-3)
+        out[tag] = r
+    out["fp64"]["stage_vs_van_albada_stage"] = out["fp64"]["stage_ms"] / ms_va
+    sl.close()
+    return out
+
+
 def march_adjoint_extra(torch, L, s, q, args, stream, E, steps=10):
     """Reverse sweep of a 10-step march (50 stages, dt fixed) with every
     stage's state and gradient kept in HBM, against the forward march."""
@@ -591,6 +640,7 @@ def main():
         line["viscous"] = viscous_extra(torch, L, m, q, args, stream, local, E)
         line["viscous"]["fp64_ns_stage_vs_euler_stage"] = line["viscous"]["fp64"]["ns_stage_ms"] / ms
         line["march_adjoint"] = march_adjoint_extra(torch, L, s, q, args, stream, E)
+        line["limiters"] = limiter_extra(torch, L, m, q, args, stream, local, E, ms)
         line["config0"] = config0_extra(torch, L, args)
         line["march"] = march_extra(torch, L, s, q, args, stream)
         if args.numbering == "rcm":

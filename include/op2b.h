@@ -86,7 +86,8 @@ typedef struct {
 #define OP2B_LOOP_FLUX2_TAN 8
 #define OP2B_LOOP_GG_TAN 9
 #define OP2B_LOOP_VISCOUS 10
-#define OP2B_NUM_LOOPS 11
+#define OP2B_LOOP_FLUX2_PHI 11
+#define OP2B_NUM_LOOPS 12
 
 /* arithmetic variant of a loop: all-FP64, or FP32 node data and arithmetic
  * (the INC precision is then fixed by the loop: FP64 residuals, FP32
@@ -278,6 +279,49 @@ int op2b_green_gauss_adjoint(op2b_ctx ctx, const op2b_arg* args,
 int op2b_green_gauss_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                              int32_t flags);
 int op2b_edge_flux_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                           const op2b_flux_params* prm);
+
+/* Node-limited second-order flux: the alternative to the van Albada edge
+ * limiter (the paper does not name Hydra's limiter; these are the two
+ * textbook node limiters, Barth & Jespersen 1989 and Venkatakrishnan 1995).
+ * Three steps per residual evaluation, after the gradients G:
+ *
+ * op2b_node_minmax: qmin_i / qmax_i = min / max of q over node i and the
+ *   nodes that share an edge of `map` with it.  q, qmin, qmax: dim 6 on the
+ *   map's to-set, all F64 or all F32, qmin and qmax distinct from q.
+ *
+ * op2b_node_limiter: for every end of every edge at node i, with d = dx at
+ *   the edge's first end and -dx at its second, D2 = G_i . d / 2 (the
+ *   unlimited extrapolation to the edge midpoint) and D1 = qmax_i - q_i if
+ *   D2 > 0, qmin_i - q_i if D2 < 0;
+ *     OP2B_LIM_BARTH_JESPERSEN  phi_e = min(1, D1 / D2),
+ *     OP2B_LIM_VENKATAKRISHNAN  phi_e = (D1^2 + eps2 + 2 D1 D2) /
+ *                                       (D1^2 + 2 D2^2 + D1 D2 + eps2),
+ *   phi_e = 1 if D2 = 0, and phi_i = min over the node's edge ends (1 for a
+ *   node without edges).  Venkatakrishnan's phi may exceed 1 slightly (it is
+ *   1 at D2/D1 = 0 and 1/2 and above 1 in between); eps2 >= 0 smooths it
+ *   (eps2 = (K h)^3 in Venkatakrishnan's notation).  q, qmin, qmax, phi dim
+ *   6 and G dim 18 on the to-set, dx dim 3 on the from-set (edges), all F64
+ *   or all F32; phi distinct from the inputs.
+ *
+ * op2b_edge_flux_limited: R_i += F(qL, qR, n), R_j -= F, with face states
+ *   qL = q_i + phi_i (G_i . dx)/2, qR = q_j - phi_j (G_j . dx)/2 and the
+ *   Rusanov flux of op2b_edge_flux.  args (10): q 0, q 1, G 0, G 1, phi 0,
+ *   phi 1 (READ), n ID READ, dx ID READ, R 0 INC, R 1 INC (F64 dim 6).
+ *   prm->order is ignored; prm->eps_lim unused.  q, G, phi, n, dx all F64,
+ *   or all F32 with FP32 arithmetic and each edge's flux converted to FP64
+ *   before it is added into R.
+ *
+ * The two node loops run as gathers over the node-sorted edge ends (no
+ * atomics, results independent of the order of the ends). */
+#define OP2B_LIM_BARTH_JESPERSEN 1
+#define OP2B_LIM_VENKATAKRISHNAN 2
+int op2b_node_minmax(op2b_ctx ctx, op2b_map map, op2b_dat q, op2b_dat qmin,
+                     op2b_dat qmax);
+int op2b_node_limiter(op2b_ctx ctx, op2b_map map, int32_t kind, double eps2,
+                      op2b_dat q, op2b_dat G, op2b_dat dx, op2b_dat qmin,
+                      op2b_dat qmax, op2b_dat phi);
+int op2b_edge_flux_limited(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                            const op2b_flux_params* prm);
 
 /* Viscous flux, the analogue of the paper's `vfluxedge` loop (named in

@@ -64,6 +64,7 @@ def residual(solver, q, n, order=2):
     """Differentiable R(q, n); the solver must be built with adjoint=True."""
     if not solver.has_adjoint:
         raise ValueError("build the EdgeSolver with adjoint=True")
-    if solver.visc is not None:
-        raise ValueError("the adjoint and tangent loops cover the inviscid residual only")
+    if solver.visc is not None or solver.limiter != "van_albada":
+        raise ValueError("the adjoint and tangent loops cover the inviscid residual with the "
+                         "van Albada limiter only")
     return ResidualFn.apply(q, n, solver, order)

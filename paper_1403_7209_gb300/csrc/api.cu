@@ -21,7 +21,7 @@ void op2b::set_thread_error(const std::string& msg) { g_init_err = msg; }
 
 static const char* kLoopName[OP2B_NUM_LOOPS] = {
     "green_gauss", "flux1", "flux2", "spectral", "flux1_adj", "flux2_adj", "gg_adj",
-    "flux1_tan", "flux2_tan", "gg_tan", "viscous"};
+    "flux1_tan", "flux2_tan", "gg_tan", "viscous", "flux2_phi"};
 
 // ------------------------------------------------------------------ Ctx
 namespace op2b {
@@ -565,6 +565,7 @@ std::string tune_key(const LoopLaunch& L, bool det) {
 
 int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);
+  if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
   return L.prec == OP2B_PREC_F32 ? launch_f32(&c, L, s) : launch_f64(&c, L, s);
 }
@@ -808,6 +809,44 @@ extern "C" int op2b_edge_flux(op2b_ctx h, const op2b_arg* a, int32_t nargs, cons
   L.t0 = D(c, *R).ptr;
   L.ldt0 = D(c, *R).ld;
   return run_loop(c, L, p->flags, &D(c, *R), nullptr, nullptr);
+}
+
+extern "C" int op2b_edge_flux_limited(op2b_ctx h, const op2b_arg* a, int32_t nargs,
+                                      const op2b_flux_params* p) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!p || !(p->gamma > 1.0)) return c.fail(OP2B_EINVAL, "edge_flux_limited: need gamma > 1");
+  static const Spec sp[10] = {{0, OP2B_READ, 6, 'P'},  {1, OP2B_READ, 6, 'P'},  {0, OP2B_READ, 18, 'P'},
+                              {1, OP2B_READ, 18, 'P'}, {0, OP2B_READ, 6, 'P'},  {1, OP2B_READ, 6, 'P'},
+                              {-1, OP2B_READ, 3, 'P'}, {-1, OP2B_READ, 3, 'P'}, {0, OP2B_INC, 6, 'D'},
+                              {1, OP2B_INC, 6, 'D'}};
+  Checked ck;
+  int rc = check_args(c, "edge_flux_limited", a, nargs, sp, 10, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = OP2B_LOOP_FLUX2_PHI;
+  L.prec = ck.prec;
+  L.order = 2;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.gamma = p->gamma;
+  L.eps = p->eps_lim;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  L.G = D(c, a[2]).ptr;
+  L.ldG = D(c, a[2]).ld;
+  L.phi = D(c, a[4]).ptr;
+  L.ldphi = D(c, a[4]).ld;
+  L.n = D(c, a[6]).ptr;
+  L.ldn = D(c, a[6]).ld;
+  L.dx = D(c, a[7]).ptr;
+  L.lddx = D(c, a[7]).ld;
+  L.t0 = D(c, a[8]).ptr;
+  L.ldt0 = D(c, a[8]).ld;
+  return run_loop(c, L, p->flags, &D(c, a[8]), nullptr, nullptr);
 }
 
 extern "C" int op2b_viscous_flux(op2b_ctx h, const op2b_arg* a, int32_t nargs,
@@ -1079,6 +1118,77 @@ extern "C" int op2b_grad_scale(op2b_ctx h, op2b_dat G, op2b_dat V) {
 
 extern "C" int op2b_grad_scale_adjoint(op2b_ctx h, op2b_dat Gb, op2b_dat V) {
   return grad_scale_impl(h, Gb, V, "grad_scale_adjoint");
+}
+
+// dats of a node gather over `map`: on the map's to-set, one type (F64/F32)
+static int gather_dat(Ctx& c, op2b_dat d, int dim, int type, op2b_set set, const char* what) {
+  if (!valid_dat(c, d)) return c.fail(OP2B_EINVAL, std::string(what) + ": bad dat");
+  const DatRec& r = c.dats[d];
+  if (r.set != set) return c.fail(OP2B_ESET, std::string(what) + ": " + r.name + " is on the wrong set");
+  if (r.dim != dim) return c.fail(OP2B_EDIM, std::string(what) + ": wrong dim (" + r.name + ")");
+  if (r.type != type) return c.fail(OP2B_ETYPE, std::string(what) + ": mixed types (" + r.name + ")");
+  return OP2B_OK;
+}
+
+extern "C" int op2b_node_minmax(op2b_ctx h, op2b_map map, op2b_dat q, op2b_dat qmin, op2b_dat qmax) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  const char* w = "node_minmax";
+  if (!valid_map(c, map) || c.maps[map].arity != 2) return c.fail(OP2B_EINVAL, "node_minmax: need an arity-2 map");
+  if (!valid_dat(c, q)) return c.fail(OP2B_EINVAL, "node_minmax: bad dat");
+  const int type = c.dats[q].type;
+  if (type != OP2B_F64 && type != OP2B_F32) return c.fail(OP2B_ETYPE, "node_minmax: F64 or F32 dats");
+  const MapRec& m = c.maps[map];
+  int rc;
+  if ((rc = gather_dat(c, q, 6, type, m.to, w)) || (rc = gather_dat(c, qmin, 6, type, m.to, w)) ||
+      (rc = gather_dat(c, qmax, 6, type, m.to, w)))
+    return rc;
+  if (qmin == q || qmax == q || qmin == qmax)
+    return c.fail(OP2B_EINVAL, "node_minmax: q, qmin and qmax must be distinct dats");
+  DevSegPlan* sp = nullptr;
+  if ((rc = c.seg_plan(map, &sp))) return rc;
+  const int64_t E = c.sets[m.from].size;
+  return node_minmax(&c, *sp, m.dev, m.dev + E, type, c.dats[q].ptr, c.dats[q].ld, c.dats[qmin].ptr,
+                     c.dats[qmin].ld, c.dats[qmax].ptr, c.dats[qmax].ld, c.sets[m.to].size);
+}
+
+extern "C" int op2b_node_limiter(op2b_ctx h, op2b_map map, int32_t kind, double eps2, op2b_dat q,
+                                 op2b_dat G, op2b_dat dx, op2b_dat qmin, op2b_dat qmax, op2b_dat phi) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  const char* w = "node_limiter";
+  if (kind != OP2B_LIM_BARTH_JESPERSEN && kind != OP2B_LIM_VENKATAKRISHNAN)
+    return c.fail(OP2B_EINVAL, "node_limiter: unknown limiter");
+  if (!(eps2 >= 0.0)) return c.fail(OP2B_EINVAL, "node_limiter: eps2 must be >= 0");
+  if (!valid_map(c, map) || c.maps[map].arity != 2) return c.fail(OP2B_EINVAL, "node_limiter: need an arity-2 map");
+  if (!valid_dat(c, q)) return c.fail(OP2B_EINVAL, "node_limiter: bad dat");
+  const int type = c.dats[q].type;
+  if (type != OP2B_F64 && type != OP2B_F32) return c.fail(OP2B_ETYPE, "node_limiter: F64 or F32 dats");
+  const MapRec& m = c.maps[map];
+  int rc;
+  if ((rc = gather_dat(c, q, 6, type, m.to, w)) || (rc = gather_dat(c, G, 18, type, m.to, w)) ||
+      (rc = gather_dat(c, qmin, 6, type, m.to, w)) || (rc = gather_dat(c, qmax, 6, type, m.to, w)) ||
+      (rc = gather_dat(c, phi, 6, type, m.to, w)) || (rc = gather_dat(c, dx, 3, type, m.from, w)))
+    return rc;
+  if (phi == q || phi == qmin || phi == qmax)
+    return c.fail(OP2B_EINVAL, "node_limiter: phi must not be an input dat");
+  DevSegPlan* sp = nullptr;
+  if ((rc = c.seg_plan(map, &sp))) return rc;
+  LimArgs la;
+  la.q = c.dats[q].ptr;
+  la.ldq = c.dats[q].ld;
+  la.G = c.dats[G].ptr;
+  la.ldG = c.dats[G].ld;
+  la.dx = c.dats[dx].ptr;
+  la.lddx = c.dats[dx].ld;
+  la.qmin = c.dats[qmin].ptr;
+  la.ldmin = c.dats[qmin].ld;
+  la.qmax = c.dats[qmax].ptr;
+  la.ldmax = c.dats[qmax].ld;
+  la.phi = c.dats[phi].ptr;
+  la.ldphi = c.dats[phi].ld;
+  la.eps2 = eps2;
+  return node_limiter(&c, *sp, kind, type, la, c.sets[m.to].size);
 }
 
 extern "C" int op2b_viscous_prims(op2b_ctx h, op2b_dat q, op2b_dat G, op2b_dat W, double gamma) {

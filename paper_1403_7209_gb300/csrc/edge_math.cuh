@@ -231,6 +231,38 @@ __device__ __forceinline__ double max_nonneg(double a, double b) {
   return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
 }
 
+// Rusanov flux of the face states (qL, qR) in FP64: the two densities are
+// inverted together, the sound speeds come from sqrt2, the larger wave
+// speed is picked by an integer comparison.
+__device__ __forceinline__ void rusanov_f64(const double* qL, const double* qR,
+                                            double nx, double ny, double nz,
+                                            const Gas<double>& g, double* F) {
+  const double gnn = g.gamma * fma(nz, nz, fma(ny, ny, nx * nx));
+  double rho[2] = {qL[0], qR[0]}, rr[2];
+  batch_reciprocal<2>(rho, 1.0, rr);
+  const double hgm1 = 0.5 * g.gm1;
+  double f[2][6], lam[2];
+#pragma unroll
+  for (int sd = 0; sd < 2; sd++) {
+    const double* q = sd ? qR : qL;
+    const double mn = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
+    const double un = mn * rr[sd];
+    const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
+    const double p = fma(-hgm1 * mm, rr[sd], g.gm1 * q[4]);
+    const double x = p * rr[sd] * gnn;
+    lam[sd] = fabs(un) + (seedable(x) ? sqrt2(x) : sqrt(x));
+    f[sd][0] = mn;  // rho u.n
+    f[sd][1] = fma(q[1], un, p * nx);
+    f[sd][2] = fma(q[2], un, p * ny);
+    f[sd][3] = fma(q[3], un, p * nz);
+    f[sd][4] = (q[4] + p) * un;
+    f[sd][5] = q[5] * un;
+  }
+  const double s = max_nonneg(lam[0], lam[1]);
+#pragma unroll
+  for (int k = 0; k < 6; k++) F[k] = 0.5 * fma(-s, qR[k] - qL[k], f[0][k] + f[1][k]);
+}
+
 // vi, vj: q (6) then G (18, component 3k+d); F: the Rusanov flux of the
 // limited face states.
 __device__ __forceinline__ void flux2_f64(const double* vi, const double* vj,
@@ -256,31 +288,7 @@ __device__ __forceinline__ void flux2_f64(const double* vi, const double* vj,
     qL[k] = fma(num[2 * k], rec[2 * k], vi[k]);
     qR[k] = fma(-num[2 * k + 1], rec[2 * k + 1], vj[k]);
   }
-  // Rusanov flux of (qL, qR)
-  const double gnn = g.gamma * fma(nz, nz, fma(ny, ny, nx * nx));
-  double rho[2] = {qL[0], qR[0]}, rr[2];
-  batch_reciprocal<2>(rho, 1.0, rr);
-  const double hgm1 = 0.5 * g.gm1;
-  double f[2][6], lam[2];
-#pragma unroll
-  for (int sd = 0; sd < 2; sd++) {
-    const double* q = sd ? qR : qL;
-    const double mn = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
-    const double un = mn * rr[sd];
-    const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
-    const double p = fma(-hgm1 * mm, rr[sd], g.gm1 * q[4]);
-    const double x = p * rr[sd] * gnn;
-    lam[sd] = fabs(un) + (seedable(x) ? sqrt2(x) : sqrt(x));
-    f[sd][0] = mn;  // rho u.n
-    f[sd][1] = fma(q[1], un, p * nx);
-    f[sd][2] = fma(q[2], un, p * ny);
-    f[sd][3] = fma(q[3], un, p * nz);
-    f[sd][4] = (q[4] + p) * un;
-    f[sd][5] = q[5] * un;
-  }
-  const double s = max_nonneg(lam[0], lam[1]);
-#pragma unroll
-  for (int k = 0; k < 6; k++) F[k] = 0.5 * fma(-s, qR[k] - qL[k], f[0][k] + f[1][k]);
+  rusanov_f64(qL, qR, nx, ny, nz, g, F);
 }
 
 // ---------------------------------------------------------------- adjoint

@@ -92,6 +92,16 @@ struct LoopLaunch {
   int64_t ldt0 = 0, ldt1 = 0, lddirect = 0;
   double gamma = 1.4, eps = 1e-12;
   double mu = 0.0, kappa = 0.0, diff = 0.0;  // viscous flux coefficients
+  const void* phi = nullptr;                  // node limiter (FLUX2_PHI)
+  int64_t ldphi = 0;
+};
+
+// Arguments of the node limiter (device pointers, leading dimensions).
+struct LimArgs {
+  const void *q = nullptr, *G = nullptr, *dx = nullptr, *qmin = nullptr, *qmax = nullptr;
+  void* phi = nullptr;
+  int64_t ldq = 0, ldG = 0, lddx = 0, ldmin = 0, ldmax = 0, ldphi = 0;
+  double eps2 = 0.0;
 };
 
 struct Ctx;
@@ -108,10 +118,16 @@ void set_thread_error(const std::string& msg);
 int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_f32(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_adj(Ctx* c, const LoopLaunch& L, const Strategy& s);
+// loops_lim.cu: FLUX2_PHI (FP64 or FP32) and the node min/max and limiter
+int launch_lim(Ctx* c, const LoopLaunch& L, const Strategy& s);
 // loops_visc.cu: VISCOUS (FP64 or FP32 arithmetic) and its node pass
 int launch_visc(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int node_viscous_prims(Ctx* c, const void* q, int64_t ldq, const void* G, int64_t ldG,
                        void* W, int64_t ldW, int type, double gamma, int64_t N);
+int node_minmax(Ctx* c, const DevSegPlan& sp, const int32_t* m0, const int32_t* m1, int type,
+                const void* q, int64_t ldq, void* qmin, int64_t ldmin, void* qmax, int64_t ldmax,
+                int64_t N);
+int node_limiter(Ctx* c, const DevSegPlan& sp, int kind, int type, const LimArgs& a, int64_t N);
 
 // Direct node loops (node_loops.cu).
 int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,

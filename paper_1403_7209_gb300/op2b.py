@@ -24,7 +24,9 @@ F64, F32, I32 = 0, 1, 2
 ID = -1
 LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
 LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ = 4, 5, 6
-LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, LOOP_VISCOUS, NUM_LOOPS = 7, 8, 9, 10, 11
+LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, LOOP_VISCOUS = 7, 8, 9, 10
+LOOP_FLUX2_PHI, NUM_LOOPS = 11, 12
+LIM_BARTH_JESPERSEN, LIM_VENKATAKRISHNAN = 1, 2
 PREC_F64, PREC_F32 = 0, 1
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
 STRAT_BLOCK_ATOMIC, STRAT_OWNER = 5, 6
@@ -110,6 +112,10 @@ _SIGS = {
     "op2b_green_gauss_tangent": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
     "op2b_edge_flux_tangent": (ctypes.c_int, [_P, _PARG, _I32,
                                               ctypes.POINTER(FluxParams)]),
+    "op2b_node_minmax": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
+    "op2b_node_limiter": (ctypes.c_int, [_P, _I32, _I32, _D, _I32, _I32, _I32, _I32, _I32,
+                                         _I32]),
+    "op2b_edge_flux_limited": (ctypes.c_int, [_P, _PARG, _I32, ctypes.POINTER(FluxParams)]),
     "op2b_viscous_prims": (ctypes.c_int, [_P, _I32, _I32, _I32, _D]),
     "op2b_viscous_flux": (ctypes.c_int, [_P, _PARG, _I32,
                                          ctypes.POINTER(ViscParams)]),
@@ -307,6 +313,21 @@ def op2b_edge_flux_tangent(ctx, args, order: int, gamma: float = 1.4,
     a, n = _args(args)
     p = FluxParams(order, flags, gamma, eps_lim)
     _check(load().op2b_edge_flux_tangent(ctx, a, n, ctypes.byref(p)), ctx)
+
+
+def op2b_node_minmax(ctx, map_: int, q: int, qmin: int, qmax: int):
+    _check(load().op2b_node_minmax(ctx, map_, q, qmin, qmax), ctx)
+
+
+def op2b_node_limiter(ctx, map_: int, kind: int, eps2: float, q: int, G: int, dx: int,
+                      qmin: int, qmax: int, phi: int):
+    _check(load().op2b_node_limiter(ctx, map_, kind, eps2, q, G, dx, qmin, qmax, phi), ctx)
+
+
+def op2b_edge_flux_limited(ctx, args, gamma: float = 1.4, flags: int = 0):
+    a, n = _args(args)
+    p = FluxParams(2, flags, gamma, 1e-12)
+    _check(load().op2b_edge_flux_limited(ctx, a, n, ctypes.byref(p)), ctx)
 
 
 def op2b_viscous_prims(ctx, q: int, G: int, W: int, gamma: float = 1.4):

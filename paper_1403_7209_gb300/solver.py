@@ -17,6 +17,8 @@ from . import op2b as L
 
 RK5_ALPHA = (0.25, 1.0 / 6.0, 0.375, 0.5, 1.0)  # Jameson's 5-stage scheme
 RENUMBER = {"none": 0, "random": 1, "rcm": 2}  # "rcb" needs coordinates
+LIMITERS = {"van_albada": 0, "barth_jespersen": L.LIM_BARTH_JESPERSEN,
+            "venkatakrishnan": L.LIM_VENKATAKRISHNAN}
 
 
 class EdgeSolver:
@@ -31,13 +33,17 @@ class EdgeSolver:
     ``mixed`` adds the FP32 shadows used by the mixed-precision path;
     ``adjoint`` the adjoint and tangent (Jacobian-vector product) dats;
     ``viscous`` = (mu, prandtl, diff) adds the viscous flux to the residual
-    (Navier-Stokes instead of Euler).
+    (Navier-Stokes instead of Euler).  ``limiter`` picks the second-order
+    reconstruction: "van_albada" (per edge, the default), or the node
+    limiters "barth_jespersen" and "venkatakrishnan" (``limiter_eps2`` is
+    Venkatakrishnan's smoothing constant).
     """
 
     def __init__(self, edge, normal, dx, volume, q=None, device: int = 0,
                  renumber: str = "none", seed: int = 0, mixed: bool = False,
                  adjoint: bool = False, gamma: float = 1.4,
-                 eps_lim: float = 1e-12, stream=None, coords=None, viscous=None):
+                 eps_lim: float = 1e-12, stream=None, coords=None, viscous=None,
+                 limiter: str = "van_albada", limiter_eps2: float = 0.0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -76,6 +82,14 @@ class EdgeSolver:
             node("G32", 18, torch.float32)
             edgd("n32", 3, torch.float32, init=normal)
             edgd("dx32", 3, torch.float32, init=dx)
+        if limiter not in LIMITERS:
+            raise ValueError("limiter must be one of %s" % sorted(LIMITERS))
+        self.limiter, self.limiter_eps2 = limiter, float(limiter_eps2)
+        if LIMITERS[limiter]:
+            for nm in ("qmin", "qmax", "phi"):
+                node(nm, 6)
+                if mixed:
+                    node(nm + "32", 6, torch.float32)
         self.visc = tuple(float(v) for v in viscous) if viscous is not None else None
         if self.visc is not None:
             node("W", 20)
@@ -177,6 +191,14 @@ class EdgeSolver:
             self.a_f2_32 = [ind("q32", 0, R), ind("q32", 1, R), ind("G32", 0, R),
                             ind("G32", 1, R), dr("n32", R), dr("dx32", R),
                             ind("R", 0, I), ind("R", 1, I)]
+        if LIMITERS[self.limiter]:
+            self.a_f2phi = [ind("q", 0, R), ind("q", 1, R), ind("G", 0, R), ind("G", 1, R),
+                            ind("phi", 0, R), ind("phi", 1, R), dr("n", R), dr("dx", R),
+                            ind("R", 0, I), ind("R", 1, I)]
+            if self.mixed:
+                self.a_f2phi32 = [ind("q32", 0, R), ind("q32", 1, R), ind("G32", 0, R),
+                                  ind("G32", 1, R), ind("phi32", 0, R), ind("phi32", 1, R),
+                                  dr("n32", R), dr("dx32", R), ind("R", 0, I), ind("R", 1, I)]
         if self.visc is not None:
             self.a_vf = [ind("W", 0, R), ind("W", 1, R), dr("n", R), dr("dx", R),
                          ind("R", 0, I), ind("R", 1, I)]
@@ -212,8 +234,21 @@ class EdgeSolver:
         L.op2b_green_gauss(c, self.a_gg32 if mixed else self.a_gg, L.ZERO_INC)
         L.op2b_grad_scale(c, self.d["G32" if mixed else "G"], self.d["V"])
 
+    def node_limiter(self, mixed=False):
+        """phi from the neighbourhood min/max and the gradients G."""
+        c, d, sfx = self.ctx, self.d, "32" if mixed else ""
+        q, G, dx = ("q32", "G32", "dx32") if mixed else ("q", "G", "dx")
+        L.op2b_node_minmax(c, self.map, d[q], d["qmin" + sfx], d["qmax" + sfx])
+        L.op2b_node_limiter(c, self.map, LIMITERS[self.limiter], self.limiter_eps2, d[q], d[G],
+                            d[dx], d["qmin" + sfx], d["qmax" + sfx], d["phi" + sfx])
+
     def flux(self, order, mixed=False):
         """R = sum of edge fluxes (R zeroed first)."""
+        if order == 2 and LIMITERS[self.limiter]:
+            self.node_limiter(mixed)
+            L.op2b_edge_flux_limited(self.ctx, self.a_f2phi32 if mixed else self.a_f2phi,
+                                     self.gamma, L.ZERO_INC)
+            return
         if order == 1:
             a = self.a_f1_32 if mixed else self.a_f1
         else:
@@ -268,9 +303,9 @@ class EdgeSolver:
         L.op2b_dat_copy(self.ctx, self.d["q32"], self.d["q"])
 
     def _inviscid_only(self, what):
-        if self.visc is not None:
-            raise NotImplementedError(what + " loops cover the inviscid residual only; "
-                                      "build the solver without viscous")
+        if self.visc is not None or LIMITERS[self.limiter]:
+            raise NotImplementedError(what + " loops cover the inviscid residual with the van "
+                                      "Albada limiter only")
 
     def adjoint(self, order=2, recompute_gradient=True):
         """qbar = dJ/dq (dat qbar) and nbar = dJ/dn (dat nbar) of J = lam . R.

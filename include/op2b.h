@@ -462,6 +462,78 @@ int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const double* n,
                             double gamma, double* R, int64_t ldR,
                             void* stream);
 
+/* ------------------------------------------ owner-compute partitions
+ * The paper's distributed-memory execution (Sec. 3; Sec. 4 "OP2 ... an
+ * owner-compute model similar to that used in OPlus"): the nodes are split
+ * into parts; a part owns its nodes, executes every edge with an owned end
+ * (a cut edge runs in both of its parts) and, before a loop reads node data
+ * through the map, refreshes its halo -- the non-owned ends of its edges --
+ * from the owners.  The results of a part are then final on its owned
+ * nodes; halo rows hold partial sums and are overwritten by the next
+ * exchange.
+ *
+ * Recursive coordinate bisection into nparts parts (Sec. 5: the mesh's 3-D
+ * coordinates are split in x, y and z in turn until there is one part per
+ * process).  xyz: host, N x 3 node-major.  part (host, N): part of each node.
+ * A range meant for k parts is ordered by (coordinate on axis depth mod 3,
+ * node id) and cut after floor(size * floor(k/2) / k) nodes, so part sizes
+ * differ by at most one node per level.  Needs 1 <= nparts <= max(N, 1);
+ * otherwise OP2B_EINVAL.  No context, no GPU. */
+int op2b_host_partition_rcb(int64_t N, const double* xyz, int32_t nparts,
+                            int32_t* part);
+
+/* Halo plan of a node partition (host only; no context, no GPU).
+ * edge: E x 2 element-major (0-based); part: N values in [0, nparts).
+ * Per part p the plan holds its local mesh -- local node l is global node
+ * nodes[l]: the n_owned owned nodes in increasing id, then the halo nodes
+ * grouped by owner (increasing part), increasing id within a group -- its
+ * edges (global ids with an owned end, increasing), the local edge->node
+ * map (2 per edge, ends in the edge's own orientation), the import list
+ * (owner and owner-local id of each halo node) and the export list (the
+ * importers, increasing, and per importer the owned local ids it receives,
+ * in that importer's halo order: export list of p for q = the q-side import
+ * rows that name p, row by row).  Errors: OP2B_EINVAL (a part id or an edge
+ * end out of range; text from op2b_last_error(NULL)), OP2B_ENOMEM.  The
+ * handle owns host memory until op2b_halo_destroy. */
+typedef struct op2b_halo_s* op2b_halo;
+int op2b_halo_create(int64_t N, int64_t E, const int32_t* edge,
+                     const int32_t* part, int32_t nparts, op2b_halo* out);
+/* sizes[6] of part p: owned nodes, halo nodes, local edges, importers
+ * (neighbours this part sends to), exported rows, local edges with a
+ * non-owned end (the redundantly executed ones). */
+int op2b_halo_sizes(op2b_halo h, int32_t p, int64_t* sizes);
+/* Copy part p's lists into caller arrays (host; any may be NULL to skip):
+ * nodes (owned + halo), edges (local edges), local_map (2 x local edges),
+ * halo_owner and halo_src (halo nodes), nbr (importers), exp_off
+ * (importers + 1), exp_idx (exported rows). */
+int op2b_halo_part(op2b_halo h, int32_t p, int32_t* nodes, int32_t* edges,
+                   int32_t* local_map, int32_t* halo_owner, int32_t* halo_src,
+                   int32_t* nbr, int64_t* exp_off, int32_t* exp_idx);
+int op2b_halo_destroy(op2b_halo h);
+
+/* Halo exchange of one dat between parts held on the context's GPU (the
+ * op_access/halo update of Sec. 3, between parts in one device's memory):
+ * for every segment s (one per importer/owner pair) and entry k of it,
+ * dst[s][c * dst_ld[s] + dst_idx[t]] = src[s][c * src_ld[s] + src_idx[t]]
+ * for c < dim, t running over the entries of all segments in order
+ * (count[s] per segment).  src / dst: device pointers of SoA dats of `type`
+ * (F64 or F32) whose leading dimensions are src_ld / dst_ld; the pointers
+ * are captured at creation (re-create the exchange after moving a dat).
+ * Indices must lie in [0, ld) of their dat (checked on the host at
+ * creation: OP2B_EINVAL).  Rows of one exchange must not be both read and
+ * written.  Index lists are host arrays, copied to the device; the handle
+ * owns that device memory until op2b_exchange_destroy (which waits for the
+ * context's stream).  op2b_exchange_run launches one kernel on the
+ * context's stream. */
+typedef struct op2b_exchange_s* op2b_exchange;
+int op2b_exchange_create(op2b_ctx ctx, int32_t type, int32_t dim, int32_t nseg,
+                         const void* const* src, const int64_t* src_ld,
+                         void* const* dst, const int64_t* dst_ld,
+                         const int64_t* count, const int32_t* src_idx,
+                         const int32_t* dst_idx, op2b_exchange* out);
+int op2b_exchange_run(op2b_ctx ctx, op2b_exchange x);
+int op2b_exchange_destroy(op2b_ctx ctx, op2b_exchange x);
+
 /* ------------------------------------------------ host-only planners
  * Pure host functions (no context, no GPU), exported for validation. */
 

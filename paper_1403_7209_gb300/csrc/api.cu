@@ -209,10 +209,6 @@ int Ctx::own_plan(int map, DevOwnPlan** out) {
     if (!(c)) return OP2B_EINVAL;                     \
   } while (0)
 
-struct op2b_ctx_s {
-  Ctx c;
-};
-
 extern "C" const char* op2b_version(void) { return OP2B_VERSION_STR; }
 
 extern "C" int op2b_init(op2b_ctx* out, int32_t device, void* stream) {

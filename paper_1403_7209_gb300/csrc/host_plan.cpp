@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <string>
 #include <thread>
 
 namespace op2b {
@@ -311,6 +312,121 @@ void owner_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
   idx->resize(E);
   std::vector<int64_t> pos(p.begin(), p.end() - 1);
   for (int64_t e = 0; e < E; e++) (*idx)[pos[std::min(m0[e], m1[e])]++] = (int32_t)e;
+}
+
+bool rcb_parts(int64_t N, const double* xyz, int32_t nparts, int32_t* part) {
+  if (N < 0 || nparts < 1 || (int64_t)nparts > std::max<int64_t>(N, 1)) return false;
+  std::vector<int32_t> ids(N);
+  for (int64_t i = 0; i < N; i++) ids[i] = (int32_t)i;
+  struct Range {
+    int64_t lo, hi;
+    int32_t p0, k, depth;
+  };
+  std::vector<Range> st;
+  st.push_back({0, N, 0, nparts, 0});
+  while (!st.empty()) {
+    const Range r = st.back();
+    st.pop_back();
+    if (r.k == 1) {
+      for (int64_t t = r.lo; t < r.hi; t++) part[ids[t]] = r.p0;
+      continue;
+    }
+    const int ax = r.depth % 3;
+    const int32_t kl = r.k / 2;
+    const int64_t cut = r.lo + (r.hi - r.lo) * kl / r.k;
+    std::nth_element(ids.begin() + r.lo, ids.begin() + cut, ids.begin() + r.hi,
+                     [&](int32_t a, int32_t b) {
+                       const double ca = xyz[3 * (int64_t)a + ax], cb = xyz[3 * (int64_t)b + ax];
+                       return ca < cb || (ca == cb && a < b);
+                     });
+    st.push_back({cut, r.hi, r.p0 + kl, r.k - kl, r.depth + 1});
+    st.push_back({r.lo, cut, r.p0, kl, r.depth + 1});
+  }
+  return true;
+}
+
+bool build_halo_plan(int64_t N, int64_t E, const int32_t* edge, const int32_t* part,
+                     int32_t nparts, std::vector<HaloPart>* out, std::string* err) {
+  if (N < 0 || E < 0 || nparts < 1 || N > INT32_MAX || E > INT32_MAX) {
+    *err = "bad sizes";
+    return false;
+  }
+  for (int64_t i = 0; i < N; i++)
+    if (part[i] < 0 || part[i] >= nparts) {
+      *err = "node " + std::to_string(i) + " has part " + std::to_string(part[i]) +
+             " outside [0, " + std::to_string(nparts) + ")";
+      return false;
+    }
+  for (int64_t e = 0; e < 2 * E; e++)
+    if (edge[e] < 0 || edge[e] >= N) {
+      *err = "edge " + std::to_string(e / 2) + " has an end outside the node set";
+      return false;
+    }
+  std::vector<HaloPart>& P = *out;
+  P.assign(nparts, HaloPart());
+  // local id of every node in its owner: rank among the owner's nodes
+  std::vector<int32_t> own_local(N);
+  for (int64_t i = 0; i < N; i++) {
+    HaloPart& h = P[part[i]];
+    own_local[i] = (int32_t)h.n_owned++;
+    h.nodes.push_back((int32_t)i);
+  }
+  // edges with an owned end, and the (owner, node) pairs of the halo
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> halo(nparts);
+  for (int64_t e = 0; e < E; e++) {
+    const int32_t a = edge[2 * e], b = edge[2 * e + 1];
+    const int32_t pa = part[a], pb = part[b];
+    P[pa].edges.push_back((int32_t)e);
+    if (pb != pa) {
+      P[pb].edges.push_back((int32_t)e);
+      halo[pa].push_back({pb, b});
+      halo[pb].push_back({pa, a});
+    }
+  }
+  std::vector<int32_t> halo_local(N, -1);
+  for (int32_t p = 0; p < nparts; p++) {
+    HaloPart& h = P[p];
+    auto& hv = halo[p];
+    std::sort(hv.begin(), hv.end());
+    hv.erase(std::unique(hv.begin(), hv.end()), hv.end());
+    h.halo_owner.resize(hv.size());
+    h.halo_src.resize(hv.size());
+    for (size_t k = 0; k < hv.size(); k++) {
+      const int32_t r = hv[k].first, g = hv[k].second;
+      halo_local[g] = (int32_t)(h.n_owned + (int64_t)k);
+      h.nodes.push_back(g);
+      h.halo_owner[k] = r;
+      h.halo_src[k] = own_local[g];
+      // part r exports g to p; p increases in this loop, so every
+      // exporter's importer list stays sorted
+      HaloPart& o = P[r];
+      if (o.nbr.empty() || o.nbr.back() != p) {
+        o.nbr.push_back(p);
+        o.exp_off.push_back((int64_t)o.exp_idx.size());
+      }
+      o.exp_idx.push_back(own_local[g]);
+    }
+    h.lmap.resize(2 * h.edges.size());
+    for (size_t t = 0; t < h.edges.size(); t++) {
+      const int64_t e = h.edges[t];
+      bool cut = false;
+      for (int s = 0; s < 2; s++) {
+        const int32_t g = edge[2 * e + s];
+        if (part[g] == p) {
+          h.lmap[2 * t + s] = own_local[g];
+        } else {
+          h.lmap[2 * t + s] = halo_local[g];
+          cut = true;
+        }
+      }
+      h.halo_edges += cut;
+    }
+    for (size_t k = 0; k < hv.size(); k++) halo_local[hv[k].second] = -1;
+    hv.clear();
+    hv.shrink_to_fit();
+  }
+  for (auto& h : P) h.exp_off.push_back((int64_t)h.exp_idx.size());
+  return true;
 }
 
 }  // namespace op2b

@@ -63,6 +63,39 @@ void node_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
 void owner_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
                std::vector<int64_t>* ptr, std::vector<int32_t>* idx);
 
+// Owner-compute partitioning (the paper's distributed-memory model, Sec. 3:
+// every partition owns a set of nodes, executes every edge that has an
+// owned end -- redundantly where an edge is cut -- and imports the halo,
+// the non-owned ends of those edges, from their owners).
+//
+// Recursive coordinate bisection into `nparts` parts (Sec. 5: the
+// coordinates are split in x, y and z in turn until there are as many
+// parts as processes).  A range of nodes meant for k parts is ordered by
+// (coordinate on the axis of its depth, id) and cut after
+// floor(size * floor(k/2) / k) nodes; the lower part gets the lower part
+// numbers.  1 <= nparts <= max(N, 1).
+bool rcb_parts(int64_t N, const double* xyz, int32_t nparts, int32_t* part);
+
+struct HaloPart {
+  int64_t n_owned = 0;
+  // local node -> global node: owned nodes in increasing id, then the halo
+  // grouped by owner (increasing part), increasing id within a group
+  std::vector<int32_t> nodes;
+  std::vector<int32_t> edges;       // global edge ids with an owned end, increasing
+  std::vector<int32_t> lmap;        // 2 per local edge: local ids of its ends
+  std::vector<int32_t> halo_owner;  // per halo node: owning part
+  std::vector<int32_t> halo_src;    // per halo node: its local id in the owner
+  std::vector<int32_t> nbr;         // parts that import from this one, increasing
+  std::vector<int64_t> exp_off;     // nbr.size()+1 offsets into exp_idx
+  std::vector<int32_t> exp_idx;     // owned local ids sent to each importer,
+                                    // in the importer's halo order
+  int64_t halo_edges = 0;           // local edges with a non-owned end
+};
+
+// Local meshes and the exchange lists of a node partition.
+bool build_halo_plan(int64_t N, int64_t E, const int32_t* edge, const int32_t* part,
+                     int32_t nparts, std::vector<HaloPart>* out, std::string* err);
+
 // Hardware threads to use for host planning.
 int host_threads();
 

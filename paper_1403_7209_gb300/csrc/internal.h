@@ -187,3 +187,8 @@ struct Ctx {
 };
 
 }  // namespace op2b
+
+// The opaque handle of the C ABI.
+struct op2b_ctx_s {
+  op2b::Ctx c;
+};

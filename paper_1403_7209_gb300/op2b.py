@@ -146,6 +146,18 @@ _SIGS = {
                                                _PI32, _PI64]),
     "op2b_host_node_csr": (ctypes.c_int, [_I64, _I64, _PI32, _PI64, _PI64]),
     "op2b_host_rcb": (ctypes.c_int, [_I64, ctypes.POINTER(ctypes.c_double), _I32, _PI32]),
+    "op2b_host_partition_rcb": (ctypes.c_int, [_I64, ctypes.POINTER(ctypes.c_double), _I32,
+                                               _PI32]),
+    "op2b_halo_create": (ctypes.c_int, [_I64, _I64, _PI32, _PI32, _I32, ctypes.POINTER(_P)]),
+    "op2b_halo_sizes": (ctypes.c_int, [_P, _I32, _PI64]),
+    "op2b_halo_part": (ctypes.c_int, [_P, _I32, _PI32, _PI32, _PI32, _PI32, _PI32, _PI32,
+                                      _PI64, _PI32]),
+    "op2b_halo_destroy": (ctypes.c_int, [_P]),
+    "op2b_exchange_create": (ctypes.c_int, [_P, _I32, _I32, _I32, ctypes.POINTER(_P), _PI64,
+                                            ctypes.POINTER(_P), _PI64, _PI64, _PI32, _PI32,
+                                            ctypes.POINTER(_P)]),
+    "op2b_exchange_run": (ctypes.c_int, [_P, _P]),
+    "op2b_exchange_destroy": (ctypes.c_int, [_P, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -460,3 +472,77 @@ def op2b_host_node_csr(num_nodes: int, edge):
     _check(load().op2b_host_node_csr(num_nodes, edge.shape[0], _i32p(edge),
                                      _i64p(rowptr), _i64p(ends)))
     return rowptr, ends[:2 * edge.shape[0]]
+
+
+def op2b_host_partition_rcb(xyz, nparts: int) -> np.ndarray:
+    """Part of every node: recursive coordinate bisection into nparts."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(xyz.shape[0], dtype=np.int32)
+    _check(load().op2b_host_partition_rcb(
+        xyz.shape[0], xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nparts, _i32p(out)))
+    return out
+
+
+# ------------------------------------------------ owner-compute partitions
+HALO_FIELDS = ("owned", "halo", "edges", "importers", "exported", "halo_edges")
+
+
+def op2b_halo_create(num_nodes: int, edge, part, nparts: int):
+    edge = np.ascontiguousarray(edge, dtype=np.int32)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    h = _P()
+    _check(load().op2b_halo_create(num_nodes, edge.shape[0], _i32p(edge), _i32p(part), nparts,
+                                   ctypes.byref(h)))
+    return h
+
+
+def op2b_halo_sizes(h, p: int) -> dict:
+    out = np.zeros(6, dtype=np.int64)
+    _check(load().op2b_halo_sizes(h, p, _i64p(out)))
+    return dict(zip(HALO_FIELDS, (int(v) for v in out)))
+
+
+def op2b_halo_part(h, p: int) -> dict:
+    """Local mesh and exchange lists of part p (numpy arrays)."""
+    z = op2b_halo_sizes(h, p)
+    nodes = np.empty(z["owned"] + z["halo"], dtype=np.int32)
+    edges = np.empty(z["edges"], dtype=np.int32)
+    lmap = np.empty(2 * z["edges"], dtype=np.int32)
+    owner = np.empty(z["halo"], dtype=np.int32)
+    src = np.empty(z["halo"], dtype=np.int32)
+    nbr = np.empty(z["importers"], dtype=np.int32)
+    off = np.empty(z["importers"] + 1, dtype=np.int64)
+    exp = np.empty(z["exported"], dtype=np.int32)
+    _check(load().op2b_halo_part(h, p, _i32p(nodes), _i32p(edges), _i32p(lmap), _i32p(owner),
+                                 _i32p(src), _i32p(nbr), _i64p(off), _i32p(exp)))
+    return {"sizes": z, "nodes": nodes, "edges": edges, "local_map": lmap.reshape(-1, 2),
+            "halo_owner": owner, "halo_src": src, "nbr": nbr, "exp_off": off, "exp_idx": exp}
+
+
+def op2b_halo_destroy(h):
+    _check(load().op2b_halo_destroy(h))
+
+
+def op2b_exchange_create(ctx, type_: int, dim: int, src_ptrs, src_ld, dst_ptrs, dst_ld,
+                         counts, src_idx, dst_idx):
+    nseg = len(counts)
+    src_a = (_P * max(nseg, 1))(*src_ptrs)
+    dst_a = (_P * max(nseg, 1))(*dst_ptrs)
+    sld = np.ascontiguousarray(src_ld, dtype=np.int64)
+    dld = np.ascontiguousarray(dst_ld, dtype=np.int64)
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    si = np.ascontiguousarray(src_idx, dtype=np.int32)
+    di = np.ascontiguousarray(dst_idx, dtype=np.int32)
+    x = _P()
+    _check(load().op2b_exchange_create(ctx, type_, dim, nseg, src_a, _i64p(sld), dst_a,
+                                       _i64p(dld), _i64p(cnt), _i32p(si), _i32p(di),
+                                       ctypes.byref(x)), ctx)
+    return x
+
+
+def op2b_exchange_run(ctx, x):
+    _check(load().op2b_exchange_run(ctx, x), ctx)
+
+
+def op2b_exchange_destroy(ctx, x):
+    _check(load().op2b_exchange_destroy(ctx, x), ctx)

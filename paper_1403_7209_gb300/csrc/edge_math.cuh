@@ -231,36 +231,72 @@ __device__ __forceinline__ double max_nonneg(double a, double b) {
   return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
 }
 
-// Rusanov flux of the face states (qL, qR) in FP64: the two densities are
-// inverted together, the sound speeds come from sqrt2, the larger wave
-// speed is picked by an integer comparison.
+// |x| as a float for ranking: truncated, 0 below the float range, +inf
+// above it (integer operations only; relative error < 2^-23 in range).
+__device__ __forceinline__ float abs_f32_rank(double x) {
+  const int hi = __double2hiint(x) & 0x7fffffff;
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned e = (unsigned)hi >> 20;
+  const float f = __int_as_float(((hi - 0x38000000) << 3) | (int)(lo >> 29));
+  return e < 897u ? 0.0f : (e > 1150u ? __int_as_float(0x7f800000) : f);
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Rusanov flux of the face states (qL, qR) in FP64.  Everything is computed
+// at half scale -- 1/(2 rho), u.n/2, p/2, (a|n|/2)^2, the half fluxes and
+// s/2 -- which is exact (powers of two), so that
+// F = f(qL).n/2 + f(qR).n/2 - (s/2)(qR - qL) needs no final halving.  The
+// two densities are inverted together.  The larger wave speed s is found
+// by ranking the two sides with FP32 estimates (error < 2^-20) and taking
+// the FP64 square root of the larger side only; when the estimates are
+// within 2^-14 of each other both sides are computed exactly and the
+// larger is picked by an integer comparison of the bit patterns (ties take
+// the left state), so s is always the exact larger value.
 __device__ __forceinline__ void rusanov_f64(const double* qL, const double* qR,
                                             double nx, double ny, double nz,
                                             const Gas<double>& g, double* F) {
   const double gnn = g.gamma * fma(nz, nz, fma(ny, ny, nx * nx));
   double rho[2] = {qL[0], qR[0]}, rr[2];
-  batch_reciprocal<2>(rho, 1.0, rr);
+  batch_reciprocal<2>(rho, 0.5, rr);  // rr = 1 / (2 rho)
   const double hgm1 = 0.5 * g.gm1;
-  double f[2][6], lam[2];
+  double f[2][6], uh[2], x[2];
+  float rank[2];
 #pragma unroll
   for (int sd = 0; sd < 2; sd++) {
     const double* q = sd ? qR : qL;
     const double mn = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
-    const double un = mn * rr[sd];
+    const double un = mn * rr[sd];  // u.n / 2
     const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
-    const double p = fma(-hgm1 * mm, rr[sd], g.gm1 * q[4]);
-    const double x = p * rr[sd] * gnn;
-    lam[sd] = fabs(un) + (seedable(x) ? sqrt2(x) : sqrt(x));
-    f[sd][0] = mn;  // rho u.n
-    f[sd][1] = fma(q[1], un, p * nx);
-    f[sd][2] = fma(q[2], un, p * ny);
-    f[sd][3] = fma(q[3], un, p * nz);
-    f[sd][4] = (q[4] + p) * un;
+    const double ph = fma(-hgm1 * mm, rr[sd], hgm1 * q[4]);  // p / 2
+    x[sd] = ph * rr[sd] * gnn;  // (a |n| / 2)^2
+    uh[sd] = fabs(un);
+    rank[sd] = abs_f32_rank(un) + (seedable(x[sd]) ? sqrt_approx(f32_of_f64(x[sd])) : 0.0f);
+    f[sd][0] = mn;  // rho u.n (halved below)
+    f[sd][1] = fma(q[1], un, ph * nx);
+    f[sd][2] = fma(q[2], un, ph * ny);
+    f[sd][3] = fma(q[3], un, ph * nz);
+    f[sd][4] = fma(2.0, ph, q[4]) * un;  // (rho E + p) u.n / 2
     f[sd][5] = q[5] * un;
   }
-  const double s = max_nonneg(lam[0], lam[1]);
+  double s;
+  const bool ranked = seedable(x[0]) && seedable(x[1]) &&
+                      (rank[0] > rank[1] * 1.00006104f || rank[1] > rank[0] * 1.00006104f);
+  if (ranked) {
+    const bool r = rank[1] > rank[0];
+    const double xs = r ? x[1] : x[0];
+    s = (r ? uh[1] : uh[0]) + sqrt2(xs);
+  } else {
+    const double l0 = uh[0] + (seedable(x[0]) ? sqrt2(x[0]) : sqrt(x[0]));
+    const double l1 = uh[1] + (seedable(x[1]) ? sqrt2(x[1]) : sqrt(x[1]));
+    s = max_nonneg(l0, l1);
+  }
+  F[0] = fma(-s, qR[0] - qL[0], 0.5 * (f[0][0] + f[1][0]));
 #pragma unroll
-  for (int k = 0; k < 6; k++) F[k] = 0.5 * fma(-s, qR[k] - qL[k], f[0][k] + f[1][k]);
+  for (int k = 1; k < 6; k++) F[k] = fma(-s, qR[k] - qL[k], f[0][k] + f[1][k]);
 }
 
 // vi, vj: q (6) then G (18, component 3k+d); F: the Rusanov flux of the

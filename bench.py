@@ -297,6 +297,62 @@ def mixed_extra(torch, L, s, args, stream, ms64, E, N):
             "loops": out_loops, "residual_rel_err_per_component": rerr}
 
 
+def ff_extra(torch, L, s, args, stream, ms64, E, N):
+    """Float-float stage: Green-Gauss and scaling in FP64, G converted to its
+    float-float shadow, the second-order flux in float-float arithmetic
+    (FP32 units), the update with the float-float shadow of q; per-loop
+    times, speed-up over the FP64 stage and the residual's difference from
+    the FP64 path's."""
+    names = ["gg", "scale", "to_ff", "flux2_ff", "update"]
+    s.set_strategy(L.LOOP_FLUX2, L.PREC_FF, L.STRAT_AUTO)
+    s.sync_shadow(ff=True)
+
+    def stage(ev=None):
+        if ev: ev[0].record(stream)
+        L.op2b_green_gauss(s.ctx, s.a_gg, L.ZERO_INC)
+        if ev: ev[1].record(stream)
+        L.op2b_grad_scale(s.ctx, s.d["G"], s.d["V"])
+        if ev: ev[2].record(stream)
+        L.op2b_dat_copy(s.ctx, s.d["G_ff"], s.d["G"])
+        if ev: ev[3].record(stream)
+        L.op2b_edge_flux(s.ctx, s.a_f2_ff, 2, s.gamma, s.eps_lim, L.ZERO_INC)
+        if ev: ev[4].record(stream)
+        L.op2b_node_update(s.ctx, s.d["q0"], s.d["q"], s.d["R"], s.d["V"], s.d["dt"], 0.25,
+                           s.d["q_ff"])
+        if ev: ev[5].record(stream)
+    for _ in range(args.warmup):
+        stage()
+    evs = [loop_events(torch, 6) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t0, t1 = loop_events(torch, 2)
+    t0.record(stream)
+    for k in range(args.steps):
+        stage(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    fms = t0.elapsed_time(t1) / args.steps
+    loops = {nm: statistics.mean(evs[k][j].elapsed_time(evs[k][j + 1]) for k in range(args.steps))
+             for j, nm in enumerate(names)}
+    fl = loops["flux2_ff"]
+    hbm, _ = read_peaks()
+    # difference from the FP64 path on one state (same q, same G)
+    s.sync_shadow(ff=True)
+    s.residual(2)
+    R64 = s.t["R"][:, :N].clone()
+    s.residual(2, ff=True)
+    Rff = s.t["R"][:, :N].clone()
+    diff = ((Rff - R64).abs().amax(dim=1) / R64.abs().amax(dim=1)).tolist()
+    return {"ms_per_stage": fms, "edges_per_s": E / (fms * 1e-3), "speedup_vs_fp64": ms64 / fms,
+            "loops": {nm: {"ms": loops[nm]} for nm in names},
+            "flux2_ff": {"ms": fl, "edges_per_s": E / (fl * 1e-3),
+                         "strategy": L.STRATEGY_NAMES[s.plan_stats(L.LOOP_FLUX2, L.PREC_FF)["strategy"]],
+                         "fp64_equivalent_tflops": FLOPS_PER_EDGE_FLUX2 * E / (fl * 1e-3) / 1e12,
+                         "vs_fp64_peak": FLOPS_PER_EDGE_FLUX2 * E / (fl * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "gbs": BYTES_PER_EDGE["flux2"] * E / (fl * 1e-3) / 1e9,
+                         "hbm_frac": BYTES_PER_EDGE["flux2"] * E / (fl * 1e-3) / 1e9 / hbm},
+            "residual_max_diff_vs_fp64_path_per_component": diff}
+
+
 def adjoint_extra(torch, s, args, stream, E):
     """Reverse sweep (flux adjoint, scaling adjoint, Green-Gauss adjoint;
     edge states recomputed, G kept from the forward pass) against the
@@ -622,11 +678,12 @@ def main():
     m, q = build_mesh(args.n, args.numbering)
     stream = torch.cuda.current_stream()
     s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=local, renumber=args.numbering,
-                   mixed=not args.no_extras, adjoint=not args.no_extras, stream=stream)
+                   mixed=not args.no_extras, adjoint=not args.no_extras, stream=stream,
+                   ff=not args.no_extras)
     if args.tune_cache and os.path.exists(args.tune_cache):
         L.op2b_load_tuning(s.ctx, args.tune_cache)
     for loop in range(L.NUM_LOOPS):
-        for prec in (0, 1):
+        for prec in range(L.NUM_PREC):
             s.set_strategy(loop, prec, L.STRAT_AUTO)
     s.time_step(0.5)
     L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
@@ -711,6 +768,7 @@ def main():
 
     if not args.no_extras:
         line["mixed"] = mixed_extra(torch, L, s, args, stream, ms, E, N)
+        line["float_float"] = ff_extra(torch, L, s, args, stream, ms, E, N)
         line["adjoint"] = adjoint_extra(torch, s, args, stream, E)
         line["tangent"] = tangent_extra(torch, s, args, stream, E)
         line["viscous"] = viscous_extra(torch, L, m, q, args, stream, local, E)

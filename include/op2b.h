@@ -62,6 +62,14 @@ typedef int32_t op2b_dat;
 #define OP2B_F64 0
 #define OP2B_F32 1
 #define OP2B_I32 2
+/* float-float: a value is the unevaluated sum hi + lo of two floats (hi
+ * first, 8 bytes per element like a double; about 47 significant bits).
+ * Shadows of F64 dats for the float-float flux (op2b_edge_flux); made by
+ * op2b_dat_copy (F64 -> FF converts with integer operations: hi = the top
+ * 24 significant bits, lo the next 23; magnitudes below 2^-126 become 0,
+ * below 2^-103 keep hi only, 2^128 and above become infinite) and by
+ * op2b_node_update's shadow output. */
+#define OP2B_FF 3
 
 /* the identity "map" of a direct argument (OP_ID in the paper) */
 #define OP2B_ID (-1)
@@ -94,6 +102,10 @@ typedef struct {
  * gradients) */
 #define OP2B_PREC_F64 0
 #define OP2B_PREC_F32 1
+/* FF node and edge data (float-float shadows), float-float arithmetic, FP64
+ * INC targets: only the second-order flux (op2b_edge_flux) */
+#define OP2B_PREC_FF 2
+#define OP2B_NUM_PREC 3
 
 /* race-resolution strategies (Sec. 4.1: mini-partitions with block
  * colouring; the other two are not in the paper) */
@@ -211,7 +223,7 @@ int op2b_renumber_rcb(op2b_ctx ctx, op2b_map edge2node, op2b_dat coords,
  * through an arity-2 edge->node map and increments both end nodes (INC).
  * All indirect arguments must use the same map.  With OP2B_ZERO_INC the
  * INC dats are zeroed first; otherwise the loop adds to them.  The loop's
- * precision (OP2B_PREC_F64 / F32) is the type of its READ node dats. */
+ * precision (OP2B_PREC_F64 / F32 / FF) is the type of its READ node dats. */
 
 /* Green-Gauss gradient sums, per edge (i, j) with normal n:
  *   Graw_i[k][d] += (q_i,k + q_j,k)/2 * n_d,  Graw_j[k][d] -= the same.
@@ -231,7 +243,13 @@ int op2b_green_gauss(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *   dx ID READ (edge, dim 3), R 0 INC, R 1 INC.
  * R is always F64 (dim 6).  q, G, n, dx are all F64 or all F32; with F32 the
  * flux arithmetic is FP32 and each edge's flux is converted to FP64 before
- * it is added into R. */
+ * it is added into R.  Order 2 also takes all four as FF (float-float)
+ * shadows: every operation of the reconstruction and the flux is then done
+ * in float-float on the FP32 units (about 2^-47 per operation relative to
+ * its operands; the flux stays within ~1e-14 of the FP64 definition
+ * relative to its terms, values within the FF range), and each edge's flux
+ * is converted to FP64 before it is added into R.  Other loops reject FF
+ * dats with OP2B_ETYPE. */
 int op2b_edge_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                    const op2b_flux_params* prm);
 
@@ -367,7 +385,8 @@ int op2b_grad_scale_adjoint(op2b_ctx ctx, op2b_dat Gbar, op2b_dat V);
 int op2b_time_step(op2b_ctx ctx, op2b_dat V, op2b_dat lam, double cfl,
                    op2b_dat dt);
 /* Runge-Kutta stage update q = q0 - alpha (dt/V) R (F64 dim 6, F64 dim 1);
- * q32 (F32 dim 6, or -1) receives the FP32 shadow of the new q. */
+ * q32 (F32 or FF dim 6, or -1) receives the FP32 or float-float shadow of
+ * the new q. */
 int op2b_node_update(op2b_ctx ctx, op2b_dat q0, op2b_dat q, op2b_dat R,
                      op2b_dat V, op2b_dat dt, double alpha, op2b_dat q32);
 /* Transpose of op2b_node_update with respect to q0 and R, the step of the
@@ -398,7 +417,8 @@ int op2b_dat_axpy(op2b_ctx ctx, op2b_dat y, double a, op2b_dat x);
 int op2b_dat_reduce(op2b_ctx ctx, op2b_dat dat, int32_t op, double* out_dev);
 /* Set every component of a dat to `value`. */
 int op2b_dat_fill(op2b_ctx ctx, op2b_dat dat, double value);
-/* dst = src component-wise (same set and dim; F64 <-> F32 conversion). */
+/* dst = src component-wise (same set and dim; F64 <-> F32 and F64 <-> FF
+ * conversions). */
 int op2b_dat_copy(op2b_ctx ctx, op2b_dat dst, op2b_dat src);
 
 /* ------------------------------------------------ planner and autotuner

@@ -18,7 +18,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libop2b.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "loops_f64.cu", "loops_f32.cu", "loops_adj.cu", "loops_visc.cu", "loops_lim.cu",
+SOURCES = ["api.cu", "loops_f64.cu", "loops_f32.cu", "loops_ff.cu", "loops_adj.cu", "loops_visc.cu", "loops_lim.cu",
            "node_loops.cu", "noalloc.cu", "halo.cu", "host_plan.cpp"]
 
 

@@ -237,7 +237,7 @@ extern "C" int op2b_init(op2b_ctx* out, int32_t device, void* stream) {
   c.smem_optin = (size_t)optin;
   // defaults: FP64 atomics everywhere until told or tuned otherwise
   for (int l = 0; l < OP2B_NUM_LOOPS; l++)
-    for (int p = 0; p < 2; p++) c.strat[l][p] = Strategy();
+    for (int p = 0; p < OP2B_NUM_PREC; p++) c.strat[l][p] = Strategy();
   *out = h;
   return OP2B_OK;
 }
@@ -327,7 +327,7 @@ extern "C" int op2b_decl_map(op2b_ctx h, op2b_set from, op2b_set to, int32_t ari
   return OP2B_OK;
 }
 
-static int esize(int type) { return type == OP2B_F64 ? 8 : 4; }
+static int esize(int type) { return (type == OP2B_F64 || type == OP2B_FF) ? 8 : 4; }
 
 extern "C" int op2b_decl_dat(op2b_ctx h, op2b_set set, int32_t dim, int32_t type, void* ptr,
                              int64_t ld, const char* name, op2b_dat* out) {
@@ -335,7 +335,7 @@ extern "C" int op2b_decl_dat(op2b_ctx h, op2b_set set, int32_t dim, int32_t type
   Ctx& c = h->c;
   if (!out || !valid_set(c, set) || dim < 1 || dim > 64)
     return c.fail(OP2B_EINVAL, "decl_dat: bad set, dim or output");
-  if (type != OP2B_F64 && type != OP2B_F32 && type != OP2B_I32)
+  if (type != OP2B_F64 && type != OP2B_F32 && type != OP2B_I32 && type != OP2B_FF)
     return c.fail(OP2B_ETYPE, "decl_dat: unknown type");
   int64_t n = c.sets[set].size;
   if (ld == 0) ld = n;
@@ -536,9 +536,10 @@ int check_args(Ctx& c, const char* loop, const op2b_arg* a, int nargs, const Spe
     if (sp[k].tcls == 'D') {
       if (d.type != OP2B_F64) return c.fail(OP2B_ETYPE, at + ": must be F64");
     } else {
-      if (d.type != OP2B_F64 && d.type != OP2B_F32) return c.fail(OP2B_ETYPE, at + ": must be F64 or F32");
+      if (d.type != OP2B_F64 && d.type != OP2B_F32 && d.type != OP2B_FF)
+        return c.fail(OP2B_ETYPE, at + ": must be F64, F32 or FF");
       if (ptype < 0) ptype = d.type;
-      if (d.type != ptype) return c.fail(OP2B_ETYPE, at + ": mixed F64/F32 data");
+      if (d.type != ptype) return c.fail(OP2B_ETYPE, at + ": mixed F64/F32/FF data");
     }
   }
   // the two ends of an indirect dat (adjacent entries 0 and 1) are one dat
@@ -546,7 +547,7 @@ int check_args(Ctx& c, const char* loop, const op2b_arg* a, int nargs, const Spe
     if (sp[k].idx == 0 && sp[k + 1].idx == 1 && a[k].dat != a[k + 1].dat)
       return c.fail(OP2B_EINVAL, std::string(loop) + ": map entries 0 and 1 of one argument use different dats");
   out->map = map;
-  out->prec = ptype == OP2B_F32 ? OP2B_PREC_F32 : OP2B_PREC_F64;
+  out->prec = ptype == OP2B_F32 ? OP2B_PREC_F32 : (ptype == OP2B_FF ? OP2B_PREC_FF : OP2B_PREC_F64);
   out->N = c.sets[m.to].size;
   out->E = c.sets[m.from].size;
   return OP2B_OK;
@@ -560,6 +561,7 @@ std::string tune_key(const LoopLaunch& L, bool det) {
 }
 
 int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
+  if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // FLUX2 only (checked there)
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);
   if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
@@ -1103,7 +1105,8 @@ static int grad_scale_impl(op2b_ctx h, op2b_dat G, op2b_dat V, const char* what)
   int rc;
   if ((rc = node_dat(c, G, 18, -1, -1, what))) return rc;
   const DatRec& g = c.dats[G];
-  if (g.type == OP2B_I32) return c.fail(OP2B_ETYPE, std::string(what) + ": G must be F64 or F32");
+  if (g.type != OP2B_F64 && g.type != OP2B_F32)
+    return c.fail(OP2B_ETYPE, std::string(what) + ": G must be F64 or F32");
   if ((rc = node_dat(c, V, 1, OP2B_F64, g.set, what))) return rc;
   return node_grad_scale(&c, g.ptr, g.type, g.ld, (const double*)c.dats[V].ptr, c.sets[g.set].size);
 }
@@ -1193,7 +1196,7 @@ extern "C" int op2b_viscous_prims(op2b_ctx h, op2b_dat q, op2b_dat G, op2b_dat W
   int rc;
   if ((rc = node_dat(c, q, 6, -1, -1, "viscous_prims"))) return rc;
   const DatRec& rq = c.dats[q];
-  if (rq.type == OP2B_I32) return c.fail(OP2B_ETYPE, "viscous_prims: q must be F64 or F32");
+  if (rq.type != OP2B_F64 && rq.type != OP2B_F32) return c.fail(OP2B_ETYPE, "viscous_prims: q must be F64 or F32");
   if ((rc = node_dat(c, G, 18, rq.type, rq.set, "viscous_prims")) ||
       (rc = node_dat(c, W, 20, rq.type, rq.set, "viscous_prims")))
     return rc;
@@ -1226,16 +1229,20 @@ extern "C" int op2b_node_update(op2b_ctx h, op2b_dat q0, op2b_dat q, op2b_dat R,
   if ((rc = node_dat(c, q, 6, OP2B_F64, s, "node_update")) || (rc = node_dat(c, R, 6, OP2B_F64, s, "node_update")) ||
       (rc = node_dat(c, V, 1, OP2B_F64, s, "node_update")) || (rc = node_dat(c, dt, 1, OP2B_F64, s, "node_update")))
     return rc;
-  float* p32 = nullptr;
-  int64_t ld32 = 0;
+  void* psh = nullptr;
+  int tsh = OP2B_F32;
+  int64_t ldsh = 0;
   if (q32 >= 0) {
-    if ((rc = node_dat(c, q32, 6, OP2B_F32, s, "node_update"))) return rc;
-    p32 = (float*)c.dats[q32].ptr;
-    ld32 = c.dats[q32].ld;
+    if ((rc = node_dat(c, q32, 6, -1, s, "node_update"))) return rc;
+    tsh = c.dats[q32].type;
+    if (tsh != OP2B_F32 && tsh != OP2B_FF)
+      return c.fail(OP2B_ETYPE, "node_update: the shadow of q must be F32 or FF");
+    psh = c.dats[q32].ptr;
+    ldsh = c.dats[q32].ld;
   }
   return node_update(&c, (const double*)c.dats[q0].ptr, c.dats[q0].ld, (double*)c.dats[q].ptr, c.dats[q].ld,
                      (const double*)c.dats[R].ptr, c.dats[R].ld, (const double*)c.dats[V].ptr,
-                     (const double*)c.dats[dt].ptr, alpha, p32, ld32, c.sets[s].size);
+                     (const double*)c.dats[dt].ptr, alpha, psh, tsh, ldsh, c.sets[s].size);
 }
 
 extern "C" int op2b_node_update_adjoint(op2b_ctx h, op2b_dat sbar, op2b_dat qbar, op2b_dat lam,
@@ -1303,7 +1310,7 @@ extern "C" int op2b_set_strategy(op2b_ctx h, int32_t loop, int32_t prec, int32_t
                                  int32_t part, int32_t staged) {
   CTX_CHECK(h);
   Ctx& c = h->c;
-  if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec != 0 && prec != 1))
+  if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec < 0 || prec >= OP2B_NUM_PREC))
     return c.fail(OP2B_EINVAL, "set_strategy: bad loop or precision");
   if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_OWNER)
     return c.fail(OP2B_EINVAL, "set_strategy: bad strategy");
@@ -1373,7 +1380,7 @@ extern "C" int op2b_load_tuning(op2b_ctx h, const char* path) {
 extern "C" int op2b_plan_stats(op2b_ctx h, int32_t loop, int32_t prec, op2b_map map, op2b_plan_stats_t* out) {
   CTX_CHECK(h);
   Ctx& c = h->c;
-  if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec != 0 && prec != 1) || !out || !valid_map(c, map))
+  if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec < 0 || prec >= OP2B_NUM_PREC) || !out || !valid_map(c, map))
     return c.fail(OP2B_EINVAL, "plan_stats: bad loop, precision, map or output");
   const Strategy& s = c.strat[loop][prec];
   memset(out, 0, sizeof *out);

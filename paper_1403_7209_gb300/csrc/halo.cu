@@ -163,8 +163,8 @@ extern "C" int op2b_exchange_create(op2b_ctx h, int32_t type, int32_t dim, int32
   Ctx* c = &h->c;
   if (!out) return c->fail(OP2B_EINVAL, "exchange_create: null output");
   *out = nullptr;
-  if (type != OP2B_F64 && type != OP2B_F32)
-    return c->fail(OP2B_ETYPE, "exchange_create: type must be F64 or F32");
+  if (type != OP2B_F64 && type != OP2B_F32 && type != OP2B_FF)
+    return c->fail(OP2B_ETYPE, "exchange_create: type must be F64, F32 or FF");
   if (dim < 1 || dim > 64) return c->fail(OP2B_EDIM, "exchange_create: dim must be in [1, 64]");
   if (nseg < 0 || (nseg > 0 && (!src || !src_ld || !dst || !dst_ld || !count)))
     return c->fail(OP2B_EINVAL, "exchange_create: bad segment arrays");
@@ -216,7 +216,7 @@ extern "C" int op2b_exchange_run(op2b_ctx h, op2b_exchange x) {
   const int block = 256;
   const int64_t want = (x->n + block - 1) / block;
   const int grid = (int)std::min<int64_t>(want, (int64_t)c->sm_count * 8);
-  if (x->type == OP2B_F64)
+  if (x->type == OP2B_F64 || x->type == OP2B_FF)  // 8-byte rows, copied bitwise
     k_exchange<double><<<grid, block, 0, c->stream>>>(x->seg, x->eseg, x->sidx, x->didx, x->n,
                                                        x->dim);
   else

@@ -117,6 +117,8 @@ void set_thread_error(const std::string& msg);
 // FLUX2_TAN, GG_TAN.
 int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_f32(Ctx* c, const LoopLaunch& L, const Strategy& s);
+// loops_ff.cu: FLUX2 with float-float arithmetic (float-float READ dats)
+int launch_ff(Ctx* c, const LoopLaunch& L, const Strategy& s);
 int launch_adj(Ctx* c, const LoopLaunch& L, const Strategy& s);
 // loops_lim.cu: FLUX2_PHI (FP64 or FP32) and the node min/max and limiter
 int launch_lim(Ctx* c, const LoopLaunch& L, const Strategy& s);
@@ -136,8 +138,8 @@ int node_time_step(Ctx* c, const double* V, const double* lam, double cfl,
                    double* dt, int64_t N);
 int node_update(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
                 const double* R, int64_t ldR, const double* V,
-                const double* dt, double alpha, float* q32, int64_t ld32,
-                int64_t N);
+                const double* dt, double alpha, void* shadow, int shadow_type,
+                int64_t ldsh, int64_t N);
 int node_update_adjoint(Ctx* c, const double* sb, int64_t ldsb, double* qb, int64_t ldqb,
                         double* lam, int64_t ldl, const double* V, const double* dt,
                         double alpha, int64_t N);
@@ -162,7 +164,7 @@ struct Ctx {
   std::vector<MapRec> maps;
   std::vector<DatRec> dats;
   std::string err;
-  Strategy strat[OP2B_NUM_LOOPS][2];
+  Strategy strat[OP2B_NUM_LOOPS][OP2B_NUM_PREC];
   std::map<std::pair<int, int>, DevBlockPlan> bplans;  // (map, part)
   std::map<int, DevSegPlan> splans;                    // map
   std::map<int, DevOwnPlan> oplans;                    // map

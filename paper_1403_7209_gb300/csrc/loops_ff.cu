@@ -1,0 +1,47 @@
+// Float-float edge loop: the second-order flux with its arithmetic in
+// float-float (FP32 instructions, ~47 significant bits), reading
+// float-float shadows of q, G, n and dx and adding each edge's flux,
+// converted to FP64, into the FP64 residual under any strategy.
+#include "ff_math.cuh"
+#include "launch.cuh"
+
+namespace op2b {
+
+// v = q (6), G (18) of one node as float-float values
+struct BodyFlux2FF {
+  using TN = float2;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = 24, OUT = 6, MODE = MODE_ANTI, DIM0 = 6;
+  const float2* q;
+  int64_t ldq;
+  const float2* G;
+  int64_t ldG;
+  const float2* n;
+  int64_t ldn;
+  const float2* dx;
+  int64_t lddx;
+  GasFF g;
+  __device__ __forceinline__ void load(int64_t i, float2* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+#pragma unroll
+    for (int c = 0; c < 18; c++) v[6 + c] = ldro(G + c * ldG + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const float2* vi, const float2* vj,
+                                       double* oi, double*) const {
+    flux2_ff(vi, vj, ldro(dx + e), ldro(dx + lddx + e), ldro(dx + 2 * lddx + e), ldro(n + e),
+             ldro(n + ldn + e), ldro(n + 2 * ldn + e), g, oi);
+  }
+};
+
+int launch_ff(Ctx* c, const LoopLaunch& L, const Strategy& s) {
+  if (L.loop != OP2B_LOOP_FLUX2)
+    return c->fail(OP2B_ETYPE, "float-float dats: only the second-order flux has a float-float variant");
+  BodyFlux2FF b{(const float2*)L.q, L.ldq, (const float2*)L.G, L.ldG, (const float2*)L.n, L.ldn,
+                (const float2*)L.dx, L.lddx, gas_ff(L.gamma, L.eps)};
+  Targets<double, 6> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};
+  return run_body(c, b, L, s, tg);
+}
+
+}  // namespace op2b

@@ -4,6 +4,7 @@
 // array is read and written with unit stride.
 #include <algorithm>
 
+#include "ff_math.cuh"
 #include "internal.h"
 
 namespace op2b {
@@ -50,13 +51,15 @@ int node_time_step(Ctx* c, const double* V, const double* lam, double cfl,
   return c->launched("time_step");
 }
 
-// q = q0 - alpha (dt/V) R, with the FP32 shadow of q when q32 != null
+// q = q0 - alpha (dt/V) R, with the shadow of q (FP32 or float-float) when
+// sh != null
+template <typename TS>
 __global__ void k_update(const double* __restrict__ q0, int64_t ld0,
                          double* __restrict__ q, int64_t ldq,
                          const double* __restrict__ R, int64_t ldR,
                          const double* __restrict__ V,
                          const double* __restrict__ dt, double alpha,
-                         float* __restrict__ q32, int64_t ld32, int64_t N) {
+                         TS* __restrict__ sh, int64_t ldsh, int64_t N) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     double a = alpha * (dt[i] / V[i]);
@@ -64,18 +67,26 @@ __global__ void k_update(const double* __restrict__ q0, int64_t ld0,
     for (int k = 0; k < 6; k++) {
       double v = q0[k * ld0 + i] - a * R[k * ldR + i];
       q[k * ldq + i] = v;
-      if (q32) q32[k * ld32 + i] = (float)v;
+      if (sh) {
+        if constexpr (sizeof(TS) == 4) sh[k * ldsh + i] = (float)v;
+        else sh[k * ldsh + i] = ff_of_f64(v);
+      }
     }
   }
 }
 
 int node_update(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
                 const double* R, int64_t ldR, const double* V,
-                const double* dt, double alpha, float* q32, int64_t ld32,
-                int64_t N) {
+                const double* dt, double alpha, void* shadow, int shadow_type,
+                int64_t ldsh, int64_t N) {
   if (N == 0) return OP2B_OK;
-  k_update<<<grid_for(c, N, 256), 256, 0, c->stream>>>(q0, ld0, q, ldq, R, ldR, V, dt,
-                                                       alpha, q32, ld32, N);
+  const unsigned g = grid_for(c, N, 256);
+  if (shadow && shadow_type == OP2B_FF)
+    k_update<float2><<<g, 256, 0, c->stream>>>(q0, ld0, q, ldq, R, ldR, V, dt, alpha,
+                                               (float2*)shadow, ldsh, N);
+  else
+    k_update<float><<<g, 256, 0, c->stream>>>(q0, ld0, q, ldq, R, ldR, V, dt, alpha,
+                                              (float*)shadow, ldsh, N);
   return c->launched("update");
 }
 
@@ -138,6 +149,8 @@ int node_fill(Ctx* c, void* p, int type, int64_t ld, int dim, int64_t n,
     k_fill<double><<<g, 256, 0, c->stream>>>((double*)p, ld, dim, n, value);
   else if (type == OP2B_F32)
     k_fill<float><<<g, 256, 0, c->stream>>>((float*)p, ld, dim, n, (float)value);
+  else if (type == OP2B_FF)
+    k_fill<float2><<<g, 256, 0, c->stream>>>((float2*)p, ld, dim, n, ff_split_host(value));
   else
     k_fill<int32_t><<<g, 256, 0, c->stream>>>((int32_t*)p, ld, dim, n, (int32_t)value);
   return c->launched("fill");
@@ -152,6 +165,20 @@ __global__ void k_copy(TD* __restrict__ d, int64_t ldd,
     for (int k = 0; k < dim; k++) d[k * ldd + i] = (TD)s[k * lds + i];
 }
 
+// double -> float-float and back (ff_of_f64 / f64_of_ff)
+__global__ void k_copy_ff(float2* __restrict__ d, int64_t ldd, const double* __restrict__ s,
+                          int64_t lds, int dim, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < dim; k++) d[k * ldd + i] = ff_of_f64(s[k * lds + i]);
+}
+__global__ void k_copy_from_ff(double* __restrict__ d, int64_t ldd, const float2* __restrict__ s,
+                               int64_t lds, int dim, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < dim; k++) d[k * ldd + i] = f64_of_ff(s[k * lds + i]);
+}
+
 int node_copy(Ctx* c, void* dst, int dtype, int64_t ldd, const void* src,
               int stype, int64_t lds, int dim, int64_t n) {
   if (n == 0 || dim == 0) return OP2B_OK;
@@ -164,6 +191,12 @@ int node_copy(Ctx* c, void* dst, int dtype, int64_t ldd, const void* src,
     k_copy<double, float><<<g, 256, 0, c->stream>>>((double*)dst, ldd, (const float*)src, lds, dim, n);
   else if (dtype == OP2B_F32 && stype == OP2B_F32)
     k_copy<float, float><<<g, 256, 0, c->stream>>>((float*)dst, ldd, (const float*)src, lds, dim, n);
+  else if (dtype == OP2B_FF && stype == OP2B_F64)
+    k_copy_ff<<<g, 256, 0, c->stream>>>((float2*)dst, ldd, (const double*)src, lds, dim, n);
+  else if (dtype == OP2B_F64 && stype == OP2B_FF)
+    k_copy_from_ff<<<g, 256, 0, c->stream>>>((double*)dst, ldd, (const float2*)src, lds, dim, n);
+  else if (dtype == OP2B_FF && stype == OP2B_FF)
+    k_copy<double, double><<<g, 256, 0, c->stream>>>((double*)dst, ldd, (const double*)src, lds, dim, n);
   else if (dtype == OP2B_I32 && stype == OP2B_I32)
     k_copy<int32_t, int32_t><<<g, 256, 0, c->stream>>>((int32_t*)dst, ldd, (const int32_t*)src, lds, dim, n);
   else

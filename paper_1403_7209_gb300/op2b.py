@@ -20,14 +20,14 @@ LIB_PATH = os.path.join(_HERE, "libop2b.so")
 OK, EINVAL, EDIM, ETYPE, EACCESS, ESET = 0, -1, -2, -3, -4, -5
 ENOMEM, ECUDA, ETIMEOUT, EPLAN, ERANGE = -6, -7, -8, -9, -10
 READ, WRITE, RW, INC = 1, 2, 3, 4
-F64, F32, I32 = 0, 1, 2
+F64, F32, I32, FF = 0, 1, 2, 3
 ID = -1
 LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
 LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ = 4, 5, 6
 LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, LOOP_VISCOUS = 7, 8, 9, 10
 LOOP_FLUX2_PHI, NUM_LOOPS = 11, 12
 LIM_BARTH_JESPERSEN, LIM_VENKATAKRISHNAN = 1, 2
-PREC_F64, PREC_F32 = 0, 1
+PREC_F64, PREC_F32, PREC_FF, NUM_PREC = 0, 1, 2, 3
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
 STRAT_BLOCK_ATOMIC, STRAT_OWNER = 5, 6
 ZERO_INC = 1

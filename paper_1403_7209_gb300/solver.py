@@ -31,6 +31,8 @@ class EdgeSolver:
     (N, 3)); :meth:`fetch_nodes` and :meth:`fetch_edges` return data in the
     caller's numbering again.
     ``mixed`` adds the FP32 shadows used by the mixed-precision path;
+    ``ff`` the float-float shadows (q, G, n, dx) of the float-float flux,
+    whose arithmetic runs on the FP32 units at about FP64 accuracy;
     ``adjoint`` the adjoint and tangent (Jacobian-vector product) dats;
     ``viscous`` = (mu, prandtl, diff) adds the viscous flux to the residual
     (Navier-Stokes instead of Euler).  ``limiter`` picks the second-order
@@ -43,7 +45,7 @@ class EdgeSolver:
                  renumber: str = "none", seed: int = 0, mixed: bool = False,
                  adjoint: bool = False, gamma: float = 1.4,
                  eps_lim: float = 1e-12, stream=None, coords=None, viscous=None,
-                 limiter: str = "van_albada", limiter_eps2: float = 0.0):
+                 limiter: str = "van_albada", limiter_eps2: float = 0.0, ff: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -95,6 +97,12 @@ class EdgeSolver:
             node("W", 20)
             if mixed:
                 node("W32", 20, torch.float32)
+        self.ff = ff
+        if ff:
+            node("q_ff", 6, "ff")
+            node("G_ff", 18, "ff")
+            edgd("n_ff", 3, "ff")
+            edgd("dx_ff", 3, "ff")
         self.has_adjoint = adjoint
         if adjoint:
             node("lam", 6)
@@ -121,11 +129,20 @@ class EdgeSolver:
                                           self.N, self.E)
             self.perm, self.order = perm.astype(np.int64), order
         self.edge = L.op2b_fetch_map(c, self.map, 2 * self.E).reshape(-1, 2)
+        if ff:
+            for nm in ("q", "n", "dx"):
+                L.op2b_dat_copy(c, self.d[nm + "_ff"], self.d[nm])
         self._build_args()
 
     # ------------------------------------------------------------ dats
     def _dat(self, name, set_, n, dim, dtype, init):
         torch = self.torch
+        if dtype == "ff":  # float-float: (hi, lo) float pairs, 8 bytes per element
+            t = torch.zeros((dim, max(n, 1), 2), dtype=torch.float32, device=self.device)
+            self.d[name] = L.op2b_decl_dat(self.ctx, set_, dim, L.FF, t.data_ptr(), t.shape[1],
+                                           name)
+            self.t[name] = t
+            return
         t = torch.zeros((dim, max(n, 1)), dtype=dtype, device=self.device)
         if init is not None and n > 0:
             a = np.asarray(init, dtype=np.float64).reshape(n, dim)
@@ -141,14 +158,19 @@ class EdgeSolver:
         L.op2b_rebind_dat(self.ctx, self.d[name], tensor.data_ptr())
         self.t[name] = tensor
 
+    def _as_f64(self, t, n):
+        if t.dim() == 3:  # float-float
+            return (t[:, :n, 0].double() + t[:, :n, 1].double()).cpu().numpy()
+        return t[:, :n].double().cpu().numpy()
+
     def fetch_nodes(self, name) -> np.ndarray:
         """(N, dim) float64 in the caller's node numbering."""
-        a = self.t[name][:, :self.N].double().cpu().numpy().T
+        a = self._as_f64(self.t[name], self.N).T
         return np.ascontiguousarray(a[self.perm])
 
     def fetch_edges(self, name) -> np.ndarray:
         """(E, dim) float64 in the caller's edge order."""
-        a = self.t[name][:, :self.E].double().cpu().numpy().T
+        a = self._as_f64(self.t[name], self.E).T
         out = np.empty_like(a)
         out[self.order] = a
         return out
@@ -191,6 +213,10 @@ class EdgeSolver:
             self.a_f2_32 = [ind("q32", 0, R), ind("q32", 1, R), ind("G32", 0, R),
                             ind("G32", 1, R), dr("n32", R), dr("dx32", R),
                             ind("R", 0, I), ind("R", 1, I)]
+        if self.ff:
+            self.a_f2_ff = [ind("q_ff", 0, R), ind("q_ff", 1, R), ind("G_ff", 0, R),
+                            ind("G_ff", 1, R), dr("n_ff", R), dr("dx_ff", R),
+                            ind("R", 0, I), ind("R", 1, I)]
         if LIMITERS[self.limiter]:
             self.a_f2phi = [ind("q", 0, R), ind("q", 1, R), ind("G", 0, R), ind("G", 1, R),
                             ind("phi", 0, R), ind("phi", 1, R), dr("n", R), dr("dx", R),
@@ -228,11 +254,14 @@ class EdgeSolver:
     def plan_stats(self, loop, prec=L.PREC_F64):
         return L.op2b_plan_stats(self.ctx, loop, prec, self.map)
 
-    def green_gauss(self, mixed=False):
-        """G = Graw / V (FP64, or FP32 into G32 with ``mixed``)."""
+    def green_gauss(self, mixed=False, ff=False):
+        """G = Graw / V (FP64, or FP32 into G32 with ``mixed``); with ``ff``
+        the FP64 G is also converted into its float-float shadow G_ff."""
         c = self.ctx
         L.op2b_green_gauss(c, self.a_gg32 if mixed else self.a_gg, L.ZERO_INC)
         L.op2b_grad_scale(c, self.d["G32" if mixed else "G"], self.d["V"])
+        if ff:
+            L.op2b_dat_copy(c, self.d["G_ff"], self.d["G"])
 
     def node_limiter(self, mixed=False):
         """phi from the neighbourhood min/max and the gradients G."""
@@ -242,8 +271,14 @@ class EdgeSolver:
         L.op2b_node_limiter(c, self.map, LIMITERS[self.limiter], self.limiter_eps2, d[q], d[G],
                             d[dx], d["qmin" + sfx], d["qmax" + sfx], d["phi" + sfx])
 
-    def flux(self, order, mixed=False):
-        """R = sum of edge fluxes (R zeroed first)."""
+    def flux(self, order, mixed=False, ff=False):
+        """R = sum of edge fluxes (R zeroed first).  ``ff``: the
+        second-order flux in float-float arithmetic."""
+        if ff:
+            if order != 2 or LIMITERS[self.limiter]:
+                raise ValueError("the float-float flux is the second-order van Albada flux")
+            L.op2b_edge_flux(self.ctx, self.a_f2_ff, 2, self.gamma, self.eps_lim, L.ZERO_INC)
+            return
         if order == 2 and LIMITERS[self.limiter]:
             self.node_limiter(mixed)
             L.op2b_edge_flux_limited(self.ctx, self.a_f2phi32 if mixed else self.a_f2phi,
@@ -267,12 +302,12 @@ class EdgeSolver:
         L.op2b_viscous_flux(c, self.a_vf32 if mixed else self.a_vf, self.gamma, mu, pr, diff,
                             L.ZERO_INC if zero else 0)
 
-    def residual(self, order=2, mixed=False):
+    def residual(self, order=2, mixed=False, ff=False):
         """R of the current state: inviscid flux of the given order, plus
         the viscous flux when the solver was built with ``viscous``."""
         if order == 2 or self.visc is not None:
-            self.green_gauss(mixed)
-        self.flux(order, mixed)
+            self.green_gauss(mixed, ff)
+        self.flux(order, mixed, ff)
         if self.visc is not None:
             self.viscous_flux(mixed)
 
@@ -284,23 +319,24 @@ class EdgeSolver:
         self.spectral_radius()
         L.op2b_time_step(self.ctx, self.d["V"], self.d["lam_s"], cfl, self.d["dt"])
 
-    def update(self, alpha, mixed=False):
+    def update(self, alpha, mixed=False, ff=False):
+        sh = self.d["q32"] if mixed else (self.d["q_ff"] if ff else -1)
         L.op2b_node_update(self.ctx, self.d["q0"], self.d["q"], self.d["R"], self.d["V"],
-                           self.d["dt"], alpha, self.d["q32"] if mixed else -1)
+                           self.d["dt"], alpha, sh)
 
-    def stage(self, alpha, order=2, mixed=False):
-        self.residual(order, mixed)
-        self.update(alpha, mixed)
+    def stage(self, alpha, order=2, mixed=False, ff=False):
+        self.residual(order, mixed, ff)
+        self.update(alpha, mixed, ff)
 
-    def step(self, order=2, mixed=False, stages=5):
+    def step(self, order=2, mixed=False, stages=5, ff=False):
         """One explicit RK step (q0 <- q, then `stages` stages)."""
         L.op2b_dat_copy(self.ctx, self.d["q0"], self.d["q"])
         for a in RK5_ALPHA[5 - stages:]:
-            self.stage(a, order, mixed)
+            self.stage(a, order, mixed, ff)
 
-    def sync_shadow(self):
-        """q32 <- q (FP32 shadow of the state)."""
-        L.op2b_dat_copy(self.ctx, self.d["q32"], self.d["q"])
+    def sync_shadow(self, ff=False):
+        """q32 <- q (FP32 shadow of the state), or q_ff <- q with ``ff``."""
+        L.op2b_dat_copy(self.ctx, self.d["q_ff" if ff else "q32"], self.d["q"])
 
     def _inviscid_only(self, what):
         if self.visc is not None or LIMITERS[self.limiter]:

@@ -298,31 +298,30 @@ def mixed_extra(torch, L, s, args, stream, ms64, E, N):
 
 
 def ff_extra(torch, L, s, args, stream, ms64, E, N):
-    """Float-float stage: Green-Gauss and scaling in FP64, G converted to its
-    float-float shadow, the second-order flux in float-float arithmetic
-    (FP32 units), the update with the float-float shadow of q; per-loop
-    times, speed-up over the FP64 stage and the residual's difference from
-    the FP64 path's."""
-    names = ["gg", "scale", "to_ff", "flux2_ff", "update"]
+    """Float-float stage: Green-Gauss (node gather) and scaling in
+    float-float from the float-float shadows of q and n, the second-order
+    flux in float-float arithmetic (FP32 units, FP64 residual), the FP64
+    update that also writes the float-float shadow of q; per-loop times,
+    speed-up over the FP64 stage and the residual's difference from the
+    FP64 path's."""
+    names = ["gg_ff", "scale_ff", "flux2_ff", "update"]
     s.set_strategy(L.LOOP_FLUX2, L.PREC_FF, L.STRAT_AUTO)
     s.sync_shadow(ff=True)
 
     def stage(ev=None):
         if ev: ev[0].record(stream)
-        L.op2b_green_gauss(s.ctx, s.a_gg, L.ZERO_INC)
+        L.op2b_green_gauss(s.ctx, s.a_gg_ff, L.ZERO_INC)
         if ev: ev[1].record(stream)
-        L.op2b_grad_scale(s.ctx, s.d["G"], s.d["V"])
+        L.op2b_grad_scale(s.ctx, s.d["G_ff"], s.d["V"])
         if ev: ev[2].record(stream)
-        L.op2b_dat_copy(s.ctx, s.d["G_ff"], s.d["G"])
-        if ev: ev[3].record(stream)
         L.op2b_edge_flux(s.ctx, s.a_f2_ff, 2, s.gamma, s.eps_lim, L.ZERO_INC)
-        if ev: ev[4].record(stream)
+        if ev: ev[3].record(stream)
         L.op2b_node_update(s.ctx, s.d["q0"], s.d["q"], s.d["R"], s.d["V"], s.d["dt"], 0.25,
                            s.d["q_ff"])
-        if ev: ev[5].record(stream)
+        if ev: ev[4].record(stream)
     for _ in range(args.warmup):
         stage()
-    evs = [loop_events(torch, 6) for _ in range(args.steps)]
+    evs = [loop_events(torch, 5) for _ in range(args.steps)]
     torch.cuda.synchronize()
     t0, t1 = loop_events(torch, 2)
     t0.record(stream)

@@ -102,8 +102,8 @@ typedef struct {
  * gradients) */
 #define OP2B_PREC_F64 0
 #define OP2B_PREC_F32 1
-/* FF node and edge data (float-float shadows), float-float arithmetic, FP64
- * INC targets: only the second-order flux (op2b_edge_flux) */
+/* FF node and edge data (float-float shadows) and float-float arithmetic:
+ * the Green-Gauss loop (FF sums) and the second-order flux (FP64 R) */
 #define OP2B_PREC_FF 2
 #define OP2B_NUM_PREC 3
 
@@ -229,7 +229,11 @@ int op2b_renumber_rcb(op2b_ctx ctx, op2b_map edge2node, op2b_dat coords,
  *   Graw_i[k][d] += (q_i,k + q_j,k)/2 * n_d,  Graw_j[k][d] -= the same.
  * args (5): q idx 0 READ, q idx 1 READ (node, dim 6), n OP2B_ID READ
  * (edge, dim 3), G idx 0 INC, G idx 1 INC (node, dim 18, component 3k+d).
- * All five of one type (F64, or F32 with FP32 sums). */
+ * All five of one type (F64, or F32 with FP32 sums, or FF: float-float
+ * arithmetic and sums).  The FF loop always runs as a node gather -- one
+ * thread per node over its edge ends sorted by node, the sums kept in
+ * registers and written once -- so it has no race to resolve, ignores the
+ * loop's strategy and is bitwise reproducible. */
 int op2b_green_gauss(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                      int32_t flags);
 
@@ -377,7 +381,7 @@ int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
 /* ----------------------------------------------------------- node loops
  * Direct loops over the node set (no map). */
 
-/* G <- G / V (G dim 18 F64 or F32, RW; V dim 1 F64, READ). */
+/* G <- G / V (G dim 18 F64, F32 or FF, RW; V dim 1 F64, READ). */
 int op2b_grad_scale(op2b_ctx ctx, op2b_dat G, op2b_dat V);
 /* Reverse of the scaling: Gbar <- Gbar / V. */
 int op2b_grad_scale_adjoint(op2b_ctx ctx, op2b_dat Gbar, op2b_dat V);

@@ -712,6 +712,10 @@ size_t dat_bytes(Ctx& c, const DatRec& d) { return (size_t)d.dim * d.ld * esize(
 // strategy lookup / tuning, optional zeroing, then the launch
 int run_loop(Ctx& c, LoopLaunch& L, int flags, const DatRec* z0, const DatRec* z1,
              const DatRec* direct) {
+  L.flags = flags;
+  // the float-float Green-Gauss loop is a node gather: it writes (or adds)
+  // each node's sums itself and has no strategy to choose
+  if (L.prec == OP2B_PREC_FF && L.loop == OP2B_LOOP_GREEN_GAUSS) return launch_ff(&c, L, Strategy());
   if ((flags & OP2B_ZERO_INC)) {
     int rc;
     if (z0 && (rc = node_fill(&c, z0->ptr, z0->type, z0->ld, z0->dim, L.N, 0.0))) return rc;
@@ -1105,8 +1109,9 @@ static int grad_scale_impl(op2b_ctx h, op2b_dat G, op2b_dat V, const char* what)
   int rc;
   if ((rc = node_dat(c, G, 18, -1, -1, what))) return rc;
   const DatRec& g = c.dats[G];
-  if (g.type != OP2B_F64 && g.type != OP2B_F32)
-    return c.fail(OP2B_ETYPE, std::string(what) + ": G must be F64 or F32");
+  const bool fwd = std::string(what) == "grad_scale";
+  if (g.type != OP2B_F64 && g.type != OP2B_F32 && !(fwd && g.type == OP2B_FF))
+    return c.fail(OP2B_ETYPE, std::string(what) + (fwd ? ": G must be F64, F32 or FF" : ": G must be F64 or F32"));
   if ((rc = node_dat(c, V, 1, OP2B_F64, g.set, what))) return rc;
   return node_grad_scale(&c, g.ptr, g.type, g.ld, (const double*)c.dats[V].ptr, c.sets[g.set].size);
 }

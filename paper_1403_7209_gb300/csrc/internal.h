@@ -76,6 +76,7 @@ struct Strategy {
 // Everything a loop launch needs; pointers are device pointers.
 struct LoopLaunch {
   int loop = 0, prec = 0, order = 1;
+  int flags = 0;  // the call's OP2B_* loop flags
   int map = -1;  // the edge->node map (plan lookup)
   int64_t N = 0, E = 0;
   const int32_t* m0 = nullptr;  // first end of every edge

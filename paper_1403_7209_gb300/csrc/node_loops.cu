@@ -26,11 +26,25 @@ __global__ void k_grad_scale(T* __restrict__ G, int64_t ld,
   }
 }
 
+// float-float G <- G * (1/V): the reciprocal of V in float-float, 18
+// float-float multiplies
+__global__ void k_grad_scale_ff(float2* __restrict__ G, int64_t ld, const double* __restrict__ V,
+                                int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 r = ff_recip(ff_of_f64(V[i]));
+#pragma unroll
+    for (int c = 0; c < 18; c++) G[c * ld + i] = ff_mul(G[c * ld + i], r);
+  }
+}
+
 int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,
                     int64_t N) {
   if (N == 0) return OP2B_OK;
   if (type == OP2B_F64)
     k_grad_scale<double><<<grid_for(c, N, 256), 256, 0, c->stream>>>((double*)G, ldG, V, N);
+  else if (type == OP2B_FF)
+    k_grad_scale_ff<<<grid_for(c, N, 256), 256, 0, c->stream>>>((float2*)G, ldG, V, N);
   else
     k_grad_scale<float><<<grid_for(c, N, 256), 256, 0, c->stream>>>((float*)G, ldG, V, N);
   return c->launched("grad_scale");

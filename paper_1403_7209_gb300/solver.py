@@ -214,6 +214,8 @@ class EdgeSolver:
                             ind("G32", 1, R), dr("n32", R), dr("dx32", R),
                             ind("R", 0, I), ind("R", 1, I)]
         if self.ff:
+            self.a_gg_ff = [ind("q_ff", 0, R), ind("q_ff", 1, R), dr("n_ff", R),
+                            ind("G_ff", 0, I), ind("G_ff", 1, I)]
             self.a_f2_ff = [ind("q_ff", 0, R), ind("q_ff", 1, R), ind("G_ff", 0, R),
                             ind("G_ff", 1, R), dr("n_ff", R), dr("dx_ff", R),
                             ind("R", 0, I), ind("R", 1, I)]
@@ -255,13 +257,15 @@ class EdgeSolver:
         return L.op2b_plan_stats(self.ctx, loop, prec, self.map)
 
     def green_gauss(self, mixed=False, ff=False):
-        """G = Graw / V (FP64, or FP32 into G32 with ``mixed``); with ``ff``
-        the FP64 G is also converted into its float-float shadow G_ff."""
+        """G = Graw / V: FP64, FP32 into G32 with ``mixed``, float-float
+        (from the float-float shadows of q and n) into G_ff with ``ff``."""
         c = self.ctx
+        if ff:
+            L.op2b_green_gauss(c, self.a_gg_ff, L.ZERO_INC)
+            L.op2b_grad_scale(c, self.d["G_ff"], self.d["V"])
+            return
         L.op2b_green_gauss(c, self.a_gg32 if mixed else self.a_gg, L.ZERO_INC)
         L.op2b_grad_scale(c, self.d["G32" if mixed else "G"], self.d["V"])
-        if ff:
-            L.op2b_dat_copy(c, self.d["G_ff"], self.d["G"])
 
     def node_limiter(self, mixed=False):
         """phi from the neighbourhood min/max and the gradients G."""

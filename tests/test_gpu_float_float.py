@@ -102,6 +102,24 @@ def test_float_float_flux2_matches_oracle(gpu_lib, mesh16, name, strat, block, p
     s.close()
 
 
+@pytest.mark.parametrize("renumber", ["none", "rcm"])
+def test_float_float_green_gauss_matches_oracle(gpu_lib, mesh16, renumber):
+    import paper_1403_7209_gb300.op2b as L
+    m, q, ref = mesh16
+    Graw, Gabs = oracle.green_gauss(m.edge, q, m.normal, with_abs=True)
+    s = make_solver(m, q, renumber=renumber)
+    L.op2b_green_gauss(s.ctx, s.a_gg_ff, L.ZERO_INC)
+    g1 = s.fetch_nodes("G_ff")
+    assert rel_err(g1, Graw, Gabs) <= TOL
+    L.op2b_green_gauss(s.ctx, s.a_gg_ff, L.ZERO_INC)
+    assert np.array_equal(s.fetch_nodes("G_ff"), g1)  # a gather: fixed order, same bits
+    L.op2b_green_gauss(s.ctx, s.a_gg_ff, 0)  # without ZERO_INC the sums are added
+    assert rel_err(s.fetch_nodes("G_ff"), 2 * Graw, 2 * Gabs) <= TOL
+    s.green_gauss(ff=True)  # sums, then the float-float scaling by 1/V
+    assert rel_err(s.fetch_nodes("G_ff"), ref["G"], Gabs / m.volume[:, None]) <= TOL
+    s.close()
+
+
 def test_float_float_residual_differs_from_fp64_only_at_rounding_level(gpu_lib, mesh16):
     m, q, ref = mesh16
     s = make_solver(m, q, renumber="rcm")
@@ -158,6 +176,6 @@ def test_other_loops_reject_float_float_dats(gpu_lib, mesh16):
         L.op2b_edge_flux(s.ctx, args, 1)
     assert e.value.code == L.ETYPE
     with pytest.raises(L.Op2bError) as e:
-        L.op2b_grad_scale(s.ctx, d["G_ff"], d["V"])
+        L.op2b_grad_scale_adjoint(s.ctx, d["G_ff"], d["V"])
     assert e.value.code == L.ETYPE
     s.close()

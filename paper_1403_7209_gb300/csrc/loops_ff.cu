@@ -35,23 +35,31 @@ struct BodyFlux2FF {
   }
 };
 
-// Green-Gauss sums as a node gather: thread per node i over its edge ends
-// (node-sorted list of the segmented plan), Graw_i = sum over the ends of
-// +-(q_i + q_j) (x) n/2 (+ at the edge's first end, - at its second),
-// accumulated in float-float registers and written once.  Every node owns
-// its sums, so there is no INC race, no atomic and the order of the ends is
-// fixed (bitwise reproducible).  With `add` the sums are added to G.
+// Green-Gauss sums as a node gather: Graw_i = sum over node i's edge ends
+// (node-sorted list of the segmented plan) of +-(q_i + q_j) (x) n/2 (+ at
+// the edge's first end, - at its second), accumulated in float-float
+// registers and written once.  Every node owns its sums, so there is no INC
+// race, no atomic and the order of the ends is fixed (bitwise
+// reproducible).  SPLIT threads share a node, each summing 6/SPLIT of its
+// components (fewer registers per thread, more warps to hide the gathers);
+// the end list and normals they read are the same addresses, so a warp
+// fetches them once.  With `add` the sums are added to G.
+template <int SPLIT>
 __global__ void k_gg_ff(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ ends,
                         const int32_t* __restrict__ m0, const int32_t* __restrict__ m1,
                         const float2* __restrict__ q, int64_t ldq, const float2* __restrict__ n,
                         int64_t ldn, float2* __restrict__ G, int64_t ldG, int64_t N, bool add) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float2 qi[6], acc[18];
+  constexpr int KC = 6 / SPLIT;
+  const int64_t total = N * SPLIT;
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < total;
+       t0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t0 / SPLIT;
+    const int k0 = (int)(t0 - i * SPLIT) * KC;
+    float2 qi[KC], acc[3 * KC];
 #pragma unroll
-    for (int k = 0; k < 6; k++) qi[k] = ldro(q + k * ldq + i);
+    for (int k = 0; k < KC; k++) qi[k] = ldro(q + (k0 + k) * ldq + i);
 #pragma unroll
-    for (int c = 0; c < 18; c++) acc[c] = make_float2(0.0f, 0.0f);
+    for (int c = 0; c < 3 * KC; c++) acc[c] = make_float2(0.0f, 0.0f);
     const int64_t t1 = rowptr[i + 1];
     for (int64_t t = rowptr[i]; t < t1; t++) {
       const int32_t end = ends[t];
@@ -63,15 +71,15 @@ __global__ void k_gg_ff(const int64_t* __restrict__ rowptr, const int32_t* __res
 #pragma unroll
       for (int d = 0; d < 3; d++) nh[d] = ff_scale(ldro(n + d * ldn + e), h);
 #pragma unroll
-      for (int k = 0; k < 6; k++) {
-        const float2 sk = ff_add(qi[k], ldro(q + k * ldq + j));
+      for (int k = 0; k < KC; k++) {
+        const float2 sk = ff_add(qi[k], ldro(q + (k0 + k) * ldq + j));
 #pragma unroll
         for (int d = 0; d < 3; d++) acc[3 * k + d] = ff_fma(sk, nh[d], acc[3 * k + d]);
       }
     }
 #pragma unroll
-    for (int c = 0; c < 18; c++) {
-      float2* g = G + c * ldG + i;
+    for (int c = 0; c < 3 * KC; c++) {
+      float2* g = G + (3 * k0 + c) * ldG + i;
       *g = add ? ff_add(*g, acc[c]) : acc[c];
     }
   }
@@ -83,8 +91,9 @@ int launch_ff(Ctx* c, const LoopLaunch& L, const Strategy& s) {
     if (int rc = c->seg_plan(L.map, &sp)) return rc;
     if (L.N == 0) return OP2B_OK;
     const int block = 128;
-    const int64_t grid = std::min<int64_t>((L.N + block - 1) / block, (int64_t)c->sm_count * 64);
-    k_gg_ff<<<(unsigned)grid, block, 0, c->stream>>>(
+    constexpr int SPLIT = 2;
+    const int64_t grid = std::min<int64_t>((L.N * SPLIT + block - 1) / block, (int64_t)c->sm_count * 64);
+    k_gg_ff<SPLIT><<<(unsigned)grid, block, 0, c->stream>>>(
         sp->rowptr, sp->ends, L.m0, L.m1, (const float2*)L.q, L.ldq, (const float2*)L.n, L.ldn,
         (float2*)L.t0, L.ldt0, L.N, !(L.flags & OP2B_ZERO_INC));
     return c->launched("green_gauss_ff");

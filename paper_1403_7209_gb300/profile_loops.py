@@ -7,7 +7,9 @@ runs each requested loop `reps` times with a device synchronisation after
 each repetition, and prints one line per loop with its mean time (CUDA
 events).  Loops: gg, flux2, gg32, flux2_32, adjoint (flux adjoint +
 scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage), visc and
-visc32 (viscous node pass + edge loop, FP64 / FP32; not with adjoint).
+visc32 (viscous node pass + edge loop, FP64 / FP32; not with adjoint),
+gg_ff, flux2_ff and ffstage (the float-float Green-Gauss + scaling, flux,
+and RK stage).
 """
 from __future__ import annotations
 
@@ -38,11 +40,12 @@ def main():
     names = args.loops.split(",")
     visc = any(nm.startswith("visc") for nm in names)
     s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber="rcm", mixed=True,
-                   adjoint=not visc, viscous=(1e-3, 0.72, 1e-3) if visc else None)
+                   adjoint=not visc, viscous=(1e-3, 0.72, 1e-3) if visc else None,
+                   ff=not visc)
     if args.tune_cache and os.path.exists(args.tune_cache):
         L.op2b_load_tuning(s.ctx, args.tune_cache)
     for loop in range(L.NUM_LOOPS):
-        for prec in (0, 1):
+        for prec in range(L.NUM_PREC):
             s.set_strategy(loop, prec, L.STRAT_AUTO)
     for f in args.force:
         s.set_strategy(*[int(x) for x in f.split(":")])
@@ -59,6 +62,9 @@ def main():
         "stage": lambda: s.stage(0.25),
         "visc": lambda: s.viscous_flux(zero=True),
         "visc32": lambda: s.viscous_flux(mixed=True, zero=True),
+        "gg_ff": lambda: s.green_gauss(ff=True),
+        "flux2_ff": lambda: s.flux(2, ff=True),
+        "ffstage": lambda: s.stage(0.25, ff=True),
     }
     if visc:
         s.green_gauss()

@@ -48,11 +48,12 @@ BYTES_PER_EDGE_VISC = {"prims": 352 / 9, "visc": 8 + 48 + (160 + 96) / 9}
 BYTES_PER_EDGE_VISC_F32 = {"prims": 176 / 9, "visc": 8 + 24 + (80 + 96) / 9}
 FLOPS_PER_EDGE_VISC = 146.0
 VISC_COEFFS = (1.0e-3, 0.72, 1.0e-3)  # mu, Prandtl number, scalar diffusivity
-# DRAM bytes per edge of the FP64 flux2 kernel (atomic strategy) from an ncu
-# capture on the 60^3 lattice (dram__bytes_read.sum + dram__bytes_write.sum =
-# 170.7 MB over 1,944,000 edges; profiles/ncu_edge_loops_n60.md), scaled to a
-# launch by its edge count.  Traffic grows in proportion to the edges.
-DRAM_BYTES_PER_EDGE_FLUX2_ATOMIC = 170.68e6 / 1944000
+# DRAM bytes per edge of the FP64 flux2 kernel (atomic strategy, 128 threads)
+# from an ncu capture on the 60^3 lattice (dram__bytes_read.sum +
+# dram__bytes_write.sum = 170.84 MB over 1,944,000 edges;
+# profiles/ncu_flux_gg_kernels_n60.md), scaled to a launch by its edge
+# count.  Traffic grows in proportion to the edges.
+DRAM_BYTES_PER_EDGE_FLUX2_ATOMIC = 170.841856e6 / 1944000
 
 
 def read_peaks():

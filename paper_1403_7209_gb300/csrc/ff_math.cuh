@@ -152,6 +152,19 @@ __device__ __forceinline__ float2 ff_div(float2 a, float2 b) {
   return ff_fast(q1, __fmul_rn(r, y));
 }
 
+// a / b as the unnormalised pair (q1, r y): |r y| is about 2^-22 |q1|, close
+// enough to normalised for an operand of ff_add, which renormalises with a
+// full two-sum (saves the fast two-sum of ff_div)
+__device__ __forceinline__ float2 ff_div_raw(float2 a, float2 b) {
+  const float y = ff_rcp_seed(b.x);
+  const float q1 = __fmul_rn(a.x, y);
+  const float p = __fmul_rn(b.x, q1);
+  const float pe = __fmaf_rn(b.x, q1, -p);
+  float r = __fsub_rn(__fsub_rn(a.x, p), pe);
+  r = __fadd_rn(r, __fmaf_rn(-b.y, q1, a.y));
+  return make_float2(q1, __fmul_rn(r, y));
+}
+
 // 1 / b
 __device__ __forceinline__ float2 ff_recip(float2 b) {
   const float y = ff_rcp_seed(b.x);
@@ -244,8 +257,8 @@ __device__ __forceinline__ void flux2_ff(const float2* vi, const float2* vj, flo
     const float2 ai = ff_fma(vi[8 + 3 * k], dz, ff_fma(vi[7 + 3 * k], dy, ff_mul(vi[6 + 3 * k], dx)));
     const float2 aj = ff_fma(vj[8 + 3 * k], dz, ff_fma(vj[7 + 3 * k], dy, ff_mul(vj[6 + 3 * k], dx)));
     const float2 b2e = ff_fma(b, b, g.two_eps);
-    const float2 phi_i = ff_div(ff_mul(ff_add(ai, b), ff_fma(ai, b, g.eps)), ff_fma(ai, ai, b2e));
-    const float2 phi_j = ff_div(ff_mul(ff_add(aj, b), ff_fma(aj, b, g.eps)), ff_fma(aj, aj, b2e));
+    const float2 phi_i = ff_div_raw(ff_mul(ff_add(ai, b), ff_fma(ai, b, g.eps)), ff_fma(ai, ai, b2e));
+    const float2 phi_j = ff_div_raw(ff_mul(ff_add(aj, b), ff_fma(aj, b, g.eps)), ff_fma(aj, aj, b2e));
     qL[k] = ff_add(vi[k], ff_scale(phi_i, 0.5f));
     qR[k] = ff_sub(vj[k], ff_scale(phi_j, 0.5f));
   }

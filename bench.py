@@ -383,15 +383,16 @@ def tangent_extra(torch, s, args, stream, E):
 
 def viscous_extra(torch, L, m, q, args, stream, device, E):
     """Navier-Stokes residual: the viscous node pass and edge loop alone
-    (FP64 and FP32-mixed) and the whole stage with them (Green-Gauss,
-    scaling, limited inviscid flux, viscous flux, update)."""
+    (FP64, FP32-mixed and float-float) and the whole stage with them
+    (Green-Gauss, scaling, limited inviscid flux, viscous flux, update)."""
     from paper_1403_7209_gb300.solver import EdgeSolver
     sv = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device,
-                    renumber=args.numbering, mixed=True, stream=stream, viscous=VISC_COEFFS)
+                    renumber=args.numbering, mixed=True, stream=stream, viscous=VISC_COEFFS,
+                    ff=True)
     if args.tune_cache and os.path.exists(args.tune_cache):
         L.op2b_load_tuning(sv.ctx, args.tune_cache)
     for loop in range(L.NUM_LOOPS):
-        for prec in (0, 1):
+        for prec in range(L.NUM_PREC):
             sv.set_strategy(loop, prec, L.STRAT_AUTO)
     sv.time_step(0.5)
     L.op2b_dat_copy(sv.ctx, sv.d["q0"], sv.d["q"])
@@ -399,10 +400,13 @@ def viscous_extra(torch, L, m, q, args, stream, device, E):
     mu, pr, diff = VISC_COEFFS
     out = {"coefficients": {"mu": mu, "prandtl": pr, "diff": diff}}
     hbm, _ = read_peaks()
-    for tag, mixed in (("fp64", False), ("mixed", True)):
-        sv.residual(2, mixed=mixed)  # tunes every loop of the stage
-        q_, G_, W_ = ("q32", "G32", "W32") if mixed else ("q", "G", "W")
-        args_v = sv.a_vf32 if mixed else sv.a_vf
+    for tag, mixed, ff in (("fp64", False, False), ("mixed", True, False),
+                           ("float_float", False, True)):
+        sv.residual(2, mixed=mixed, ff=ff)  # tunes every loop of the stage
+        q_, G_, W_ = ("q32", "G32", "W32") if mixed else (
+            ("q_ff", "G_ff", "W_ff") if ff else ("q", "G", "W"))
+        args_v = sv.a_vf32 if mixed else (sv.a_vf_ff if ff else sv.a_vf)
+        prec = L.PREC_F32 if mixed else (L.PREC_FF if ff else L.PREC_F64)
 
         def prims():
             L.op2b_viscous_prims(sv.ctx, sv.d[q_], sv.d[G_], sv.d[W_], sv.gamma)
@@ -414,15 +418,15 @@ def viscous_extra(torch, L, m, q, args, stream, device, E):
             visc()
         pms = timed(torch, prims, args.steps, stream)
         vms = timed(torch, visc, args.steps, stream)
-        sms = timed(torch, lambda: sv.stage(0.25, 2, mixed=mixed), args.steps, stream)
+        sms = timed(torch, lambda: sv.stage(0.25, 2, mixed=mixed, ff=ff), args.steps, stream)
         bpe = BYTES_PER_EDGE_VISC_F32 if mixed else BYTES_PER_EDGE_VISC
         r = {"prims_ms": pms, "visc_ms": vms, "ns_stage_ms": sms,
              "ns_stage_edges_per_s": E / (sms * 1e-3),
-             "visc_strategy": L.STRATEGY_NAMES[sv.plan_stats(L.LOOP_VISCOUS, int(mixed))["strategy"]],
+             "visc_strategy": L.STRATEGY_NAMES[sv.plan_stats(L.LOOP_VISCOUS, prec)["strategy"]],
              "visc_gbs": bpe["visc"] * E / (vms * 1e-3) / 1e9,
              "visc_hbm_frac": bpe["visc"] * E / (vms * 1e-3) / 1e9 / hbm,
              "prims_gbs": bpe["prims"] * E / (pms * 1e-3) / 1e9}
-        if not mixed:
+        if not mixed:  # FP64-equivalent for float-float
             ach = FLOPS_PER_EDGE_VISC * E / (vms * 1e-3) / 1e12
             r["visc_fp64_tflops"] = ach
             r["visc_fp64_frac"] = ach / FP64_PEAK_TFLOPS
@@ -438,6 +442,12 @@ def viscous_extra(torch, L, m, q, args, stream, device, E):
     R32 = sv.t["R"][:, :sv.N].clone()
     out["mixed_visc_rel_err_per_component"] = (
         (R32 - R64)[1:].abs().amax(dim=1) / R64[1:].abs().amax(dim=1)).cpu().tolist()
+    sv.sync_shadow(ff=True)
+    sv.green_gauss(ff=True)
+    sv.viscous_flux(zero=True, ff=True)
+    Rff = sv.t["R"][:, :sv.N].clone()
+    out["float_float_visc_max_diff_vs_fp64_per_component"] = (
+        (Rff - R64)[1:].abs().amax(dim=1) / R64[1:].abs().amax(dim=1)).cpu().tolist()
     out["fp64_ns_stage_vs_euler_stage"] = None
     sv.close()
     return out

@@ -103,7 +103,8 @@ typedef struct {
 #define OP2B_PREC_F64 0
 #define OP2B_PREC_F32 1
 /* FF node and edge data (float-float shadows) and float-float arithmetic:
- * the Green-Gauss loop (FF sums) and the second-order flux (FP64 R) */
+ * the Green-Gauss loop (FF sums), the second-order flux and the viscous
+ * flux (FP64 R) */
 #define OP2B_PREC_FF 2
 #define OP2B_NUM_PREC 3
 
@@ -358,8 +359,8 @@ int op2b_edge_flux_limited(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *     W[17 + d] = (dc/dx_d) / 2   (gradients halved),
  *   by the quotient rule (grad u_a = (grad m_a - u_a grad rho) / rho,
  *   grad p = (gamma-1)(grad E - u . grad m + |u|^2/2 grad rho),
- *   grad T = (grad p - T grad rho) / rho).  q, G, W (dim 20) all F64 or all
- *   F32 on one set.
+ *   grad T = (grad p - T grad rho) / rho).  q, G, W (dim 20) all F64, all
+ *   F32 or all FF (float-float arithmetic) on one set.
  *
  * op2b_viscous_flux: edge loop, per edge (i, j) with normal n and
  *   dx = x_j - x_i: for phi in (u_x, u_y, u_z, T, c) the face gradient
@@ -371,8 +372,9 @@ int op2b_edge_flux_limited(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *   otherwise the viscous flux is added to R, e.g. onto the inviscid flux).
  *   args (6): W 0 READ, W 1 READ (dim 20), n ID READ, dx ID READ (edge,
  *   dim 3), R 0 INC, R 1 INC (F64 dim 6).  W, n, dx all F64, or all F32
- *   with FP32 arithmetic and each edge's flux converted to FP64 before it
- *   is added into R.  |dx| must be nonzero. */
+ *   with FP32 arithmetic, or all FF with float-float arithmetic; with F32
+ *   or FF each edge's flux is converted to FP64 before it is added into R.
+ *   |dx| must be nonzero. */
 int op2b_viscous_prims(op2b_ctx ctx, op2b_dat q, op2b_dat G, op2b_dat W,
                        double gamma);
 int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,

@@ -561,7 +561,8 @@ std::string tune_key(const LoopLaunch& L, bool det) {
 }
 
 int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
-  if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // FLUX2 only (checked there)
+  if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);  // F64, F32 or FF
+  if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // GG and FLUX2 only (checked there)
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);
   if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
@@ -1201,7 +1202,8 @@ extern "C" int op2b_viscous_prims(op2b_ctx h, op2b_dat q, op2b_dat G, op2b_dat W
   int rc;
   if ((rc = node_dat(c, q, 6, -1, -1, "viscous_prims"))) return rc;
   const DatRec& rq = c.dats[q];
-  if (rq.type != OP2B_F64 && rq.type != OP2B_F32) return c.fail(OP2B_ETYPE, "viscous_prims: q must be F64 or F32");
+  if (rq.type != OP2B_F64 && rq.type != OP2B_F32 && rq.type != OP2B_FF)
+    return c.fail(OP2B_ETYPE, "viscous_prims: q must be F64, F32 or FF");
   if ((rc = node_dat(c, G, 18, rq.type, rq.set, "viscous_prims")) ||
       (rc = node_dat(c, W, 20, rq.type, rq.set, "viscous_prims")))
     return rc;

@@ -204,6 +204,40 @@ inline float2 ff_split_host(double x) {
   return make_float2(hi, (float)(x - (double)hi));
 }
 
+// A float-float value with arithmetic operators, so that loop bodies and
+// node loops written for a scalar type T (double, float) also instantiate
+// for float-float.  Conversions: from double (device: ff_of_f64; host: the
+// rounded split) and to double (f64_of_ff, device only).
+struct ffv {
+  float2 v;
+  ffv() = default;
+  __host__ __device__ __forceinline__ explicit ffv(float2 x) : v(x) {}
+  __host__ __device__ __forceinline__ explicit ffv(double x) {
+#ifdef __CUDA_ARCH__
+    v = ff_of_f64(x);
+#else
+    v = ff_split_host(x);
+#endif
+  }
+  __device__ __forceinline__ explicit operator double() const { return f64_of_ff(v); }
+};
+__device__ __forceinline__ ffv operator+(ffv a, ffv b) { return ffv(ff_add(a.v, b.v)); }
+__device__ __forceinline__ ffv operator-(ffv a, ffv b) { return ffv(ff_sub(a.v, b.v)); }
+__device__ __forceinline__ ffv operator-(ffv a) { return ffv(ff_neg(a.v)); }
+__device__ __forceinline__ ffv operator*(ffv a, ffv b) { return ffv(ff_mul(a.v, b.v)); }
+__device__ __forceinline__ ffv operator/(ffv a, ffv b) { return ffv(ff_div(a.v, b.v)); }
+__device__ __forceinline__ ffv& operator+=(ffv& a, ffv b) { return a = a + b; }
+// the float-float fma joins the global (double, float) overloads instead of
+// hiding them inside this namespace
+using ::fma;
+__device__ __forceinline__ ffv fma(ffv a, ffv b, ffv c) { return ffv(ff_fma(a.v, b.v, c.v)); }
+__device__ __forceinline__ ffv neg(ffv a) { return -a; }
+__device__ __forceinline__ ffv recip(ffv a) { return ffv(ff_recip(a.v)); }
+template <>
+__device__ __forceinline__ ffv ldro<ffv>(const ffv* p) {
+  return ffv(__ldg(reinterpret_cast<const float2*>(p)));
+}
+
 inline GasFF gas_ff(double gamma, double eps) {
   return {ff_split_host(gamma), ff_split_host(gamma - 1.0), ff_split_host(eps),
           ff_split_host(2.0 * eps)};

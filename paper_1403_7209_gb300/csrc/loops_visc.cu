@@ -17,9 +17,15 @@
 // its memory traffic.
 #include <algorithm>
 
+#include <type_traits>
+
+#include "ff_math.cuh"
 #include "launch.cuh"
 
 namespace op2b {
+
+template <typename T>
+__device__ __forceinline__ T recip_dd(T dd);
 
 // ------------------------------------------------------------- node pass
 // W layout (dim 20, component-major):
@@ -32,7 +38,7 @@ __global__ void k_viscous_prims(const T* __restrict__ q, int64_t ldq,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const T rho = q[i];
-    const T r = T(1) / rho;
+    const T r = recip_dd(rho);
     const T hr = T(0.5) * r;
     T u[3];
 #pragma unroll
@@ -64,10 +70,12 @@ __global__ void k_viscous_prims(const T* __restrict__ q, int64_t ldq,
 // ------------------------------------------------------------- edge body
 template <typename T>
 __device__ __forceinline__ T recip_dd(T dd) {
-  if constexpr (sizeof(T) == 8)
+  if constexpr (std::is_same<T, double>::value)
     return seedable(dd) ? recip2(dd) : 1.0 / dd;
-  else
+  else if constexpr (std::is_same<T, float>::value)
     return 1.0f / dd;
+  else
+    return recip(dd);  // float-float
 }
 
 // One edge: oi receives -Fv components 1..5 (component 0 is zero and is not
@@ -149,6 +157,11 @@ int launch_visc(Ctx* c, const LoopLaunch& L, const Strategy& s) {
                        (const double*)L.dx, L.lddx, L.mu, L.kappa, L.diff};
     return run_body(c, b, L, s, tg);
   }
+  if (L.prec == OP2B_PREC_FF) {
+    BodyVisc<ffv> b{(const ffv*)L.q, L.ldq, (const ffv*)L.n, L.ldn, (const ffv*)L.dx, L.lddx,
+                    ffv(L.mu), ffv(L.kappa), ffv(L.diff)};
+    return run_body(c, b, L, s, tg);
+  }
   BodyVisc<float> b{(const float*)L.q, L.ldq, (const float*)L.n, L.ldn,
                     (const float*)L.dx, L.lddx, (float)L.mu, (float)L.kappa, (float)L.diff};
   return run_body(c, b, L, s, tg);
@@ -163,6 +176,9 @@ int node_viscous_prims(Ctx* c, const void* q, int64_t ldq, const void* G, int64_
   if (type == OP2B_F64)
     k_viscous_prims<double><<<grid, block, 0, c->stream>>>(
         (const double*)q, ldq, (const double*)G, ldG, (double*)W, ldW, gamma - 1.0, N);
+  else if (type == OP2B_FF)
+    k_viscous_prims<ffv><<<grid, block, 0, c->stream>>>(
+        (const ffv*)q, ldq, (const ffv*)G, ldG, (ffv*)W, ldW, ffv(gamma - 1.0), N);
   else
     k_viscous_prims<float><<<grid, block, 0, c->stream>>>(
         (const float*)q, ldq, (const float*)G, ldG, (float*)W, ldW, (float)(gamma - 1.0), N);

@@ -103,6 +103,8 @@ class EdgeSolver:
             node("G_ff", 18, "ff")
             edgd("n_ff", 3, "ff")
             edgd("dx_ff", 3, "ff")
+            if self.visc is not None:
+                node("W_ff", 20, "ff")
         self.has_adjoint = adjoint
         if adjoint:
             node("lam", 6)
@@ -233,6 +235,9 @@ class EdgeSolver:
             if self.mixed:
                 self.a_vf32 = [ind("W32", 0, R), ind("W32", 1, R), dr("n32", R),
                                dr("dx32", R), ind("R", 0, I), ind("R", 1, I)]
+            if self.ff:
+                self.a_vf_ff = [ind("W_ff", 0, R), ind("W_ff", 1, R), dr("n_ff", R),
+                                dr("dx_ff", R), ind("R", 0, I), ind("R", 1, I)]
         if self.has_adjoint:
             self.a_fa1 = [ind("lam", 0, R), ind("lam", 1, R), ind("q", 0, R), ind("q", 1, R),
                           dr("n", R), ind("qbar", 0, I), ind("qbar", 1, I), dr("nbar", W)]
@@ -294,11 +299,17 @@ class EdgeSolver:
             a = self.a_f2_32 if mixed else self.a_f2
         L.op2b_edge_flux(self.ctx, a, order, self.gamma, self.eps_lim, L.ZERO_INC)
 
-    def viscous_flux(self, mixed=False, zero=False):
+    def viscous_flux(self, mixed=False, zero=False, ff=False):
         """R -= viscous fluxes (R zeroed first with ``zero``); uses the
-        scaled gradients G (G32 with ``mixed``)."""
+        scaled gradients G (G32 with ``mixed``, G_ff in float-float with
+        ``ff``)."""
         mu, pr, diff = self.visc
         c = self.ctx
+        if ff:
+            L.op2b_viscous_prims(c, self.d["q_ff"], self.d["G_ff"], self.d["W_ff"], self.gamma)
+            L.op2b_viscous_flux(c, self.a_vf_ff, self.gamma, mu, pr, diff,
+                                L.ZERO_INC if zero else 0)
+            return
         if mixed:
             L.op2b_viscous_prims(c, self.d["q32"], self.d["G32"], self.d["W32"], self.gamma)
         else:
@@ -313,7 +324,7 @@ class EdgeSolver:
             self.green_gauss(mixed, ff)
         self.flux(order, mixed, ff)
         if self.visc is not None:
-            self.viscous_flux(mixed)
+            self.viscous_flux(mixed, ff=ff)
 
     def spectral_radius(self):
         L.op2b_spectral_radius(self.ctx, self.a_sr, self.gamma, L.ZERO_INC)

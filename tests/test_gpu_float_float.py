@@ -179,3 +179,43 @@ def test_other_loops_reject_float_float_dats(gpu_lib, mesh16):
         L.op2b_grad_scale_adjoint(s.ctx, d["G_ff"], d["V"])
     assert e.value.code == L.ETYPE
     s.close()
+
+
+# ------------------------------------------------------- viscous flux
+VISC = (2.0e-3, 0.72, 1.5e-3)
+
+
+@pytest.fixture(scope="module")
+def visc16(mesh16):
+    m, q, ref = mesh16
+    mu, pr, diff = VISC
+    Rv, Rva = oracle.viscous(m.edge, q, ref["G"], m.normal, m.dx, 1.4, mu, pr, diff, with_abs=True)
+    Gr = np.random.default_rng(5).normal(scale=0.3, size=ref["G"].shape)
+    Rr, Rra = oracle.viscous(m.edge, q, Gr, m.normal, m.dx, 1.4, mu, pr, diff, with_abs=True)
+    return dict(Rv=Rv, Rva=Rva, Gr=Gr, Rr=Rr, Rra=Rra)
+
+
+@pytest.mark.parametrize("strat,block,part,staged", [(1, 256, 0, 0), (2, 128, 256, 1),
+                                                      (3, 256, 0, 0), (6, 128, 0, 0)])
+def test_float_float_viscous_matches_oracle(gpu_lib, mesh16, visc16, strat, block, part, staged):
+    import paper_1403_7209_gb300.op2b as L
+    m, q, ref = mesh16
+    s = make_solver(m, q, renumber="rcm", viscous=VISC)
+    s.set_strategy(gpu_lib.LOOP_VISCOUS, gpu_lib.PREC_FF, strat, block, part, staged)
+    for G, R, Ra in ((ref["G"], visc16["Rv"], visc16["Rva"]),
+                     (visc16["Gr"], visc16["Rr"], visc16["Rra"])):
+        s.load_nodes("G", G)
+        L.op2b_dat_copy(s.ctx, s.d["G_ff"], s.d["G"])
+        s.viscous_flux(zero=True, ff=True)
+        Rg = s.fetch_nodes("R")
+        assert np.all(Rg[:, 0] == 0.0)
+        assert rel_err(Rg, R, Ra) <= TOL
+    s.close()
+
+
+def test_float_float_navier_stokes_residual(gpu_lib, mesh16, visc16):
+    m, q, ref = mesh16
+    s = make_solver(m, q, renumber="rcm", viscous=VISC)
+    s.residual(2, ff=True)
+    assert rel_err(s.fetch_nodes("R"), ref["R2"] + visc16["Rv"], ref["R2a"] + visc16["Rva"]) <= TOL
+    s.close()

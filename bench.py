@@ -353,7 +353,7 @@ def ff_extra(torch, L, s, args, stream, ms64, E, N):
             "residual_max_diff_vs_fp64_path_per_component": diff}
 
 
-def adjoint_extra(torch, s, args, stream, E):
+def adjoint_extra(torch, L, s, args, stream, E):
     """Reverse sweep (flux adjoint, scaling adjoint, Green-Gauss adjoint;
     edge states recomputed, G kept from the forward pass) against the
     forward residual (Green-Gauss, scaling, flux) it differentiates."""
@@ -364,8 +364,21 @@ def adjoint_extra(torch, s, args, stream, E):
     ams = timed(torch, lambda: s.adjoint(2, recompute_gradient=False), args.steps, stream)
     rms = timed(torch, lambda: s.adjoint(2), args.steps, stream)
     fms = timed(torch, lambda: s.residual(2), args.steps, stream)
-    return {"ms": ams, "forward_residual_ms": fms, "ratio_to_forward": ams / fms,
-            "ms_with_gradient_recompute": rms, "edges_per_s": E / (ams * 1e-3)}
+    out = {"ms": ams, "forward_residual_ms": fms, "ratio_to_forward": ams / fms,
+           "ms_with_gradient_recompute": rms, "edges_per_s": E / (ams * 1e-3)}
+    if s.ff:  # the flux adjoint in float-float (scaling and Green-Gauss adjoints FP64)
+        s.sync_shadow(ff=True)
+        s.residual(2, ff=True)
+        for _ in range(max(1, args.warmup)):
+            s.adjoint(2, recompute_gradient=False, ff=True)
+        fams = timed(torch, lambda: s.adjoint(2, recompute_gradient=False, ff=True), args.steps,
+                     stream)
+        ffms = timed(torch, lambda: s.residual(2, ff=True), args.steps, stream)
+        out["float_float"] = {"ms": fams, "forward_residual_ms": ffms,
+                              "ratio_to_forward": fams / ffms, "speedup_vs_fp64_adjoint": ams / fams,
+                              "strategy": L.STRATEGY_NAMES[
+                                  s.plan_stats(L.LOOP_FLUX2_ADJ, L.PREC_FF)["strategy"]]}
+    return out
 
 
 def tangent_extra(torch, s, args, stream, E):
@@ -779,7 +792,7 @@ def main():
     if not args.no_extras:
         line["mixed"] = mixed_extra(torch, L, s, args, stream, ms, E, N)
         line["float_float"] = ff_extra(torch, L, s, args, stream, ms, E, N)
-        line["adjoint"] = adjoint_extra(torch, s, args, stream, E)
+        line["adjoint"] = adjoint_extra(torch, L, s, args, stream, E)
         line["tangent"] = tangent_extra(torch, s, args, stream, E)
         line["viscous"] = viscous_extra(torch, L, m, q, args, stream, local, E)
         line["viscous"]["fp64_ns_stage_vs_euler_stage"] = line["viscous"]["fp64"]["ns_stage_ms"] / ms

@@ -65,9 +65,9 @@ typedef int32_t op2b_dat;
 /* float-float: a value is the unevaluated sum hi + lo of two floats (hi
  * first, 8 bytes per element like a double; about 47 significant bits).
  * Shadows of F64 dats for the float-float flux (op2b_edge_flux); made by
- * op2b_dat_copy (F64 -> FF converts with integer operations: hi = the top
- * 24 significant bits, lo the next 23; magnitudes below 2^-126 become 0,
- * below 2^-103 keep hi only, 2^128 and above become infinite) and by
+ * op2b_dat_copy (F64 -> FF: hi = the top 24 significant bits, lo = the
+ * remaining bits rounded to a float, relative error at most 2^-48;
+ * magnitudes below 2^-126 become 0, 2^128 and above infinite) and by
  * op2b_node_update's shadow output. */
 #define OP2B_FF 3
 

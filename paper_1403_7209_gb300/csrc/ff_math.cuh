@@ -13,9 +13,9 @@
 // FP64 definition relative to the size of its terms.
 //
 // Storage: one float2 per value (x = hi, y = lo), 8 bytes like a double.
-// Range: values of magnitude below 2^-126 convert to zero, below 2^-103 to
-// hi alone (24 bits); values of magnitude 2^128 or more become infinite, as
-// do intermediate results beyond the float range.
+// Range: values of magnitude below 2^-126 convert to zero; values of
+// magnitude 2^128 or more become infinite, as do intermediate results
+// beyond the float range.
 //
 // Every primitive uses the explicitly rounded intrinsics (__fadd_rn, ...),
 // which the compiler never contracts into FMAs: the error-free transforms
@@ -29,9 +29,12 @@ namespace op2b {
 
 // ------------------------------------------------------------ conversions
 
-// double -> float-float with integer operations only: hi = the top 24
-// significant bits (truncated), lo = the next 23 bits.  Relative error
-// below 2^-46 for |x| in [2^-103, 2^128).
+// double -> float-float: hi = the top 24 significant bits of x (truncated,
+// integer operations), lo = the remaining 29 bits rounded to a float
+// (24 significant bits, round to nearest) and scaled exactly.  Relative
+// error at most 2^-48 for |x| in [2^-75, 2^128) (below 2^-75 lo may lose
+// bits to the float subnormal range); |x| below 2^-126 becomes 0, 2^128 and
+// above infinite.
 __device__ __forceinline__ float2 ff_of_f64(double x) {
   const unsigned hw = (unsigned)__double2hiint(x);
   const unsigned lw = (unsigned)__double2loint(x);
@@ -40,17 +43,18 @@ __device__ __forceinline__ float2 ff_of_f64(double x) {
   const unsigned ex = ax >> 20;  // biased double exponent
   // hi: exponent re-biased from 1023 to 127, fraction bits 51..29
   unsigned hb = sign | __funnelshift_l(lw, ax - 0x38000000u, 3);
-  // lo = (fraction bits 28..6) x 2^(E-46), E = ex - 1023: built as
-  // (2^(E-23) + m 2^(E-46)) - 2^(E-23), an exact float subtraction
-  const unsigned m = (lw >> 6) & 0x7fffffu;
-  const unsigned eb = (ex - 919u) << 23;
-  const float f1 = __uint_as_float(sign | eb | m);
-  const float f2 = __uint_as_float(sign | eb);
-  float lo = __fsub_rn(f1, f2);
+  // lo = (fraction bits 28..0) x 2^(E-52), E = ex - 1023: the 29-bit
+  // integer rounded to a float, times 2^(E-52) -- for small x as
+  // 2^(E-52+64) and then 2^-64, so that each factor is a normal float
+  const float rem = __uint2float_rn(lw & 0x1fffffffu);
+  const bool big = ex >= 949u;
+  const float s1 = __uint_as_float((big ? ex - 948u : ex - 884u) << 23);
+  float lo = __fmul_rn(__fmul_rn(rem, s1), big ? 1.0f : 0x1p-64f);
+  lo = __uint_as_float(__float_as_uint(lo) | sign);
   const unsigned inf_nan = sign | 0x7f800000u |
                            ((ex == 2047u && ((ax & 0xfffffu) | lw)) ? 0x400000u : 0u);
   hb = ex > 1150u ? inf_nan : (ex >= 897u ? hb : sign);
-  lo = (ex >= 920u && ex <= 1150u) ? lo : 0.0f;
+  lo = (ex >= 897u && ex <= 1150u) ? lo : 0.0f;
   return make_float2(__uint_as_float(hb), lo);
 }
 
@@ -233,6 +237,16 @@ using ::fma;
 __device__ __forceinline__ ffv fma(ffv a, ffv b, ffv c) { return ffv(ff_fma(a.v, b.v, c.v)); }
 __device__ __forceinline__ ffv neg(ffv a) { return -a; }
 __device__ __forceinline__ ffv recip(ffv a) { return ffv(ff_recip(a.v)); }
+using ::sqrt;
+using ::fabs;
+__device__ __forceinline__ ffv sqrt(ffv a) { return ffv(ff_sqrt(a.v)); }
+__device__ __forceinline__ ffv fabs(ffv a) { return ffv(ff_abs(a.v)); }
+__device__ __forceinline__ bool operator>=(ffv a, ffv b) { return ff_ge(a.v, b.v); }
+// sign(x) v with sign(0) = 0
+__device__ __forceinline__ ffv sign_times(ffv x, ffv v) {
+  return x.v.x > 0.0f ? v : (x.v.x < 0.0f ? -v : ffv(make_float2(0.0f, 0.0f)));
+}
+__device__ __forceinline__ ffv ffk(float f) { return ffv(make_float2(f, 0.0f)); }
 template <>
 __device__ __forceinline__ ffv ldro<ffv>(const ffv* p) {
   return ffv(__ldg(reinterpret_cast<const float2*>(p)));
@@ -297,6 +311,147 @@ __device__ __forceinline__ void flux2_ff(const float2* vi, const float2* vj, flo
     qR[k] = ff_sub(vj[k], ff_scale(phi_j, 0.5f));
   }
   rusanov_ff(qL, qR, nx, ny, nz, g, F);
+}
+
+// ------------------------------------------- adjoint of the second-order flux
+// The reverse sweep of flux2 (the same steps as flux2_adj_f64: face states
+// recomputed from q, G, n, dx, the Rusanov flux reversed side by side, the
+// van Albada limiter's partial derivatives), written for a scalar type T
+// with operators and instantiated for float-float.  Plain reciprocals and
+// square roots instead of the FP64 batching; non-smooth points as in the
+// FP64 sweep: d|x|/dx = sign(x) (0 at 0), the max picks L on ties.
+
+template <typename T>
+struct SideStateT {
+  T rr, un, mm, p, a, ra;  // 1/rho, u.n, |m|^2, p, sound speed, 1/a
+};
+
+template <typename T>
+__device__ __forceinline__ T side_state_t(const T* q, T nx, T ny, T nz, T rr, T nn, T gamma,
+                                          T gm1, SideStateT<T>& s) {
+  s.rr = rr;
+  s.un = fma(q[3], nz, fma(q[2], ny, q[1] * nx)) * rr;
+  s.mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
+  s.p = gm1 * (q[4] - ffk(0.5f) * s.mm * rr);
+  s.a = sqrt(gamma * s.p * rr);
+  s.ra = recip(s.a);
+  return fabs(s.un) + s.a * nn;  // wave speed
+}
+
+// fb = adjoint of f(q).n (6), lamb = adjoint of the side's wave speed
+template <typename T>
+__device__ __forceinline__ void side_reverse_t(const T* q, T nx, T ny, T nz,
+                                               const SideStateT<T>& s, T nn, T rn, T gamma,
+                                               T gm1, const T* fb, T lamb, T* qb, T* nb) {
+  const T half = ffk(0.5f);
+  T unb = sign_times(s.un, lamb);
+  const T ab = lamb * nn;
+  const T rnb = lamb * s.a * rn;  // d|n|/dn = n / |n|
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    qb[k] = fma(fb[k], s.un, qb[k]);
+    unb = fma(fb[k], q[k], unb);
+  }
+  unb = fma(fb[4], s.p, unb);
+  T pb = fma(fb[3], nz, fma(fb[2], ny, fma(fb[1], nx, fb[4] * s.un)));
+  pb = fma(half * gamma * ab, s.rr * s.ra, pb);  // a = sqrt(gamma p / rho)
+  const T gpb = gm1 * pb;
+  const T ur = unb * s.rr;
+  const T gpr = gpb * s.rr;
+  const T n3[3] = {nx, ny, nz};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    nb[d] = fma(fb[1 + d], s.p, fma(rnb, n3[d], fma(ur, q[1 + d], nb[d])));
+    qb[1 + d] = fma(-gpr, q[1 + d], fma(ur, n3[d], qb[1 + d]));
+  }
+  qb[4] = qb[4] + gpb;
+  // rho enters through 1/rho in u.n, p and a
+  qb[0] = qb[0] + fma(half * gpr, s.mm * s.rr, fma(-(half * ab), s.a * s.rr, -(ur * s.un)));
+}
+
+template <typename T>
+__device__ __forceinline__ void rusanov_reverse_t(const T* qL, const T* qR, T nx, T ny, T nz,
+                                                  T gamma, T gm1, const T* w, T* qLb, T* qRb,
+                                                  T* nb) {
+  const T half = ffk(0.5f);
+  const T nn = sqrt(fma(nz, nz, fma(ny, ny, nx * nx)));
+  const T rn = recip(nn);
+  SideStateT<T> sL, sR;
+  const T lL = side_state_t(qL, nx, ny, nz, recip(qL[0]), nn, gamma, gm1, sL);
+  const T lR = side_state_t(qR, nx, ny, nz, recip(qR[0]), nn, gamma, gm1, sR);
+  const bool left = lL >= lR;
+  const T hs = half * (left ? lL : lR);
+  T fb[6];
+  T sb = ffk(0.0f);
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    fb[k] = half * w[k];
+    sb = fma(w[k], qR[k] - qL[k], sb);
+    qRb[k] = fma(-hs, w[k], qRb[k]);
+    qLb[k] = fma(hs, w[k], qLb[k]);
+  }
+  sb = -(half * sb);
+  const T zero = ffk(0.0f);
+  side_reverse_t(qL, nx, ny, nz, sL, nn, rn, gamma, gm1, fb, left ? sb : zero, qLb, nb);
+  side_reverse_t(qR, nx, ny, nz, sR, nn, rn, gamma, gm1, fb, left ? zero : sb, qRb, nb);
+}
+
+// Adjoint of the second-order flux of edge (i, j).  vi, vj: lam (6), q (6),
+// G (18).  oi, oj: qbar (6) then Gbar (18) of each end; nb: nbar (3).
+template <typename T>
+__device__ __forceinline__ void flux2_adj_t(const T* vi, const T* vj, T dx, T dy, T dz, T nx,
+                                            T ny, T nz, T gamma, T gm1, T eps, T two_eps, T* oi,
+                                            T* oj, T* nb) {
+  const T half = ffk(0.5f);
+  const T* qi = vi + 6;
+  const T* qj = vj + 6;
+  const T* Gi = vi + 12;
+  const T* Gj = vj + 12;
+  T qL[6], qR[6], pa[12], pb[12];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const T b = qj[k] - qi[k];
+    const T be = fma(b, b, eps);
+    const T b2e = fma(b, b, two_eps);
+    const T b2 = b + b;
+    const T a[2] = {fma(Gi[3 * k + 2], dz, fma(Gi[3 * k + 1], dy, Gi[3 * k] * dx)),
+                    fma(Gj[3 * k + 2], dz, fma(Gj[3 * k + 1], dy, Gj[3 * k] * dx))};
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const T x = a[sd];
+      const T rd = recip(fma(x, x, b2e));
+      const T phi = (x + b) * fma(x, b, eps) * rd;
+      // d phi / da = (b^2 + eps + 2a(b - phi)) / D,
+      // d phi / db = (a^2 + eps + 2b(a - phi)) / D
+      pa[2 * k + sd] = fma(x + x, b - phi, be) * rd;
+      pb[2 * k + sd] = fma(b2, x - phi, fma(x, x, eps)) * rd;
+      if (sd == 0) qL[k] = fma(half, phi, qi[k]);
+      else qR[k] = fma(-half, phi, qj[k]);
+    }
+  }
+  T w[6], qLb[6], qRb[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    w[k] = vi[k] - vj[k];
+    qLb[k] = ffk(0.0f);
+    qRb[k] = ffk(0.0f);
+  }
+  nb[0] = nb[1] = nb[2] = ffk(0.0f);
+  rusanov_reverse_t(qL, qR, nx, ny, nz, gamma, gm1, w, qLb, qRb, nb);
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const T phib = half * qLb[k], phjb = -(half * qRb[k]);
+    const T aib = phib * pa[2 * k], ajb = phjb * pa[2 * k + 1];
+    const T bb = fma(phib, pb[2 * k], phjb * pb[2 * k + 1]);
+    oi[k] = qLb[k] - bb;
+    oj[k] = qRb[k] + bb;
+    oi[6 + 3 * k] = aib * dx;
+    oi[7 + 3 * k] = aib * dy;
+    oi[8 + 3 * k] = aib * dz;
+    oj[6 + 3 * k] = ajb * dx;
+    oj[7 + 3 * k] = ajb * dy;
+    oj[8 + 3 * k] = ajb * dz;
+  }
 }
 
 }  // namespace op2b

@@ -85,7 +85,54 @@ __global__ void k_gg_ff(const int64_t* __restrict__ rowptr, const int32_t* __res
   }
 }
 
+// Adjoint of the second-order flux in float-float: v = lam (6), q (6),
+// G (18) as float-float shadows; per end qbar (6) then Gbar (18) converted to
+// FP64 and accumulated into the FP64 targets; nbar written in FP64.
+struct BodyFluxAdjFF {
+  using TN = ffv;
+  using TE = ffv;
+  using TA = double;
+  static constexpr int NIN = 30, OUT = 24, MODE = MODE_GEN, DIM0 = 6;
+  const ffv* lam;
+  int64_t ldl;
+  const ffv* q;
+  int64_t ldq;
+  const ffv* G;
+  int64_t ldG;
+  const ffv* n;
+  int64_t ldn;
+  const ffv* dx;
+  int64_t lddx;
+  double* nbar;
+  int64_t ldnb;
+  ffv gamma, gm1, eps, two_eps;
+  __device__ __forceinline__ void load(int64_t i, ffv* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(lam + k * ldl + i);
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[6 + k] = ldro(q + k * ldq + i);
+#pragma unroll
+    for (int c = 0; c < 18; c++) v[12 + c] = ldro(G + c * ldG + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const ffv* vi, const ffv* vj, ffv* oi,
+                                       ffv* oj) const {
+    ffv nb[3];
+    flux2_adj_t(vi, vj, ldro(dx + e), ldro(dx + lddx + e), ldro(dx + 2 * lddx + e), ldro(n + e),
+                ldro(n + ldn + e), ldro(n + 2 * ldn + e), gamma, gm1, eps, two_eps, oi, oj, nb);
+    nbar[e] = (double)nb[0];
+    nbar[ldnb + e] = (double)nb[1];
+    nbar[2 * ldnb + e] = (double)nb[2];
+  }
+};
+
 int launch_ff(Ctx* c, const LoopLaunch& L, const Strategy& s) {
+  if (L.loop == OP2B_LOOP_FLUX2_ADJ) {
+    BodyFluxAdjFF b{(const ffv*)L.lam, L.ldl, (const ffv*)L.q, L.ldq, (const ffv*)L.G, L.ldG,
+                    (const ffv*)L.n, L.ldn, (const ffv*)L.dx, L.lddx, (double*)L.direct,
+                    L.lddirect, ffv(L.gamma), ffv(L.gamma - 1.0), ffv(L.eps), ffv(2.0 * L.eps)};
+    Targets<double, 6> tg{(double*)L.t0, L.ldt0, (double*)L.t1, L.ldt1};
+    return run_body(c, b, L, s, tg);
+  }
   if (L.loop == OP2B_LOOP_GREEN_GAUSS) {
     DevSegPlan* sp = nullptr;
     if (int rc = c->seg_plan(L.map, &sp)) return rc;
@@ -99,8 +146,8 @@ int launch_ff(Ctx* c, const LoopLaunch& L, const Strategy& s) {
     return c->launched("green_gauss_ff");
   }
   if (L.loop != OP2B_LOOP_FLUX2)
-    return c->fail(OP2B_ETYPE, "float-float dats: only the Green-Gauss loop and the second-order "
-                               "flux have float-float variants");
+    return c->fail(OP2B_ETYPE, "float-float dats: only the Green-Gauss loop, the second-order flux, "
+                               "its adjoint and the viscous flux have float-float variants");
   BodyFlux2FF b{(const float2*)L.q, L.ldq, (const float2*)L.G, L.ldG, (const float2*)L.n, L.ldn,
                 (const float2*)L.dx, L.lddx, gas_ff(L.gamma, L.eps)};
   Targets<double, 6> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};

@@ -119,6 +119,8 @@ class EdgeSolver:
             node("sbar", 6)     # march adjoint: adjoint of the current state
             node("qacc", 6)     # march adjoint: per-step accumulator
             edgd("nbar_acc", 3)  # march adjoint: dJ/dn summed over the stages
+            if ff:
+                node("lam_ff", 6, "ff")  # float-float shadow of the adjoint weights
         self.perm = np.arange(self.N, dtype=np.int64)   # new id of old node
         self.order = np.arange(self.E, dtype=np.int64)  # old edge of new slot
         if renumber == "rcb":
@@ -254,6 +256,12 @@ class EdgeSolver:
                           dr("n", R), dr("nd", R), dr("dx", R), ind("Rd", 0, I), ind("Rd", 1, I)]
             self.a_gga = [ind("Gbar", 0, R), ind("Gbar", 1, R), ind("q", 0, R), ind("q", 1, R),
                           dr("n", R), ind("qbar", 0, I), ind("qbar", 1, I), dr("nbar", RWa)]
+            if self.ff:
+                self.a_fa2_ff = [ind("lam_ff", 0, R), ind("lam_ff", 1, R), ind("q_ff", 0, R),
+                                 ind("q_ff", 1, R), ind("G_ff", 0, R), ind("G_ff", 1, R),
+                                 dr("n_ff", R), dr("dx_ff", R), ind("qbar", 0, I),
+                                 ind("qbar", 1, I), ind("Gbar", 0, I), ind("Gbar", 1, I),
+                                 dr("nbar", W)]
 
     def set_strategy(self, loop, prec, strategy, block=0, part=0, staged=0):
         L.op2b_set_strategy(self.ctx, loop, prec, strategy, block, part, staged)
@@ -358,14 +366,27 @@ class EdgeSolver:
             raise NotImplementedError(what + " loops cover the inviscid residual with the van "
                                       "Albada limiter only")
 
-    def adjoint(self, order=2, recompute_gradient=True):
+    def adjoint(self, order=2, recompute_gradient=True, ff=False):
         """qbar = dJ/dq (dat qbar) and nbar = dJ/dn (dat nbar) of J = lam . R.
 
         The edge states are recomputed from the node data.  With
         ``recompute_gradient=False`` the dat G must still hold the gradient
-        of the current q and n (as the forward residual left it)."""
+        of the current q and n (as the forward residual left it; G_ff with
+        ``ff``).  ``ff``: the flux adjoint in float-float arithmetic from
+        the float-float shadows of lam, q, G, n and dx (q_ff must match q);
+        the scaling and Green-Gauss adjoints stay FP64."""
         self._inviscid_only("adjoint")
         c = self.ctx
+        if ff:
+            if order != 2:
+                raise ValueError("the float-float adjoint is the second-order one")
+            if recompute_gradient:
+                self.green_gauss(ff=True)
+            L.op2b_dat_copy(c, self.d["lam_ff"], self.d["lam"])
+            L.op2b_edge_flux_adjoint(c, self.a_fa2_ff, 2, self.gamma, self.eps_lim, L.ZERO_INC)
+            L.op2b_grad_scale_adjoint(c, self.d["Gbar"], self.d["V"])
+            L.op2b_green_gauss_adjoint(c, self.a_gga, 0)
+            return
         if order == 1:
             L.op2b_edge_flux_adjoint(c, self.a_fa1, 1, self.gamma, self.eps_lim, L.ZERO_INC)
             return

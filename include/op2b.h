@@ -122,10 +122,14 @@ typedef struct {
                                   numbered end it is: that end's data loaded
                                   once and its sum kept in registers; atomic
                                   adds for the other end only */
+#define OP2B_STRAT_GATHER 7    /* Green-Gauss loop only: thread(s) per node
+                                  over the node's sorted edge ends, sums kept
+                                  in registers and written once (no scatter,
+                                  no race, no atomics) */
 #define OP2B_STRAT_AUTO_DET 4  /* autotune among the deterministic strategies
-                                  only (colour, segmented): their sums run in
-                                  a fixed order, so results are bitwise
-                                  reproducible from run to run, which
+                                  only (colour, segmented, gather): their sums
+                                  run in a fixed order, so results are
+                                  bitwise reproducible from run to run, which
                                   finite-difference uses of the loops need;
                                   the atomic strategy's order is not fixed */
 

@@ -606,6 +606,13 @@ std::vector<Strategy> candidates(const LoopLaunch& L, bool det) {
     s.block = b;
     v.push_back(s);
   }
+  if (L.loop == OP2B_LOOP_GREEN_GAUSS)
+    for (int b : {128, 256}) {
+      Strategy s;
+      s.strategy = OP2B_STRAT_GATHER;
+      s.block = b;
+      v.push_back(s);
+    }
   if (!det)
     for (int b : {128, 256}) {
       Strategy s;
@@ -1321,8 +1328,10 @@ extern "C" int op2b_set_strategy(op2b_ctx h, int32_t loop, int32_t prec, int32_t
   Ctx& c = h->c;
   if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec < 0 || prec >= OP2B_NUM_PREC))
     return c.fail(OP2B_EINVAL, "set_strategy: bad loop or precision");
-  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_OWNER)
+  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_GATHER)
     return c.fail(OP2B_EINVAL, "set_strategy: bad strategy");
+  if (strategy == OP2B_STRAT_GATHER && loop != OP2B_LOOP_GREEN_GAUSS)
+    return c.fail(OP2B_EINVAL, "set_strategy: the gather strategy serves the Green-Gauss loop only");
   if (block != 0 && (block < 32 || block > 1024 || block % 32))
     return c.fail(OP2B_EINVAL, "set_strategy: block must be a multiple of 32 in [32, 1024]");
   if (part != 0 && (part < 64 || part > 8192)) return c.fail(OP2B_EINVAL, "set_strategy: part must be in [64, 8192]");
@@ -1378,7 +1387,7 @@ extern "C" int op2b_load_tuning(op2b_ctx h, const char* path) {
                " \"%255[^\"]\": {\"strategy\": %d, \"block\": %d, \"part\": %d, \"staged\": %d, \"ms\": %lf}",
                key, &s.strategy, &s.block, &s.part, &s.staged, &s.tuned_ms) == 6) {
       if (s.strategy < OP2B_STRAT_ATOMIC || s.strategy == OP2B_STRAT_AUTO_DET ||
-          s.strategy > OP2B_STRAT_OWNER)
+          s.strategy > OP2B_STRAT_GATHER)
         return c.fail(OP2B_EINVAL, "load_tuning: bad strategy in table");
       c.tuned[key] = s;
     }

@@ -67,6 +67,33 @@ def test_green_gauss_matches_oracle(gpu_lib, mesh16, ref16, name, strat, block, 
     s.close()
 
 
+@pytest.mark.parametrize("block", [128, 256])
+@pytest.mark.parametrize("renumber", ["none", "rcm"])
+def test_green_gauss_gather_matches_oracle(gpu_lib, mesh16, ref16, block, renumber):
+    # the node-gather strategy (Green-Gauss only) in FP64 and FP32, with
+    # and without zeroing, and bitwise reproducible
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber=renumber, mixed=True)
+    for prec in (0, 1):
+        s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, prec, gpu_lib.STRAT_GATHER, block)
+    s.green_gauss()
+    G = s.fetch_nodes("G")
+    assert rel_err(G, ref16["G"], ref16["Gabs"]) <= TOL
+    s.green_gauss()
+    assert np.array_equal(s.fetch_nodes("G"), G)
+    gpu_lib.op2b_green_gauss(s.ctx, s.a_gg, 0)  # no ZERO_INC: the sums are added
+    Graw, Gabs = oracle.green_gauss(m.edge, q, m.normal, with_abs=True)
+    assert rel_err(s.fetch_nodes("G"), ref16["G"] + Graw, ref16["Gabs"] + Gabs) <= TOL
+    s.sync_shadow()
+    s.green_gauss(mixed=True)
+    err = np.max(np.abs(s.fetch_nodes("G32") - ref16["G"]), axis=0) / np.max(np.abs(ref16["G"]), axis=0)
+    assert np.all(err <= 1e-5), err
+    with pytest.raises(gpu_lib.Op2bError) as e:
+        s.set_strategy(gpu_lib.LOOP_FLUX2, 0, gpu_lib.STRAT_GATHER, block)
+    assert e.value.code == gpu_lib.EINVAL
+    s.close()
+
+
 @pytest.mark.parametrize("name,strat,block,part,staged", STRATS)
 def test_flux2_matches_oracle(gpu_lib, mesh16, ref16, name, strat, block, part, staged):
     m, q = mesh16

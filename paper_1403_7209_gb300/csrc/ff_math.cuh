@@ -107,19 +107,24 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
 
 __device__ __forceinline__ float2 ff_sub(float2 a, float2 b) { return ff_add(a, ff_neg(b)); }
 
+// Products are returned as the pair (p, e) without the final fast two-sum:
+// a product cannot cancel, so |e| stays within about 2^-23 |p| (the
+// rounding error of p plus the two cross terms), close enough to
+// normalised for every operation here, all of which take such pairs (the
+// additions renormalise).
 __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
   const float p = __fmul_rn(a.x, b.x);
   float e = __fmaf_rn(a.x, b.x, -p);
   e = __fmaf_rn(a.x, b.y, e);
   e = __fmaf_rn(a.y, b.x, e);
-  return ff_fast(p, e);
+  return make_float2(p, e);
 }
 
 __device__ __forceinline__ float2 ff_sqr(float2 a) {
   const float p = __fmul_rn(a.x, a.x);
   float e = __fmaf_rn(a.x, a.x, -p);
   e = __fmaf_rn(__fadd_rn(a.x, a.x), a.y, e);
-  return ff_fast(p, e);
+  return make_float2(p, e);
 }
 
 // a b + c with one rounding of the leading parts

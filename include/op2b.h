@@ -122,10 +122,16 @@ typedef struct {
                                   numbered end it is: that end's data loaded
                                   once and its sum kept in registers; atomic
                                   adds for the other end only */
-#define OP2B_STRAT_GATHER 7    /* Green-Gauss loop only: thread(s) per node
-                                  over the node's sorted edge ends, sums kept
-                                  in registers and written once (no scatter,
-                                  no race, no atomics) */
+#define OP2B_STRAT_GATHER 7    /* thread per node over the node's sorted
+                                  edge ends, sums kept in registers and
+                                  written once (no scatter, no race, no
+                                  atomics); every edge is evaluated at both
+                                  ends in its own orientation (bitwise the
+                                  same result), so it costs twice the edge
+                                  arithmetic -- except for Green-Gauss, whose
+                                  gather forms each end's share directly.
+                                  Not for the adjoint loops (per-edge
+                                  outputs) */
 #define OP2B_STRAT_AUTO_DET 4  /* autotune among the deterministic strategies
                                   only (colour, segmented, gather): their sums
                                   run in a fixed order, so results are

@@ -606,7 +606,7 @@ std::vector<Strategy> candidates(const LoopLaunch& L, bool det) {
     s.block = b;
     v.push_back(s);
   }
-  if (L.loop == OP2B_LOOP_GREEN_GAUSS)
+  if (L.loop != OP2B_LOOP_FLUX1_ADJ && L.loop != OP2B_LOOP_FLUX2_ADJ && L.loop != OP2B_LOOP_GG_ADJ)
     for (int b : {128, 256}) {
       Strategy s;
       s.strategy = OP2B_STRAT_GATHER;
@@ -1330,8 +1330,9 @@ extern "C" int op2b_set_strategy(op2b_ctx h, int32_t loop, int32_t prec, int32_t
     return c.fail(OP2B_EINVAL, "set_strategy: bad loop or precision");
   if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_GATHER)
     return c.fail(OP2B_EINVAL, "set_strategy: bad strategy");
-  if (strategy == OP2B_STRAT_GATHER && loop != OP2B_LOOP_GREEN_GAUSS)
-    return c.fail(OP2B_EINVAL, "set_strategy: the gather strategy serves the Green-Gauss loop only");
+  if (strategy == OP2B_STRAT_GATHER &&
+      (loop == OP2B_LOOP_FLUX1_ADJ || loop == OP2B_LOOP_FLUX2_ADJ || loop == OP2B_LOOP_GG_ADJ))
+    return c.fail(OP2B_EINVAL, "set_strategy: the gather strategy needs a loop without per-edge outputs");
   if (block != 0 && (block < 32 || block > 1024 || block % 32))
     return c.fail(OP2B_EINVAL, "set_strategy: block must be a multiple of 32 in [32, 1024]");
   if (part != 0 && (part < 64 || part > 8192)) return c.fail(OP2B_EINVAL, "set_strategy: part must be in [64, 8192]");

@@ -439,6 +439,71 @@ __global__ void k_owner(P ph, const int32_t* __restrict__ m0,
   }
 }
 
+// (6) redundant gather: thread per node over its edge ends (the node-sorted
+// list of the segmented plan); every edge is computed at both of its ends,
+// each time in the edge's own orientation (first end, second end), so the
+// two evaluations are bitwise identical and the INC stays exactly
+// antisymmetric (MODE_ANTI) or symmetric (MODE_SYM).  Each node's sum is
+// kept in registers and written once: no race, no atomics, a fixed order
+// (bitwise reproducible), at twice the arithmetic.  For bodies without
+// per-edge (direct) outputs.  With `add` the sums are added to the targets.
+template <class P, class = void>
+struct HasDirectOutput {
+  static constexpr bool value = false;
+};
+template <class P>
+struct HasDirectOutput<P, std::void_t<decltype(&P::nbar)>> {
+  static constexpr bool value = true;
+};
+
+template <class P>
+__global__ void k_gather_nodes(P ph, const int64_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ ends, const int32_t* __restrict__ m0,
+                               const int32_t* __restrict__ m1, int64_t N,
+                               Targets<typename P::TA, P::DIM0> tg, bool add) {
+  using TN = typename P::TN;
+  using TE = typename P::TE;
+  using TA = typename P::TA;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TN vs[P::NIN];
+    ph.load(i, vs);
+    TA acc[P::OUT];
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) acc[c] = TA(0);
+    const int64_t t1 = rowptr[i + 1];
+    for (int64_t t = rowptr[i]; t < t1; t++) {
+      const int32_t end = ends[t];
+      const int64_t e = end >> 1;
+      const bool second = end & 1;
+      TN vo[P::NIN];
+      ph.load(second ? m0[e] : m1[e], vo);
+      // the edge's own orientation whichever end this is (no divergence:
+      // the operands are selected, the body runs once)
+      TN va[P::NIN], vb[P::NIN];
+#pragma unroll
+      for (int k = 0; k < P::NIN; k++) {
+        va[k] = second ? vo[k] : vs[k];
+        vb[k] = second ? vs[k] : vo[k];
+      }
+      TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
+      ph.edge(e, va, vb, oi, oj);
+#pragma unroll
+      for (int c = 0; c < P::OUT; c++) {
+        const TA a = to_acc<TA>(oi[c]);
+        if constexpr (P::MODE == MODE_ANTI) acc[c] += second ? neg(a) : a;
+        else if constexpr (P::MODE == MODE_SYM) acc[c] += a;
+        else acc[c] += second ? to_acc<TA>(oj[c]) : a;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < P::OUT; c++) {
+      TA* p = tg.at(c, i);
+      *p = add ? *p + acc[c] : acc[c];
+    }
+  }
+}
+
 // Device view of a block plan (mini-partitions + colours).
 struct BlockView {
   const int32_t* cblocks;  // blocks of the colour being launched (null: all

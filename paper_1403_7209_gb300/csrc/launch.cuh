@@ -127,6 +127,21 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
                                                        (const TE*)buf, tg);
       return c->launched("segmented nodes");
     }
+    case OP2B_STRAT_GATHER: {
+      if constexpr (HasDirectOutput<P>::value) {
+        return c->fail(OP2B_EINVAL, "the gather strategy needs a loop without per-edge outputs");
+      } else {
+        DevSegPlan* sp = nullptr;
+        int rc = c->seg_plan(L.map, &sp);
+        if (rc) return rc;
+        if ((rc = check_block(c, k_gather_nodes<P>, block))) return rc;
+        int64_t grid = std::min<int64_t>((L.N + block - 1) / block, cap);
+        if (grid == 0) return OP2B_OK;
+        k_gather_nodes<P><<<(unsigned)grid, block, 0, c->stream>>>(
+            ph, sp->rowptr, sp->ends, L.m0, L.m1, L.N, tg, !(L.flags & OP2B_ZERO_INC));
+        return c->launched("gather");
+      }
+    }
     default:
       return c->fail(OP2B_EINVAL, "unknown strategy");
   }

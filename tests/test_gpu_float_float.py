@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 STRATS = [("atomic", 1, 256, 0, 0), ("colour", 2, 256, 512, 0),
           ("colour_staged", 2, 128, 256, 1), ("segmented", 3, 256, 0, 0),
-          ("block_atomic", 5, 256, 1024, 0), ("owner", 6, 128, 0, 0)]
+          ("block_atomic", 5, 256, 1024, 0), ("owner", 6, 128, 0, 0), ("gather", 7, 128, 0, 0)]
 
 
 def rel_err(gpu, ref, scale):

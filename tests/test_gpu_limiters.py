@@ -22,7 +22,7 @@ KINDS = [("barth_jespersen", oracle.LIM_BJ, 0.0), ("venkatakrishnan", oracle.LIM
          ("venkatakrishnan", oracle.LIM_VENKAT, 1e-3)]
 STRATS = [(1, 256, 0, 0), (1, 128, 0, 0), (2, 256, 512, 0), (2, 128, 256, 1),
           (2, 256, 1024, 1), (3, 256, 0, 0), (5, 256, 1024, 0), (5, 128, 512, 1),
-          (6, 128, 0, 0)]
+          (6, 128, 0, 0), (7, 128, 0, 0)]
 
 
 def rel_err(gpu, ref, scale):

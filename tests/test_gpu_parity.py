@@ -15,7 +15,7 @@ from paper_1403_7209_gb300 import meshgen
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
-STRATS = [("atomic", 1, 256, 0, 0), ("atomic128", 1, 128, 0, 0),
+STRATS = [("atomic", 1, 256, 0, 0), ("atomic128", 1, 128, 0, 0), ("gather", 7, 128, 0, 0),
           ("colour", 2, 256, 512, 0), ("colour_staged", 2, 128, 256, 1),
           ("colour_staged_big", 2, 256, 1024, 1), ("segmented", 3, 256, 0, 0),
           ("block_atomic", 5, 256, 1024, 0), ("block_atomic_staged", 5, 128, 512, 1),
@@ -88,8 +88,8 @@ def test_green_gauss_gather_matches_oracle(gpu_lib, mesh16, ref16, block, renumb
     s.green_gauss(mixed=True)
     err = np.max(np.abs(s.fetch_nodes("G32") - ref16["G"]), axis=0) / np.max(np.abs(ref16["G"]), axis=0)
     assert np.all(err <= 1e-5), err
-    with pytest.raises(gpu_lib.Op2bError) as e:
-        s.set_strategy(gpu_lib.LOOP_FLUX2, 0, gpu_lib.STRAT_GATHER, block)
+    with pytest.raises(gpu_lib.Op2bError) as e:  # per-edge outputs: no gather
+        s.set_strategy(gpu_lib.LOOP_FLUX2_ADJ, 0, gpu_lib.STRAT_GATHER, block)
     assert e.value.code == gpu_lib.EINVAL
     s.close()
 
@@ -186,7 +186,7 @@ def test_march_ten_steps(gpu_lib):
     s.close()
 
 
-@pytest.mark.parametrize("strat", [1, 2, 3, 5, 6])
+@pytest.mark.parametrize("strat", [1, 2, 3, 5, 6, 7])
 def test_mixed_precision_residual_error(gpu_lib, mesh16, ref16, strat):
     m, q = mesh16
     s = make_solver(gpu_lib, m, q, mixed=True, renumber="rcm")

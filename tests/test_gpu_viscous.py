@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 MU, PR, DIFF = 2.0e-3, 0.72, 1.5e-3
 VISC = (MU, PR, DIFF)
-STRATS = [("atomic", 1, 256, 0, 0), ("atomic128", 1, 128, 0, 0),
+STRATS = [("atomic", 1, 256, 0, 0), ("atomic128", 1, 128, 0, 0), ("gather", 7, 128, 0, 0),
           ("colour", 2, 256, 512, 0), ("colour_staged", 2, 128, 256, 1),
           ("colour_staged_big", 2, 256, 1024, 1), ("segmented", 3, 256, 0, 0),
           ("block_atomic", 5, 256, 1024, 0), ("block_atomic_staged", 5, 128, 512, 1),

@@ -132,6 +132,12 @@ typedef struct {
                                   gather forms each end's share directly.
                                   Not for the adjoint loops (per-edge
                                   outputs) */
+#define OP2B_STRAT_HYBRID 8    /* FP64 Green-Gauss only: one launch in which
+                                  half the blocks gather components 0-2 per
+                                  node (FP64 pipe) while the other half
+                                  scatter components 3-5 with atomic adds
+                                  (L2 atomic units), so the two bounds
+                                  overlap */
 #define OP2B_STRAT_AUTO_DET 4  /* autotune among the deterministic strategies
                                   only (colour, segmented, gather): their sums
                                   run in a fixed order, so results are

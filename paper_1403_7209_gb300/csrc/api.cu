@@ -606,6 +606,13 @@ std::vector<Strategy> candidates(const LoopLaunch& L, bool det) {
     s.block = b;
     v.push_back(s);
   }
+  if (!det && L.loop == OP2B_LOOP_GREEN_GAUSS && L.prec == OP2B_PREC_F64)
+    for (int b : {128, 256}) {
+      Strategy s;
+      s.strategy = OP2B_STRAT_HYBRID;
+      s.block = b;
+      v.push_back(s);
+    }
   if (L.loop != OP2B_LOOP_FLUX1_ADJ && L.loop != OP2B_LOOP_FLUX2_ADJ && L.loop != OP2B_LOOP_GG_ADJ)
     for (int b : {128, 256}) {
       Strategy s;
@@ -1328,8 +1335,10 @@ extern "C" int op2b_set_strategy(op2b_ctx h, int32_t loop, int32_t prec, int32_t
   Ctx& c = h->c;
   if (loop < 0 || loop >= OP2B_NUM_LOOPS || (prec < 0 || prec >= OP2B_NUM_PREC))
     return c.fail(OP2B_EINVAL, "set_strategy: bad loop or precision");
-  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_GATHER)
+  if (strategy < OP2B_STRAT_AUTO || strategy > OP2B_STRAT_HYBRID)
     return c.fail(OP2B_EINVAL, "set_strategy: bad strategy");
+  if (strategy == OP2B_STRAT_HYBRID && (loop != OP2B_LOOP_GREEN_GAUSS || prec != OP2B_PREC_F64))
+    return c.fail(OP2B_EINVAL, "set_strategy: the hybrid strategy serves the FP64 Green-Gauss loop only");
   if (strategy == OP2B_STRAT_GATHER &&
       (loop == OP2B_LOOP_FLUX1_ADJ || loop == OP2B_LOOP_FLUX2_ADJ || loop == OP2B_LOOP_GG_ADJ))
     return c.fail(OP2B_EINVAL, "set_strategy: the gather strategy needs a loop without per-edge outputs");
@@ -1388,7 +1397,7 @@ extern "C" int op2b_load_tuning(op2b_ctx h, const char* path) {
                " \"%255[^\"]\": {\"strategy\": %d, \"block\": %d, \"part\": %d, \"staged\": %d, \"ms\": %lf}",
                key, &s.strategy, &s.block, &s.part, &s.staged, &s.tuned_ms) == 6) {
       if (s.strategy < OP2B_STRAT_ATOMIC || s.strategy == OP2B_STRAT_AUTO_DET ||
-          s.strategy > OP2B_STRAT_GATHER)
+          s.strategy > OP2B_STRAT_HYBRID)
         return c.fail(OP2B_EINVAL, "load_tuning: bad strategy in table");
       c.tuned[key] = s;
     }

@@ -90,4 +90,86 @@ int launch_gg_gather(Ctx* c, const LoopLaunch& L, int block) {
   return c->launched("green_gauss gather");
 }
 
+// Hybrid Green-Gauss (FP64): one launch whose first `gblocks` blocks gather
+// components 0..2 of every node (as k_gg_gather, one thread per node, on
+// the FP64 pipe) while the remaining blocks scatter components 3..5 edge by
+// edge with atomic adds (in the L2's atomic units).  The two halves are
+// bound by different units, so running them side by side on every SM
+// overlaps the FP64-pipe time of the one with the atomic time of the other.
+// Both halves always add into G (the caller zeroes it for OP2B_ZERO_INC).
+static __global__ void k_gg_hybrid(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ ends,
+                            const int32_t* __restrict__ m0, const int32_t* __restrict__ m1,
+                            const double* __restrict__ q, int64_t ldq,
+                            const double* __restrict__ n, int64_t ldn, double* __restrict__ G,
+                            int64_t ldG, int64_t N, int64_t E, unsigned gblocks) {
+  if (blockIdx.x < gblocks) {
+    const int64_t stride = (int64_t)gblocks * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += stride) {
+      double qi[3], acc[9];
+#pragma unroll
+      for (int k = 0; k < 3; k++) qi[k] = ldro(q + k * ldq + i);
+#pragma unroll
+      for (int c = 0; c < 9; c++) acc[c] = 0.0;
+      const int64_t t1 = rowptr[i + 1];
+      for (int64_t t = rowptr[i]; t < t1; t++) {
+        const int32_t end = ends[t];
+        const int64_t e = end >> 1;
+        const bool second = end & 1;
+        const int64_t j = second ? m0[e] : m1[e];
+        double nh[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const double v = 0.5 * ldro(n + d * ldn + e);
+          nh[d] = second ? neg(v) : v;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          const double sk = qi[k] + ldro(q + k * ldq + j);
+#pragma unroll
+          for (int d = 0; d < 3; d++) acc[3 * k + d] = fma(sk, nh[d], acc[3 * k + d]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 9; c++) G[c * ldG + i] += acc[c];
+    }
+  } else {
+    const int64_t stride = (int64_t)(gridDim.x - gblocks) * blockDim.x;
+    for (int64_t e = (blockIdx.x - gblocks) * (int64_t)blockDim.x + threadIdx.x; e < E;
+         e += stride) {
+      const int64_t i = m0[e], j = m1[e];
+      const double h[3] = {0.5 * ldro(n + e), 0.5 * ldro(n + ldn + e),
+                           0.5 * ldro(n + 2 * ldn + e)};
+#pragma unroll
+      for (int k = 3; k < 6; k++) {
+        const double sk = ldro(q + k * ldq + i) + ldro(q + k * ldq + j);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const double v = sk * h[d];
+          atomicAdd(G + (3 * k + d) * ldG + i, v);
+          atomicAdd(G + (3 * k + d) * ldG + j, neg(v));
+        }
+      }
+    }
+  }
+}
+
+inline int launch_gg_hybrid(Ctx* c, const LoopLaunch& L, int block) {
+  DevSegPlan* sp = nullptr;
+  if (int rc = c->seg_plan(L.map, &sp)) return rc;
+  if (L.N == 0) return OP2B_OK;
+  if (block <= 0) block = 128;
+  if (block < 32 || block > 1024 || block % 32)
+    return c->fail(OP2B_EINVAL, "block size must be a multiple of 32 in [32, 1024]");
+  // both roles resident on every SM at once: an equal number of blocks each
+  const int per_sm = std::max(1, 1024 / block);
+  const unsigned gblocks = (unsigned)std::min<int64_t>((L.N + block - 1) / block,
+                                                       (int64_t)c->sm_count * per_sm / 2);
+  const unsigned ablocks = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((L.E + block - 1) / block, (int64_t)c->sm_count * per_sm / 2));
+  k_gg_hybrid<<<gblocks + ablocks, block, 0, c->stream>>>(
+      sp->rowptr, sp->ends, L.m0, L.m1, (const double*)L.q, L.ldq, (const double*)L.n, L.ldn,
+      (double*)L.t0, L.ldt0, L.N, L.E, gblocks);
+  return c->launched("green_gauss hybrid");
+}
+
 }  // namespace op2b

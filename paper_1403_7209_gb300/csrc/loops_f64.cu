@@ -9,6 +9,7 @@ int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s) {
   switch (L.loop) {
     case OP2B_LOOP_GREEN_GAUSS: {
       if (s.strategy == OP2B_STRAT_GATHER) return launch_gg_gather<double, 2>(c, L, s.block);
+      if (s.strategy == OP2B_STRAT_HYBRID) return launch_gg_hybrid(c, L, s.block);
       BodyGG<double> b{(const double*)L.q, L.ldq, (const double*)L.n, L.ldn};
       Targets<double, 18> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};
       return run_body(c, b, L, s, tg);

@@ -29,13 +29,13 @@ LOOP_FLUX2_PHI, NUM_LOOPS = 11, 12
 LIM_BARTH_JESPERSEN, LIM_VENKATAKRISHNAN = 1, 2
 PREC_F64, PREC_F32, PREC_FF, NUM_PREC = 0, 1, 2, 3
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
-STRAT_BLOCK_ATOMIC, STRAT_OWNER, STRAT_GATHER = 5, 6, 7
+STRAT_BLOCK_ATOMIC, STRAT_OWNER, STRAT_GATHER, STRAT_HYBRID = 5, 6, 7, 8
 ZERO_INC = 1
 RED_SUM, RED_L2, RED_MAXABS, RED_MIN = 0, 1, 2, 3
 STRATEGY_NAMES = {STRAT_AUTO: "auto", STRAT_ATOMIC: "atomic",
                   STRAT_COLOUR: "colour", STRAT_SEGMENTED: "segmented",
                   STRAT_AUTO_DET: "auto-deterministic", STRAT_BLOCK_ATOMIC: "block-atomic",
-                  STRAT_OWNER: "owner", STRAT_GATHER: "gather"}
+                  STRAT_OWNER: "owner", STRAT_GATHER: "gather", STRAT_HYBRID: "hybrid"}
 ERROR_NAMES = {EINVAL: "EINVAL", EDIM: "EDIM", ETYPE: "ETYPE",
                EACCESS: "EACCESS", ESET: "ESET", ENOMEM: "ENOMEM",
                ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EPLAN: "EPLAN",

@@ -94,6 +94,24 @@ def test_green_gauss_gather_matches_oracle(gpu_lib, mesh16, ref16, block, renumb
     s.close()
 
 
+@pytest.mark.parametrize("block", [128, 256])
+def test_green_gauss_hybrid_matches_oracle(gpu_lib, mesh16, ref16, block):
+    # FP64 only: gathered components 0-2, atomically scattered 3-5, one launch
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber="rcm")
+    s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, 0, gpu_lib.STRAT_HYBRID, block)
+    s.green_gauss()
+    assert rel_err(s.fetch_nodes("G"), ref16["G"], ref16["Gabs"]) <= TOL
+    gpu_lib.op2b_green_gauss(s.ctx, s.a_gg, 0)  # no ZERO_INC: the sums are added
+    Graw, Gabs = oracle.green_gauss(m.edge, q, m.normal, with_abs=True)
+    assert rel_err(s.fetch_nodes("G"), ref16["G"] + Graw, ref16["Gabs"] + Gabs) <= TOL
+    for loop, prec in ((gpu_lib.LOOP_GREEN_GAUSS, 1), (gpu_lib.LOOP_FLUX2, 0)):
+        with pytest.raises(gpu_lib.Op2bError) as e:
+            s.set_strategy(loop, prec, gpu_lib.STRAT_HYBRID, block)
+        assert e.value.code == gpu_lib.EINVAL
+    s.close()
+
+
 @pytest.mark.parametrize("name,strat,block,part,staged", STRATS)
 def test_flux2_matches_oracle(gpu_lib, mesh16, ref16, name, strat, block, part, staged):
     m, q = mesh16

@@ -582,27 +582,37 @@ def config0_extra(torch, L, args):
 
 
 def march_extra(torch, L, s, q, args, stream, steps=50):
-    """50-step explicit march in FP64 and in FP32-mixed from the same state;
-    relative max-norm state difference per component after the march."""
+    """50-step explicit march in FP64, in FP32-mixed and in float-float from
+    the same state; relative max-norm state difference per component from
+    the FP64 march after it."""
     N = s.N
 
-    def run(mixed):
+    def run(mixed, ff=False):
         s.load_nodes("q", q)
         if mixed:
             s.sync_shadow()
+        if ff:
+            s.sync_shadow(ff=True)
         s.time_step(0.5)
         torch.cuda.synchronize()
         t = time.perf_counter()
         for _ in range(steps):
-            s.step(order=2, mixed=mixed)
+            s.step(order=2, mixed=mixed, ff=ff)
         torch.cuda.synchronize()
         return s.t["q"][:, :N].clone(), time.perf_counter() - t
+
+    def rel(a, b):
+        return ((a - b).abs().amax(dim=1) / b.abs().amax(dim=1)).cpu().tolist()
     q64, t64 = run(False)
     q32, t32 = run(True)
-    err = ((q32 - q64).abs().amax(dim=1) / q64.abs().amax(dim=1)).cpu().tolist()
-    ok = bool(torch.isfinite(q64).all().item())
-    return {"steps": steps, "stages_per_step": 5, "fp64_s": t64, "mixed_s": t32,
-            "mixed_state_rel_err_per_component": err, "fp64_finite": ok}
+    out = {"steps": steps, "stages_per_step": 5, "fp64_s": t64, "mixed_s": t32,
+           "mixed_state_rel_err_per_component": rel(q32, q64),
+           "fp64_finite": bool(torch.isfinite(q64).all().item())}
+    if s.ff:
+        qff, tff = run(False, ff=True)
+        out["float_float_s"] = tff
+        out["float_float_state_rel_diff_per_component"] = rel(qff, q64)
+    return out
 
 
 def numbering_extra(torch, L, m, q, args, stream, ms_rcm, device):

@@ -540,6 +540,8 @@ def march_adjoint_extra(torch, L, s, q, args, stream, E, steps=10):
     stored = (steps * 5 + 1) * 6 * N * 8 + steps * 5 * 18 * N * 8
     return {"steps": steps, "stages": 5 * steps, "forward_march_ms": f_ms,
             "adjoint_march_ms": r_ms, "ratio_to_forward": r_ms / f_ms,
+            "adjoint_march_includes": "the forward march that stores every stage, then the "
+                                      "reverse sweep",
             "adjoint_march_recompute_gradients_ms": rr_ms,
             "stored_gb": stored / 1e9, "edges_per_s_per_stage": E * 5 * steps / (r_ms * 1e-3)}
 

@@ -289,7 +289,12 @@ int op2b_spectral_radius(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *   qbar 0 INC, qbar 1 INC, nbar ID WRITE.
  * order 2 args (13): lam 0, lam 1, q 0, q 1, G 0, G 1 (READ), n ID READ,
  *   dx ID READ, qbar 0 INC, qbar 1 INC, Gbar 0 INC, Gbar 1 INC (dim 18),
- *   nbar ID WRITE (edge, dim 3).  All F64. */
+ *   nbar ID WRITE (edge, dim 3).  All F64; or, order 2 only, the eight READ
+ *   dats FF (float-float shadows): the reverse sweep then runs in
+ *   float-float arithmetic on the FP32 units and its per-edge results are
+ *   converted to FP64 for qbar, Gbar (INC) and nbar (WRITE), all F64.  The
+ *   float-float sweep's error is about 1e-12 of max |qbar| per component
+ *   (the sweep's terms cancel by about two orders of magnitude). */
 int op2b_edge_flux_adjoint(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                            const op2b_flux_params* prm);
 

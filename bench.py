@@ -473,23 +473,26 @@ def limiter_extra(torch, L, m, q, args, stream, device, E, ms_va):
     from paper_1403_7209_gb300.solver import EdgeSolver
     sl = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device,
                     renumber=args.numbering, mixed=True, stream=stream,
-                    limiter="barth_jespersen")
+                    limiter="barth_jespersen", ff=True)
     if args.tune_cache and os.path.exists(args.tune_cache):
         L.op2b_load_tuning(sl.ctx, args.tune_cache)
     for loop in range(L.NUM_LOOPS):
-        for prec in (0, 1):
+        for prec in range(L.NUM_PREC):
             sl.set_strategy(loop, prec, L.STRAT_AUTO)
     sl.time_step(0.5)
     L.op2b_dat_copy(sl.ctx, sl.d["q0"], sl.d["q"])
     sl.sync_shadow()
+    sl.sync_shadow(ff=True)
     c, d = sl.ctx, sl.d
     out = {}
-    for tag, mixed in (("fp64", False), ("mixed", True)):
-        sfx = "32" if mixed else ""
-        qn, Gn, dxn = ("q32", "G32", "dx32") if mixed else ("q", "G", "dx")
-        sl.residual(2, mixed=mixed)  # tunes
+    for tag, mixed, ff in (("fp64", False, False), ("mixed", True, False),
+                           ("float_float", False, True)):
+        sfx = "32" if mixed else ("_ff" if ff else "")
+        qn, Gn, dxn = "q" + sfx, "G" + sfx, "dx" + sfx
+        prec = L.PREC_F32 if mixed else (L.PREC_FF if ff else L.PREC_F64)
+        sl.residual(2, mixed=mixed, ff=ff)  # tunes
         for _ in range(max(1, args.warmup)):
-            sl.stage(0.25, 2, mixed=mixed)
+            sl.stage(0.25, 2, mixed=mixed, ff=ff)
 
         def mm():
             L.op2b_node_minmax(c, sl.map, d[qn], d["qmin" + sfx], d["qmax" + sfx])
@@ -499,15 +502,17 @@ def limiter_extra(torch, L, m, q, args, stream, device, E, ms_va):
                                 d["qmax" + sfx], d["phi" + sfx])
 
         def fl():
-            L.op2b_edge_flux_limited(c, sl.a_f2phi32 if mixed else sl.a_f2phi, sl.gamma,
+            L.op2b_edge_flux_limited(c, sl.a_f2phi32 if mixed else (sl.a_f2phi_ff if ff else
+                                                                     sl.a_f2phi), sl.gamma,
                                      L.ZERO_INC)
         r = {"minmax_ms": timed(torch, mm, args.steps, stream),
              "limiter_bj_ms": timed(torch, lambda: lim(L.LIM_BARTH_JESPERSEN), args.steps, stream),
              "limiter_venkat_ms": timed(torch, lambda: lim(L.LIM_VENKATAKRISHNAN), args.steps,
                                         stream),
              "flux_limited_ms": timed(torch, fl, args.steps, stream),
-             "stage_ms": timed(torch, lambda: sl.stage(0.25, 2, mixed=mixed), args.steps, stream),
-             "flux_strategy": L.STRATEGY_NAMES[sl.plan_stats(L.LOOP_FLUX2_PHI, int(mixed))["strategy"]]}
+             "stage_ms": timed(torch, lambda: sl.stage(0.25, 2, mixed=mixed, ff=ff), args.steps,
+                               stream),
+             "flux_strategy": L.STRATEGY_NAMES[sl.plan_stats(L.LOOP_FLUX2_PHI, prec)["strategy"]]}
         r["stage_edges_per_s"] = E / (r["stage_ms"] * 1e-3)
         out[tag] = r
     out["fp64"]["stage_vs_van_albada_stage"] = out["fp64"]["stage_ms"] / ms_va

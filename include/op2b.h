@@ -103,8 +103,8 @@ typedef struct {
 #define OP2B_PREC_F64 0
 #define OP2B_PREC_F32 1
 /* FF node and edge data (float-float shadows) and float-float arithmetic:
- * the Green-Gauss loop (FF sums), the second-order flux and the viscous
- * flux (FP64 R) */
+ * the Green-Gauss loop (FF sums), the second-order flux, the node-limited
+ * flux and the viscous flux (FP64 R), the flux adjoint (FP64 results) */
 #define OP2B_PREC_FF 2
 #define OP2B_NUM_PREC 3
 
@@ -332,7 +332,7 @@ int op2b_edge_flux_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *
  * op2b_node_minmax: qmin_i / qmax_i = min / max of q over node i and the
  *   nodes that share an edge of `map` with it.  q, qmin, qmax: dim 6 on the
- *   map's to-set, all F64 or all F32, qmin and qmax distinct from q.
+ *   map's to-set, all F64, all F32 or all FF, qmin and qmax distinct from q.
  *
  * op2b_node_limiter: for every end of every edge at node i, with d = dx at
  *   the edge's first end and -dx at its second, D2 = G_i . d / 2 (the
@@ -345,16 +345,17 @@ int op2b_edge_flux_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *   node without edges).  Venkatakrishnan's phi may exceed 1 slightly (it is
  *   1 at D2/D1 = 0 and 1/2 and above 1 in between); eps2 >= 0 smooths it
  *   (eps2 = (K h)^3 in Venkatakrishnan's notation).  q, qmin, qmax, phi dim
- *   6 and G dim 18 on the to-set, dx dim 3 on the from-set (edges), all F64
- *   or all F32; phi distinct from the inputs.
+ *   6 and G dim 18 on the to-set, dx dim 3 on the from-set (edges), all F64,
+ *   all F32 or all FF (float-float arithmetic); phi distinct from the inputs.
  *
  * op2b_edge_flux_limited: R_i += F(qL, qR, n), R_j -= F, with face states
  *   qL = q_i + phi_i (G_i . dx)/2, qR = q_j - phi_j (G_j . dx)/2 and the
  *   Rusanov flux of op2b_edge_flux.  args (10): q 0, q 1, G 0, G 1, phi 0,
  *   phi 1 (READ), n ID READ, dx ID READ, R 0 INC, R 1 INC (F64 dim 6).
  *   prm->order is ignored; prm->eps_lim unused.  q, G, phi, n, dx all F64,
- *   or all F32 with FP32 arithmetic and each edge's flux converted to FP64
- *   before it is added into R.
+ *   or all F32 with FP32 arithmetic, or all FF with float-float arithmetic;
+ *   with F32 or FF each edge's flux is converted to FP64 before it is added
+ *   into R.
  *
  * The two node loops run as gathers over the node-sorted edge ends (no
  * atomics, results independent of the order of the ends). */
@@ -564,7 +565,7 @@ int op2b_halo_destroy(op2b_halo h);
  * dst[s][c * dst_ld[s] + dst_idx[t]] = src[s][c * src_ld[s] + src_idx[t]]
  * for c < dim, t running over the entries of all segments in order
  * (count[s] per segment).  src / dst: device pointers of SoA dats of `type`
- * (F64 or F32) whose leading dimensions are src_ld / dst_ld; the pointers
+ * (F64, F32 or FF) whose leading dimensions are src_ld / dst_ld; the pointers
  * are captured at creation (re-create the exchange after moving a dat).
  * Indices must lie in [0, ld) of their dat (checked on the host at
  * creation: OP2B_EINVAL).  Rows of one exchange must not be both read and

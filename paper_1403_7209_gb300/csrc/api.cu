@@ -562,7 +562,8 @@ std::string tune_key(const LoopLaunch& L, bool det) {
 
 int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);  // F64, F32 or FF
-  if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // GG and FLUX2 only (checked there)
+  if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);  // F64, F32 or FF
+  if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // GG, FLUX2, FLUX2_ADJ (checked there)
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);
   if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
@@ -1158,7 +1159,8 @@ extern "C" int op2b_node_minmax(op2b_ctx h, op2b_map map, op2b_dat q, op2b_dat q
   if (!valid_map(c, map) || c.maps[map].arity != 2) return c.fail(OP2B_EINVAL, "node_minmax: need an arity-2 map");
   if (!valid_dat(c, q)) return c.fail(OP2B_EINVAL, "node_minmax: bad dat");
   const int type = c.dats[q].type;
-  if (type != OP2B_F64 && type != OP2B_F32) return c.fail(OP2B_ETYPE, "node_minmax: F64 or F32 dats");
+  if (type != OP2B_F64 && type != OP2B_F32 && type != OP2B_FF)
+    return c.fail(OP2B_ETYPE, "node_minmax: F64, F32 or FF dats");
   const MapRec& m = c.maps[map];
   int rc;
   if ((rc = gather_dat(c, q, 6, type, m.to, w)) || (rc = gather_dat(c, qmin, 6, type, m.to, w)) ||
@@ -1184,7 +1186,8 @@ extern "C" int op2b_node_limiter(op2b_ctx h, op2b_map map, int32_t kind, double 
   if (!valid_map(c, map) || c.maps[map].arity != 2) return c.fail(OP2B_EINVAL, "node_limiter: need an arity-2 map");
   if (!valid_dat(c, q)) return c.fail(OP2B_EINVAL, "node_limiter: bad dat");
   const int type = c.dats[q].type;
-  if (type != OP2B_F64 && type != OP2B_F32) return c.fail(OP2B_ETYPE, "node_limiter: F64 or F32 dats");
+  if (type != OP2B_F64 && type != OP2B_F32 && type != OP2B_FF)
+    return c.fail(OP2B_ETYPE, "node_limiter: F64, F32 or FF dats");
   const MapRec& m = c.maps[map];
   int rc;
   if ((rc = gather_dat(c, q, 6, type, m.to, w)) || (rc = gather_dat(c, G, 18, type, m.to, w)) ||

@@ -198,9 +198,11 @@ __device__ __forceinline__ float2 ff_sqrt(float2 x) {
 
 __device__ __forceinline__ float2 ff_abs(float2 a) { return a.x < 0.0f ? ff_neg(a) : a; }
 
-// a >= b (hi parts first, then lo)
+// a >= b by the sign of the renormalised difference: correct for
+// unnormalised operands too (products), whose hi parts alone may order
+// them wrongly when they are within ~2^-23 of each other
 __device__ __forceinline__ bool ff_ge(float2 a, float2 b) {
-  return a.x > b.x || (a.x == b.x && a.y >= b.y);
+  return ff_sub(a, b).x >= 0.0f;
 }
 
 // host-side split of a double constant
@@ -247,6 +249,16 @@ using ::fabs;
 __device__ __forceinline__ ffv sqrt(ffv a) { return ffv(ff_sqrt(a.v)); }
 __device__ __forceinline__ ffv fabs(ffv a) { return ffv(ff_abs(a.v)); }
 __device__ __forceinline__ bool operator>=(ffv a, ffv b) { return ff_ge(a.v, b.v); }
+// order of float-float values: the sign of the renormalised difference
+// (see ff_ge)
+__device__ __forceinline__ bool operator<(ffv a, ffv b) { return ff_sub(a.v, b.v).x < 0.0f; }
+__device__ __forceinline__ bool operator>(ffv a, ffv b) { return b < a; }
+__device__ __forceinline__ bool operator==(ffv a, ffv b) {
+  return a.v.x == b.v.x && a.v.y == b.v.y;
+}
+__device__ __forceinline__ bool operator!=(ffv a, ffv b) { return !(a == b); }
+using ::fmin;
+__device__ __forceinline__ ffv fmin(ffv a, ffv b) { return b < a ? b : a; }
 // sign(x) v with sign(0) = 0
 __device__ __forceinline__ ffv sign_times(ffv x, ffv v) {
   return x.v.x > 0.0f ? v : (x.v.x < 0.0f ? -v : ffv(make_float2(0.0f, 0.0f)));

@@ -17,7 +17,9 @@
 // is scattered, so there is no race to resolve and the result does not
 // depend on the order of the ends.
 #include <algorithm>
+#include <type_traits>
 
+#include "ff_math.cuh"
 #include "launch.cuh"
 
 namespace op2b {
@@ -45,6 +47,17 @@ struct MinMaxAcc<double> {
   }
   __device__ __forceinline__ double min() const { return unkey(lo); }
   __device__ __forceinline__ double max() const { return unkey(hi); }
+};
+template <>
+struct MinMaxAcc<ffv> {
+  ffv lo, hi;
+  __device__ __forceinline__ void init(ffv v) { lo = hi = v; }
+  __device__ __forceinline__ void take(ffv v) {
+    lo = v < lo ? v : lo;
+    hi = hi < v ? v : hi;
+  }
+  __device__ __forceinline__ ffv min() const { return lo; }
+  __device__ __forceinline__ ffv max() const { return hi; }
 };
 template <>
 struct MinMaxAcc<float> {
@@ -167,7 +180,8 @@ __global__ void k_limiter(const int64_t* __restrict__ rowptr, const int32_t* __r
 template <typename T>
 struct BodyFlux2Phi {
   using TN = T;
-  using TE = T;
+  // float-float: each edge's flux leaves the float-float Rusanov as FP64
+  using TE = typename std::conditional<std::is_same<T, ffv>::value, double, T>::type;
   using TA = double;
   static constexpr int NIN = 30, OUT = 6, MODE = MODE_ANTI, DIM0 = 6;
   const T* q;
@@ -202,15 +216,27 @@ struct BodyFlux2Phi {
       qR[k] = fma(neg(vj[24 + k]), aj, vj[k]);
     }
     const T nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
-    if constexpr (sizeof(T) == 8)
+    if constexpr (std::is_same<T, double>::value) {
       rusanov_f64(qL, qR, nx, ny, nz, g, oi);
-    else
+    } else if constexpr (std::is_same<T, ffv>::value) {
+      const GasFF gf{g.gamma.v, g.gm1.v, g.eps.v, g.two_eps.v};
+      rusanov_ff(reinterpret_cast<const float2*>(qL), reinterpret_cast<const float2*>(qR), nx.v,
+                 ny.v, nz.v, gf, oi);
+    } else {
       rusanov(qL, qR, nx, ny, nz, g, oi);
+    }
   }
 };
 
 int launch_lim(Ctx* c, const LoopLaunch& L, const Strategy& s) {
   Targets<double, 6> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};
+  if (L.prec == OP2B_PREC_FF) {
+    Gas<ffv> g{ffv(L.gamma), ffv(L.gamma - 1.0), ffv(L.eps), ffv(2.0 * L.eps)};
+    BodyFlux2Phi<ffv> b{(const ffv*)L.q,   L.ldq,   (const ffv*)L.G, L.ldG,
+                        (const ffv*)L.phi, L.ldphi, (const ffv*)L.n, L.ldn,
+                        (const ffv*)L.dx,  L.lddx,  g};
+    return run_body(c, b, L, s, tg);
+  }
   if (L.prec == OP2B_PREC_F64) {
     Gas<double> g{L.gamma, L.gamma - 1.0, L.eps, 2.0 * L.eps};
     BodyFlux2Phi<double> b{(const double*)L.q,   L.ldq,   (const double*)L.G, L.ldG,
@@ -239,6 +265,10 @@ int node_minmax(Ctx* c, const DevSegPlan& sp, const int32_t* m0, const int32_t* 
     k_minmax<double><<<node_grid(c, N, block), block, 0, c->stream>>>(
         sp.rowptr, sp.ends, m0, m1, (const double*)q, ldq, (double*)qmin, ldmin,
         (double*)qmax, ldmax, N);
+  else if (type == OP2B_FF)
+    k_minmax<ffv><<<node_grid(c, N, block), block, 0, c->stream>>>(
+        sp.rowptr, sp.ends, m0, m1, (const ffv*)q, ldq, (ffv*)qmin, ldmin, (ffv*)qmax, ldmax,
+        N);
   else
     k_minmax<float><<<node_grid(c, N, block), block, 0, c->stream>>>(
         sp.rowptr, sp.ends, m0, m1, (const float*)q, ldq, (float*)qmin, ldmin, (float*)qmax,
@@ -261,6 +291,9 @@ int node_limiter(Ctx* c, const DevSegPlan& sp, int kind, int type, const LimArgs
   if (type == OP2B_F64) {
     if (bj) launch_limiter_t<double, OP2B_LIM_BARTH_JESPERSEN>(c, sp, a, N);
     else launch_limiter_t<double, OP2B_LIM_VENKATAKRISHNAN>(c, sp, a, N);
+  } else if (type == OP2B_FF) {
+    if (bj) launch_limiter_t<ffv, OP2B_LIM_BARTH_JESPERSEN>(c, sp, a, N);
+    else launch_limiter_t<ffv, OP2B_LIM_VENKATAKRISHNAN>(c, sp, a, N);
   } else {
     if (bj) launch_limiter_t<float, OP2B_LIM_BARTH_JESPERSEN>(c, sp, a, N);
     else launch_limiter_t<float, OP2B_LIM_VENKATAKRISHNAN>(c, sp, a, N);

@@ -92,6 +92,8 @@ class EdgeSolver:
                 node(nm, 6)
                 if mixed:
                     node(nm + "32", 6, torch.float32)
+                if ff:
+                    node(nm + "_ff", 6, "ff")
         self.visc = tuple(float(v) for v in viscous) if viscous is not None else None
         if self.visc is not None:
             node("W", 20)
@@ -231,6 +233,10 @@ class EdgeSolver:
                 self.a_f2phi32 = [ind("q32", 0, R), ind("q32", 1, R), ind("G32", 0, R),
                                   ind("G32", 1, R), ind("phi32", 0, R), ind("phi32", 1, R),
                                   dr("n32", R), dr("dx32", R), ind("R", 0, I), ind("R", 1, I)]
+            if self.ff:
+                self.a_f2phi_ff = [ind("q_ff", 0, R), ind("q_ff", 1, R), ind("G_ff", 0, R),
+                                   ind("G_ff", 1, R), ind("phi_ff", 0, R), ind("phi_ff", 1, R),
+                                   dr("n_ff", R), dr("dx_ff", R), ind("R", 0, I), ind("R", 1, I)]
         if self.visc is not None:
             self.a_vf = [ind("W", 0, R), ind("W", 1, R), dr("n", R), dr("dx", R),
                          ind("R", 0, I), ind("R", 1, I)]
@@ -280,10 +286,11 @@ class EdgeSolver:
         L.op2b_green_gauss(c, self.a_gg32 if mixed else self.a_gg, L.ZERO_INC)
         L.op2b_grad_scale(c, self.d["G32" if mixed else "G"], self.d["V"])
 
-    def node_limiter(self, mixed=False):
-        """phi from the neighbourhood min/max and the gradients G."""
-        c, d, sfx = self.ctx, self.d, "32" if mixed else ""
-        q, G, dx = ("q32", "G32", "dx32") if mixed else ("q", "G", "dx")
+    def node_limiter(self, mixed=False, ff=False):
+        """phi from the neighbourhood min/max and the gradients G (FP32 with
+        ``mixed``, float-float with ``ff``)."""
+        c, d, sfx = self.ctx, self.d, "32" if mixed else ("_ff" if ff else "")
+        q, G, dx = ("q" + sfx, "G" + sfx, "dx" + sfx)
         L.op2b_node_minmax(c, self.map, d[q], d["qmin" + sfx], d["qmax" + sfx])
         L.op2b_node_limiter(c, self.map, LIMITERS[self.limiter], self.limiter_eps2, d[q], d[G],
                             d[dx], d["qmin" + sfx], d["qmax" + sfx], d["phi" + sfx])
@@ -292,9 +299,13 @@ class EdgeSolver:
         """R = sum of edge fluxes (R zeroed first).  ``ff``: the
         second-order flux in float-float arithmetic."""
         if ff:
-            if order != 2 or LIMITERS[self.limiter]:
-                raise ValueError("the float-float flux is the second-order van Albada flux")
-            L.op2b_edge_flux(self.ctx, self.a_f2_ff, 2, self.gamma, self.eps_lim, L.ZERO_INC)
+            if order != 2:
+                raise ValueError("the float-float flux is the second-order flux")
+            if LIMITERS[self.limiter]:
+                self.node_limiter(ff=True)
+                L.op2b_edge_flux_limited(self.ctx, self.a_f2phi_ff, self.gamma, L.ZERO_INC)
+            else:
+                L.op2b_edge_flux(self.ctx, self.a_f2_ff, 2, self.gamma, self.eps_lim, L.ZERO_INC)
             return
         if order == 2 and LIMITERS[self.limiter]:
             self.node_limiter(mixed)

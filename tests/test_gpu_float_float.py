@@ -247,3 +247,40 @@ def test_float_float_adjoint_matches_oracle_reverse(gpu_lib, mesh16, strat):
     assert _adj_ok(s.fetch_nodes("qbar"), qb)
     assert _adj_ok(s.fetch_edges("nbar"), nb)
     s.close()
+
+
+# ------------------------------------------------------- node limiters
+LIMS = [("barth_jespersen", oracle.LIM_BJ, 0.0), ("venkatakrishnan", oracle.LIM_VENKAT, 0.0),
+        ("venkatakrishnan", oracle.LIM_VENKAT, 1e-3)]
+
+
+@pytest.mark.parametrize("name,kind,eps2", LIMS)
+def test_float_float_limiter_matches_oracle(gpu_lib, mesh16, name, kind, eps2):
+    import paper_1403_7209_gb300.op2b as L
+    m, q, ref = mesh16
+    lo, hi = oracle.minmax(m.edge, q)
+    rng = np.random.default_rng(kind)
+    for Gin in (ref["G"], rng.normal(scale=0.5, size=ref["G"].shape)):  # mild, strong limiting
+        s = make_solver(m, q, renumber="rcm", limiter=name, limiter_eps2=eps2)
+        s.load_nodes("G", Gin)
+        L.op2b_dat_copy(s.ctx, s.d["G_ff"], s.d["G"])
+        s.node_limiter(ff=True)
+        # the extrema of the float-float shadows of q (within 2^-48 of q)
+        assert np.all(np.abs(s.fetch_nodes("qmin_ff") - lo) <= 2.0 ** -47 * np.abs(lo))
+        assert np.all(np.abs(s.fetch_nodes("qmax_ff") - hi) <= 2.0 ** -47 * np.abs(hi))
+        phi = oracle.limiter(kind, m.edge, q, Gin, m.dx, lo, hi, eps2)
+        assert np.max(np.abs(s.fetch_nodes("phi_ff") - phi)) <= TOL
+        assert np.min(phi) < 0.9  # the limiter is active on this data
+        s.close()
+
+
+@pytest.mark.parametrize("strat", [1, 3, 6, 7])
+@pytest.mark.parametrize("name,kind,eps2", LIMS[:2])
+def test_float_float_limited_residual_matches_oracle(gpu_lib, mesh16, name, kind, eps2, strat):
+    m, q, ref = mesh16
+    s = make_solver(m, q, renumber="rcm", limiter=name, limiter_eps2=eps2)
+    s.set_strategy(gpu_lib.LOOP_FLUX2_PHI, gpu_lib.PREC_FF, strat, 128)
+    s.residual(2, ff=True)
+    o = oracle.residual_limited(kind, m.edge, q, m.normal, m.dx, m.volume, eps2, with_abs=True)
+    assert rel_err(s.fetch_nodes("R"), o["R"], o["Rabs"]) <= TOL
+    s.close()

@@ -54,6 +54,12 @@ VISC_COEFFS = (1.0e-3, 0.72, 1.0e-3)  # mu, Prandtl number, scalar diffusivity
 # profiles/ncu_flux_gg_kernels_n60.md), scaled to a launch by its edge
 # count.  Traffic grows in proportion to the edges.
 DRAM_BYTES_PER_EDGE_FLUX2_ATOMIC = 170.841856e6 / 1944000
+# FP64 instructions per edge of the same kernel in the same capture
+# (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on per cycle x
+# cycles / edges: 105.5 DFMA + 92.0 DMUL + 34.1 DADD)
+FP64_INSTR_PER_EDGE_FLUX2 = 231.6
+# FP64 instruction peak: 152 SMs x 2 per clock x 2.07 GHz
+FP64_PEAK_GINSTR = 152 * 2 * 2.07
 
 
 def read_peaks():
@@ -798,7 +804,16 @@ def main():
                                      "60^3 ncu capture of the same kernel",
                      "peak_source": "FP64 FMA units x clock (152 SMs x 2/clk x 2 flop x 2.07 GHz)",
                      "hbm_frac": BYTES_PER_EDGE["flux2"] * E / (fl_ms * 1e-3) / 1e9 / hbm,
-                     "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src},
+                     "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
+                     "fp64_pipe": {
+                         "instr_per_edge": FP64_INSTR_PER_EDGE_FLUX2,
+                         "achieved_ginstr_s": FP64_INSTR_PER_EDGE_FLUX2 * E / (fl_ms * 1e-3) / 1e9,
+                         "peak_ginstr_s": FP64_PEAK_GINSTR,
+                         "frac": FP64_INSTR_PER_EDGE_FLUX2 * E / (fl_ms * 1e-3) / 1e9
+                                 / FP64_PEAK_GINSTR,
+                         "note": "FP64 instructions per edge from the ncu capture of this kernel; "
+                                 "frac above is algorithmic flops (FMA = 2) over the FP64 flop "
+                                 "peak, lower because 55% of the instructions are not FMAs"}},
         "gpu_launches": launches,
         "clocks": clocks,
         "loops": {nm: {"ms": loop_ms[nm], "edges_per_s": E / (loop_ms[nm] * 1e-3),

@@ -213,7 +213,17 @@ __device__ __forceinline__ void batch_reciprocal(const double* d, double scale,
 #pragma unroll
     for (int k = 1; k < K; k++) p[k] = p[k - 1] * d[k];
     const double pk = p[K - 1];
-    double inv = scale * (seedable(pk) ? recip2(pk) : 1.0 / pk);
+    double inv;
+    if (seedable(pk)) {
+      inv = recip2(pk);  // a normal double within the float exponent range
+      // scale = 1/2 exactly: decrement the exponent on the integer pipe
+      if (scale == 0.5)
+        inv = __hiloint2double(__double2hiint(inv) - 0x00100000, __double2loint(inv));
+      else if (scale != 1.0)
+        inv *= scale;
+    } else {
+      inv = scale / pk;
+    }
 #pragma unroll
     for (int k = K - 1; k > 0; k--) {
       r[k] = inv * p[k - 1];
@@ -255,7 +265,9 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // the FP64 square root of the larger side only; when the estimates are
 // within 2^-14 of each other both sides are computed exactly and the
 // larger is picked by an integer comparison of the bit patterns (ties take
-// the left state), so s is always the exact larger value.
+// the left state), so s is always the exact larger value.  The two sides'
+// fluxes are summed as they are formed (q_L u_L + q_R u_R + (p_L + p_R) n
+// in one chain of multiply-adds) instead of side by side.
 __device__ __forceinline__ void rusanov_f64(const double* qL, const double* qR,
                                             double nx, double ny, double nz,
                                             const Gas<double>& g, double* F) {
@@ -263,24 +275,20 @@ __device__ __forceinline__ void rusanov_f64(const double* qL, const double* qR,
   double rho[2] = {qL[0], qR[0]}, rr[2];
   batch_reciprocal<2>(rho, 0.5, rr);  // rr = 1 / (2 rho)
   const double hgm1 = 0.5 * g.gm1;
-  double f[2][6], uh[2], x[2];
+  double mn[2], un[2], ph[2], e4[2], uh[2], x[2];
   float rank[2];
 #pragma unroll
   for (int sd = 0; sd < 2; sd++) {
     const double* q = sd ? qR : qL;
-    const double mn = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
-    const double un = mn * rr[sd];  // u.n / 2
+    mn[sd] = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
+    un[sd] = mn[sd] * rr[sd];  // u.n / 2
     const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
-    const double ph = fma(-hgm1 * mm, rr[sd], hgm1 * q[4]);  // p / 2
-    x[sd] = ph * rr[sd] * gnn;  // (a |n| / 2)^2
-    uh[sd] = fabs(un);
-    rank[sd] = abs_f32_rank(un) + (seedable(x[sd]) ? sqrt_approx(f32_of_f64(x[sd])) : 0.0f);
-    f[sd][0] = mn;  // rho u.n (halved below)
-    f[sd][1] = fma(q[1], un, ph * nx);
-    f[sd][2] = fma(q[2], un, ph * ny);
-    f[sd][3] = fma(q[3], un, ph * nz);
-    f[sd][4] = fma(2.0, ph, q[4]) * un;  // (rho E + p) u.n / 2
-    f[sd][5] = q[5] * un;
+    ph[sd] = fma(-hgm1 * mm, rr[sd], hgm1 * q[4]);  // p / 2
+    e4[sd] = fma(2.0, ph[sd], q[4]);                // rho E + p
+    x[sd] = ph[sd] * rr[sd] * gnn;                  // (a |n| / 2)^2
+    uh[sd] = fabs(un[sd]);
+    rank[sd] = abs_f32_rank(un[sd]) +
+               (seedable(x[sd]) ? sqrt_approx(f32_of_f64(x[sd])) : 0.0f);
   }
   double s;
   const bool ranked = seedable(x[0]) && seedable(x[1]) &&
@@ -294,9 +302,17 @@ __device__ __forceinline__ void rusanov_f64(const double* qL, const double* qR,
     const double l1 = uh[1] + (seedable(x[1]) ? sqrt2(x[1]) : sqrt(x[1]));
     s = max_nonneg(l0, l1);
   }
-  F[0] = fma(-s, qR[0] - qL[0], 0.5 * (f[0][0] + f[1][0]));
+  // the two sides' half fluxes summed directly:
+  // f_k(L) + f_k(R) = q_k,L un_L + q_k,R un_R (+ (ph_L + ph_R) n for the momenta)
+  const double php = ph[0] + ph[1];
+  const double n3[3] = {nx, ny, nz};
+  F[0] = fma(-s, qR[0] - qL[0], 0.5 * (mn[0] + mn[1]));
 #pragma unroll
-  for (int k = 1; k < 6; k++) F[k] = fma(-s, qR[k] - qL[k], f[0][k] + f[1][k]);
+  for (int d = 0; d < 3; d++)
+    F[1 + d] = fma(-s, qR[1 + d] - qL[1 + d],
+                   fma(qL[1 + d], un[0], fma(qR[1 + d], un[1], php * n3[d])));
+  F[4] = fma(-s, qR[4] - qL[4], fma(e4[0], un[0], e4[1] * un[1]));
+  F[5] = fma(-s, qR[5] - qL[5], fma(qL[5], un[0], qR[5] * un[1]));
 }
 
 // vi, vj: q (6) then G (18, component 3k+d); F: the Rusanov flux of the

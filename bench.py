@@ -50,14 +50,14 @@ FLOPS_PER_EDGE_VISC = 146.0
 VISC_COEFFS = (1.0e-3, 0.72, 1.0e-3)  # mu, Prandtl number, scalar diffusivity
 # DRAM bytes per edge of the FP64 flux2 kernel (atomic strategy, 128 threads)
 # from an ncu capture on the 60^3 lattice (dram__bytes_read.sum +
-# dram__bytes_write.sum = 170.84 MB over 1,944,000 edges;
+# dram__bytes_write.sum = 170.81 MB over 1,944,000 edges;
 # profiles/ncu_flux_gg_kernels_n60.md), scaled to a launch by its edge
 # count.  Traffic grows in proportion to the edges.
-DRAM_BYTES_PER_EDGE_FLUX2_ATOMIC = 170.841856e6 / 1944000
+DRAM_BYTES_PER_EDGE_FLUX2_ATOMIC = 170.809088e6 / 1944000
 # FP64 instructions per edge of the same kernel in the same capture
 # (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd}_pred_on per cycle x
-# cycles / edges: 105.5 DFMA + 92.0 DMUL + 34.1 DADD)
-FP64_INSTR_PER_EDGE_FLUX2 = 231.6
+# cycles / edges: 106.6 DFMA + 85.8 DMUL + 31.0 DADD)
+FP64_INSTR_PER_EDGE_FLUX2 = 223.5
 # FP64 instruction peak: 152 SMs x 2 per clock x 2.07 GHz
 FP64_PEAK_GINSTR = 152 * 2 * 2.07
 
@@ -813,7 +813,7 @@ def main():
                                  / FP64_PEAK_GINSTR,
                          "note": "FP64 instructions per edge from the ncu capture of this kernel; "
                                  "frac above is algorithmic flops (FMA = 2) over the FP64 flop "
-                                 "peak, lower because 55% of the instructions are not FMAs"}},
+                                 "peak, lower because 52% of the instructions are not FMAs"}},
         "gpu_launches": launches,
         "clocks": clocks,
         "loops": {nm: {"ms": loop_ms[nm], "edges_per_s": E / (loop_ms[nm] * 1e-3),

@@ -1,7 +1,12 @@
-// Float-float edge loop: the second-order flux with its arithmetic in
-// float-float (FP32 instructions, ~47 significant bits), reading
-// float-float shadows of q, G, n and dx and adding each edge's flux,
-// converted to FP64, into the FP64 residual under any strategy.
+// Float-float edge loops (arithmetic on the FP32 units, ~47 significant
+// bits, reading float-float shadows of the node and edge data):
+//   second-order flux   each edge's flux converted to FP64 and added into
+//                       the FP64 residual under any strategy;
+//   flux adjoint        the templated reverse sweep (flux2_adj_t) for
+//                       float-float, results converted to FP64;
+//   Green-Gauss         the node gather of gg_gather.cuh (float-float sums).
+// The viscous flux and the node limiters instantiate their own templates
+// for float-float (loops_visc.cu, loops_lim.cu).
 #include "ff_math.cuh"
 #include "gg_gather.cuh"
 #include "launch.cuh"

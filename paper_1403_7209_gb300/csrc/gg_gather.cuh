@@ -49,6 +49,9 @@ __global__ void k_gg_gather(const int64_t* __restrict__ rowptr, const int32_t* _
 #pragma unroll
     for (int c = 0; c < 3 * KC; c++) acc[c] = gg_zero<T>();
     const int64_t t1 = rowptr[i + 1];
+    // unrolled so that the dependent loads (end -> edge -> other node ->
+    // its q) of several ends are in flight together
+#pragma unroll 4
     for (int64_t t = rowptr[i]; t < t1; t++) {
       const int32_t end = ends[t];
       const int64_t e = end >> 1;

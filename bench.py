@@ -387,7 +387,7 @@ def adjoint_extra(torch, L, s, args, stream, E):
     return out
 
 
-def tangent_extra(torch, s, args, stream, E):
+def tangent_extra(torch, L, s, args, stream, E):
     """Jacobian-vector product (tangent loops, G kept from the forward pass)."""
     s.t["qd"].normal_()
     s.t["nd"].normal_()
@@ -396,8 +396,19 @@ def tangent_extra(torch, s, args, stream, E):
         s.tangent(2, recompute_gradient=False)
     tms = timed(torch, lambda: s.tangent(2, recompute_gradient=False), args.steps, stream)
     fms = timed(torch, lambda: s.residual(2), args.steps, stream)
-    return {"ms": tms, "forward_residual_ms": fms, "ratio_to_forward": tms / fms,
-            "edges_per_s": E / (tms * 1e-3)}
+    out = {"ms": tms, "forward_residual_ms": fms, "ratio_to_forward": tms / fms,
+           "edges_per_s": E / (tms * 1e-3)}
+    if s.ff:  # the flux tangent in float-float (Green-Gauss tangent and scaling FP64)
+        s.sync_shadow(ff=True)
+        s.residual(2, ff=True)
+        for _ in range(max(1, args.warmup)):
+            s.tangent(2, recompute_gradient=False, ff=True)
+        ftms = timed(torch, lambda: s.tangent(2, recompute_gradient=False, ff=True), args.steps,
+                     stream)
+        out["float_float"] = {"ms": ftms, "speedup_vs_fp64_tangent": tms / ftms,
+                              "strategy": L.STRATEGY_NAMES[
+                                  s.plan_stats(L.LOOP_FLUX2_TAN, L.PREC_FF)["strategy"]]}
+    return out
 
 
 def viscous_extra(torch, L, m, q, args, stream, device, E):
@@ -825,7 +836,7 @@ def main():
         line["mixed"] = mixed_extra(torch, L, s, args, stream, ms, E, N)
         line["float_float"] = ff_extra(torch, L, s, args, stream, ms, E, N)
         line["adjoint"] = adjoint_extra(torch, L, s, args, stream, E)
-        line["tangent"] = tangent_extra(torch, s, args, stream, E)
+        line["tangent"] = tangent_extra(torch, L, s, args, stream, E)
         line["viscous"] = viscous_extra(torch, L, m, q, args, stream, local, E)
         line["viscous"]["fp64_ns_stage_vs_euler_stage"] = line["viscous"]["fp64"]["ns_stage_ms"] / ms
         line["march_adjoint"] = march_adjoint_extra(torch, L, s, q, args, stream, E)

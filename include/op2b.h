@@ -104,7 +104,8 @@ typedef struct {
 #define OP2B_PREC_F32 1
 /* FF node and edge data (float-float shadows) and float-float arithmetic:
  * the Green-Gauss loop (FF sums), the second-order flux, the node-limited
- * flux and the viscous flux (FP64 R), the flux adjoint (FP64 results) */
+ * flux and the viscous flux (FP64 R), the flux adjoint and tangent (FP64
+ * results) */
 #define OP2B_PREC_FF 2
 #define OP2B_NUM_PREC 3
 
@@ -319,7 +320,10 @@ int op2b_green_gauss_adjoint(op2b_ctx ctx, const op2b_arg* args,
  *     Rd 0 INC, Rd 1 INC.
  *   order 2 args (13): q 0, q 1, qd 0, qd 1, G 0, G 1, Gd 0, Gd 1 (READ,
  *     G and Gd scaled), n ID READ, nd ID READ, dx ID READ, Rd 0 INC,
- *     Rd 1 INC.  All F64. */
+ *     Rd 1 INC.  All F64; or, for op2b_edge_flux_tangent order 2, the
+ *     eleven READ dats FF (float-float shadows): the linearisation then
+ *     runs in float-float arithmetic and each edge's Fd is converted to
+ *     FP64 before it is added into Rd (F64). */
 int op2b_green_gauss_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                              int32_t flags);
 int op2b_edge_flux_tangent(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,

@@ -1062,18 +1062,20 @@ extern "C" int op2b_edge_flux_tangent(op2b_ctx h, const op2b_arg* a, int32_t nar
   static const Spec s1[8] = {{0, OP2B_READ, 6, 'D'},  {1, OP2B_READ, 6, 'D'},  {0, OP2B_READ, 6, 'D'},
                              {1, OP2B_READ, 6, 'D'},  {-1, OP2B_READ, 3, 'D'}, {-1, OP2B_READ, 3, 'D'},
                              {0, OP2B_INC, 6, 'D'},   {1, OP2B_INC, 6, 'D'}};
-  static const Spec s2[13] = {{0, OP2B_READ, 6, 'D'},   {1, OP2B_READ, 6, 'D'},  {0, OP2B_READ, 6, 'D'},
-                              {1, OP2B_READ, 6, 'D'},   {0, OP2B_READ, 18, 'D'}, {1, OP2B_READ, 18, 'D'},
-                              {0, OP2B_READ, 18, 'D'},  {1, OP2B_READ, 18, 'D'}, {-1, OP2B_READ, 3, 'D'},
-                              {-1, OP2B_READ, 3, 'D'},  {-1, OP2B_READ, 3, 'D'}, {0, OP2B_INC, 6, 'D'},
+  static const Spec s2[13] = {{0, OP2B_READ, 6, 'P'},   {1, OP2B_READ, 6, 'P'},  {0, OP2B_READ, 6, 'P'},
+                              {1, OP2B_READ, 6, 'P'},   {0, OP2B_READ, 18, 'P'}, {1, OP2B_READ, 18, 'P'},
+                              {0, OP2B_READ, 18, 'P'},  {1, OP2B_READ, 18, 'P'}, {-1, OP2B_READ, 3, 'P'},
+                              {-1, OP2B_READ, 3, 'P'},  {-1, OP2B_READ, 3, 'P'}, {0, OP2B_INC, 6, 'D'},
                               {1, OP2B_INC, 6, 'D'}};
   Checked ck;
   int rc = p->order == 1 ? check_args(c, "edge_flux_tangent", a, nargs, s1, 8, &ck)
                          : check_args(c, "edge_flux_tangent", a, nargs, s2, 13, &ck);
   if (rc) return rc;
+  if (ck.prec == OP2B_PREC_F32)
+    return c.fail(OP2B_ETYPE, "edge_flux_tangent: READ dats must be F64 (or FF for order 2)");
   LoopLaunch L;
   L.loop = p->order == 1 ? OP2B_LOOP_FLUX1_TAN : OP2B_LOOP_FLUX2_TAN;
-  L.prec = OP2B_PREC_F64;
+  L.prec = ck.prec;
   L.order = p->order;
   L.map = ck.map;
   L.N = ck.N;

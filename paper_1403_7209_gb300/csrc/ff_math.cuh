@@ -471,4 +471,109 @@ __device__ __forceinline__ void flux2_adj_t(const T* vi, const T* vj, T dx, T dy
   }
 }
 
+// ------------------------------------------- tangent of the second-order flux
+// Forward-mode linearisation in the direction (qd, Gd, nd), dx fixed: the
+// same steps as flux2_tan_f64 (side by side: f(q).n, its tangent, the wave
+// speed and its tangent; the limiter's partial derivatives), written for a
+// scalar type T with operators and instantiated for float-float.
+// Non-smooth points as in the FP64 sweep: d|x|/dx = sign(x) (0 at 0), the
+// max picks L on ties.
+
+template <typename T>
+__device__ __forceinline__ void side_tangent_t(const T* q, const T* qd, T nx, T ny, T nz, T ndx,
+                                               T ndy, T ndz, T rr, T nn, T nnd, T gamma, T gm1,
+                                               T* f, T* fd, T& lam, T& lamd) {
+  const T half = ffk(0.5f);
+  const T mn = fma(q[3], nz, fma(q[2], ny, q[1] * nx));
+  const T mnd = fma(qd[3], nz, fma(qd[2], ny, fma(qd[1], nx,
+                fma(q[3], ndz, fma(q[2], ndy, q[1] * ndx)))));
+  const T un = mn * rr;
+  const T und = fma(-un, qd[0], mnd) * rr;  // (mnd - un rhod) / rho
+  const T mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
+  const T mmd = ffk(2.0f) * fma(q[3], qd[3], fma(q[2], qd[2], q[1] * qd[1]));
+  const T hgm1 = half * gm1;
+  const T p = gm1 * (q[4] - half * mm * rr);
+  // pd = (gamma-1) (Ed - mmd/(2 rho) + mm rhod / (2 rho^2))
+  const T pd = fma(gm1, qd[4], hgm1 * rr * fma(mm * rr, qd[0], -mmd));
+  const T a = sqrt(gamma * p * rr);
+  const T ra = recip(a);
+  // 2 a ad = (gamma pd - a^2 rhod) / rho
+  const T ad = half * ra * rr * fma(-(a * a), qd[0], gamma * pd);
+  lam = fabs(un) + a * nn;
+  lamd = sign_times(un, und) + fma(ad, nn, a * nnd);
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    f[k] = q[k] * un;
+    fd[k] = fma(qd[k], un, q[k] * und);
+  }
+  const T n3[3] = {nx, ny, nz}, nd3[3] = {ndx, ndy, ndz};
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    f[1 + d] = fma(p, n3[d], f[1 + d]);
+    fd[1 + d] = fma(pd, n3[d], fma(p, nd3[d], fd[1 + d]));
+  }
+  f[4] = fma(p, un, f[4]);
+  fd[4] = fma(pd, un, fma(p, und, fd[4]));
+}
+
+template <typename T>
+__device__ __forceinline__ void rusanov_tangent_t(const T* qL, const T* qLd, const T* qR,
+                                                  const T* qRd, T nx, T ny, T nz, T ndx, T ndy,
+                                                  T ndz, T gamma, T gm1, T* Fd) {
+  const T half = ffk(0.5f);
+  const T nn = sqrt(fma(nz, nz, fma(ny, ny, nx * nx)));
+  const T rn = recip(nn);
+  const T nnd = fma(nz, ndz, fma(ny, ndy, nx * ndx)) * rn;
+  T fL[6], fLd[6], fR[6], fRd[6], lL, lLd, lR, lRd;
+  side_tangent_t(qL, qLd, nx, ny, nz, ndx, ndy, ndz, recip(qL[0]), nn, nnd, gamma, gm1, fL, fLd,
+                 lL, lLd);
+  side_tangent_t(qR, qRd, nx, ny, nz, ndx, ndy, ndz, recip(qR[0]), nn, nnd, gamma, gm1, fR, fRd,
+                 lR, lRd);
+  const bool left = lL >= lR;
+  const T hs = half * (left ? lL : lR), hsd = half * (left ? lLd : lRd);
+#pragma unroll
+  for (int k = 0; k < 6; k++)
+    Fd[k] = fma(half, fLd[k] + fRd[k], -fma(hsd, qR[k] - qL[k], hs * (qRd[k] - qLd[k])));
+}
+
+// vi, vj: q (6), qd (6), G (18), Gd (18); Fd: the flux's tangent (6)
+template <typename T>
+__device__ __forceinline__ void flux2_tan_t(const T* vi, const T* vj, T dx, T dy, T dz, T nx,
+                                            T ny, T nz, T ndx, T ndy, T ndz, T gamma, T gm1,
+                                            T eps, T two_eps, T* Fd) {
+  const T half = ffk(0.5f);
+  const T *qi = vi, *qid = vi + 6, *Gi = vi + 12, *Gid = vi + 30;
+  const T *qj = vj, *qjd = vj + 6, *Gj = vj + 12, *Gjd = vj + 30;
+  T qL[6], qR[6], qLd[6], qRd[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    const T b = qj[k] - qi[k];
+    const T bd = qjd[k] - qid[k];
+    const T be = fma(b, b, eps);
+    const T b2e = fma(b, b, two_eps);
+    const T b2 = b + b;
+    const T a[2] = {fma(Gi[3 * k + 2], dz, fma(Gi[3 * k + 1], dy, Gi[3 * k] * dx)),
+                    fma(Gj[3 * k + 2], dz, fma(Gj[3 * k + 1], dy, Gj[3 * k] * dx))};
+    const T ad[2] = {fma(Gid[3 * k + 2], dz, fma(Gid[3 * k + 1], dy, Gid[3 * k] * dx)),
+                     fma(Gjd[3 * k + 2], dz, fma(Gjd[3 * k + 1], dy, Gjd[3 * k] * dx))};
+#pragma unroll
+    for (int sd = 0; sd < 2; sd++) {
+      const T x = a[sd];
+      const T rd = recip(fma(x, x, b2e));
+      const T phi = (x + b) * fma(x, b, eps) * rd;
+      const T pa = fma(x + x, b - phi, be) * rd;
+      const T pb = fma(b2, x - phi, fma(x, x, eps)) * rd;
+      const T phid = fma(pa, ad[sd], pb * bd);
+      if (sd == 0) {
+        qL[k] = fma(half, phi, qi[k]);
+        qLd[k] = fma(half, phid, qid[k]);
+      } else {
+        qR[k] = fma(-half, phi, qj[k]);
+        qRd[k] = fma(-half, phid, qjd[k]);
+      }
+    }
+  }
+  rusanov_tangent_t(qL, qLd, qR, qRd, nx, ny, nz, ndx, ndy, ndz, gamma, gm1, Fd);
+}
+
 }  // namespace op2b

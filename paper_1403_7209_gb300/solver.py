@@ -123,6 +123,9 @@ class EdgeSolver:
             edgd("nbar_acc", 3)  # march adjoint: dJ/dn summed over the stages
             if ff:
                 node("lam_ff", 6, "ff")  # float-float shadow of the adjoint weights
+                node("qd_ff", 6, "ff")   # ... and of the tangent's direction
+                node("Gd_ff", 18, "ff")
+                edgd("nd_ff", 3, "ff")
         self.perm = np.arange(self.N, dtype=np.int64)   # new id of old node
         self.order = np.arange(self.E, dtype=np.int64)  # old edge of new slot
         if renumber == "rcb":
@@ -263,6 +266,11 @@ class EdgeSolver:
             self.a_gga = [ind("Gbar", 0, R), ind("Gbar", 1, R), ind("q", 0, R), ind("q", 1, R),
                           dr("n", R), ind("qbar", 0, I), ind("qbar", 1, I), dr("nbar", RWa)]
             if self.ff:
+                self.a_ft2_ff = [ind("q_ff", 0, R), ind("q_ff", 1, R), ind("qd_ff", 0, R),
+                                 ind("qd_ff", 1, R), ind("G_ff", 0, R), ind("G_ff", 1, R),
+                                 ind("Gd_ff", 0, R), ind("Gd_ff", 1, R), dr("n_ff", R),
+                                 dr("nd_ff", R), dr("dx_ff", R), ind("Rd", 0, I),
+                                 ind("Rd", 1, I)]
                 self.a_fa2_ff = [ind("lam_ff", 0, R), ind("lam_ff", 1, R), ind("q_ff", 0, R),
                                  ind("q_ff", 1, R), ind("G_ff", 0, R), ind("G_ff", 1, R),
                                  dr("n_ff", R), dr("dx_ff", R), ind("qbar", 0, I),
@@ -407,13 +415,26 @@ class EdgeSolver:
         L.op2b_grad_scale_adjoint(c, self.d["Gbar"], self.d["V"])
         L.op2b_green_gauss_adjoint(c, self.a_gga, 0)
 
-    def tangent(self, order=2, recompute_gradient=True):
+    def tangent(self, order=2, recompute_gradient=True, ff=False):
         """Rd = dR/dq . qd + dR/dn . nd (dats qd, nd in, Rd out).
 
         With ``recompute_gradient=False`` the dat G must hold the gradient of
-        the current q and n."""
+        the current q and n (G_ff with ``ff``).  ``ff``: the flux tangent in
+        float-float arithmetic from the float-float shadows (q_ff must match
+        q); the Green-Gauss tangent and its scaling stay FP64."""
         self._inviscid_only("tangent")
         c = self.ctx
+        if ff:
+            if order != 2:
+                raise ValueError("the float-float tangent is the second-order one")
+            if recompute_gradient:
+                self.green_gauss(ff=True)
+            L.op2b_green_gauss_tangent(c, self.a_ggt, L.ZERO_INC)
+            L.op2b_grad_scale(c, self.d["Gd"], self.d["V"])
+            for nm in ("qd", "Gd", "nd"):
+                L.op2b_dat_copy(c, self.d[nm + "_ff"], self.d[nm])
+            L.op2b_edge_flux_tangent(c, self.a_ft2_ff, 2, self.gamma, self.eps_lim, L.ZERO_INC)
+            return
         if order == 1:
             L.op2b_edge_flux_tangent(c, self.a_ft1, 1, self.gamma, self.eps_lim, L.ZERO_INC)
             return

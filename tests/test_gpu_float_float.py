@@ -284,3 +284,27 @@ def test_float_float_limited_residual_matches_oracle(gpu_lib, mesh16, name, kind
     o = oracle.residual_limited(kind, m.edge, q, m.normal, m.dx, m.volume, eps2, with_abs=True)
     assert rel_err(s.fetch_nodes("R"), o["R"], o["Rabs"]) <= TOL
     s.close()
+
+
+# ------------------------------------------------------------ tangent
+@pytest.mark.parametrize("strat", [1, 3, 6, 7])
+def test_float_float_tangent_matches_oracle(gpu_lib, mesh16, strat):
+    m, q, ref = mesh16
+    qd = meshgen.adjoint_seed(m.num_nodes, stream=meshgen.STREAM_V)
+    nd = meshgen.normal(0, meshgen.STREAM_V, np.arange(3 * m.num_edges, dtype=np.uint64)).reshape(-1, 3)
+    s = make_solver(m, q, renumber="rcm", adjoint=True)
+    s.set_strategy(gpu_lib.LOOP_FLUX2_TAN, gpu_lib.PREC_FF, strat, 128)
+    s.load_nodes("qd", qd)
+    s.load_edges("nd", nd)
+    s.tangent(2, ff=True)
+    ref_t = oracle.residual_tangent(2, m.edge, q, m.normal, m.dx, m.volume, qd, nd)
+    assert _adj_ok(s.fetch_nodes("Rd"), ref_t)
+    # dot-product test against the float-float adjoint: <lam, J v> = <J^T lam, v>
+    lam = meshgen.adjoint_seed(m.num_nodes)
+    s.load_nodes("lam", lam)
+    s.adjoint(2, ff=True)
+    Rd = s.fetch_nodes("Rd")
+    lhs = np.sum(lam * Rd)
+    rhs = np.sum(s.fetch_nodes("qbar") * qd) + np.sum(s.fetch_edges("nbar") * nd)
+    assert abs(lhs - rhs) <= 1e-11 * np.sum(np.abs(lam * Rd))
+    s.close()

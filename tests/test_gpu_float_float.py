@@ -308,3 +308,40 @@ def test_float_float_tangent_matches_oracle(gpu_lib, mesh16, strat):
     rhs = np.sum(s.fetch_nodes("qbar") * qd) + np.sum(s.fetch_edges("nbar") * nd)
     assert abs(lhs - rhs) <= 1e-11 * np.sum(np.abs(lam * Rd))
     s.close()
+
+
+# ------------------------------------------------ irregular and ragged meshes
+@pytest.mark.parametrize("limiter", ["van_albada", "barth_jespersen"])
+def test_float_float_irregular_and_ragged(gpu_lib, limiter):
+    # a random graph (ragged degrees, unsorted ends) and two small lattices
+    # (3^3: every node touches itself through the periodic wrap's
+    # neighbours twice) under every strategy of the float-float flux
+    kind = {"van_albada": None, "barth_jespersen": oracle.LIM_BJ}[limiter]
+    for m in (meshgen.random_graph_mesh(3000, seed=8), meshgen.lattice(3, seed=1),
+              meshgen.lattice(5, seed=2)):
+        q = meshgen.flow_state(m, seed=3)
+        if kind is None:
+            R, _, Ra = oracle.residual(2, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
+        else:
+            o = oracle.residual_limited(kind, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
+            R, Ra = o["R"], o["Rabs"]
+        s = make_solver(m, q, renumber="rcm", limiter=limiter)
+        loop = gpu_lib.LOOP_FLUX2 if kind is None else gpu_lib.LOOP_FLUX2_PHI
+        for strat, block, part, staged in ((1, 64, 0, 0), (2, 64, 64, 1), (3, 64, 0, 0),
+                                           (5, 64, 256, 0), (6, 64, 0, 0), (7, 64, 0, 0)):
+            s.set_strategy(loop, gpu_lib.PREC_FF, strat, block, part, staged)
+            s.residual(2, ff=True)
+            assert rel_err(s.fetch_nodes("R"), R, Ra) <= TOL, (m.num_edges, strat)
+        s.close()
+
+
+def test_float_float_empty_edge_set(gpu_lib):
+    # nodes without edges: every float-float loop runs and leaves R zero
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    q = np.tile([1.0, 0.5, 0.0, 0.0, 2.5, 0.1], (5, 1))
+    s = EdgeSolver(np.zeros((0, 2), np.int32), np.zeros((0, 3)), np.zeros((0, 3)), np.ones(5), q,
+                   ff=True)
+    s.load_nodes("R", np.ones((5, 6)))
+    s.residual(2, ff=True)
+    assert np.all(s.fetch_nodes("R") == 0.0) and np.all(s.fetch_nodes("G_ff") == 0.0)
+    s.close()

@@ -674,27 +674,28 @@ def numbering_extra(torch, L, m, q, args, stream, ms_rcm, device):
 def partition_extra(torch, L, m, q, args, stream, ms_whole, device, strat):
     """Owner-compute execution on one GPU: the FP64 stage over P parts (RCB,
     each part RCM-numbered, halo of q and G refreshed by the exchange
-    kernel) against the whole mesh, with the halo statistics of the paper's
-    table of halo sizes for the same partitions."""
+    kernel; the parts one after another, or on concurrent streams) against
+    the whole mesh, with the halo statistics of the paper's table of halo
+    sizes for the same partitions."""
     from paper_1403_7209_gb300.partition import PartitionedSolver, halo_stats
     out = {"whole_mesh_ms": ms_whole}
-    for P in (8, 64):
+    for P, conc in ((8, False), (64, False), (64, True)):
         ps = PartitionedSolver(m.edge, m.normal, m.dx, m.volume, q, coords=m.coords, nparts=P,
-                               device=device, renumber="rcm", stream=stream)
+                               device=device, renumber="rcm", stream=stream, concurrent=conc)
         for loop, nm in ((L.LOOP_GREEN_GAUSS, "gg"), (L.LOOP_FLUX2, "flux2")):
             z = strat[nm]
             ps.set_strategy(loop, 0, z["strategy"], z["block"], z["part"], z["staged"])
         ps.set_strategy(L.LOOP_SPECTRAL, 0, L.STRAT_ATOMIC, 256)
         ps.time_step(0.5)
-        for sv in ps.solvers:
-            L.op2b_dat_copy(sv.ctx, sv.d["q0"], sv.d["q"])
+        ps._each(lambda sv: L.op2b_dat_copy(sv.ctx, sv.d["q0"], sv.d["q"]))
         for _ in range(args.warmup):
             ps.stage(0.25)
         ms = timed(torch, lambda: ps.stage(0.25), args.steps, stream)
         ex = timed(torch, lambda: (ps.exchange("q"), ps.exchange("G")), args.steps, stream)
         st = halo_stats(ps.parts)
         executed = sum(P_["sizes"]["edges"] for P_ in ps.parts)
-        out["parts_%d" % P] = {"ms": ms, "edges_per_s": m.num_edges / (ms * 1e-3),
+        out["parts_%d%s" % (P, "_concurrent" if conc else "")] = {
+                               "ms": ms, "edges_per_s": m.num_edges / (ms * 1e-3),
                                "vs_whole_mesh": ms / ms_whole,
                                "exchange_q_and_G_ms": ex,
                                "executed_edges_over_mesh_edges": executed / m.num_edges,

@@ -66,13 +66,19 @@ class PartitionedSolver:
     overrides the RCB partition.  Each part is renumbered internally with
     ``renumber`` (as :class:`EdgeSolver`).  :meth:`fetch_nodes` assembles
     the owned rows of every part in the caller's numbering.
+
+    With ``concurrent`` the parts' loops run on a pool of up to 16 CUDA
+    streams (part p on stream p mod 16), forked from and joined back to
+    ``stream`` with events around every halo exchange, which runs on
+    ``stream``; small parts then fill the GPU together instead of one
+    after another.  Without it every part runs on ``stream`` in turn.
     """
 
     EXCHANGED = {"q": (6, L.F64), "G": (18, L.F64), "q32": (6, L.F32), "G32": (18, L.F32)}
 
     def __init__(self, edge, normal, dx, volume, q, coords=None, nparts=2, part=None,
                  device: int = 0, renumber: str = "rcm", mixed: bool = False, stream=None,
-                 gamma: float = 1.4, eps_lim: float = 1e-12):
+                 gamma: float = 1.4, eps_lim: float = 1e-12, concurrent: bool = False):
         import torch
         edge = np.ascontiguousarray(edge, dtype=np.int32)
         normal = np.asarray(normal, dtype=np.float64).reshape(-1, 3)
@@ -88,15 +94,22 @@ class PartitionedSolver:
         self.nparts = int(nparts)
         self.mixed = mixed
         self.parts = halo_plan(self.N, edge, self.part, self.nparts)
+        self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.streams = ([torch.cuda.Stream(device=device) for _ in range(min(self.nparts, 16))]
+                        if concurrent else [])
+        self._fork_ev = torch.cuda.Event()
+        self._join_ev = [torch.cuda.Event() for _ in self.streams]
         self.solvers = []
-        for P in self.parts:
+        for p, P in enumerate(self.parts):
             nodes, edges = P["nodes"], P["edges"]
+            st = self.streams[p % len(self.streams)] if concurrent else self.stream
             self.solvers.append(EdgeSolver(P["local_map"], normal[edges], dx[edges],
                                            volume[nodes], q[nodes], device=device,
-                                           renumber=renumber, mixed=mixed, stream=self.stream,
+                                           renumber=renumber, mixed=mixed, stream=st,
                                            gamma=gamma, eps_lim=eps_lim))
-        self.ctx = self.solvers[0].ctx  # launches the exchanges
+        # the exchanges launch on `stream` from a context of their own
+        self.ctx = L.op2b_init(device, self.stream.cuda_stream)
         self.x = {}
         for name in ("q", "G") + (("q32", "G32") if mixed else ()):
             self.x[name] = self._exchange(name)
@@ -129,45 +142,65 @@ class PartitionedSolver:
     def exchange(self, name):
         L.op2b_exchange_run(self.ctx, self.x[name])
 
+    def _fork(self):
+        """Part streams wait for the work already queued on `stream`."""
+        if self.streams:
+            self._fork_ev.record(self.stream)
+            for st in self.streams:
+                st.wait_event(self._fork_ev)
+
+    def _join(self):
+        """`stream` waits for the work queued on the part streams."""
+        for st, ev in zip(self.streams, self._join_ev):
+            ev.record(st)
+            self.stream.wait_event(ev)
+
     # ------------------------------------------------------------ loops
     def set_strategy(self, loop, prec, strategy, block=0, part=0, staged=0):
         for s in self.solvers:
             s.set_strategy(loop, prec, strategy, block, part, staged)
 
-    def residual(self, order=2, mixed=False):
-        """R of the current state on every part's owned nodes."""
+    def _each(self, fn):
+        """fn(solver) for every part, between a fork and a join."""
+        self._fork()
+        for s in self.solvers:
+            fn(s)
+        self._join()
+
+    def residual(self, order=2, mixed=False, update_alpha=None):
+        """R of the current state on every part's owned nodes (then the
+        stage update with `update_alpha`, in the same fork)."""
         sfx = "32" if mixed else ""
         self.exchange("q" + sfx)
         if order == 2:
-            for s in self.solvers:
-                s.green_gauss(mixed)
+            self._each(lambda s: s.green_gauss(mixed))
             self.exchange("G" + sfx)
-        for s in self.solvers:
+
+        def flux(s):
             s.flux(order, mixed)
+            if update_alpha is not None:
+                s.update(update_alpha, mixed)
+        self._each(flux)
 
     def time_step(self, cfl=0.5):
         self.exchange("q")
-        for s in self.solvers:
-            s.time_step(cfl)
+        self._each(lambda s: s.time_step(cfl))
 
     def stage(self, alpha, order=2, mixed=False):
-        self.residual(order, mixed)
-        for s in self.solvers:
-            s.update(alpha, mixed)
+        self.residual(order, mixed, update_alpha=alpha)
 
     def step(self, order=2, mixed=False, stages=5):
-        for s in self.solvers:
-            L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
+        self._each(lambda s: L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"]))
         for a in RK5_ALPHA[5 - stages:]:
             self.stage(a, order, mixed)
 
     def sync_shadow(self):
-        for s in self.solvers:
-            s.sync_shadow()
+        self._each(lambda s: s.sync_shadow())
 
     # ------------------------------------------------------------- data
     def fetch_nodes(self, name) -> np.ndarray:
         """(N, dim) float64: every node's row from its owner."""
+        self.torch.cuda.synchronize()  # the parts may run on streams of their own
         out = None
         for P, s in zip(self.parts, self.solvers):
             n_own = P["sizes"]["owned"]
@@ -178,13 +211,15 @@ class PartitionedSolver:
         return out
 
     def launch_count(self):
-        return sum(s.launch_count() for s in self.solvers)
+        return sum(s.launch_count() for s in self.solvers) + L.op2b_launch_count(self.ctx)
 
     def close(self):
         if self.solvers:
+            self.torch.cuda.synchronize()
             for x in self.x.values():
                 L.op2b_exchange_destroy(self.ctx, x)
             self.x = {}
+            L.op2b_finalize(self.ctx)
             for s in self.solvers:
                 s.close()
             self.solvers = []

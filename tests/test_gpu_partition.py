@@ -36,11 +36,12 @@ def mesh12():
     return m, q, dict(R1=R1, R1a=R1a, R2=R2, R2a=R2a, G=G)
 
 
+@pytest.mark.parametrize("concurrent", [False, True])
 @pytest.mark.parametrize("nparts", [1, 2, 3, 8, 27])
 @pytest.mark.parametrize("strat", [1, 3, 6])
-def test_partitioned_residual_matches_oracle(gpu_lib, mesh12, nparts, strat):
+def test_partitioned_residual_matches_oracle(gpu_lib, mesh12, nparts, strat, concurrent):
     m, q, ref = mesh12
-    s = make(m, q, nparts)
+    s = make(m, q, nparts, concurrent=concurrent)
     for loop in (gpu_lib.LOOP_GREEN_GAUSS, gpu_lib.LOOP_FLUX1, gpu_lib.LOOP_FLUX2):
         s.set_strategy(loop, 0, strat, 128)
     s.residual(1)
@@ -67,10 +68,11 @@ def test_halo_rows_come_from_the_exchange(gpu_lib, mesh12):
     s.close()
 
 
-def test_partitioned_march_matches_oracle(gpu_lib):
+@pytest.mark.parametrize("concurrent", [False, True])
+def test_partitioned_march_matches_oracle(gpu_lib, concurrent):
     m = meshgen.lattice(8)
     q = meshgen.flow_state(m)
-    s = make(m, q, 5)
+    s = make(m, q, 5, concurrent=concurrent)
     s.time_step(0.5)
     for _ in range(10):
         s.step(order=2)

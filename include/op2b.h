@@ -461,9 +461,9 @@ int op2b_dat_copy(op2b_ctx ctx, op2b_dat dst, op2b_dat src);
 /* Fix the strategy of (loop, prec) (OP2B_STRAT_*).  block: threads per CTA (32..1024,
  * 0 = default); part: edges per block for OP2B_STRAT_COLOUR (64..8192,
  * 0 = default); staged: stage each block's node data in shared memory
- * (COLOUR only).  OP2B_STRAT_AUTO makes the next call of the loop time the
- * candidates (writing into scratch copies of its INC dats) and keep the
- * fastest. */
+ * (COLOUR and BLOCK_ATOMIC; ignored elsewhere).  OP2B_STRAT_AUTO makes the
+ * next call of the loop time the candidates (writing into scratch copies of
+ * its INC dats) and keep the fastest. */
 int op2b_set_strategy(op2b_ctx ctx, int32_t loop, int32_t prec,
                       int32_t strategy, int32_t block, int32_t part,
                       int32_t staged);

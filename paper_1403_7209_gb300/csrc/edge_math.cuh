@@ -54,11 +54,45 @@ __device__ __forceinline__ double f64_exact(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// value of a per-edge result in the accumulation type of its target
+// Exact float -> double for zero and normal floats only (integer
+// re-biasing, no special cases).
+__device__ __forceinline__ double f64_of_normal(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu;
+  const unsigned hi = mag ? (sign | ((mag >> 3) + 0x38000000u)) : sign;
+  return __hiloint2double((int)hi, (int)(mag << 29));
+}
+__device__ __forceinline__ bool normal_or_zero(float f) {
+  const unsigned mag = __float_as_uint(f) & 0x7fffffffu;
+  return mag - 0x00800000u < 0x7f000000u || mag == 0u;
+}
+
+// value of a per-edge result in the accumulation type of its target; a
+// float goes the short integer route unless it is subnormal, infinite or NaN
 template <typename TA, typename TE>
 __device__ __forceinline__ TA to_acc(TE x) {
-  if constexpr (sizeof(TA) == 8 && sizeof(TE) == 4) return f64_exact(x);
-  else return (TA)x;
+  if constexpr (sizeof(TA) == 8 && sizeof(TE) == 4) {
+    if (__builtin_expect(normal_or_zero(x), 1)) return f64_of_normal(x);
+    return f64_exact(x);
+  } else {
+    return (TA)x;
+  }
+}
+
+// Quotient of the flux arithmetic: the IEEE division for double (and the
+// float-float division for float-float); for float the reciprocal-based
+// quotient __fdividef (within 2 ulp for divisors of magnitude below 2^126:
+// the limiter denominators are at least 2 eps and the densities of order
+// one), a fraction of the instructions of the IEEE float division.  The
+// FP32 path's error budget (1e-5 of the residual) is set by its 24-bit
+// arithmetic, not by these last-bit differences.
+template <typename T>
+__device__ __forceinline__ T quot(T a, T b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float quot<float>(float a, float b) {
+  return __fdividef(a, b);
 }
 
 // Euler flux through the face of normal n, and the state's largest wave
@@ -67,7 +101,7 @@ template <typename T>
 __device__ __forceinline__ void euler_side(const T* q, T nx, T ny, T nz,
                                            T nn2, const Gas<T>& g, T* f,
                                            T& lam) {
-  T rr = T(1) / q[0];
+  T rr = quot(T(1), q[0]);
   T un = (q[1] * nx + q[2] * ny + q[3] * nz) * rr;
   T mm = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
   T p = g.gm1 * (q[4] - T(0.5) * mm * rr);
@@ -100,7 +134,7 @@ __device__ __forceinline__ void rusanov(const T* qL, const T* qR, T nx, T ny,
 // function, with the b-only part b2e = b^2 + 2 eps shared by both ends.
 template <typename T>
 __device__ __forceinline__ T van_albada(T a, T b, T eps, T b2e) {
-  return (a + b) * fma(a, b, eps) / fma(a, a, b2e);
+  return quot((a + b) * fma(a, b, eps), fma(a, a, b2e));
 }
 
 // Limited linear reconstruction of the two face states.  vi, vj: q (6)

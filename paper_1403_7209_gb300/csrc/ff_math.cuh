@@ -58,19 +58,6 @@ __device__ __forceinline__ float2 ff_of_f64(double x) {
   return make_float2(__uint_as_float(hb), lo);
 }
 
-// Exact float -> double for zero and normal floats only (integer
-// re-biasing, no special cases).
-__device__ __forceinline__ double f64_of_normal(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned sign = b & 0x80000000u, mag = b & 0x7fffffffu;
-  const unsigned hi = mag ? (sign | ((mag >> 3) + 0x38000000u)) : sign;
-  return __hiloint2double((int)hi, (int)(mag << 29));
-}
-__device__ __forceinline__ bool normal_or_zero(float f) {
-  const unsigned mag = __float_as_uint(f) & 0x7fffffffu;
-  return mag - 0x00800000u < 0x7f000000u || mag == 0u;
-}
-
 // float-float -> double: both limbs exactly (integer re-biasing), one FP64
 // addition.  The general conversion (subnormal, infinite and NaN limbs) is
 // branched to only for the lanes that need it.

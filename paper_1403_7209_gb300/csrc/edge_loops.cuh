@@ -413,9 +413,13 @@ __global__ void k_owner(P ph, const int32_t* __restrict__ m0,
     TA acc[P::OUT];
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) acc[c] = TA(0);
+    // the next owned edge's id and ends are fetched one iteration ahead, so
+    // only the other end's data load is left on each iteration's path
+    int64_t e = own_idx[t0];
+    int64_t i = m0[e], j = m1[e];
     for (int64_t t = t0; t < t1; t++) {
-      const int64_t e = own_idx[t];
-      const int64_t i = m0[e], j = m1[e];
+      const int64_t en = t + 1 < t1 ? (int64_t)own_idx[t + 1] : e;
+      const int64_t in = m0[en], jn = m1[en];
       const bool first = (i == v);
       const int64_t w = first ? j : i;
       TN vw[P::NIN];
@@ -433,6 +437,9 @@ __global__ void k_owner(P ph, const int32_t* __restrict__ m0,
         acc[c] += first ? a : b;
         atomicAdd(tg.at(c, w), first ? b : a);
       }
+      e = en;
+      i = in;
+      j = jn;
     }
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) atomicAdd(tg.at(c, v), acc[c]);
@@ -471,13 +478,17 @@ __global__ void k_gather_nodes(P ph, const int64_t* __restrict__ rowptr,
     TA acc[P::OUT];
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) acc[c] = TA(0);
-    const int64_t t1 = rowptr[i + 1];
-    for (int64_t t = rowptr[i]; t < t1; t++) {
-      const int32_t end = ends[t];
+    const int64_t t0 = rowptr[i], t1 = rowptr[i + 1];
+    // the next end's edge and other node are fetched one iteration ahead
+    int32_t end = t0 < t1 ? ends[t0] : 0;
+    int64_t o = t0 < t1 ? (end & 1 ? m0[end >> 1] : m1[end >> 1]) : 0;
+    for (int64_t t = t0; t < t1; t++) {
       const int64_t e = end >> 1;
       const bool second = end & 1;
+      const int32_t endn = t + 1 < t1 ? ends[t + 1] : end;
+      const int64_t on = endn & 1 ? m0[endn >> 1] : m1[endn >> 1];
       TN vo[P::NIN];
-      ph.load(second ? m0[e] : m1[e], vo);
+      ph.load(o, vo);
       // the edge's own orientation whichever end this is (no divergence:
       // the operands are selected, the body runs once)
       TN va[P::NIN], vb[P::NIN];
@@ -495,6 +506,8 @@ __global__ void k_gather_nodes(P ph, const int64_t* __restrict__ rowptr,
         else if constexpr (P::MODE == MODE_SYM) acc[c] += a;
         else acc[c] += second ? to_acc<TA>(oj[c]) : a;
       }
+      end = endn;
+      o = on;
     }
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) {

@@ -54,8 +54,7 @@ struct BodyGG {
   }
   __device__ __forceinline__ void edge(int64_t e, const T* vi, const T* vj,
                                        TE* oi, TE*) const {
-    T hx = T(0.5) * ldro(n + e), hy = T(0.5) * ldro(n + ldn + e),
-      hz = T(0.5) * ldro(n + 2 * ldn + e);
+    T hx = halve(ldro(n + e)), hy = halve(ldro(n + ldn + e)), hz = halve(ldro(n + 2 * ldn + e));
 #pragma unroll
     for (int k = 0; k < 6; k++) {
       T s = vi[k] + vj[k];
@@ -72,9 +71,9 @@ struct BodyGG {
                                        TE* st) const {
 #pragma unroll
     for (int k = 0; k < 6; k++) st[k] = vi[k] + vj[k];
-    st[6] = T(0.5) * ldro(n + e);
-    st[7] = T(0.5) * ldro(n + ldn + e);
-    st[8] = T(0.5) * ldro(n + 2 * ldn + e);
+    st[6] = halve(ldro(n + e));
+    st[7] = halve(ldro(n + ldn + e));
+    st[8] = halve(ldro(n + 2 * ldn + e));
   }
   template <class Get>
   __device__ __forceinline__ static void unpack_add(Get get, bool second,
@@ -258,8 +257,8 @@ struct BodyGGAdj {
   __device__ __forceinline__ void edge(int64_t e, const double* vi,
                                        const double* vj, double* oi,
                                        double*) const {
-    double hx = 0.5 * ldro(n + e), hy = 0.5 * ldro(n + ldn + e),
-           hz = 0.5 * ldro(n + 2 * ldn + e);
+    double hx = half_exact(ldro(n + e)), hy = half_exact(ldro(n + ldn + e)),
+           hz = half_exact(ldro(n + 2 * ldn + e));
     double nbx = 0.0, nby = 0.0, nbz = 0.0;
 #pragma unroll
     for (int k = 0; k < 6; k++) {
@@ -267,7 +266,7 @@ struct BodyGGAdj {
       double dyk = vi[3 * k + 1] - vj[3 * k + 1];
       double dzk = vi[3 * k + 2] - vj[3 * k + 2];
       oi[k] = dxk * hx + dyk * hy + dzk * hz;
-      double hq = 0.5 * (vi[18 + k] + vj[18 + k]);
+      double hq = half_exact(vi[18 + k] + vj[18 + k]);
       nbx += hq * dxk;
       nby += hq * dyk;
       nbz += hq * dzk;
@@ -301,9 +300,10 @@ struct BodyGGTan {
   }
   __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
                                        double* oi, double*) const {
-    const double h[3] = {0.5 * ldro(n + e), 0.5 * ldro(n + ldn + e), 0.5 * ldro(n + 2 * ldn + e)};
-    const double hd[3] = {0.5 * ldro(nd + e), 0.5 * ldro(nd + ldnd + e),
-                          0.5 * ldro(nd + 2 * ldnd + e)};
+    const double h[3] = {half_exact(ldro(n + e)), half_exact(ldro(n + ldn + e)),
+                         half_exact(ldro(n + 2 * ldn + e))};
+    const double hd[3] = {half_exact(ldro(nd + e)), half_exact(ldro(nd + ldnd + e)),
+                          half_exact(ldro(nd + 2 * ldnd + e))};
 #pragma unroll
     for (int k = 0; k < 6; k++) {
       const double sv = vi[k] + vj[k], sd = vi[6 + k] + vj[6 + k];

@@ -28,6 +28,29 @@ __device__ __forceinline__ float neg(float x) {
   return __int_as_float(__float_as_int(x) ^ (int)0x80000000);
 }
 
+// x / 2 exactly, on the integer pipe for zero and for normal x whose half is
+// normal (exponent field 2..2046: decrement it); the rest (subnormal, the
+// smallest normals, infinity, NaN) takes the FP64 multiply.
+__device__ __forceinline__ double half_exact(double x) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const unsigned ex = ((unsigned)hi >> 20) & 0x7ffu;
+  const bool norm = ex - 2u < 2045u;
+  const bool zero = ((hi & 0x7fffffff) | lo) == 0;
+  if (__builtin_expect(norm || zero, 1))
+    return norm ? __hiloint2double(hi - 0x00100000, lo) : x;
+  return x * 0.5;
+}
+
+// x / 2 in the loop's arithmetic type (exact; integer route for double)
+template <typename T>
+__device__ __forceinline__ T halve(T x) {
+  return T(0.5) * x;
+}
+template <>
+__device__ __forceinline__ double halve<double>(double x) {
+  return half_exact(x);
+}
+
 // Exact float -> double on the integer pipe (the conversion instruction runs
 // at the FP64 rate): re-bias the exponent and move the mantissa.  Zero,
 // subnormal, infinite and NaN inputs are handled with integer selects too,

@@ -18,8 +18,11 @@
 
 namespace op2b {
 
-// x * h for h = +-1/2 (exact)
-__device__ __forceinline__ double gg_scale(double x, float h) { return x * (double)h; }
+// x * h for h = +-1/2 (exact; for double the sign flip and the halving are
+// integer operations, so the FP64 pipe is left to the sums)
+__device__ __forceinline__ double gg_scale(double x, float h) {
+  return half_exact(h < 0.0f ? neg(x) : x);
+}
 __device__ __forceinline__ float gg_scale(float x, float h) { return x * h; }
 __device__ __forceinline__ ffv gg_scale(ffv x, float h) { return ffv(ff_scale(x.v, h)); }
 
@@ -121,10 +124,7 @@ static __global__ void k_gg_hybrid(const int64_t* __restrict__ rowptr, const int
         const int64_t j = second ? m0[e] : m1[e];
         double nh[3];
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-          const double v = 0.5 * ldro(n + d * ldn + e);
-          nh[d] = second ? neg(v) : v;
-        }
+        for (int d = 0; d < 3; d++) nh[d] = gg_scale(ldro(n + d * ldn + e), second ? -0.5f : 0.5f);
 #pragma unroll
         for (int k = 0; k < 3; k++) {
           const double sk = qi[k] + ldro(q + k * ldq + j);
@@ -140,8 +140,8 @@ static __global__ void k_gg_hybrid(const int64_t* __restrict__ rowptr, const int
     for (int64_t e = (blockIdx.x - gblocks) * (int64_t)blockDim.x + threadIdx.x; e < E;
          e += stride) {
       const int64_t i = m0[e], j = m1[e];
-      const double h[3] = {0.5 * ldro(n + e), 0.5 * ldro(n + ldn + e),
-                           0.5 * ldro(n + 2 * ldn + e)};
+      const double h[3] = {half_exact(ldro(n + e)), half_exact(ldro(n + ldn + e)),
+                           half_exact(ldro(n + 2 * ldn + e))};
 #pragma unroll
       for (int k = 3; k < 6; k++) {
         const double sk = ldro(q + k * ldq + i) + ldro(q + k * ldq + j);

@@ -34,6 +34,31 @@ __device__ __forceinline__ double unkey(long long k) {
   return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
 }
 
+// Sign tests and the comparison of two non-negative values: on the bit
+// patterns for double (an FP64 comparison issues on the FP64 pipe, which
+// GB300 runs at 1/64 of the FP32 rate), plain comparisons otherwise.
+__device__ __forceinline__ bool is_zero(double x) {
+  return ((__double2hiint(x) & 0x7fffffff) | __double2loint(x)) == 0;
+}
+__device__ __forceinline__ bool is_pos(double x) {
+  return __double2hiint(x) >= 0 && !is_zero(x);
+}
+__device__ __forceinline__ bool less_nonneg(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+template <typename T>
+__device__ __forceinline__ bool is_zero(T x) {
+  return x == T(0);
+}
+template <typename T>
+__device__ __forceinline__ bool is_pos(T x) {
+  return x > T(0);
+}
+template <typename T>
+__device__ __forceinline__ bool less_nonneg(T a, T b) {
+  return a < b;
+}
+
 template <typename T>
 struct MinMaxAcc;
 template <>
@@ -121,21 +146,27 @@ __global__ void k_limiter(const int64_t* __restrict__ rowptr, const int32_t* __r
       d1p[k] = qmax[k * ldmax + i] - qi;
       d1m[k] = qmin[k * ldmin + i] - qi;
     }
-    // Barth-Jespersen: running max / min of D2; Venkatakrishnan: best pair
+    // Barth-Jespersen: running max / min of D2; Venkatakrishnan: best pair,
+    // with the per-node parts D1^2 + eps2 and 2 D1 of both signs formed once
     MinMaxAcc<T> ext[6];
-    T bn[6], bd[6];
+    T bn[6], bd[6], ap[6], am[6], tp[6], tm[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) {
       ext[k].init(T(0));
       bn[k] = T(1);
       bd[k] = T(0);  // ratio +inf: the first end always replaces it
+      if constexpr (KIND != OP2B_LIM_BARTH_JESPERSEN) {
+        ap[k] = fma(d1p[k], d1p[k], eps2);
+        am[k] = fma(d1m[k], d1m[k], eps2);
+        tp[k] = d1p[k] + d1p[k];
+        tm[k] = d1m[k] + d1m[k];
+      }
     }
     const int64_t t1 = rowptr[i + 1];
     for (int64_t t = rowptr[i]; t < t1; t++) {
       const int32_t end = ends[t];
       const int64_t e = end >> 1;
-      T h[3] = {T(0.5) * ldro(dx + e), T(0.5) * ldro(dx + lddx + e),
-                T(0.5) * ldro(dx + 2 * lddx + e)};
+      T h[3] = {halve(ldro(dx + e)), halve(ldro(dx + lddx + e)), halve(ldro(dx + 2 * lddx + e))};
       if (end & 1) {
         h[0] = neg(h[0]);
         h[1] = neg(h[1]);
@@ -147,14 +178,16 @@ __global__ void k_limiter(const int64_t* __restrict__ rowptr, const int32_t* __r
         if constexpr (KIND == OP2B_LIM_BARTH_JESPERSEN) {
           ext[k].take(d2);
         } else {
-          T num = T(1), den = T(1);  // D2 = 0: phi_e = 1
-          if (d2 != T(0)) {
-            const T d1 = d2 > T(0) ? d1p[k] : d1m[k];
-            const T a = fma(d1, d1, eps2);
-            num = fma(T(2) * d1, d2, a);
-            den = fma(d2, fma(T(2), d2, d1), a);
-          }
-          if (num * bd[k] < bn[k] * den) {
+          // D1 takes the sign of D2, so every term below is >= 0; D2 = 0
+          // gives phi_e = 1 (selected, not branched)
+          const bool pos = is_pos(d2);
+          const T d1 = pos ? d1p[k] : d1m[k];
+          const T a = pos ? ap[k] : am[k];
+          const T num0 = fma(pos ? tp[k] : tm[k], d2, a);
+          const T den0 = fma(d2, fma(T(2), d2, d1), a);
+          const bool zero = is_zero(d2);
+          const T num = zero ? T(1) : num0, den = zero ? T(1) : den0;
+          if (less_nonneg(num * bd[k], bn[k] * den)) {
             bn[k] = num;
             bd[k] = den;
           }

@@ -9,7 +9,8 @@ events).  Loops: gg, flux2, gg32, flux2_32, adjoint (flux adjoint +
 scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage), visc and
 visc32 (viscous node pass + edge loop, FP64 / FP32; not with adjoint),
 gg_ff, flux2_ff and ffstage (the float-float Green-Gauss + scaling, flux,
-and RK stage).
+and RK stage), adjoint_ff (the float-float flux adjoint with the FP64
+scaling and Green-Gauss adjoints).
 """
 from __future__ import annotations
 
@@ -59,6 +60,7 @@ def main():
         "gg32": lambda: s.green_gauss(mixed=True),
         "flux2_32": lambda: s.flux(2, mixed=True),
         "adjoint": lambda: s.adjoint(2, recompute_gradient=False),
+        "adjoint_ff": lambda: s.adjoint(2, recompute_gradient=False, ff=True),
         "stage": lambda: s.stage(0.25),
         "visc": lambda: s.viscous_flux(zero=True),
         "visc32": lambda: s.viscous_flux(mixed=True, zero=True),

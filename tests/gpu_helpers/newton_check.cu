@@ -35,3 +35,22 @@ extern "C" int f64_exact_check(const unsigned* bits, double* out, int64_t n) {
   k_f64_exact<<<(unsigned)((n + 255) / 256), 256>>>(bits, out, n);
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
 }
+
+// which = 0: the increments' float -> double conversion (to_acc, with its
+// normal-number fast path); which = 1: x / 2 on the integer pipe
+// (half_exact), on the bit patterns given (as 64-bit words).
+__global__ void k_int_paths(const unsigned long long* bits, double* out, int64_t n, int which) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (which == 0)
+    out[i] = op2b::to_acc<double>(__int_as_float((int)(unsigned)bits[i]));
+  else
+    out[i] = op2b::half_exact(__longlong_as_double((long long)bits[i]));
+}
+
+extern "C" int int_paths_check(const unsigned long long* bits, double* out, int64_t n,
+                               int which) {
+  if (n <= 0) return 0;
+  k_int_paths<<<(unsigned)((n + 255) / 256), 256>>>(bits, out, n, which);
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}

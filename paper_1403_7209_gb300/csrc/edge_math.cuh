@@ -548,7 +548,8 @@ __device__ __forceinline__ void side_reverse_f64(
   }
   qb[4] += gpb;
   // rho enters through 1/rho in u.n, p and a
-  const double rhob = fma(0.5 * gpr, s.mm * s.rr, fma(-0.5 * ab, s.a * s.rr, -ur * s.un));
+  const double rhob =
+      fma(0.5 * gpr, s.mm * s.rr, fma(-0.5 * ab, s.a * s.rr, -ur * s.un));
   qb[0] += rhob;
 }
 
@@ -609,21 +610,22 @@ __device__ __forceinline__ void flux2_adj_f64(const double* vi,
     }
   }
   batch_reciprocal<12>(den, 1.0, rd);
-  double qL[6], qR[6], pa[12], pb[12];
+  // d phi / da = 2 P / D with P = a(b - phi) + (b^2 + eps)/2,
+  // d phi / db = 2 Q / D with Q = b(a - phi) + (a^2 + eps)/2;
+  // the factor 2 cancels the 1/2 of the face states; P and Q are kept
+  // divided by D
+  double qL[6], qR[6], P[12], Q[12];
 #pragma unroll
   for (int k = 0; k < 6; k++) {
     const double b = bk[k];
-    const double be = fma(b, b, g.eps);
-    const double b2 = b + b;
+    const double hbe = 0.5 * fma(b, b, g.eps);
 #pragma unroll
     for (int sd = 0; sd < 2; sd++) {
       const int c = 2 * k + sd;
       const double x = a[c];
       const double phi = num[c] * rd[c];
-      // d phi / da = (b^2 + eps + 2a(b - phi)) / D,
-      // d phi / db = (a^2 + eps + 2b(a - phi)) / D
-      pa[c] = fma(x + x, b - phi, be) * rd[c];
-      pb[c] = fma(b2, x - phi, fma(x, x, g.eps)) * rd[c];
+      P[c] = fma(x, b - phi, hbe) * rd[c];
+      Q[c] = fma(b, x - phi, fma(0.5 * x, x, 0.5 * g.eps)) * rd[c];
       if (sd == 0) qL[k] = fma(0.5, phi, qi[k]);
       else qR[k] = fma(-0.5, phi, qj[k]);
     }
@@ -638,9 +640,9 @@ __device__ __forceinline__ void flux2_adj_f64(const double* vi,
   rusanov_reverse_f64(qL, qR, nx, ny, nz, g, w, qLb, qRb, nb);
 #pragma unroll
   for (int k = 0; k < 6; k++) {
-    const double phib = 0.5 * qLb[k], phjb = -0.5 * qRb[k];
-    const double aib = phib * pa[2 * k], ajb = phjb * pa[2 * k + 1];
-    const double bb = fma(phib, pb[2 * k], phjb * pb[2 * k + 1]);
+    // phi_i bar = qLb/2, phi_j bar = -qRb/2
+    const double aib = qLb[k] * P[2 * k], ajb = neg(qRb[k] * P[2 * k + 1]);
+    const double bb = fma(qLb[k], Q[2 * k], neg(qRb[k] * Q[2 * k + 1]));
     oi[k] = qLb[k] - bb;
     oj[k] = qRb[k] + bb;
     oi[6 + 3 * k] = aib * dx;

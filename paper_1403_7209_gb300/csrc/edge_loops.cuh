@@ -424,9 +424,18 @@ __global__ void k_owner(P ph, const int32_t* __restrict__ m0,
       const int64_t w = first ? j : i;
       TN vw[P::NIN];
       ph.load(w, vw);
+      // the edge's own orientation whichever end v is: the operands are
+      // selected and the body runs once (a branch between two calls would
+      // run both bodies in a warp whose threads own edges of both
+      // orientations)
+      TN va[P::NIN], vb[P::NIN];
+#pragma unroll
+      for (int k = 0; k < P::NIN; k++) {
+        va[k] = first ? vv[k] : vw[k];
+        vb[k] = first ? vw[k] : vv[k];
+      }
       TE oi[P::OUT], oj[P::MODE == MODE_GEN ? P::OUT : 1];
-      if (first) ph.edge(e, vv, vw, oi, oj);
-      else ph.edge(e, vw, vv, oi, oj);
+      ph.edge(e, va, vb, oi, oj);
 #pragma unroll
       for (int c = 0; c < P::OUT; c++) {
         const TA a = to_acc<TA>(oi[c]);

@@ -33,9 +33,11 @@ METRIC = "edges/s & HBM GB/s (FP64, FP32-mixed, adjoint) vs oracle; fraction of 
 # Algorithmic (compulsory) FP64 bytes per edge of each loop: edge data read
 # once, node data read once and INC targets written once, node bytes spread
 # over the 9 edges per node.
-BYTES_PER_EDGE = {"gg": 8 + 24 + (48 + 144) / 9, "flux2": 8 + 24 + 24 + (48 + 144 + 48) / 9,
+# "gg": the Green-Gauss loop with the gradient scaling (one pass over G when
+# fused: q, n read, V read, G written once)
+BYTES_PER_EDGE = {"gg": 8 + 24 + (48 + 8 + 144) / 9, "flux2": 8 + 24 + 24 + (48 + 144 + 48) / 9,
                   "scale": 296 / 9, "update": 160 / 9}
-BYTES_PER_EDGE_F32 = {"gg": 8 + 12 + (24 + 72) / 9, "flux2": 8 + 12 + 12 + (24 + 72 + 48) / 9,
+BYTES_PER_EDGE_F32 = {"gg": 8 + 12 + (24 + 8 + 72) / 9, "flux2": 8 + 12 + 12 + (24 + 72 + 48) / 9,
                       "scale": 148 / 9, "update": 184 / 9}
 # FP64 operations per edge of the flux2 definition (reconstruction 198 +
 # Rusanov 97), each add, multiply, divide and square root counted once.
@@ -259,22 +261,20 @@ def loop_events(torch, n):
 def mixed_extra(torch, L, s, args, stream, ms64, E, N):
     """FP32-mixed stage: per-loop times, speed-up and residual error."""
     s.sync_shadow()
-    names = ["gg32", "scale32", "flux2_32", "update"]
+    names = ["gg32", "flux2_32", "update"]
 
     def stage(ev=None):
         if ev: ev[0].record(stream)
-        L.op2b_green_gauss(s.ctx, s.a_gg32, L.ZERO_INC)
+        L.op2b_green_gauss_scaled(s.ctx, s.a_gg32, s.d["V"], L.ZERO_INC)
         if ev: ev[1].record(stream)
-        L.op2b_grad_scale(s.ctx, s.d["G32"], s.d["V"])
-        if ev: ev[2].record(stream)
         L.op2b_edge_flux(s.ctx, s.a_f2_32, 2, s.gamma, s.eps_lim, L.ZERO_INC)
-        if ev: ev[3].record(stream)
+        if ev: ev[2].record(stream)
         L.op2b_node_update(s.ctx, s.d["q0"], s.d["q"], s.d["R"], s.d["V"], s.d["dt"], 0.25,
                            s.d["q32"])
-        if ev: ev[4].record(stream)
+        if ev: ev[3].record(stream)
     for _ in range(args.warmup):
         stage()
-    evs = [loop_events(torch, 5) for _ in range(args.steps)]
+    evs = [loop_events(torch, 4) for _ in range(args.steps)]
     torch.cuda.synchronize()
     t0, t1 = loop_events(torch, 2)
     t0.record(stream)
@@ -285,8 +285,8 @@ def mixed_extra(torch, L, s, args, stream, ms64, E, N):
     mms = t0.elapsed_time(t1) / args.steps
     loops = {nm: statistics.mean(evs[k][j].elapsed_time(evs[k][j + 1]) for k in range(args.steps))
              for j, nm in enumerate(names)}
-    bpe = {"gg32": BYTES_PER_EDGE_F32["gg"], "scale32": BYTES_PER_EDGE_F32["scale"],
-           "flux2_32": BYTES_PER_EDGE_F32["flux2"], "update": BYTES_PER_EDGE_F32["update"]}
+    bpe = {"gg32": BYTES_PER_EDGE_F32["gg"], "flux2_32": BYTES_PER_EDGE_F32["flux2"],
+           "update": BYTES_PER_EDGE_F32["update"]}
     strat = {"gg32": L.STRATEGY_NAMES[s.plan_stats(L.LOOP_GREEN_GAUSS, 1)["strategy"]],
              "flux2_32": L.STRATEGY_NAMES[s.plan_stats(L.LOOP_FLUX2, 1)["strategy"]]}
     hbm, _ = read_peaks()
@@ -311,24 +311,22 @@ def ff_extra(torch, L, s, args, stream, ms64, E, N):
     update that also writes the float-float shadow of q; per-loop times,
     speed-up over the FP64 stage and the residual's difference from the
     FP64 path's."""
-    names = ["gg_ff", "scale_ff", "flux2_ff", "update"]
+    names = ["gg_ff", "flux2_ff", "update"]
     s.set_strategy(L.LOOP_FLUX2, L.PREC_FF, L.STRAT_AUTO)
     s.sync_shadow(ff=True)
 
     def stage(ev=None):
         if ev: ev[0].record(stream)
-        L.op2b_green_gauss(s.ctx, s.a_gg_ff, L.ZERO_INC)
+        L.op2b_green_gauss_scaled(s.ctx, s.a_gg_ff, s.d["V"], L.ZERO_INC)
         if ev: ev[1].record(stream)
-        L.op2b_grad_scale(s.ctx, s.d["G_ff"], s.d["V"])
-        if ev: ev[2].record(stream)
         L.op2b_edge_flux(s.ctx, s.a_f2_ff, 2, s.gamma, s.eps_lim, L.ZERO_INC)
-        if ev: ev[3].record(stream)
+        if ev: ev[2].record(stream)
         L.op2b_node_update(s.ctx, s.d["q0"], s.d["q"], s.d["R"], s.d["V"], s.d["dt"], 0.25,
                            s.d["q_ff"])
-        if ev: ev[4].record(stream)
+        if ev: ev[3].record(stream)
     for _ in range(args.warmup):
         stage()
-    evs = [loop_events(torch, 5) for _ in range(args.steps)]
+    evs = [loop_events(torch, 4) for _ in range(args.steps)]
     torch.cuda.synchronize()
     t0, t1 = loop_events(torch, 2)
     t0.record(stream)
@@ -747,18 +745,16 @@ def main():
     L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
 
     # per-loop events inside each timed step
-    names = ["gg", "scale", "flux2", "update"]
+    names = ["gg", "flux2", "update"]
 
     def stage(ev=None):
         if ev: ev[0].record(stream)
-        L.op2b_green_gauss(s.ctx, s.a_gg, L.ZERO_INC)
+        L.op2b_green_gauss_scaled(s.ctx, s.a_gg, s.d["V"], L.ZERO_INC)
         if ev: ev[1].record(stream)
-        L.op2b_grad_scale(s.ctx, s.d["G"], s.d["V"])
-        if ev: ev[2].record(stream)
         L.op2b_edge_flux(s.ctx, s.a_f2, 2, s.gamma, s.eps_lim, L.ZERO_INC)
-        if ev: ev[3].record(stream)
+        if ev: ev[2].record(stream)
         L.op2b_node_update(s.ctx, s.d["q0"], s.d["q"], s.d["R"], s.d["V"], s.d["dt"], 0.25, -1)
-        if ev: ev[4].record(stream)
+        if ev: ev[3].record(stream)
 
     clk = Clocks(local).start()
     for _ in range(args.warmup):
@@ -767,7 +763,7 @@ def main():
     if args.tune_cache and rank == 0:
         L.op2b_save_tuning(s.ctx, args.tune_cache)
     def timed_region():
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()

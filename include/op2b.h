@@ -255,6 +255,18 @@ int op2b_renumber_rcb(op2b_ctx ctx, op2b_map edge2node, op2b_dat coords,
 int op2b_green_gauss(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                      int32_t flags);
 
+/* Green-Gauss gradients with the scaling by the node volume (Sec. 4.1.1's
+ * direct loop op2b_grad_scale) applied to the sums: G = (G_in + sums) / V,
+ * G_in = 0 with OP2B_ZERO_INC.  args as op2b_green_gauss; V: node dat,
+ * dim 1, F64, on the map's to-set (else OP2B_ESET / OP2B_EDIM /
+ * OP2B_ETYPE).  Under the node gather (the FF loop, or OP2B_STRAT_GATHER)
+ * each node's sums are multiplied by its 1/V as they are written, formed
+ * exactly as op2b_grad_scale forms it, so the result is bitwise that of
+ * op2b_green_gauss followed by op2b_grad_scale, in one pass over G; the
+ * other strategies run the scaling loop after the edge loop. */
+int op2b_green_gauss_scaled(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
+                            op2b_dat V, int32_t flags);
+
 /* Rusanov edge flux (Euler, 6 conserved variables incl. a passive scalar):
  *   R_i += F(qL, qR, n),  R_j -= F(qL, qR, n).
  * order 1: qL = q_i, qR = q_j.  args (5): q 0 READ, q 1 READ, n ID READ,

@@ -560,14 +560,28 @@ std::string tune_key(const LoopLaunch& L, bool det) {
          ":E" + std::to_string(L.E) + (det ? ":det" : "");
 }
 
-int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
+// whether the Green-Gauss launch divides by the volumes itself (the node
+// gather writes each node's finished sums); otherwise the scaling loop runs
+// after it
+static bool gg_scale_fused(const LoopLaunch& L, const Strategy& s) {
+  return L.prec == OP2B_PREC_FF || s.strategy == OP2B_STRAT_GATHER;
+}
+
+static int launch_loop(Ctx& c, const LoopLaunch& L, const Strategy& s) {
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);  // F64, F32 or FF
   if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);  // F64, F32 or FF
   if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // GG, FLUX2, FLUX2_ADJ (checked there)
-  if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);
-  if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
   return L.prec == OP2B_PREC_F32 ? launch_f32(&c, L, s) : launch_f64(&c, L, s);
+}
+
+int dispatch(Ctx& c, const LoopLaunch& L, const Strategy& s) {
+  int rc = launch_loop(c, L, s);
+  if (rc == OP2B_OK && L.vol && L.loop == OP2B_LOOP_GREEN_GAUSS && !gg_scale_fused(L, s)) {
+    const int type = L.prec == OP2B_PREC_F32 ? OP2B_F32 : OP2B_F64;
+    rc = node_grad_scale(&c, L.t0, type, L.ldt0, L.vol, L.N);
+  }
+  return rc;
 }
 
 // wait for an event with a host-side deadline
@@ -732,11 +746,6 @@ int run_loop(Ctx& c, LoopLaunch& L, int flags, const DatRec* z0, const DatRec* z
   // the float-float Green-Gauss loop is a node gather: it writes (or adds)
   // each node's sums itself and has no strategy to choose
   if (L.prec == OP2B_PREC_FF && L.loop == OP2B_LOOP_GREEN_GAUSS) return launch_ff(&c, L, Strategy());
-  if ((flags & OP2B_ZERO_INC)) {
-    int rc;
-    if (z0 && (rc = node_fill(&c, z0->ptr, z0->type, z0->ld, z0->dim, L.N, 0.0))) return rc;
-    if (z1 && (rc = node_fill(&c, z1->ptr, z1->type, z1->ld, z1->dim, L.N, 0.0))) return rc;
-  }
   Strategy& s = c.strat[L.loop][L.prec];
   if (s.strategy == OP2B_STRAT_AUTO || s.strategy == OP2B_STRAT_AUTO_DET) {
     const bool det = s.strategy == OP2B_STRAT_AUTO_DET;
@@ -752,20 +761,36 @@ int run_loop(Ctx& c, LoopLaunch& L, int flags, const DatRec* z0, const DatRec* z
     }
     s = best;
   }
+  // the Green-Gauss node gather writes every node's 18 sums, so its targets
+  // need no zeroing first
+  const bool writes_all = L.loop == OP2B_LOOP_GREEN_GAUSS && s.strategy == OP2B_STRAT_GATHER;
+  if ((flags & OP2B_ZERO_INC) && !writes_all) {
+    int rc;
+    if (z0 && (rc = node_fill(&c, z0->ptr, z0->type, z0->ld, z0->dim, L.N, 0.0))) return rc;
+    if (z1 && (rc = node_fill(&c, z1->ptr, z1->type, z1->ld, z1->dim, L.N, 0.0))) return rc;
+  }
   return dispatch(c, L, s);
 }
 
 }  // namespace
 
 // ------------------------------------------------------------ edge loops
-extern "C" int op2b_green_gauss(op2b_ctx h, const op2b_arg* a, int32_t nargs, int32_t flags) {
+static int node_dat(Ctx& c, op2b_dat d, int dim, int type, op2b_set set, const char* what);
+
+static int green_gauss_impl(op2b_ctx h, const op2b_arg* a, int32_t nargs, op2b_dat V,
+                            int32_t flags, const char* what) {
   CTX_CHECK(h);
   Ctx& c = h->c;
   static const Spec sp[5] = {{0, OP2B_READ, 6, 'P'}, {1, OP2B_READ, 6, 'P'}, {-1, OP2B_READ, 3, 'P'},
                              {0, OP2B_INC, 18, 'P'}, {1, OP2B_INC, 18, 'P'}};
   Checked ck;
-  int rc = check_args(c, "green_gauss", a, nargs, sp, 5, &ck);
+  int rc = check_args(c, what, a, nargs, sp, 5, &ck);
   if (rc) return rc;
+  const double* vol = nullptr;
+  if (V >= 0) {
+    if ((rc = node_dat(c, V, 1, OP2B_F64, c.maps[ck.map].to, what))) return rc;
+    vol = (const double*)c.dats[V].ptr;
+  }
   LoopLaunch L;
   L.loop = OP2B_LOOP_GREEN_GAUSS;
   L.prec = ck.prec;
@@ -780,7 +805,17 @@ extern "C" int op2b_green_gauss(op2b_ctx h, const op2b_arg* a, int32_t nargs, in
   L.ldn = D(c, a[2]).ld;
   L.t0 = D(c, a[3]).ptr;
   L.ldt0 = D(c, a[3]).ld;
+  L.vol = vol;
   return run_loop(c, L, flags, &D(c, a[3]), nullptr, nullptr);
+}
+
+extern "C" int op2b_green_gauss(op2b_ctx h, const op2b_arg* a, int32_t nargs, int32_t flags) {
+  return green_gauss_impl(h, a, nargs, -1, flags, "green_gauss");
+}
+
+extern "C" int op2b_green_gauss_scaled(op2b_ctx h, const op2b_arg* a, int32_t nargs, op2b_dat V,
+                                       int32_t flags) {
+  return green_gauss_impl(h, a, nargs, V, flags, "green_gauss_scaled");
 }
 
 extern "C" int op2b_edge_flux(op2b_ctx h, const op2b_arg* a, int32_t nargs, const op2b_flux_params* p) {

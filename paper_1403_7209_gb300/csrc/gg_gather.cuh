@@ -3,7 +3,8 @@
 //
 // Graw_i = sum over node i's edge ends (the node-sorted list of the
 // segmented plan) of +-(q_i + q_j) (x) n/2: + at the edge's first end, - at
-// its second.  Each node's sums stay in registers and are written once, so
+// its second.  Each node's sums stay in registers and are written once (and
+// divided by the node's volume there when the scaling is fused), so
 // there is no INC race, no atomic and a fixed order of the ends (bitwise
 // reproducible).  SPLIT threads share a node, each summing 6/SPLIT of its
 // components (fewer registers per thread, more warps to hide the gathers of
@@ -35,11 +36,18 @@ __device__ __forceinline__ ffv gg_zero<ffv>() {
   return ffv(make_float2(0.0f, 0.0f));
 }
 
+// 1/V in the gradient's type, formed as the scaling loop forms it, so that
+// the fused scaling gives the scaling loop's bits
+__device__ __forceinline__ void gg_rvol(double V, double& r) { r = 1.0 / V; }
+__device__ __forceinline__ void gg_rvol(double V, float& r) { r = (float)(1.0 / V); }
+__device__ __forceinline__ void gg_rvol(double V, ffv& r) { r = ffv(ff_recip(ff_of_f64(V))); }
+
 template <typename T, int SPLIT>
 __global__ void k_gg_gather(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ ends,
                             const int32_t* __restrict__ m0, const int32_t* __restrict__ m1,
                             const T* __restrict__ q, int64_t ldq, const T* __restrict__ n,
-                            int64_t ldn, T* __restrict__ G, int64_t ldG, int64_t N, bool add) {
+                            int64_t ldn, T* __restrict__ G, int64_t ldG, int64_t N, bool add,
+                            const double* __restrict__ vol) {
   constexpr int KC = 6 / SPLIT;
   const int64_t total = N * SPLIT;
   for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < total;
@@ -71,10 +79,14 @@ __global__ void k_gg_gather(const int64_t* __restrict__ rowptr, const int32_t* _
         for (int d = 0; d < 3; d++) acc[3 * k + d] = fma(sk, nh[d], acc[3 * k + d]);
       }
     }
+    // with vol: G = (sum) / V, the gradient scaling fused into the write
+    T r = gg_zero<T>();
+    if (vol) gg_rvol(ldro(vol + i), r);
 #pragma unroll
     for (int c = 0; c < 3 * KC; c++) {
       T* g = G + (3 * k0 + c) * ldG + i;
-      *g = add ? *g + acc[c] : acc[c];
+      const T v = add ? *g + acc[c] : acc[c];
+      *g = vol ? v * r : v;
     }
   }
 }
@@ -92,7 +104,7 @@ int launch_gg_gather(Ctx* c, const LoopLaunch& L, int block) {
       std::min<int64_t>((L.N * SPLIT + block - 1) / block, (int64_t)c->sm_count * 64);
   k_gg_gather<T, SPLIT><<<(unsigned)grid, block, 0, c->stream>>>(
       sp->rowptr, sp->ends, L.m0, L.m1, (const T*)L.q, L.ldq, (const T*)L.n, L.ldn, (T*)L.t0,
-      L.ldt0, L.N, !(L.flags & OP2B_ZERO_INC));
+      L.ldt0, L.N, !(L.flags & OP2B_ZERO_INC), L.vol);
   return c->launched("green_gauss gather");
 }
 

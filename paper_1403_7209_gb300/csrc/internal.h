@@ -95,6 +95,9 @@ struct LoopLaunch {
   double mu = 0.0, kappa = 0.0, diff = 0.0;  // viscous flux coefficients
   const void* phi = nullptr;                  // node limiter (FLUX2_PHI)
   int64_t ldphi = 0;
+  // Green-Gauss: node volumes; when set, the sums are divided by them (the
+  // gradient scaling, fused into the node gather, else run after the loop)
+  const double* vol = nullptr;
 };
 
 // Arguments of the node limiter (device pointers, leading dimensions).

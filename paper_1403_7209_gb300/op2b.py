@@ -103,6 +103,7 @@ _SIGS = {
     "op2b_renumber": (ctypes.c_int, [_P, _I32, _I32, _U64, _PI32, _PI64]),
     "op2b_renumber_rcb": (ctypes.c_int, [_P, _I32, _I32, _I32, _PI32, _PI64]),
     "op2b_green_gauss": (ctypes.c_int, [_P, _PARG, _I32, _I32]),
+    "op2b_green_gauss_scaled": (ctypes.c_int, [_P, _PARG, _I32, _I32, _I32]),
     "op2b_edge_flux": (ctypes.c_int, [_P, _PARG, _I32,
                                       ctypes.POINTER(FluxParams)]),
     "op2b_spectral_radius": (ctypes.c_int, [_P, _PARG, _I32, _D, _I32]),
@@ -289,6 +290,11 @@ def op2b_renumber_rcb(ctx, map_: int, coords_dat: int, leaf: int, num_nodes: int
 def op2b_green_gauss(ctx, args, flags: int = 0):
     a, n = _args(args)
     _check(load().op2b_green_gauss(ctx, a, n, flags), ctx)
+
+
+def op2b_green_gauss_scaled(ctx, args, V: int, flags: int = 0):
+    a, n = _args(args)
+    _check(load().op2b_green_gauss_scaled(ctx, a, n, V, flags), ctx)
 
 
 def op2b_edge_flux(ctx, args, order: int, gamma: float = 1.4,

@@ -286,13 +286,8 @@ class EdgeSolver:
     def green_gauss(self, mixed=False, ff=False):
         """G = Graw / V: FP64, FP32 into G32 with ``mixed``, float-float
         (from the float-float shadows of q and n) into G_ff with ``ff``."""
-        c = self.ctx
-        if ff:
-            L.op2b_green_gauss(c, self.a_gg_ff, L.ZERO_INC)
-            L.op2b_grad_scale(c, self.d["G_ff"], self.d["V"])
-            return
-        L.op2b_green_gauss(c, self.a_gg32 if mixed else self.a_gg, L.ZERO_INC)
-        L.op2b_grad_scale(c, self.d["G32" if mixed else "G"], self.d["V"])
+        a = self.a_gg_ff if ff else (self.a_gg32 if mixed else self.a_gg)
+        L.op2b_green_gauss_scaled(self.ctx, a, self.d["V"], L.ZERO_INC)
 
     def node_limiter(self, mixed=False, ff=False):
         """phi from the neighbourhood min/max and the gradients G (FP32 with

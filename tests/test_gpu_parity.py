@@ -94,6 +94,46 @@ def test_green_gauss_gather_matches_oracle(gpu_lib, mesh16, ref16, block, renumb
     s.close()
 
 
+@pytest.mark.parametrize("prec,strat", [(0, 7), (0, 3), (0, 2), (1, 7), (1, 3), (2, 0)])
+def test_green_gauss_scaled_is_the_loop_then_the_scaling(gpu_lib, mesh16, ref16, prec, strat):
+    """op2b_green_gauss_scaled gives the bits of op2b_green_gauss followed by
+    op2b_grad_scale: fused into the node gather (7; the float-float loop,
+    prec 2), the scaling loop after the others (segmented 3, colour 2: both
+    in a fixed order, so bitwise comparable); with and without ZERO_INC."""
+    import torch
+    m, q = mesh16
+    s = make_solver(gpu_lib, m, q, renumber="rcm", mixed=True, ff=True)
+    s.sync_shadow()
+    s.sync_shadow(ff=True)
+    if prec < 2:
+        s.set_strategy(gpu_lib.LOOP_GREEN_GAUSS, prec, strat, 128, 256, 0)
+    a = (s.a_gg, s.a_gg32, s.a_gg_ff)[prec]
+    G = ("G", "G32", "G_ff")[prec]
+    c, V = s.ctx, s.d["V"]
+    gpu_lib.op2b_green_gauss(c, a, gpu_lib.ZERO_INC)
+    gpu_lib.op2b_grad_scale(c, s.d[G], V)
+    two = s.t[G].clone()
+    s.t[G].fill_(float("nan"))
+    gpu_lib.op2b_green_gauss_scaled(c, a, V, gpu_lib.ZERO_INC)
+    assert torch.equal(s.t[G], two)
+    # without ZERO_INC: G = (G_in + sums) / V
+    gpu_lib.op2b_green_gauss(c, a, 0)
+    gpu_lib.op2b_grad_scale(c, s.d[G], V)
+    two_add = s.t[G].clone()
+    s.t[G].copy_(two)
+    gpu_lib.op2b_green_gauss_scaled(c, a, V, 0)
+    assert torch.equal(s.t[G], two_add)
+    if prec == 0:
+        s.green_gauss()
+        assert rel_err(s.fetch_nodes("G"), ref16["G"], ref16["Gabs"]) <= TOL
+    # V must be a node dat of dim 1 in FP64
+    for bad, code in ((s.d["q"], gpu_lib.EDIM), (s.d["n"], gpu_lib.ESET)):
+        with pytest.raises(gpu_lib.Op2bError) as e:
+            gpu_lib.op2b_green_gauss_scaled(c, a, bad, gpu_lib.ZERO_INC)
+        assert e.value.code == code
+    s.close()
+
+
 @pytest.mark.parametrize("block", [128, 256])
 def test_green_gauss_hybrid_matches_oracle(gpu_lib, mesh16, ref16, block):
     # FP64 only: gathered components 0-2, atomically scattered 3-5, one launch

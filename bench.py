@@ -30,11 +30,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "edges/s & HBM GB/s (FP64, FP32-mixed, adjoint) vs oracle; fraction of roofline"
 
-# Algorithmic (compulsory) FP64 bytes per edge of each loop: edge data read
-# once, node data read once and INC targets written once, node bytes spread
-# over the 9 edges per node.
-# "gg": the Green-Gauss loop with the gradient scaling (one pass over G when
-# fused: q, n read, V read, G written once)
+# Algorithmic (compulsory) bytes per edge of each loop: edge data read once
+# (map 8 B, n and dx 3 values each), node data read once and INC targets
+# written once, node bytes spread over the 9 edges per node.  "gg": the
+# Green-Gauss loop with the gradient scaling (q, n and V read, G written
+# once, as the fused pass does).
 BYTES_PER_EDGE = {"gg": 8 + 24 + (48 + 8 + 144) / 9, "flux2": 8 + 24 + 24 + (48 + 144 + 48) / 9,
                   "scale": 296 / 9, "update": 160 / 9}
 BYTES_PER_EDGE_F32 = {"gg": 8 + 12 + (24 + 8 + 72) / 9, "flux2": 8 + 12 + 12 + (24 + 72 + 48) / 9,

@@ -66,6 +66,10 @@ def _load():
                 "ora_spectral_radius": [I64, I64, P, P, P, D, P],
                 "ora_time_step": [I64, P, P, D, P],
                 "ora_rk_update": [I64, P, P, P, P, D, P],
+                "ora_flux_jacobian": [P, P, D, P],
+                "ora_jacobi_blocks": [I64, I64, P, P, P, D, P],
+                "ora_block_invert": [I64, P, P],
+                "ora_precond_update": [I64, P, P, P, D, P],
                 "ora_check_state": [I64, P, D],
                 "ora_march": [I, I, I, I64, I64, P, P, P, P, P, D, D, D,
                               P, P, P, P, P],
@@ -99,6 +103,7 @@ def _load():
             lib.ora_march.restype = I64
             lib.ora_march_dt.restype = I64
             lib.ora_limiter_edge.restype = D
+            lib.ora_block_invert.restype = I64
             _lib = lib
     return _lib
 
@@ -222,6 +227,41 @@ def rk_update(q0, R, V, dt, alpha):
     q = np.empty_like(q0)
     _load().ora_rk_update(q0.shape[0], _p(q0), _p(R), _p(V), _p(dt), alpha,
                           _p(q))
+    return q
+
+
+def flux_jacobian(q, n, gamma=GAMMA):
+    """A = d(f(q).n)/dq, 6 x 6 (row = flux component)."""
+    q, n = _f64(q), _f64(n)
+    A = np.empty((6, 6))
+    _load().ora_flux_jacobian(_p(q), _p(n), gamma, _p(A))
+    return A
+
+
+def jacobi_blocks(edge, q, n, gamma=GAMMA):
+    """Block-Jacobi blocks M (N x 6 x 6): the diagonal blocks of the
+    first-order Rusanov residual's Jacobian, wave speeds held fixed."""
+    edge, q, n = _i32(edge), _f64(q), _f64(n)
+    N = q.shape[0]
+    M = np.empty((N, 6, 6))
+    _load().ora_jacobi_blocks(N, edge.shape[0], _p(edge), _p(q), _p(n), gamma, _p(M))
+    return M
+
+
+def block_invert(M):
+    """(P, number of singular blocks): P_i = M_i^{-1} by Gauss-Jordan with
+    partial pivoting."""
+    M = _f64(M)
+    P = np.empty_like(M)
+    bad = int(_load().ora_block_invert(M.shape[0], _p(M), _p(P)))
+    return P, bad
+
+
+def precond_update(q0, R, P, alpha_sigma):
+    """q = q0 - alpha sigma P R per node."""
+    q0, R, P = _f64(q0), _f64(R), _f64(P)
+    q = np.empty_like(q0)
+    _load().ora_precond_update(q0.shape[0], _p(q0), _p(R), _p(P), alpha_sigma, _p(q))
     return q
 
 

@@ -228,6 +228,125 @@ void ora_rk_update(int64_t N, const double* q0, const double* R,
       q[NV * i + k] = q0[NV * i + k] - alpha * (dt[i] / V[i]) * R[NV * i + k];
 }
 
+/* ------------------------------------------------- block-Jacobi blocks
+ * Hydra's Runge-Kutta march is block-Jacobi preconditioned (Sec. 2) and its
+ * per-node blocks are inverted in a direct loop (`invjacs`, Table
+ * "loopperfmpi").  The paper prints neither the block nor the scheme; the
+ * reading taken here:
+ *   M_i = sum over the edges e of node i of
+ *           ( A(q_i, n_e) + s_e I) / 2   when i is the first end,
+ *           (-A(q_i, n_e) + s_e I) / 2   when i is the second end,
+ * the diagonal block of the Jacobian of the first-order Rusanov residual
+ * with the wave speed s_e (of the states q_i, q_j) held fixed, where
+ * A(q, n) = d(f(q).n)/dq is the Euler flux Jacobian;  P_i = M_i^{-1};
+ * preconditioned stage  q = q0 - alpha sigma P_i R_i. */
+
+/* A[r*6+c] = d (f(q).n)_r / d q_c, f as in ora_euler_flux (textbook
+ * Jacobian of the conservative Euler flux with a passive scalar) */
+void ora_flux_jacobian(const double q[NV], const double n[3], double gamma,
+                       double A[NV * NV]) {
+  double rho = q[0];
+  double u[3] = {q[1] / rho, q[2] / rho, q[3] / rho};
+  double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  double k = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  double g1 = gamma - 1.0;
+  double p = pressure(q, gamma);
+  double H = (q[4] + p) / rho;
+  double c = q[5] / rho;
+  memset(A, 0, sizeof(double) * NV * NV);
+  /* mass flux m.n */
+  for (int b = 0; b < 3; b++) A[0 * NV + 1 + b] = n[b];
+  /* momentum m_a un + p n_a */
+  for (int a = 0; a < 3; a++) {
+    A[(1 + a) * NV + 0] = -u[a] * un + g1 * k * n[a];
+    for (int b = 0; b < 3; b++)
+      A[(1 + a) * NV + 1 + b] = (a == b ? un : 0.0) + u[a] * n[b] - g1 * n[a] * u[b];
+    A[(1 + a) * NV + 4] = g1 * n[a];
+  }
+  /* energy (E + p) un */
+  A[4 * NV + 0] = un * (g1 * k - H);
+  for (int b = 0; b < 3; b++) A[4 * NV + 1 + b] = H * n[b] - g1 * un * u[b];
+  A[4 * NV + 4] = gamma * un;
+  /* passive scalar c un */
+  A[5 * NV + 0] = -c * un;
+  for (int b = 0; b < 3; b++) A[5 * NV + 1 + b] = c * n[b];
+  A[5 * NV + 5] = un;
+}
+
+/* M (N x 36, node-major, row-major blocks) */
+void ora_jacobi_blocks(int64_t N, int64_t E, const int32_t* edge,
+                       const double* q, const double* n, double gamma,
+                       double* M) {
+  memset(M, 0, sizeof(double) * NV * NV * N);
+  for (int64_t e = 0; e < E; e++) {
+    int64_t i = edge[2 * e], j = edge[2 * e + 1];
+    double sL = ora_wave_speed(q + NV * i, n + 3 * e, gamma);
+    double sR = ora_wave_speed(q + NV * j, n + 3 * e, gamma);
+    double s = (sL >= sR) ? sL : sR;
+    double Ai[NV * NV], Aj[NV * NV];
+    ora_flux_jacobian(q + NV * i, n + 3 * e, gamma, Ai);
+    ora_flux_jacobian(q + NV * j, n + 3 * e, gamma, Aj);
+    for (int r = 0; r < NV * NV; r++) {
+      M[NV * NV * i + r] += 0.5 * Ai[r];
+      M[NV * NV * j + r] -= 0.5 * Aj[r];
+    }
+    for (int r = 0; r < NV; r++) {
+      M[NV * NV * i + r * NV + r] += 0.5 * s;
+      M[NV * NV * j + r * NV + r] += 0.5 * s;
+    }
+  }
+}
+
+/* P_i = M_i^{-1} by Gauss-Jordan elimination on [M_i | I] with partial
+ * pivoting (the largest |pivot| in the column, the first on ties).
+ * Returns the number of blocks with a zero pivot (their P is not finite). */
+int64_t ora_block_invert(int64_t N, const double* M, double* P) {
+  int64_t singular = 0;
+  for (int64_t i = 0; i < N; i++) {
+    double a[NV][2 * NV];
+    for (int r = 0; r < NV; r++)
+      for (int c = 0; c < NV; c++) {
+        a[r][c] = M[NV * NV * i + r * NV + c];
+        a[r][NV + c] = (r == c) ? 1.0 : 0.0;
+      }
+    int bad = 0;
+    for (int k = 0; k < NV; k++) {
+      int piv = k;
+      for (int r = k + 1; r < NV; r++)
+        if (fabs(a[r][k]) > fabs(a[piv][k])) piv = r;
+      if (piv != k)
+        for (int c = 0; c < 2 * NV; c++) {
+          double t = a[k][c];
+          a[k][c] = a[piv][c];
+          a[piv][c] = t;
+        }
+      if (a[k][k] == 0.0) bad = 1;
+      double inv = 1.0 / a[k][k];
+      for (int c = 0; c < 2 * NV; c++) a[k][c] *= inv;
+      for (int r = 0; r < NV; r++) {
+        if (r == k) continue;
+        double f = a[r][k];
+        for (int c = 0; c < 2 * NV; c++) a[r][c] -= f * a[k][c];
+      }
+    }
+    singular += bad;
+    for (int r = 0; r < NV; r++)
+      for (int c = 0; c < NV; c++) P[NV * NV * i + r * NV + c] = a[r][NV + c];
+  }
+  return singular;
+}
+
+/* preconditioned stage: q = q0 - alpha sigma P R, per node */
+void ora_precond_update(int64_t N, const double* q0, const double* R,
+                        const double* P, double alpha_sigma, double* q) {
+  for (int64_t i = 0; i < N; i++)
+    for (int r = 0; r < NV; r++) {
+      double s = 0.0;
+      for (int c = 0; c < NV; c++) s += P[NV * NV * i + r * NV + c] * R[NV * i + c];
+      q[NV * i + r] = q0[NV * i + r] - alpha_sigma * s;
+    }
+}
+
 /* ---------------------------------------------------------- viscous flux
  * Edge-based Navier-Stokes viscous flux (Hydra's `vfluxedge` analogue; the
  * paper names the loop, Table "loopperfmpi", but not its formula):

@@ -95,7 +95,8 @@ typedef struct {
 #define OP2B_LOOP_GG_TAN 9
 #define OP2B_LOOP_VISCOUS 10
 #define OP2B_LOOP_FLUX2_PHI 11
-#define OP2B_NUM_LOOPS 12
+#define OP2B_LOOP_JACOBI 12
+#define OP2B_NUM_LOOPS 13
 
 /* arithmetic variant of a loop: all-FP64, or FP32 node data and arithmetic
  * (the INC precision is then fixed by the loop: FP64 residuals, FP32
@@ -254,6 +255,37 @@ int op2b_renumber_rcb(op2b_ctx ctx, op2b_map edge2node, op2b_dat coords,
  * loop's strategy and is bitwise reproducible. */
 int op2b_green_gauss(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                      int32_t flags);
+
+/* ------------------------------------------------ block-Jacobi blocks
+ * Sec. 2: Hydra's Runge-Kutta march is block-Jacobi preconditioned; Table
+ * "loopperfmpi": the per-node blocks are inverted in a direct loop
+ * (`invjacs`).  The paper gives neither the block nor the scheme; here the
+ * block of node i is the diagonal block of the Jacobian of the first-order
+ * Rusanov residual with every edge's wave speed s_e held fixed:
+ *   M_i += ( A(q_i, n) + s_e I)/2  at the first end of edge e,
+ *   M_j += (-A(q_j, n) + s_e I)/2  at the second,
+ * A(q, n) = d(f(q).n)/dq the Euler flux Jacobian (6 x 6 with the passive
+ * scalar), s_e = max(|u_i.n| + a_i|n|, |u_j.n| + a_j|n|).
+ * args (5): q idx 0 READ, q idx 1 READ (node, dim 6), n OP2B_ID READ (edge,
+ * dim 3), M idx 0 INC, M idx 1 INC (node, dim 36, component 6r + c = row r,
+ * column c), all F64 (else OP2B_ETYPE).  An edge loop like the others: any
+ * strategy, tuned as OP2B_LOOP_JACOBI. */
+int op2b_jacobi_blocks(op2b_ctx ctx, const op2b_arg* args, int32_t nargs, double gamma,
+                       int32_t flags);
+
+/* P_i = M_i^{-1} for every node (direct loop): Gauss-Jordan elimination on
+ * [M_i | I] with partial pivoting (largest |pivot| of the column, the first
+ * on ties), in FP64 registers.  M, P: node dats, dim 36, F64, on one set, P
+ * distinct from M.  A block with a zero pivot gets a non-finite P (no error
+ * is reported for it). */
+int op2b_block_invert(op2b_ctx ctx, op2b_dat M, op2b_dat P);
+
+/* Preconditioned stage (direct loop): q = q0 - alpha_sigma P R per node
+ * (P dim 36 as above; q0, q, R dim 6); all F64 on one set.  With P from
+ * op2b_block_invert and alpha_sigma = alpha_k sigma this is the
+ * block-Jacobi preconditioned form of op2b_node_update. */
+int op2b_node_update_precond(op2b_ctx ctx, op2b_dat q0, op2b_dat q, op2b_dat R, op2b_dat P,
+                             double alpha_sigma);
 
 /* Green-Gauss gradients with the scaling by the node volume (Sec. 4.1.1's
  * direct loop op2b_grad_scale) applied to the sums: G = (G_in + sums) / V,

@@ -21,7 +21,7 @@ void op2b::set_thread_error(const std::string& msg) { g_init_err = msg; }
 
 static const char* kLoopName[OP2B_NUM_LOOPS] = {
     "green_gauss", "flux1", "flux2", "spectral", "flux1_adj", "flux2_adj", "gg_adj",
-    "flux1_tan", "flux2_tan", "gg_tan", "viscous", "flux2_phi"};
+    "flux1_tan", "flux2_tan", "gg_tan", "viscous", "flux2_phi", "jacobi"};
 
 // ------------------------------------------------------------------ Ctx
 namespace op2b {
@@ -571,6 +571,7 @@ static int launch_loop(Ctx& c, const LoopLaunch& L, const Strategy& s) {
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);  // F64, F32 or FF
   if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);  // F64, F32 or FF
   if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // GG, FLUX2, FLUX2_ADJ (checked there)
+  if (L.loop == OP2B_LOOP_JACOBI) return launch_f64(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
   return L.prec == OP2B_PREC_F32 ? launch_f32(&c, L, s) : launch_f64(&c, L, s);
 }
@@ -806,6 +807,34 @@ static int green_gauss_impl(op2b_ctx h, const op2b_arg* a, int32_t nargs, op2b_d
   L.t0 = D(c, a[3]).ptr;
   L.ldt0 = D(c, a[3]).ld;
   L.vol = vol;
+  return run_loop(c, L, flags, &D(c, a[3]), nullptr, nullptr);
+}
+
+extern "C" int op2b_jacobi_blocks(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamma,
+                                  int32_t flags) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  if (!(gamma > 1.0)) return c.fail(OP2B_EINVAL, "jacobi_blocks: need gamma > 1");
+  static const Spec sp[5] = {{0, OP2B_READ, 6, 'D'}, {1, OP2B_READ, 6, 'D'}, {-1, OP2B_READ, 3, 'D'},
+                             {0, OP2B_INC, 36, 'D'}, {1, OP2B_INC, 36, 'D'}};
+  Checked ck;
+  int rc = check_args(c, "jacobi_blocks", a, nargs, sp, 5, &ck);
+  if (rc) return rc;
+  LoopLaunch L;
+  L.loop = OP2B_LOOP_JACOBI;
+  L.prec = OP2B_PREC_F64;
+  L.map = ck.map;
+  L.N = ck.N;
+  L.E = ck.E;
+  L.m0 = c.maps[ck.map].dev;
+  L.m1 = c.maps[ck.map].dev + ck.E;
+  L.gamma = gamma;
+  L.q = D(c, a[0]).ptr;
+  L.ldq = D(c, a[0]).ld;
+  L.n = D(c, a[2]).ptr;
+  L.ldn = D(c, a[2]).ld;
+  L.t0 = D(c, a[3]).ptr;
+  L.ldt0 = D(c, a[3]).ld;
   return run_loop(c, L, flags, &D(c, a[3]), nullptr, nullptr);
 }
 
@@ -1169,6 +1198,36 @@ static int grad_scale_impl(op2b_ctx h, op2b_dat G, op2b_dat V, const char* what)
     return c.fail(OP2B_ETYPE, std::string(what) + (fwd ? ": G must be F64, F32 or FF" : ": G must be F64 or F32"));
   if ((rc = node_dat(c, V, 1, OP2B_F64, g.set, what))) return rc;
   return node_grad_scale(&c, g.ptr, g.type, g.ld, (const double*)c.dats[V].ptr, c.sets[g.set].size);
+}
+
+extern "C" int op2b_block_invert(op2b_ctx h, op2b_dat M, op2b_dat P) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  const char* w = "block_invert";
+  int rc;
+  if ((rc = node_dat(c, M, 36, OP2B_F64, -1, w))) return rc;
+  if ((rc = node_dat(c, P, 36, OP2B_F64, c.dats[M].set, w))) return rc;
+  if (M == P) return c.fail(OP2B_EINVAL, "block_invert: M and P must be distinct dats");
+  const DatRec &m = c.dats[M], &p = c.dats[P];
+  return node_block_invert(&c, (const double*)m.ptr, m.ld, (double*)p.ptr, p.ld, c.sets[m.set].size);
+}
+
+extern "C" int op2b_node_update_precond(op2b_ctx h, op2b_dat q0, op2b_dat q, op2b_dat R,
+                                        op2b_dat P, double alpha_sigma) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  const char* w = "node_update_precond";
+  int rc;
+  if ((rc = node_dat(c, q0, 6, OP2B_F64, -1, w))) return rc;
+  const op2b_set set = c.dats[q0].set;
+  if ((rc = node_dat(c, q, 6, OP2B_F64, set, w)) || (rc = node_dat(c, R, 6, OP2B_F64, set, w)) ||
+      (rc = node_dat(c, P, 36, OP2B_F64, set, w)))
+    return rc;
+  if (R == q) return c.fail(OP2B_EINVAL, "node_update_precond: R and q must be distinct dats");
+  const DatRec &a = c.dats[q0], &b = c.dats[q], &r = c.dats[R], &p = c.dats[P];
+  return node_update_precond(&c, (const double*)a.ptr, a.ld, (double*)b.ptr, b.ld,
+                             (const double*)r.ptr, r.ld, (const double*)p.ptr, p.ld, alpha_sigma,
+                             c.sets[set].size);
 }
 
 extern "C" int op2b_grad_scale(op2b_ctx h, op2b_dat G, op2b_dat V) {

@@ -149,7 +149,41 @@ struct BodyFlux2 {
   }
 };
 
-// Spectral radius: s_e = max wave speed of the two node states, to both.
+// Block-Jacobi blocks: the first end gets (A(q_i, n) + s I)/2, the second
+// (-A(q_j, n) + s I)/2, s the Rusanov wave speed of the two node states.
+struct BodyJacobi {
+  using TN = double;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = 6, OUT = 36, MODE = MODE_GEN, DIM0 = 36;
+  const double* q;
+  int64_t ldq;
+  const double* n;
+  int64_t ldn;
+  Gas<double> g;
+  __device__ __forceinline__ void load(int64_t i, double* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
+                                       double* oi, double* oj) const {
+    const double nv[3] = {ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e)};
+    const double nn2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+    double f[6], lL, lR;
+    euler_side(vi, nv[0], nv[1], nv[2], nn2, g, f, lL);
+    euler_side(vj, nv[0], nv[1], nv[2], nn2, g, f, lR);
+    const double hs = 0.5 * (lL >= lR ? lL : lR);
+    flux_jacobian_f64(vi, nv, g, 0.5, oi);
+    flux_jacobian_f64(vj, nv, g, -0.5, oj);
+#pragma unroll
+    for (int r = 0; r < 6; r++) {
+      oi[7 * r] += hs;
+      oj[7 * r] += hs;
+    }
+  }
+};
+
+// Spectral radius: s_e = max wave speed of the two node states, to both.// Spectral radius: s_e = max wave speed of the two node states, to both.
 struct BodySpectral {
   using TN = double;
   using TE = double;

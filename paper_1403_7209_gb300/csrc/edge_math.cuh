@@ -118,6 +118,49 @@ __device__ __forceinline__ float quot<float>(float a, float b) {
   return __fdividef(a, b);
 }
 
+// Euler flux Jacobian d(f(q).n)/dq (row r = flux component, column c =
+// conserved variable), scaled by h and written to out[6r + c]: with
+// u = m/rho, u_n = u.n, k = |u|^2/2, H = (E + p)/rho, c = q_5/rho,
+//   row 0: (0, n, 0, 0)
+//   row 1+a: (-u_a u_n + (g-1) k n_a, u_n e_a + u_a n - (g-1) n_a u, (g-1) n_a, 0)
+//   row 4: (u_n ((g-1) k - H), H n - (g-1) u_n u, g u_n, 0)
+//   row 5: (-c u_n, c n, 0, u_n).
+__device__ __forceinline__ void flux_jacobian_f64(const double* q, const double* nv,
+                                                  const Gas<double>& g, double h, double* out) {
+  const double rr = 1.0 / q[0];
+  const double u[3] = {q[1] * rr, q[2] * rr, q[3] * rr};
+  const double un = u[0] * nv[0] + u[1] * nv[1] + u[2] * nv[2];
+  const double k = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double p = g.gm1 * (q[4] - q[0] * k);
+  const double H = (q[4] + p) * rr;
+  const double cs = q[5] * rr;
+  out[0] = 0.0;
+#pragma unroll
+  for (int b = 0; b < 3; b++) out[1 + b] = h * nv[b];
+  out[4] = 0.0;
+  out[5] = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    double* row = out + 6 * (1 + a);
+    row[0] = h * (g.gm1 * k * nv[a] - u[a] * un);
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+      row[1 + b] = h * ((a == b ? un : 0.0) + u[a] * nv[b] - g.gm1 * nv[a] * u[b]);
+    row[4] = h * g.gm1 * nv[a];
+    row[5] = 0.0;
+  }
+  out[24] = h * un * (g.gm1 * k - H);
+#pragma unroll
+  for (int b = 0; b < 3; b++) out[25 + b] = h * (H * nv[b] - g.gm1 * un * u[b]);
+  out[28] = h * g.gamma * un;
+  out[29] = 0.0;
+  out[30] = -h * cs * un;
+#pragma unroll
+  for (int b = 0; b < 3; b++) out[31 + b] = h * cs * nv[b];
+  out[34] = 0.0;
+  out[35] = h * un;
+}
+
 // Euler flux through the face of normal n, and the state's largest wave
 // speed |u.n| + a|n| (a = sqrt(gamma p / rho); nn2 = |n|^2).
 template <typename T>

@@ -138,6 +138,10 @@ int node_limiter(Ctx* c, const DevSegPlan& sp, int kind, int type, const LimArgs
 // Direct node loops (node_loops.cu).
 int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,
                     int64_t N);
+int node_block_invert(Ctx* c, const double* M, int64_t ldM, double* P, int64_t ldP, int64_t N);
+int node_update_precond(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
+                        const double* R, int64_t ldR, const double* P, int64_t ldP, double as,
+                        int64_t N);
 int node_time_step(Ctx* c, const double* V, const double* lam, double cfl,
                    double* dt, int64_t N);
 int node_update(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,

@@ -1,4 +1,5 @@
-// FP64 edge loops: Green-Gauss, first- and second-order flux, spectral radius.
+// FP64 edge loops: Green-Gauss, first- and second-order flux, spectral radius,
+// block-Jacobi blocks.
 #include "gg_gather.cuh"
 #include "launch.cuh"
 
@@ -23,6 +24,11 @@ int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s) {
       BodyFlux2<double> b{(const double*)L.q, L.ldq, (const double*)L.G, L.ldG,
                           (const double*)L.n, L.ldn, (const double*)L.dx, L.lddx, g};
       Targets<double, 6> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};
+      return run_body(c, b, L, s, tg);
+    }
+    case OP2B_LOOP_JACOBI: {
+      BodyJacobi b{(const double*)L.q, L.ldq, (const double*)L.n, L.ldn, g};
+      Targets<double, 36> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};
       return run_body(c, b, L, s, tg);
     }
     case OP2B_LOOP_SPECTRAL: {

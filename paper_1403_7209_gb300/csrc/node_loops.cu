@@ -320,6 +320,98 @@ static int reduce_op(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, do
   return c->launched("reduce final");
 }
 
+// Block-Jacobi inverse: P_i = M_i^{-1} by Gauss-Jordan elimination on
+// [M_i | I] with partial pivoting, every index a compile-time constant (the
+// row exchange is done with selects), so the 72 values stay in registers.
+__global__ void k_block_invert(const double* __restrict__ M, int64_t ldM, double* __restrict__ P,
+                               int64_t ldP, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double a[6][12];
+#pragma unroll
+    for (int r = 0; r < 6; r++)
+#pragma unroll
+      for (int c = 0; c < 6; c++) {
+        a[r][c] = M[(6 * r + c) * ldM + i];
+        a[r][6 + c] = r == c ? 1.0 : 0.0;
+      }
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      // the largest |a[r][k]| for r >= k, the first on ties
+      int piv = k;
+      double best = fabs(a[k][k]);
+#pragma unroll
+      for (int r = k + 1; r < 6; r++) {
+        const double v = fabs(a[r][k]);
+        piv = v > best ? r : piv;
+        best = v > best ? v : best;
+      }
+#pragma unroll
+      for (int r = k + 1; r < 6; r++) {
+        const bool sw = piv == r;
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+          const double t = a[k][c];
+          a[k][c] = sw ? a[r][c] : t;
+          a[r][c] = sw ? t : a[r][c];
+        }
+      }
+      const double inv = 1.0 / a[k][k];
+#pragma unroll
+      for (int c = 0; c < 12; c++) a[k][c] *= inv;
+#pragma unroll
+      for (int r = 0; r < 6; r++) {
+        if (r == k) continue;
+        const double f = a[r][k];
+#pragma unroll
+        for (int c = 0; c < 12; c++) a[r][c] = fma(-f, a[k][c], a[r][c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 6; r++)
+#pragma unroll
+      for (int c = 0; c < 6; c++) P[(6 * r + c) * ldP + i] = a[r][6 + c];
+  }
+}
+
+int node_block_invert(Ctx* c, const double* M, int64_t ldM, double* P, int64_t ldP, int64_t N) {
+  if (N == 0) return OP2B_OK;
+  k_block_invert<<<grid_for(c, N, 128), 128, 0, c->stream>>>(M, ldM, P, ldP, N);
+  return c->launched("block_invert");
+}
+
+// Preconditioned stage: q = q0 - alpha_sigma P R per node.
+__global__ void k_update_precond(const double* __restrict__ q0, int64_t ld0,
+                                 double* __restrict__ q, int64_t ldq,
+                                 const double* __restrict__ R, int64_t ldR,
+                                 const double* __restrict__ P, int64_t ldP, double as,
+                                 int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double r[6], out[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) r[k] = R[k * ldR + i];
+#pragma unroll
+    for (int row = 0; row < 6; row++) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; k++) acc = fma(P[(6 * row + k) * ldP + i], r[k], acc);
+      out[row] = fma(-as, acc, q0[row * ld0 + i]);
+    }
+#pragma unroll
+    for (int row = 0; row < 6; row++) q[row * ldq + i] = out[row];
+  }
+}
+
+int node_update_precond(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
+                        const double* R, int64_t ldR, const double* P, int64_t ldP, double as,
+                        int64_t N) {
+  if (N == 0) return OP2B_OK;
+  k_update_precond<<<grid_for(c, N, 256), 256, 0, c->stream>>>(q0, ld0, q, ldq, R, ldR, P, ldP,
+                                                               as, N);
+  return c->launched("update_precond");
+}
+
 int node_reduce(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, int op, double* out) {
   switch (op) {
     case OP2B_RED_SUM: return reduce_op<OP2B_RED_SUM>(c, x, ld, dim, n, out);

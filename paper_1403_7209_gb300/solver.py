@@ -38,14 +38,16 @@ class EdgeSolver:
     (Navier-Stokes instead of Euler).  ``limiter`` picks the second-order
     reconstruction: "van_albada" (per edge, the default), or the node
     limiters "barth_jespersen" and "venkatakrishnan" (``limiter_eps2`` is
-    Venkatakrishnan's smoothing constant).
+    Venkatakrishnan's smoothing constant).  ``precond`` adds the block-Jacobi
+    blocks and their inverses for preconditioned steps (``step(sigma=...)``).
     """
 
     def __init__(self, edge, normal, dx, volume, q=None, device: int = 0,
                  renumber: str = "none", seed: int = 0, mixed: bool = False,
                  adjoint: bool = False, gamma: float = 1.4,
                  eps_lim: float = 1e-12, stream=None, coords=None, viscous=None,
-                 limiter: str = "van_albada", limiter_eps2: float = 0.0, ff: bool = False):
+                 limiter: str = "van_albada", limiter_eps2: float = 0.0, ff: bool = False,
+                 precond: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -107,6 +109,10 @@ class EdgeSolver:
             edgd("dx_ff", 3, "ff")
             if self.visc is not None:
                 node("W_ff", 20, "ff")
+        self.precond = precond
+        if precond:
+            node("M", 36)  # block-Jacobi blocks (row-major 6 x 6 per node)
+            node("P", 36)  # their inverses
         self.has_adjoint = adjoint
         if adjoint:
             node("lam", 6)
@@ -214,6 +220,9 @@ class EdgeSolver:
                      dr("n", R), dr("dx", R), ind("R", 0, I), ind("R", 1, I)]
         self.a_sr = [ind("q", 0, R), ind("q", 1, R), dr("n", R), ind("lam_s", 0, I),
                      ind("lam_s", 1, I)]
+        if self.precond:
+            self.a_jac = [ind("q", 0, R), ind("q", 1, R), dr("n", R), ind("M", 0, I),
+                          ind("M", 1, I)]
         if self.mixed:
             self.a_gg32 = [ind("q32", 0, R), ind("q32", 1, R), dr("n32", R),
                            ind("G32", 0, I), ind("G32", 1, I)]
@@ -356,20 +365,41 @@ class EdgeSolver:
         self.spectral_radius()
         L.op2b_time_step(self.ctx, self.d["V"], self.d["lam_s"], cfl, self.d["dt"])
 
-    def update(self, alpha, mixed=False, ff=False):
+    def precondition(self):
+        """Block-Jacobi preconditioner of the current state: the blocks M
+        (diagonal blocks of the first-order residual's Jacobian, wave speeds
+        held fixed) and their inverses P."""
+        if not self.precond:
+            raise RuntimeError("EdgeSolver(precond=True) declares the block dats")
+        L.op2b_jacobi_blocks(self.ctx, self.a_jac, self.gamma, L.ZERO_INC)
+        L.op2b_block_invert(self.ctx, self.d["M"], self.d["P"])
+
+    def update(self, alpha, mixed=False, ff=False, sigma=None):
+        """q = q0 - alpha (dt/V) R, or with ``sigma`` the block-Jacobi
+        preconditioned stage q = q0 - alpha sigma P R (FP64 only)."""
+        if sigma is not None:
+            if mixed or ff:
+                raise NotImplementedError("the preconditioned stage is FP64")
+            L.op2b_node_update_precond(self.ctx, self.d["q0"], self.d["q"], self.d["R"],
+                                       self.d["P"], alpha * sigma)
+            return
         sh = self.d["q32"] if mixed else (self.d["q_ff"] if ff else -1)
         L.op2b_node_update(self.ctx, self.d["q0"], self.d["q"], self.d["R"], self.d["V"],
                            self.d["dt"], alpha, sh)
 
-    def stage(self, alpha, order=2, mixed=False, ff=False):
+    def stage(self, alpha, order=2, mixed=False, ff=False, sigma=None):
         self.residual(order, mixed, ff)
-        self.update(alpha, mixed, ff)
+        self.update(alpha, mixed, ff, sigma)
 
-    def step(self, order=2, mixed=False, stages=5, ff=False):
-        """One explicit RK step (q0 <- q, then `stages` stages)."""
+    def step(self, order=2, mixed=False, stages=5, ff=False, sigma=None):
+        """One explicit RK step (q0 <- q, then `stages` stages).  With
+        ``sigma``: block-Jacobi preconditioned, the blocks formed from the
+        step's initial state and kept for its stages."""
         L.op2b_dat_copy(self.ctx, self.d["q0"], self.d["q"])
+        if sigma is not None:
+            self.precondition()
         for a in RK5_ALPHA[5 - stages:]:
-            self.stage(a, order, mixed, ff)
+            self.stage(a, order, mixed, ff, sigma)
 
     def sync_shadow(self, ff=False):
         """q32 <- q (FP32 shadow of the state), or q_ff <- q with ``ff``."""

@@ -535,6 +535,49 @@ def limiter_extra(torch, L, m, q, args, stream, device, E, ms_va):
     return out
 
 
+def block_jacobi_extra(torch, L, m, q, args, stream, device, E):
+    """Block-Jacobi preconditioning (FP64): the factored blocks (edge loop
+    of four sums, one node pass forming and inverting the blocks) and the
+    direct form (36-value edge loop, inversion loop), each tuned; the
+    preconditioned update, and a preconditioned step (blocks and inverses of
+    the step's initial state, five stages) against a plain step."""
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    sj = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device,
+                    renumber=args.numbering, stream=stream, precond=True)
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        L.op2b_load_tuning(sj.ctx, args.tune_cache)
+    for loop in range(L.NUM_LOOPS):
+        for prec in range(L.NUM_PREC):
+            sj.set_strategy(loop, prec, L.STRAT_AUTO)
+    sj.time_step(0.5)
+    c, d = sj.ctx, sj.d
+    sj.precondition(factored=False)  # tunes both blocks' loops
+    sj.precondition()
+    sj.residual(2)
+    L.op2b_dat_copy(c, d["q0"], d["q"])
+    nb = max(2, args.steps // 4)
+    out = {
+        "sums_ms": timed(torch, lambda: L.op2b_jacobi_sums(c, sj.a_jsum, sj.gamma, L.ZERO_INC),
+                         nb, stream),
+        "sums_strategy": L.STRATEGY_NAMES[sj.plan_stats(L.LOOP_JACOBI_SUMS)["strategy"]],
+        "form_and_invert_ms": timed(torch, lambda: L.op2b_jacobi_from_sums(
+            c, d["q"], d["JS"], -1, d["P"], sj.gamma), nb, stream),
+        "direct_blocks_ms": timed(torch, lambda: L.op2b_jacobi_blocks(c, sj.a_jac, sj.gamma,
+                                                                      L.ZERO_INC), nb, stream),
+        "direct_blocks_strategy": L.STRATEGY_NAMES[sj.plan_stats(L.LOOP_JACOBI)["strategy"]],
+        "invert_ms": timed(torch, lambda: L.op2b_block_invert(c, d["M"], d["P"]), nb, stream),
+        "update_precond_ms": timed(torch, lambda: L.op2b_node_update_precond(
+            c, d["q0"], d["q"], d["R"], d["P"], 0.1), nb, stream),
+    }
+    q_keep = sj.t["q"].clone()
+    out["precond_step_ms"] = timed(torch, lambda: sj.step(order=2, sigma=0.25), nb, stream)
+    sj.t["q"].copy_(q_keep)
+    out["step_ms"] = timed(torch, lambda: sj.step(order=2), nb, stream)
+    out["precond_step_over_step"] = out["precond_step_ms"] / out["step_ms"]
+    sj.close()
+    return out
+
+
 def march_adjoint_extra(torch, L, s, q, args, stream, E, steps=10):
     """Reverse sweep of a 10-step march (50 stages, dt fixed) with every
     stage's state and gradient kept in HBM, against the forward march."""
@@ -838,6 +881,7 @@ def main():
         line["viscous"]["fp64_ns_stage_vs_euler_stage"] = line["viscous"]["fp64"]["ns_stage_ms"] / ms
         line["march_adjoint"] = march_adjoint_extra(torch, L, s, q, args, stream, E)
         line["limiters"] = limiter_extra(torch, L, m, q, args, stream, local, E, ms)
+        line["block_jacobi"] = block_jacobi_extra(torch, L, m, q, args, stream, local, E)
         line["config0"] = config0_extra(torch, L, args)
         line["march"] = march_extra(torch, L, s, q, args, stream)
         if args.numbering == "rcm":

@@ -96,7 +96,8 @@ typedef struct {
 #define OP2B_LOOP_VISCOUS 10
 #define OP2B_LOOP_FLUX2_PHI 11
 #define OP2B_LOOP_JACOBI 12
-#define OP2B_NUM_LOOPS 13
+#define OP2B_LOOP_JACOBI_SUMS 13
+#define OP2B_NUM_LOOPS 14
 
 /* arithmetic variant of a loop: all-FP64, or FP32 node data and arithmetic
  * (the INC precision is then fixed by the loop: FP64 residuals, FP32
@@ -272,6 +273,22 @@ int op2b_green_gauss(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  * strategy, tuned as OP2B_LOOP_JACOBI. */
 int op2b_jacobi_blocks(op2b_ctx ctx, const op2b_arg* args, int32_t nargs, double gamma,
                        int32_t flags);
+
+/* The same blocks in factored form.  A(q, n) is linear in n, so
+ *   M_i = (Lambda_i I + A(q_i, S_i)) / 2,  Lambda_i = sum_e s_e,
+ *   S_i = sum_e (+n_e at the first end, -n_e at the second):
+ * op2b_jacobi_sums is the edge loop of the four sums -- args (5): q idx 0
+ * READ, q idx 1 READ (node, dim 6), n OP2B_ID READ (edge, dim 3), S idx 0
+ * INC, S idx 1 INC (node, dim 4: Lambda, S_x, S_y, S_z), all F64; tuned as
+ * OP2B_LOOP_JACOBI_SUMS -- and op2b_jacobi_from_sums the node loop that forms
+ * each block from q and S and writes it to M and/or its inverse (as
+ * op2b_block_invert) to P (a dat handle < 0 skips that output; M, P dim 36
+ * F64 and q dim 6, S dim 4 F64, all on one set).  Equal to
+ * op2b_jacobi_blocks up to rounding, with 4 instead of 36 sums per edge end. */
+int op2b_jacobi_sums(op2b_ctx ctx, const op2b_arg* args, int32_t nargs, double gamma,
+                     int32_t flags);
+int op2b_jacobi_from_sums(op2b_ctx ctx, op2b_dat q, op2b_dat S, op2b_dat M, op2b_dat P,
+                          double gamma);
 
 /* P_i = M_i^{-1} for every node (direct loop): Gauss-Jordan elimination on
  * [M_i | I] with partial pivoting (largest |pivot| of the column, the first

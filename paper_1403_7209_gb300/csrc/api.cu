@@ -21,7 +21,7 @@ void op2b::set_thread_error(const std::string& msg) { g_init_err = msg; }
 
 static const char* kLoopName[OP2B_NUM_LOOPS] = {
     "green_gauss", "flux1", "flux2", "spectral", "flux1_adj", "flux2_adj", "gg_adj",
-    "flux1_tan", "flux2_tan", "gg_tan", "viscous", "flux2_phi", "jacobi"};
+    "flux1_tan", "flux2_tan", "gg_tan", "viscous", "flux2_phi", "jacobi", "jacobi_sums"};
 
 // ------------------------------------------------------------------ Ctx
 namespace op2b {
@@ -571,7 +571,7 @@ static int launch_loop(Ctx& c, const LoopLaunch& L, const Strategy& s) {
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);  // F64, F32 or FF
   if (L.loop == OP2B_LOOP_FLUX2_PHI) return launch_lim(&c, L, s);  // F64, F32 or FF
   if (L.prec == OP2B_PREC_FF) return launch_ff(&c, L, s);  // GG, FLUX2, FLUX2_ADJ (checked there)
-  if (L.loop == OP2B_LOOP_JACOBI) return launch_f64(&c, L, s);
+  if (L.loop == OP2B_LOOP_JACOBI || L.loop == OP2B_LOOP_JACOBI_SUMS) return launch_f64(&c, L, s);
   if (L.loop >= OP2B_LOOP_FLUX1_ADJ) return launch_adj(&c, L, s);
   return L.prec == OP2B_PREC_F32 ? launch_f32(&c, L, s) : launch_f64(&c, L, s);
 }
@@ -810,18 +810,20 @@ static int green_gauss_impl(op2b_ctx h, const op2b_arg* a, int32_t nargs, op2b_d
   return run_loop(c, L, flags, &D(c, a[3]), nullptr, nullptr);
 }
 
-extern "C" int op2b_jacobi_blocks(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamma,
-                                  int32_t flags) {
+static int jacobi_loop(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamma,
+                       int32_t flags, bool sums) {
   CTX_CHECK(h);
   Ctx& c = h->c;
-  if (!(gamma > 1.0)) return c.fail(OP2B_EINVAL, "jacobi_blocks: need gamma > 1");
-  static const Spec sp[5] = {{0, OP2B_READ, 6, 'D'}, {1, OP2B_READ, 6, 'D'}, {-1, OP2B_READ, 3, 'D'},
-                             {0, OP2B_INC, 36, 'D'}, {1, OP2B_INC, 36, 'D'}};
+  const char* w = sums ? "jacobi_sums" : "jacobi_blocks";
+  if (!(gamma > 1.0)) return c.fail(OP2B_EINVAL, std::string(w) + ": need gamma > 1");
+  const int dim = sums ? 4 : 36;
+  const Spec sp[5] = {{0, OP2B_READ, 6, 'D'}, {1, OP2B_READ, 6, 'D'}, {-1, OP2B_READ, 3, 'D'},
+                      {0, OP2B_INC, dim, 'D'}, {1, OP2B_INC, dim, 'D'}};
   Checked ck;
-  int rc = check_args(c, "jacobi_blocks", a, nargs, sp, 5, &ck);
+  int rc = check_args(c, w, a, nargs, sp, 5, &ck);
   if (rc) return rc;
   LoopLaunch L;
-  L.loop = OP2B_LOOP_JACOBI;
+  L.loop = sums ? OP2B_LOOP_JACOBI_SUMS : OP2B_LOOP_JACOBI;
   L.prec = OP2B_PREC_F64;
   L.map = ck.map;
   L.N = ck.N;
@@ -836,6 +838,16 @@ extern "C" int op2b_jacobi_blocks(op2b_ctx h, const op2b_arg* a, int32_t nargs, 
   L.t0 = D(c, a[3]).ptr;
   L.ldt0 = D(c, a[3]).ld;
   return run_loop(c, L, flags, &D(c, a[3]), nullptr, nullptr);
+}
+
+extern "C" int op2b_jacobi_blocks(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamma,
+                                  int32_t flags) {
+  return jacobi_loop(h, a, nargs, gamma, flags, false);
+}
+
+extern "C" int op2b_jacobi_sums(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamma,
+                                int32_t flags) {
+  return jacobi_loop(h, a, nargs, gamma, flags, true);
 }
 
 extern "C" int op2b_green_gauss(op2b_ctx h, const op2b_arg* a, int32_t nargs, int32_t flags) {
@@ -1210,6 +1222,27 @@ extern "C" int op2b_block_invert(op2b_ctx h, op2b_dat M, op2b_dat P) {
   if (M == P) return c.fail(OP2B_EINVAL, "block_invert: M and P must be distinct dats");
   const DatRec &m = c.dats[M], &p = c.dats[P];
   return node_block_invert(&c, (const double*)m.ptr, m.ld, (double*)p.ptr, p.ld, c.sets[m.set].size);
+}
+
+extern "C" int op2b_jacobi_from_sums(op2b_ctx h, op2b_dat q, op2b_dat S, op2b_dat M, op2b_dat P,
+                                     double gamma) {
+  CTX_CHECK(h);
+  Ctx& c = h->c;
+  const char* w = "jacobi_from_sums";
+  if (!(gamma > 1.0)) return c.fail(OP2B_EINVAL, "jacobi_from_sums: need gamma > 1");
+  int rc;
+  if ((rc = node_dat(c, q, 6, OP2B_F64, -1, w))) return rc;
+  const op2b_set set = c.dats[q].set;
+  if ((rc = node_dat(c, S, 4, OP2B_F64, set, w))) return rc;
+  if (M >= 0 && (rc = node_dat(c, M, 36, OP2B_F64, set, w))) return rc;
+  if (P >= 0 && (rc = node_dat(c, P, 36, OP2B_F64, set, w))) return rc;
+  if (M >= 0 && M == P) return c.fail(OP2B_EINVAL, "jacobi_from_sums: M and P must be distinct dats");
+  const DatRec &dq = c.dats[q], &ds = c.dats[S];
+  double* mp = M >= 0 ? (double*)c.dats[M].ptr : nullptr;
+  double* pp = P >= 0 ? (double*)c.dats[P].ptr : nullptr;
+  return node_jacobi_from_sums(&c, (const double*)dq.ptr, dq.ld, (const double*)ds.ptr, ds.ld, mp,
+                               M >= 0 ? c.dats[M].ld : 0, pp, P >= 0 ? c.dats[P].ld : 0, gamma,
+                               c.sets[set].size);
 }
 
 extern "C" int op2b_node_update_precond(op2b_ctx h, op2b_dat q0, op2b_dat q, op2b_dat R,

@@ -183,6 +183,39 @@ struct BodyJacobi {
   }
 };
 
+// Sums of the factored block-Jacobi blocks: (s, n) to the first end,
+// (s, -n) to the second, s the Rusanov wave speed of the two node states.
+struct BodyJacobiSums {
+  using TN = double;
+  using TE = double;
+  using TA = double;
+  static constexpr int NIN = 6, OUT = 4, MODE = MODE_GEN, DIM0 = 4;
+  const double* q;
+  int64_t ldq;
+  const double* n;
+  int64_t ldn;
+  Gas<double> g;
+  __device__ __forceinline__ void load(int64_t i, double* v) const {
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+  }
+  __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
+                                       double* oi, double* oj) const {
+    const double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
+    const double nn2 = nx * nx + ny * ny + nz * nz;
+    double f[6], lL, lR;
+    euler_side(vi, nx, ny, nz, nn2, g, f, lL);
+    euler_side(vj, nx, ny, nz, nn2, g, f, lR);
+    oi[0] = oj[0] = lL >= lR ? lL : lR;
+    oi[1] = nx;
+    oi[2] = ny;
+    oi[3] = nz;
+    oj[1] = neg(nx);
+    oj[2] = neg(ny);
+    oj[3] = neg(nz);
+  }
+};
+
 // Spectral radius: s_e = max wave speed of the two node states, to both.// Spectral radius: s_e = max wave speed of the two node states, to both.
 struct BodySpectral {
   using TN = double;

@@ -139,6 +139,9 @@ int node_limiter(Ctx* c, const DevSegPlan& sp, int kind, int type, const LimArgs
 int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,
                     int64_t N);
 int node_block_invert(Ctx* c, const double* M, int64_t ldM, double* P, int64_t ldP, int64_t N);
+int node_jacobi_from_sums(Ctx* c, const double* q, int64_t ldq, const double* S, int64_t ldS,
+                          double* M, int64_t ldM, double* P, int64_t ldP, double gamma,
+                          int64_t N);
 int node_update_precond(Ctx* c, const double* q0, int64_t ld0, double* q, int64_t ldq,
                         const double* R, int64_t ldR, const double* P, int64_t ldP, double as,
                         int64_t N);

@@ -31,6 +31,11 @@ int launch_f64(Ctx* c, const LoopLaunch& L, const Strategy& s) {
       Targets<double, 36> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};
       return run_body(c, b, L, s, tg);
     }
+    case OP2B_LOOP_JACOBI_SUMS: {
+      BodyJacobiSums b{(const double*)L.q, L.ldq, (const double*)L.n, L.ldn, g};
+      Targets<double, 4> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};
+      return run_body(c, b, L, s, tg);
+    }
     case OP2B_LOOP_SPECTRAL: {
       BodySpectral b{(const double*)L.q, L.ldq, (const double*)L.n, L.ldn, g};
       Targets<double, 1> tg{(double*)L.t0, L.ldt0, (double*)L.t0, L.ldt0};

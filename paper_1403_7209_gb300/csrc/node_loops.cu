@@ -320,58 +320,107 @@ static int reduce_op(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, do
   return c->launched("reduce final");
 }
 
-// Block-Jacobi inverse: P_i = M_i^{-1} by Gauss-Jordan elimination on
-// [M_i | I] with partial pivoting, every index a compile-time constant (the
-// row exchange is done with selects), so the 72 values stay in registers.
+// Block-Jacobi inverse: p = m^{-1} (6 x 6, row-major) by Gauss-Jordan
+// elimination on [m | I] with partial pivoting, every index a compile-time
+// constant (the row exchange is done with selects), so the 72 values stay
+// in registers.
+__device__ __forceinline__ void gj_invert6(const double* m, double* p) {
+  double a[6][12];
+#pragma unroll
+  for (int r = 0; r < 6; r++)
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+      a[r][c] = m[6 * r + c];
+      a[r][6 + c] = r == c ? 1.0 : 0.0;
+    }
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    // the largest |a[r][k]| for r >= k, the first on ties
+    int piv = k;
+    double best = fabs(a[k][k]);
+#pragma unroll
+    for (int r = k + 1; r < 6; r++) {
+      const double v = fabs(a[r][k]);
+      piv = v > best ? r : piv;
+      best = v > best ? v : best;
+    }
+#pragma unroll
+    for (int r = k + 1; r < 6; r++) {
+      const bool sw = piv == r;
+#pragma unroll
+      for (int c = 0; c < 12; c++) {
+        const double t = a[k][c];
+        a[k][c] = sw ? a[r][c] : t;
+        a[r][c] = sw ? t : a[r][c];
+      }
+    }
+    const double inv = 1.0 / a[k][k];
+#pragma unroll
+    for (int c = 0; c < 12; c++) a[k][c] *= inv;
+#pragma unroll
+    for (int r = 0; r < 6; r++) {
+      if (r == k) continue;
+      const double f = a[r][k];
+#pragma unroll
+      for (int c = 0; c < 12; c++) a[r][c] = fma(-f, a[k][c], a[r][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 6; r++)
+#pragma unroll
+    for (int c = 0; c < 6; c++) p[6 * r + c] = a[r][6 + c];
+}
+
 __global__ void k_block_invert(const double* __restrict__ M, int64_t ldM, double* __restrict__ P,
                                int64_t ldP, int64_t N) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double a[6][12];
+    double m[36], p[36];
 #pragma unroll
-    for (int r = 0; r < 6; r++)
+    for (int c = 0; c < 36; c++) m[c] = M[c * ldM + i];
+    gj_invert6(m, p);
 #pragma unroll
-      for (int c = 0; c < 6; c++) {
-        a[r][c] = M[(6 * r + c) * ldM + i];
-        a[r][6 + c] = r == c ? 1.0 : 0.0;
-      }
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      // the largest |a[r][k]| for r >= k, the first on ties
-      int piv = k;
-      double best = fabs(a[k][k]);
-#pragma unroll
-      for (int r = k + 1; r < 6; r++) {
-        const double v = fabs(a[r][k]);
-        piv = v > best ? r : piv;
-        best = v > best ? v : best;
-      }
-#pragma unroll
-      for (int r = k + 1; r < 6; r++) {
-        const bool sw = piv == r;
-#pragma unroll
-        for (int c = 0; c < 12; c++) {
-          const double t = a[k][c];
-          a[k][c] = sw ? a[r][c] : t;
-          a[r][c] = sw ? t : a[r][c];
-        }
-      }
-      const double inv = 1.0 / a[k][k];
-#pragma unroll
-      for (int c = 0; c < 12; c++) a[k][c] *= inv;
-#pragma unroll
-      for (int r = 0; r < 6; r++) {
-        if (r == k) continue;
-        const double f = a[r][k];
-#pragma unroll
-        for (int c = 0; c < 12; c++) a[r][c] = fma(-f, a[k][c], a[r][c]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < 6; r++)
-#pragma unroll
-      for (int c = 0; c < 6; c++) P[(6 * r + c) * ldP + i] = a[r][6 + c];
+    for (int c = 0; c < 36; c++) P[c * ldP + i] = p[c];
   }
+}
+
+// Factored blocks: M_i = (Lambda_i I + A(q_i, S_i)) / 2 from the node's
+// sums S = (Lambda, S_x, S_y, S_z); writes M and/or P = M^{-1} (null skips).
+__global__ void k_jacobi_from_sums(const double* __restrict__ q, int64_t ldq,
+                                   const double* __restrict__ S, int64_t ldS,
+                                   double* __restrict__ M, int64_t ldM, double* __restrict__ P,
+                                   int64_t ldP, Gas<double> g, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double qi[6], m[36];
+#pragma unroll
+    for (int k = 0; k < 6; k++) qi[k] = q[k * ldq + i];
+    const double sv[3] = {S[ldS + i], S[2 * ldS + i], S[3 * ldS + i]};
+    flux_jacobian_f64(qi, sv, g, 0.5, m);
+    const double hl = 0.5 * S[i];
+#pragma unroll
+    for (int r = 0; r < 6; r++) m[7 * r] += hl;
+    if (M) {
+#pragma unroll
+      for (int c = 0; c < 36; c++) M[c * ldM + i] = m[c];
+    }
+    if (P) {
+      double p[36];
+      gj_invert6(m, p);
+#pragma unroll
+      for (int c = 0; c < 36; c++) P[c * ldP + i] = p[c];
+    }
+  }
+}
+
+int node_jacobi_from_sums(Ctx* c, const double* q, int64_t ldq, const double* S, int64_t ldS,
+                          double* M, int64_t ldM, double* P, int64_t ldP, double gamma,
+                          int64_t N) {
+  if (N == 0) return OP2B_OK;
+  Gas<double> g{gamma, gamma - 1.0, 0.0, 0.0};
+  k_jacobi_from_sums<<<grid_for(c, N, 128), 128, 0, c->stream>>>(q, ldq, S, ldS, M, ldM, P, ldP,
+                                                                 g, N);
+  return c->launched("jacobi_from_sums");
 }
 
 int node_block_invert(Ctx* c, const double* M, int64_t ldM, double* P, int64_t ldP, int64_t N) {

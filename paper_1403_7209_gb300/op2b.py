@@ -25,7 +25,7 @@ ID = -1
 LOOP_GREEN_GAUSS, LOOP_FLUX1, LOOP_FLUX2, LOOP_SPECTRAL = 0, 1, 2, 3
 LOOP_FLUX1_ADJ, LOOP_FLUX2_ADJ, LOOP_GG_ADJ = 4, 5, 6
 LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, LOOP_VISCOUS = 7, 8, 9, 10
-LOOP_FLUX2_PHI, LOOP_JACOBI, NUM_LOOPS = 11, 12, 13
+LOOP_FLUX2_PHI, LOOP_JACOBI, LOOP_JACOBI_SUMS, NUM_LOOPS = 11, 12, 13, 14
 LIM_BARTH_JESPERSEN, LIM_VENKATAKRISHNAN = 1, 2
 PREC_F64, PREC_F32, PREC_FF, NUM_PREC = 0, 1, 2, 3
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
@@ -123,6 +123,8 @@ _SIGS = {
     "op2b_grad_scale": (ctypes.c_int, [_P, _I32, _I32]),
     "op2b_jacobi_blocks": (ctypes.c_int, [_P, _PARG, _I32, _D, _I32]),
     "op2b_block_invert": (ctypes.c_int, [_P, _I32, _I32]),
+    "op2b_jacobi_sums": (ctypes.c_int, [_P, _PARG, _I32, _D, _I32]),
+    "op2b_jacobi_from_sums": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _D]),
     "op2b_node_update_precond": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _D]),
     "op2b_grad_scale_adjoint": (ctypes.c_int, [_P, _I32, _I32]),
     "op2b_time_step": (ctypes.c_int, [_P, _I32, _I32, _D, _I32]),
@@ -369,6 +371,15 @@ def op2b_grad_scale(ctx, G: int, V: int):
 def op2b_jacobi_blocks(ctx, args, gamma: float = 1.4, flags: int = 0):
     a, n = _args(args)
     _check(load().op2b_jacobi_blocks(ctx, a, n, gamma, flags), ctx)
+
+
+def op2b_jacobi_sums(ctx, args, gamma: float = 1.4, flags: int = 0):
+    a, n = _args(args)
+    _check(load().op2b_jacobi_sums(ctx, a, n, gamma, flags), ctx)
+
+
+def op2b_jacobi_from_sums(ctx, q: int, S: int, M: int, P: int, gamma: float = 1.4):
+    _check(load().op2b_jacobi_from_sums(ctx, q, S, M, P, gamma), ctx)
 
 
 def op2b_block_invert(ctx, M: int, P: int):

@@ -113,6 +113,7 @@ class EdgeSolver:
         if precond:
             node("M", 36)  # block-Jacobi blocks (row-major 6 x 6 per node)
             node("P", 36)  # their inverses
+            node("JS", 4)  # the blocks' factored sums (Lambda, S)
         self.has_adjoint = adjoint
         if adjoint:
             node("lam", 6)
@@ -223,6 +224,8 @@ class EdgeSolver:
         if self.precond:
             self.a_jac = [ind("q", 0, R), ind("q", 1, R), dr("n", R), ind("M", 0, I),
                           ind("M", 1, I)]
+            self.a_jsum = [ind("q", 0, R), ind("q", 1, R), dr("n", R), ind("JS", 0, I),
+                           ind("JS", 1, I)]
         if self.mixed:
             self.a_gg32 = [ind("q32", 0, R), ind("q32", 1, R), dr("n32", R),
                            ind("G32", 0, I), ind("G32", 1, I)]
@@ -365,14 +368,22 @@ class EdgeSolver:
         self.spectral_radius()
         L.op2b_time_step(self.ctx, self.d["V"], self.d["lam_s"], cfl, self.d["dt"])
 
-    def precondition(self):
+    def precondition(self, factored=True):
         """Block-Jacobi preconditioner of the current state: the blocks M
         (diagonal blocks of the first-order residual's Jacobian, wave speeds
-        held fixed) and their inverses P."""
+        held fixed) and their inverses P.  ``factored``: from the four
+        per-node sums (Lambda, sum of signed normals) and one node pass that
+        forms and inverts each block; else the 36-value edge loop and the
+        inversion loop."""
         if not self.precond:
             raise RuntimeError("EdgeSolver(precond=True) declares the block dats")
-        L.op2b_jacobi_blocks(self.ctx, self.a_jac, self.gamma, L.ZERO_INC)
-        L.op2b_block_invert(self.ctx, self.d["M"], self.d["P"])
+        c, d = self.ctx, self.d
+        if factored:
+            L.op2b_jacobi_sums(c, self.a_jsum, self.gamma, L.ZERO_INC)
+            L.op2b_jacobi_from_sums(c, d["q"], d["JS"], d["M"], d["P"], self.gamma)
+            return
+        L.op2b_jacobi_blocks(c, self.a_jac, self.gamma, L.ZERO_INC)
+        L.op2b_block_invert(c, d["M"], d["P"])
 
     def update(self, alpha, mixed=False, ff=False, sigma=None):
         """q = q0 - alpha (dt/V) R, or with ``sigma`` the block-Jacobi

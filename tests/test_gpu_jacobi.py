@@ -38,14 +38,30 @@ def test_blocks_and_inverses_match_oracle(gpu_lib, mesh, strat, block, part, ren
     P, bad = oracle.block_invert(M)
     assert bad == 0
     s = make(m, q, renumber=renumber)
-    s.set_strategy(gpu_lib.LOOP_JACOBI, 0, strat, block, part, 0)
-    s.precondition()
+    for loop in (gpu_lib.LOOP_JACOBI, gpu_lib.LOOP_JACOBI_SUMS):
+        s.set_strategy(loop, 0, strat, block, part, 0)
+    # the 36-value edge loop, then the inversion loop
+    s.precondition(factored=False)
     assert s.plan_stats(gpu_lib.LOOP_JACOBI, 0)["strategy"] == strat
     assert blockwise(s.fetch_nodes("M"), M) <= 1e-13
     assert blockwise(s.fetch_nodes("P"), P) <= 1e-12
     # without ZERO_INC the blocks are added
     gpu_lib.op2b_jacobi_blocks(s.ctx, s.a_jac, s.gamma, 0)
     assert blockwise(s.fetch_nodes("M"), 2 * M) <= 1e-13
+    # factored: four sums per node, one pass forming and inverting the blocks
+    s.t["M"].zero_()
+    s.t["P"].zero_()
+    s.precondition()
+    assert s.plan_stats(gpu_lib.LOOP_JACOBI_SUMS, 0)["strategy"] == strat
+    assert blockwise(s.fetch_nodes("M"), M) <= 1e-13
+    assert blockwise(s.fetch_nodes("P"), P) <= 1e-12
+    lam = oracle.spectral_radius(m.edge, q, m.normal)
+    JS = s.fetch_nodes("JS")
+    assert np.max(np.abs(JS[:, 0] - lam) / lam) <= 1e-14
+    # P alone (M skipped)
+    s.t["P"].zero_()
+    gpu_lib.op2b_jacobi_from_sums(s.ctx, s.d["q"], s.d["JS"], -1, s.d["P"], s.gamma)
+    assert blockwise(s.fetch_nodes("P"), P) <= 1e-12
     s.close()
 
 
@@ -128,4 +144,10 @@ def test_jacobi_argument_checks(gpu_lib, mesh):
     with pytest.raises(L.Op2bError) as e:
         L.op2b_node_update_precond(s.ctx, s.d["q0"], s.d["R"], s.d["R"], s.d["P"], 0.1)
     assert e.value.code == L.EINVAL
+    for args, code in (((s.d["q"], s.d["M"], s.d["M"], s.d["P"]), L.EDIM),
+                       ((s.d["q"], s.d["JS"], s.d["P"], s.d["P"]), L.EINVAL),
+                       ((s.d["q32"], s.d["JS"], s.d["M"], -1), L.ETYPE)):
+        with pytest.raises(L.Op2bError) as e:
+            L.op2b_jacobi_from_sums(s.ctx, *args, s.gamma)
+        assert e.value.code == code
     s.close()

@@ -321,21 +321,21 @@ static int reduce_op(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, do
 }
 
 // Block-Jacobi inverse: p = m^{-1} (6 x 6, row-major) by Gauss-Jordan
-// elimination on [m | I] with partial pivoting, every index a compile-time
-// constant (the row exchange is done with selects), so the 72 values stay
-// in registers.
+// elimination with partial pivoting (the largest |pivot| of the column, the
+// first on ties), in place: the pivot column is replaced by the inverse's
+// column as it is eliminated (6 x 6 storage and 216 multiply-adds, half of
+// the eliminations on [m | I]), the row exchanges are undone on the columns
+// at the end.  Every index is a compile-time constant (exchanges are done
+// with selects), so the values stay in registers.
 __device__ __forceinline__ void gj_invert6(const double* m, double* p) {
-  double a[6][12];
+  double a[6][6];
 #pragma unroll
   for (int r = 0; r < 6; r++)
 #pragma unroll
-    for (int c = 0; c < 6; c++) {
-      a[r][c] = m[6 * r + c];
-      a[r][6 + c] = r == c ? 1.0 : 0.0;
-    }
+    for (int c = 0; c < 6; c++) a[r][c] = m[6 * r + c];
+  int pv[6];
 #pragma unroll
   for (int k = 0; k < 6; k++) {
-    // the largest |a[r][k]| for r >= k, the first on ties
     int piv = k;
     double best = fabs(a[k][k]);
 #pragma unroll
@@ -344,31 +344,49 @@ __device__ __forceinline__ void gj_invert6(const double* m, double* p) {
       piv = v > best ? r : piv;
       best = v > best ? v : best;
     }
+    pv[k] = piv;
 #pragma unroll
     for (int r = k + 1; r < 6; r++) {
       const bool sw = piv == r;
 #pragma unroll
-      for (int c = 0; c < 12; c++) {
+      for (int c = 0; c < 6; c++) {
         const double t = a[k][c];
         a[k][c] = sw ? a[r][c] : t;
         a[r][c] = sw ? t : a[r][c];
       }
     }
     const double inv = 1.0 / a[k][k];
+    a[k][k] = 1.0;
 #pragma unroll
-    for (int c = 0; c < 12; c++) a[k][c] *= inv;
+    for (int c = 0; c < 6; c++) a[k][c] *= inv;
 #pragma unroll
     for (int r = 0; r < 6; r++) {
       if (r == k) continue;
       const double f = a[r][k];
+      a[r][k] = 0.0;
 #pragma unroll
-      for (int c = 0; c < 12; c++) a[r][c] = fma(-f, a[k][c], a[r][c]);
+      for (int c = 0; c < 6; c++) a[r][c] = fma(-f, a[k][c], a[r][c]);
+    }
+  }
+  // undo the row exchanges on the columns, the last one first
+#pragma unroll
+  for (int kk = 0; kk < 6; kk++) {
+    const int k = 5 - kk;
+#pragma unroll
+    for (int c2 = 0; c2 < 6; c2++) {  // constant bounds keep a[][] in registers
+      const bool sw = c2 > k && pv[k] == c2;
+#pragma unroll
+      for (int r = 0; r < 6; r++) {
+        const double t = a[r][k];
+        a[r][k] = sw ? a[r][c2] : t;
+        a[r][c2] = sw ? t : a[r][c2];
+      }
     }
   }
 #pragma unroll
   for (int r = 0; r < 6; r++)
 #pragma unroll
-    for (int c = 0; c < 6; c++) p[6 * r + c] = a[r][6 + c];
+    for (int c = 0; c < 6; c++) p[6 * r + c] = a[r][c];
 }
 
 __global__ void k_block_invert(const double* __restrict__ M, int64_t ldM, double* __restrict__ P,

@@ -168,10 +168,9 @@ struct BodyJacobi {
   __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
                                        double* oi, double* oj) const {
     const double nv[3] = {ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e)};
-    const double nn2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
-    double f[6], lL, lR;
-    euler_side(vi, nv[0], nv[1], nv[2], nn2, g, f, lL);
-    euler_side(vj, nv[0], nv[1], nv[2], nn2, g, f, lR);
+    const double nn2 = fma(nv[2], nv[2], fma(nv[1], nv[1], nv[0] * nv[0]));
+    const double lL = wave_speed_f64(vi, nv[0], nv[1], nv[2], nn2, g);
+    const double lR = wave_speed_f64(vj, nv[0], nv[1], nv[2], nn2, g);
     const double hs = 0.5 * (lL >= lR ? lL : lR);
     flux_jacobian_f64(vi, nv, g, 0.5, oi);
     flux_jacobian_f64(vj, nv, g, -0.5, oj);
@@ -202,10 +201,9 @@ struct BodyJacobiSums {
   __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
                                        double* oi, double* oj) const {
     const double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
-    const double nn2 = nx * nx + ny * ny + nz * nz;
-    double f[6], lL, lR;
-    euler_side(vi, nx, ny, nz, nn2, g, f, lL);
-    euler_side(vj, nx, ny, nz, nn2, g, f, lR);
+    const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
+    const double lL = wave_speed_f64(vi, nx, ny, nz, nn2, g);
+    const double lR = wave_speed_f64(vj, nx, ny, nz, nn2, g);
     oi[0] = oj[0] = lL >= lR ? lL : lR;
     oi[1] = nx;
     oi[2] = ny;
@@ -234,10 +232,10 @@ struct BodySpectral {
   __device__ __forceinline__ void edge(int64_t e, const double* vi,
                                        const double* vj, double* oi,
                                        double*) const {
-    double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
-    double nn2 = nx * nx + ny * ny + nz * nz, f[6], lL, lR;
-    euler_side(vi, nx, ny, nz, nn2, g, f, lL);
-    euler_side(vj, nx, ny, nz, nn2, g, f, lR);
+    const double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
+    const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
+    const double lL = wave_speed_f64(vi, nx, ny, nz, nn2, g);
+    const double lR = wave_speed_f64(vj, nx, ny, nz, nn2, g);
     oi[0] = lL >= lR ? lL : lR;
   }
 };

@@ -294,6 +294,20 @@ __device__ __forceinline__ double rsqrt2(double x) {
   return fma(0.5 * r1, fma(-x * r1, r1, 1.0), r1);
 }
 
+// Largest wave speed |u.n| + a|n| of one state (a = sqrt(gamma p / rho),
+// nn2 = |n|^2) with the FP32-seeded Newton reciprocal and square root (full
+// double precision) where the arguments allow, else the IEEE operations.
+__device__ __forceinline__ double wave_speed_f64(const double* q, double nx, double ny,
+                                                 double nz, double nn2, const Gas<double>& g) {
+  const double rr = seedable(q[0]) ? recip2(q[0]) : 1.0 / q[0];
+  const double un = fma(q[3], nz, fma(q[2], ny, q[1] * nx)) * rr;
+  const double mm = fma(q[3], q[3], fma(q[2], q[2], q[1] * q[1]));
+  const double p = g.gm1 * fma(-0.5 * mm, rr, q[4]);
+  const double a2n = g.gamma * p * rr * nn2;
+  const double an = seedable(a2n) ? sqrt2(a2n) : sqrt(a2n);
+  return fabs(un) + an;
+}
+
 __device__ __forceinline__ bool exp_in_range(double x, int lim) {
   // |x| in [2^-lim, 2^lim] (x finite, nonzero)
   const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;

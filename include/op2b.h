@@ -576,8 +576,8 @@ int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const double* n,
                             void* stream);
 
 /* ------------------------------------------ owner-compute partitions
- * The paper's distributed-memory execution (Sec. 3; Sec. 4 "OP2 ... an
- * owner-compute model similar to that used in OPlus"): the nodes are split
+ * The paper's distributed-memory execution (Sec. 3.2: OP2's MPI back-end
+ * follows OPlus's owner-compute model; Sec. 2: OPlus's halo updates): the nodes are split
  * into parts; a part owns its nodes, executes every edge with an owned end
  * (a cut edge runs in both of its parts) and, before a loop reads node data
  * through the map, refreshes its halo -- the non-owned ends of its edges --
@@ -585,7 +585,7 @@ int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const double* n,
  * nodes; halo rows hold partial sums and are overwritten by the next
  * exchange.
  *
- * Recursive coordinate bisection into nparts parts (Sec. 5: the mesh's 3-D
+ * Recursive coordinate bisection into nparts parts (Sec. 4: the mesh's 3-D
  * coordinates are split in x, y and z in turn until there is one part per
  * process).  xyz: host, N x 3 node-major.  part (host, N): part of each node.
  * A range meant for k parts is ordered by (coordinate on axis depth mod 3,
@@ -625,7 +625,7 @@ int op2b_halo_part(op2b_halo h, int32_t p, int32_t* nodes, int32_t* edges,
 int op2b_halo_destroy(op2b_halo h);
 
 /* Halo exchange of one dat between parts held on the context's GPU (the
- * op_access/halo update of Sec. 3, between parts in one device's memory):
+ * halo update of Sec. 2, between parts in one device's memory):
  * for every segment s (one per importer/owner pair) and entry k of it,
  * dst[s][c * dst_ld[s] + dst_idx[t]] = src[s][c * src_ld[s] + src_idx[t]]
  * for c < dim, t running over the entries of all segments in order

@@ -1,8 +1,8 @@
 // Owner-compute partitions of an edge mesh (the paper's distributed-memory
-// execution, Sec. 3: each process owns a part of the nodes, runs every edge
-// with an owned end and refreshes its halo -- the non-owned ends of those
-// edges -- from their owners before a loop reads them; Sec. 5: the parts
-// come from recursive coordinate bisection).
+// execution, Sec. 2 and 3.2: each process owns a part of the nodes, runs
+// every edge with an owned end and refreshes its halo -- the non-owned ends
+// of those edges -- from their owners before a loop reads them; Sec. 4: the
+// parts come from recursive coordinate bisection).
 //
 // Host side: RCB partitioning and the halo plan (local meshes, import and
 // export lists), exported as plain host functions.  Device side: the halo

@@ -63,12 +63,12 @@ void node_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
 void owner_csr(int64_t N, int64_t E, const int32_t* m0, const int32_t* m1,
                std::vector<int64_t>* ptr, std::vector<int32_t>* idx);
 
-// Owner-compute partitioning (the paper's distributed-memory model, Sec. 3:
+// Owner-compute partitioning (the paper's distributed-memory model, Sec. 2 and 3.2:
 // every partition owns a set of nodes, executes every edge that has an
 // owned end -- redundantly where an edge is cut -- and imports the halo,
 // the non-owned ends of those edges, from their owners).
 //
-// Recursive coordinate bisection into `nparts` parts (Sec. 5: the
+// Recursive coordinate bisection into `nparts` parts (Sec. 4: the
 // coordinates are split in x, y and z in turn until there are as many
 // parts as processes).  A range of nodes meant for k parts is ordered by
 // (coordinate on the axis of its depth, id) and cut after

@@ -1,8 +1,9 @@
 """Owner-compute execution of the edge loops over node partitions.
 
-The paper's distributed-memory back-end (Sec. 3, Sec. 4: an owner-compute
-model like OPlus's) splits the nodes into parts -- by recursive coordinate
-bisection in Sec. 5 -- and gives each part the edges with an owned end; a
+The paper's distributed-memory back-end (Sec. 3.2: an owner-compute model
+like OPlus's, whose halo updates Sec. 2 describes) splits the nodes into
+parts -- by recursive coordinate bisection in Sec. 4 -- and gives each part
+the edges with an owned end; a
 cut edge runs in both of its parts.  Before a loop reads node data through
 the map, a part refreshes its halo (the non-owned ends of its edges) from
 the owners; its INC results are then complete on its owned nodes.
@@ -41,7 +42,7 @@ def halo_plan(num_nodes, edge, part, nparts):
 
 
 def halo_stats(parts):
-    """Per-partition figures of the paper's halo table (Sec. 5): average
+    """Per-partition figures of the paper's halo table (Sec. 4.2): average
     number of neighbours a part exchanges with, average elements (nodes +
     edges) held per part, and the average share of halo elements (halo
     nodes + redundantly executed cut edges) in them."""

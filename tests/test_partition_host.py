@@ -28,7 +28,7 @@ def lattice_index(m, n):
 
 
 def test_rcb_splits_x_then_y_then_z(lib):
-    # Sec. 5: the coordinates are split in x, y and z in turn.  The lattice
+    # Sec. 4: the coordinates are split in x, y and z in turn.  The lattice
     # jitter (0.1) is below half the spacing, so the cuts fall between
     # lattice planes and the parts have a closed form.
     n = 8
@@ -121,7 +121,7 @@ def test_halo_plan_rejects_bad_input(lib):
 
 
 def test_halo_stats_on_the_lattice(lib):
-    # Sec. 5 (table of halo sizes): the share of halo elements grows with
+    # Sec. 4.2 (table of halo sizes): the share of halo elements grows with
     # the number of parts.  Split into octants, a part of the periodic
     # lattice reaches the 6 octants that differ from it in one or two
     # coordinates; the one opposite it in all three would need a

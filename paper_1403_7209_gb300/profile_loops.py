@@ -10,7 +10,8 @@ scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage), visc and
 visc32 (viscous node pass + edge loop, FP64 / FP32; not with adjoint),
 gg_ff, flux2_ff and ffstage (the float-float Green-Gauss + scaling, flux,
 and RK stage), adjoint_ff (the float-float flux adjoint with the FP64
-scaling and Green-Gauss adjoints).
+scaling and Green-Gauss adjoints), jacobi (the factored block-Jacobi blocks
+and their inverses).
 """
 from __future__ import annotations
 
@@ -42,7 +43,7 @@ def main():
     visc = any(nm.startswith("visc") for nm in names)
     s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber="rcm", mixed=True,
                    adjoint=not visc, viscous=(1e-3, 0.72, 1e-3) if visc else None,
-                   ff=not visc)
+                   ff=not visc, precond="jacobi" in names)
     if args.tune_cache and os.path.exists(args.tune_cache):
         L.op2b_load_tuning(s.ctx, args.tune_cache)
     for loop in range(L.NUM_LOOPS):
@@ -61,6 +62,7 @@ def main():
         "flux2_32": lambda: s.flux(2, mixed=True),
         "adjoint": lambda: s.adjoint(2, recompute_gradient=False),
         "adjoint_ff": lambda: s.adjoint(2, recompute_gradient=False, ff=True),
+        "jacobi": lambda: s.precondition(),
         "stage": lambda: s.stage(0.25),
         "visc": lambda: s.viscous_flux(zero=True),
         "visc32": lambda: s.viscous_flux(mixed=True, zero=True),

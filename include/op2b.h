@@ -290,17 +290,18 @@ int op2b_jacobi_sums(op2b_ctx ctx, const op2b_arg* args, int32_t nargs, double g
 int op2b_jacobi_from_sums(op2b_ctx ctx, op2b_dat q, op2b_dat S, op2b_dat M, op2b_dat P,
                           double gamma);
 
-/* P_i = M_i^{-1} for every node (direct loop): Gauss-Jordan elimination on
- * [M_i | I] with partial pivoting (largest |pivot| of the column, the first
- * on ties), in FP64 registers.  M, P: node dats, dim 36, F64, on one set, P
- * distinct from M.  A block with a zero pivot gets a non-finite P (no error
- * is reported for it). */
+/* P_i = M_i^{-1} for every node (direct loop): Gauss-Jordan elimination in
+ * place with partial pivoting (largest |pivot| of the column, the first on
+ * ties), in FP64 registers.  M, P: node dats, dim 36, F64, on one set, P
+ * distinct from M (else OP2B_EINVAL); M is not modified.  A block with a
+ * zero pivot gets a non-finite P (no error is reported for it). */
 int op2b_block_invert(op2b_ctx ctx, op2b_dat M, op2b_dat P);
 
 /* Preconditioned stage (direct loop): q = q0 - alpha_sigma P R per node
- * (P dim 36 as above; q0, q, R dim 6); all F64 on one set.  With P from
- * op2b_block_invert and alpha_sigma = alpha_k sigma this is the
- * block-Jacobi preconditioned form of op2b_node_update. */
+ * (P dim 36 as above; q0, q, R dim 6); all F64 on one set.  q may be q0;
+ * R must differ from q (else OP2B_EINVAL).  With P from op2b_block_invert
+ * and alpha_sigma = alpha_k sigma this is the block-Jacobi preconditioned
+ * form of op2b_node_update. */
 int op2b_node_update_precond(op2b_ctx ctx, op2b_dat q0, op2b_dat q, op2b_dat R, op2b_dat P,
                              double alpha_sigma);
 

@@ -52,6 +52,24 @@ int Ctx::need_scratch(size_t bytes, void** out) {
   return OP2B_OK;
 }
 
+int Ctx::need_aux(size_t bytes, void** out) {
+  if (bytes > aux_bytes) {
+    if (aux) {
+      cudaStreamSynchronize(stream);
+      cudaFree(aux);
+      aux = nullptr;
+      aux_bytes = 0;
+    }
+    if (cudaMalloc(&aux, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(OP2B_ENOMEM, "aux allocation of " + std::to_string(bytes) + " B failed");
+    }
+    aux_bytes = bytes;
+  }
+  *out = aux;
+  return OP2B_OK;
+}
+
 template <typename T>
 static int upload(Ctx* c, T** dst, const std::vector<T>& v) {
   size_t b = std::max<size_t>(1, v.size() * sizeof(T));
@@ -254,6 +272,7 @@ extern "C" int op2b_finalize(op2b_ctx h) {
   }
   for (auto& m : c.maps) cudaFree(m.dev);
   cudaFree(c.scratch);
+  cudaFree(c.aux);
   delete h;
   return OP2B_OK;
 }
@@ -833,6 +852,13 @@ static int jacobi_loop(op2b_ctx h, const op2b_arg* a, int32_t nargs, double gamm
   L.gamma = gamma;
   L.q = D(c, a[0]).ptr;
   L.ldq = D(c, a[0]).ld;
+  if (sums) {  // the sums need only each node's (u, a), formed once per node
+    void* W = nullptr;
+    if ((rc = c.need_aux((size_t)4 * std::max<int64_t>(ck.N, 1) * sizeof(double), &W))) return rc;
+    if ((rc = node_wave_prims(&c, (const double*)L.q, L.ldq, (double*)W, gamma, ck.N))) return rc;
+    L.q = W;
+    L.ldq = ck.N;
+  }
   L.n = D(c, a[2]).ptr;
   L.ldn = D(c, a[2]).ld;
   L.t0 = D(c, a[3]).ptr;
@@ -997,8 +1023,14 @@ extern "C" int op2b_spectral_radius(op2b_ctx h, const op2b_arg* a, int32_t nargs
   L.m0 = c.maps[ck.map].dev;
   L.m1 = c.maps[ck.map].dev + ck.E;
   L.gamma = gamma;
-  L.q = D(c, a[0]).ptr;
-  L.ldq = D(c, a[0]).ld;
+  // the edge loop reads each node's (u, a), formed once per node
+  void* W = nullptr;
+  if ((rc = c.need_aux((size_t)4 * std::max<int64_t>(ck.N, 1) * sizeof(double), &W))) return rc;
+  if ((rc = node_wave_prims(&c, (const double*)D(c, a[0]).ptr, D(c, a[0]).ld, (double*)W, gamma,
+                            ck.N)))
+    return rc;
+  L.q = W;
+  L.ldq = ck.N;
   L.n = D(c, a[2]).ptr;
   L.ldn = D(c, a[2]).ld;
   L.t0 = D(c, a[3]).ptr;

@@ -184,27 +184,25 @@ struct BodyJacobi {
 
 // Sums of the factored block-Jacobi blocks: (s, n) to the first end,
 // (s, -n) to the second, s the Rusanov wave speed of the two node states.
+// v = (u_x, u_y, u_z, a) of each node (the wave-primitive node pass).
 struct BodyJacobiSums {
   using TN = double;
   using TE = double;
   using TA = double;
-  static constexpr int NIN = 6, OUT = 4, MODE = MODE_GEN, DIM0 = 4;
-  const double* q;
-  int64_t ldq;
+  static constexpr int NIN = 4, OUT = 4, MODE = MODE_GEN, DIM0 = 4;
+  const double* w;
+  int64_t ldw;
   const double* n;
   int64_t ldn;
   Gas<double> g;
   __device__ __forceinline__ void load(int64_t i, double* v) const {
 #pragma unroll
-    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+    for (int k = 0; k < 4; k++) v[k] = ldro(w + k * ldw + i);
   }
   __device__ __forceinline__ void edge(int64_t e, const double* vi, const double* vj,
                                        double* oi, double* oj) const {
     const double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
-    const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
-    const double lL = wave_speed_f64(vi, nx, ny, nz, nn2, g);
-    const double lR = wave_speed_f64(vj, nx, ny, nz, nn2, g);
-    oi[0] = oj[0] = lL >= lR ? lL : lR;
+    oi[0] = oj[0] = edge_wave_speed(vi, vj, nx, ny, nz);
     oi[1] = nx;
     oi[2] = ny;
     oi[3] = nz;
@@ -214,29 +212,26 @@ struct BodyJacobiSums {
   }
 };
 
-// Spectral radius: s_e = max wave speed of the two node states, to both.// Spectral radius: s_e = max wave speed of the two node states, to both.
+// Spectral radius: s_e = max wave speed of the two node states, to both.
+// v = (u_x, u_y, u_z, a) of each node (the wave-primitive node pass).
 struct BodySpectral {
   using TN = double;
   using TE = double;
   using TA = double;
-  static constexpr int NIN = 6, OUT = 1, MODE = MODE_SYM, DIM0 = 1;
-  const double* q;
-  int64_t ldq;
+  static constexpr int NIN = 4, OUT = 1, MODE = MODE_SYM, DIM0 = 1;
+  const double* w;
+  int64_t ldw;
   const double* n;
   int64_t ldn;
   Gas<double> g;
   __device__ __forceinline__ void load(int64_t i, double* v) const {
 #pragma unroll
-    for (int k = 0; k < 6; k++) v[k] = ldro(q + k * ldq + i);
+    for (int k = 0; k < 4; k++) v[k] = ldro(w + k * ldw + i);
   }
   __device__ __forceinline__ void edge(int64_t e, const double* vi,
                                        const double* vj, double* oi,
                                        double*) const {
-    const double nx = ldro(n + e), ny = ldro(n + ldn + e), nz = ldro(n + 2 * ldn + e);
-    const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
-    const double lL = wave_speed_f64(vi, nx, ny, nz, nn2, g);
-    const double lR = wave_speed_f64(vj, nx, ny, nz, nn2, g);
-    oi[0] = lL >= lR ? lL : lR;
+    oi[0] = edge_wave_speed(vi, vj, ldro(n + e), ldro(n + ldn + e), ldro(n + 2 * ldn + e));
   }
 };
 

@@ -308,6 +308,17 @@ __device__ __forceinline__ double wave_speed_f64(const double* q, double nx, dou
   return fabs(un) + an;
 }
 
+// The larger wave speed of an edge from its two ends' (u_x, u_y, u_z, a):
+// max(|u_i.n| + a_i|n|, |u_j.n| + a_j|n|), ties to the first end.
+__device__ __forceinline__ double edge_wave_speed(const double* wi, const double* wj, double nx,
+                                                  double ny, double nz) {
+  const double nn2 = fma(nz, nz, fma(ny, ny, nx * nx));
+  const double nn = seedable(nn2) ? sqrt2(nn2) : sqrt(nn2);
+  const double lL = fma(wi[3], nn, fabs(fma(wi[2], nz, fma(wi[1], ny, wi[0] * nx))));
+  const double lR = fma(wj[3], nn, fabs(fma(wj[2], nz, fma(wj[1], ny, wj[0] * nx))));
+  return lL >= lR ? lL : lR;
+}
+
 __device__ __forceinline__ bool exp_in_range(double x, int lim) {
   // |x| in [2^-lim, 2^lim] (x finite, nonzero)
   const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;

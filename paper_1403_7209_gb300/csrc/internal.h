@@ -139,6 +139,8 @@ int node_limiter(Ctx* c, const DevSegPlan& sp, int kind, int type, const LimArgs
 int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,
                     int64_t N);
 int node_block_invert(Ctx* c, const double* M, int64_t ldM, double* P, int64_t ldP, int64_t N);
+// W = (u_x, u_y, u_z, a) per node from q (SoA, ld N), a = sqrt(gamma p / rho)
+int node_wave_prims(Ctx* c, const double* q, int64_t ldq, double* W, double gamma, int64_t N);
 int node_jacobi_from_sums(Ctx* c, const double* q, int64_t ldq, const double* S, int64_t ldS,
                           double* M, int64_t ldM, double* P, int64_t ldP, double gamma,
                           int64_t N);
@@ -181,6 +183,10 @@ struct Ctx {
   std::map<int, DevOwnPlan> oplans;                    // map
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  // node-pass results an edge loop reads (apart from `scratch`, which the
+  // loop's own strategy may use)
+  void* aux = nullptr;
+  size_t aux_bytes = 0;
   double tune_deadline_ms = 20000.0;
   int64_t launches = 0;
   std::map<std::string, Strategy> tuned;  // persistent table
@@ -193,6 +199,7 @@ struct Ctx {
   int launched(const char* what);
   // scratch of at least `bytes` (grows, never shrinks)
   int need_scratch(size_t bytes, void** out);
+  int need_aux(size_t bytes, void** out);
   // plans (built or rebuilt on demand)
   int block_plan(int map, int32_t part, DevBlockPlan** out);
   int seg_plan(int map, DevSegPlan** out);

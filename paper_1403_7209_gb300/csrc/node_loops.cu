@@ -479,6 +479,35 @@ int node_update_precond(Ctx* c, const double* q0, int64_t ld0, double* q, int64_
   return c->launched("update_precond");
 }
 
+// Per-node wave primitives for the wave-speed loops: u = m/rho and the
+// sound speed a = sqrt(gamma p / rho), so that an edge needs only
+// |u.n| + a|n| of each end (FP32-seeded Newton reciprocal and square root
+// where the arguments allow).
+__global__ void k_wave_prims(const double* __restrict__ q, int64_t ldq, double* __restrict__ W,
+                             double gamma, int64_t N) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = q[k * ldq + i];
+    const double rr = seedable(v[0]) ? recip2(v[0]) : 1.0 / v[0];
+    const double u0 = v[1] * rr, u1 = v[2] * rr, u2 = v[3] * rr;
+    const double mm = fma(v[3], v[3], fma(v[2], v[2], v[1] * v[1]));
+    const double p = (gamma - 1.0) * fma(-0.5 * mm, rr, v[4]);
+    const double a2 = gamma * p * rr;
+    W[i] = u0;
+    W[N + i] = u1;
+    W[2 * N + i] = u2;
+    W[3 * N + i] = seedable(a2) ? sqrt2(a2) : sqrt(a2);
+  }
+}
+
+int node_wave_prims(Ctx* c, const double* q, int64_t ldq, double* W, double gamma, int64_t N) {
+  if (N == 0) return OP2B_OK;
+  k_wave_prims<<<grid_for(c, N, 256), 256, 0, c->stream>>>(q, ldq, W, gamma, N);
+  return c->launched("wave_prims");
+}
+
 int node_reduce(Ctx* c, const double* x, int64_t ld, int dim, int64_t n, int op, double* out) {
   switch (op) {
     case OP2B_RED_SUM: return reduce_op<OP2B_RED_SUM>(c, x, ld, dim, n, out);

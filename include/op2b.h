@@ -185,7 +185,14 @@ typedef struct {
 int op2b_init(op2b_ctx* out, int32_t device, void* cuda_stream);
 /* Free every library-owned allocation of the context. */
 int op2b_finalize(op2b_ctx ctx);
-/* Launch subsequent work on another stream. */
+/* Launch subsequent work on another stream (a cudaStream_t; NULL is the
+ * legacy default stream).  The context's loops share its scratch buffers
+ * and plans, so the switch orders the new stream after the work already
+ * queued on the old one (an event recorded on the old stream, waited for on
+ * the new one): work the context launched before the call finishes before
+ * any it launches after.  Work that other code queues on the old stream
+ * later is not ordered.  OP2B_ECUDA if the event cannot be recorded or
+ * waited for; the context then keeps the old stream. */
 int op2b_set_stream(op2b_ctx ctx, void* cuda_stream);
 /* Text of the context's last error ("" if none).  Valid until the next
  * call on the context.  With ctx == NULL: the last init failure. */
@@ -560,14 +567,22 @@ int64_t op2b_launch_count(op2b_ctx ctx);
  * op2b_host_node_csr.  Launches on `stream` (a cudaStream_t) on the current
  * device and returns without waiting.
  *
+ * R must not share memory with q or n (OP2B_EINVAL): it is zeroed before
+ * the inputs are read.
+ *
  * Limits and sharing: E must not exceed OP2B_NOALLOC_MAX_EDGES (larger sets
  * give OP2B_ERANGE and launch nothing).  The scratch array (6 x that many
  * doubles, 12 MiB) exists once per device for the life of the process and
  * every call uses it, so calls whose work overlaps on the GPU (concurrent
- * streams, or several host threads) race on it; serialise them.  The first
- * call on a device looks up the array's device address (a runtime query that
- * allocates nothing) and caches it; make that first call before any stream
- * capture.  On error op2b_last_error(NULL) gives the reason. */
+ * streams, or several host threads) race on it; serialise them.  A device
+ * reserves the array when the library's module is loaded on it: under lazy
+ * module loading (the CUDA default) that is this entry point's first call
+ * on the device, under eager loading the creation of the CUDA context.  The
+ * first call also looks up the array's device address and caches it.  Make
+ * that first call at set-up -- before a memory pool takes the device's free
+ * memory (else the reservation can fail with OP2B_ECUDA) and before any
+ * stream capture; later calls allocate nothing.  On error
+ * op2b_last_error(NULL) gives the reason. */
 #define OP2B_NOALLOC_MAX_EDGES 262144
 int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const double* n,
                             int64_t ldn, const int32_t* edge_first,

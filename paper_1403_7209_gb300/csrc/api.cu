@@ -279,7 +279,27 @@ extern "C" int op2b_finalize(op2b_ctx h) {
 
 extern "C" int op2b_set_stream(op2b_ctx h, void* stream) {
   CTX_CHECK(h);
-  h->c.stream = (cudaStream_t)stream;
+  Ctx& c = h->c;
+  cudaStream_t ns = (cudaStream_t)stream;
+  if (ns == c.stream) return OP2B_OK;
+  // Every loop shares the context's scratch, aux buffer and plans: work
+  // launched on the new stream must not start before the work already
+  // queued on the old one, so the new stream waits for an event recorded on
+  // the old stream at the switch.
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(OP2B_ECUDA, "set_stream: event creation failed");
+  }
+  cudaError_t e = cudaEventRecord(ev, c.stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ns, ev, 0);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return c.fail(OP2B_ECUDA, std::string("set_stream: ordering after the old stream failed: ") +
+                                  cudaGetErrorString(e));
+  }
+  c.stream = ns;
   return OP2B_OK;
 }
 
@@ -579,12 +599,16 @@ std::string tune_key(const LoopLaunch& L, bool det) {
          ":E" + std::to_string(L.E) + (det ? ":det" : "");
 }
 
-// whether the Green-Gauss launch divides by the volumes itself (the node
-// gather writes each node's finished sums); otherwise the scaling loop runs
-// after it
-static bool gg_scale_fused(const LoopLaunch& L, const Strategy& s) {
-  return L.prec == OP2B_PREC_FF || s.strategy == OP2B_STRAT_GATHER;
+// whether the Green-Gauss launch writes every node's finished sums itself
+// (the node gather, and the node phase of the segmented strategy): its
+// targets then need no zeroing, and it divides by the volumes as it writes;
+// otherwise the scaling loop runs after it
+static bool gg_writes_all(const LoopLaunch& L, const Strategy& s) {
+  return L.loop == OP2B_LOOP_GREEN_GAUSS &&
+         (L.prec == OP2B_PREC_FF || s.strategy == OP2B_STRAT_GATHER ||
+          s.strategy == OP2B_STRAT_SEGMENTED);
 }
+static bool gg_scale_fused(const LoopLaunch& L, const Strategy& s) { return gg_writes_all(L, s); }
 
 static int launch_loop(Ctx& c, const LoopLaunch& L, const Strategy& s) {
   if (L.loop == OP2B_LOOP_VISCOUS) return launch_visc(&c, L, s);  // F64, F32 or FF
@@ -716,7 +740,16 @@ int autotune(Ctx& c, const LoopLaunch& L, size_t b0, size_t b1, size_t bd, bool 
     }
     cudaEventRecord(e0, c.stream);
     const int reps = 3;
-    for (int k = 0; k < reps && !r; k++) r = dispatch(c, T, s);
+    // the zeroing of the targets that run_loop does before this strategy is
+    // part of its cost
+    const bool zero = (L.flags & OP2B_ZERO_INC) && !gg_writes_all(L, s);
+    for (int k = 0; k < reps && !r; k++) {
+      if (zero) {
+        if (b0) cudaMemsetAsync(t0, 0, b0, c.stream);
+        if (b1) cudaMemsetAsync(t1, 0, b1, c.stream);
+      }
+      r = dispatch(c, T, s);
+    }
     cudaEventRecord(e1, c.stream);
     if (r) {
       rc = r;
@@ -781,10 +814,9 @@ int run_loop(Ctx& c, LoopLaunch& L, int flags, const DatRec* z0, const DatRec* z
     }
     s = best;
   }
-  // the Green-Gauss node gather writes every node's 18 sums, so its targets
-  // need no zeroing first
-  const bool writes_all = L.loop == OP2B_LOOP_GREEN_GAUSS && s.strategy == OP2B_STRAT_GATHER;
-  if ((flags & OP2B_ZERO_INC) && !writes_all) {
+  // the Green-Gauss node gather and segmented node phase write every node's
+  // 18 sums, so their targets need no zeroing first
+  if ((flags & OP2B_ZERO_INC) && !gg_writes_all(L, s)) {
     int rc;
     if (z0 && (rc = node_fill(&c, z0->ptr, z0->type, z0->ld, z0->dim, L.N, 0.0))) return rc;
     if (z1 && (rc = node_fill(&c, z1->ptr, z1->type, z1->ld, z1->dim, L.N, 0.0))) return rc;

@@ -790,12 +790,18 @@ __global__ void k_seg_edges(P ph, const int32_t* __restrict__ m0,
   }
 }
 
-// Phase 2 for bodies with a packed per-edge form.
+// Phase 2 for bodies with a packed per-edge form (Green-Gauss).  Every
+// node's sums are written once: added to the targets with `add`, else
+// written over them (no zeroing pass needed), and with `vol` multiplied by
+// the node's 1/V as they are written -- the gradient scaling fused into the
+// write, formed as the scaling loop forms it (1/V in FP64, then rounded to
+// the target type), so the result is bitwise the two loops'.
 template <class P>
 __global__ void k_seg_nodes_packed(const int64_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ ends, int64_t N,
                                    int64_t E, const typename P::TE* __restrict__ ebuf,
-                                   Targets<typename P::TA, P::DIM0> tg) {
+                                   Targets<typename P::TA, P::DIM0> tg,
+                                   const double* __restrict__ vol, bool add) {
   using TA = typename P::TA;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
@@ -811,10 +817,12 @@ __global__ void k_seg_nodes_packed(const int64_t* __restrict__ rowptr,
       copy16<typename P::TE, SP>(st, ebuf + (int64_t)(end >> 1) * SP);
       P::unpack_add([&](int c) { return st[c]; }, (end & 1) != 0, acc);
     }
+    const TA r = vol ? (TA)(1.0 / vol[i]) : TA(1);
 #pragma unroll
     for (int c = 0; c < P::OUT; c++) {
       TA* p = tg.at(c, i);
-      *p = *p + acc[c];
+      const TA v = add ? *p + acc[c] : acc[c];
+      *p = vol ? v * r : v;
     }
   }
 }

@@ -118,9 +118,10 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
       if ((rc = c->launched("segmented edges"))) return rc;
       int64_t gridn = std::min<int64_t>((L.N + block - 1) / block, cap);
       if (gridn == 0) return OP2B_OK;
-      if constexpr (HasPack<P>::value)
-        k_seg_nodes_packed<P><<<(unsigned)gridn, block, 0, c->stream>>>(sp->rowptr, sp->ends, L.N,
-                                                                       L.E, (const TE*)buf, tg);
+      if constexpr (HasPack<P>::value)  // writes every node (scaling fused when L.vol)
+        k_seg_nodes_packed<P><<<(unsigned)gridn, block, 0, c->stream>>>(
+            sp->rowptr, sp->ends, L.N, L.E, (const TE*)buf, tg, L.vol,
+            !(L.flags & OP2B_ZERO_INC));
       else
         k_seg_nodes<TE, typename P::TA, P::OUT, P::MODE, P::DIM0>
             <<<(unsigned)gridn, block, 0, c->stream>>>(sp->rowptr, sp->ends, L.N, L.E,

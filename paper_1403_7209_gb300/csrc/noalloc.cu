@@ -8,6 +8,7 @@
 // growable scratch buffer on demand, so they cannot serve these callers.
 // This entry point takes every input and the output from the caller and
 // keeps its per-edge scratch in a fixed array compiled into the library.
+#include <cstdint>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -21,8 +22,10 @@ namespace {
 constexpr int64_t kMaxEdges = OP2B_NOALLOC_MAX_EDGES;
 
 // Per-edge fluxes, 6 doubles per edge, edge-major (6 x kMaxEdges doubles =
-// 12 MiB).  Every GPU that loads the library reserves this array until the
-// process exits.
+// 12 MiB).  A GPU reserves this array when the module holding it is loaded
+// there -- at the first call on that device under lazy module loading (the
+// CUDA default), at context creation under eager loading -- and keeps it
+// until the process exits.
 static __device__ __align__(256) double g_flux_scratch[6 * kMaxEdges];
 
 std::mutex g_mu;
@@ -59,6 +62,18 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+// Do the byte ranges [a, a + na) and [b, b + nb) overlap?
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  if (!a || !b || na == 0 || nb == 0) return false;
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
+
+// bytes spanned by `dim` rows of `n` doubles at leading dimension ld
+size_t span(int dim, int64_t ld, int64_t n) {
+  return n > 0 ? ((size_t)(dim - 1) * (size_t)ld + (size_t)n) * sizeof(double) : 0;
+}
+
 }  // namespace
 
 extern "C" int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const double* n, int64_t ldn,
@@ -75,6 +90,11 @@ extern "C" int op2b_edge_flux1_noalloc(const double* q, int64_t ldq, const doubl
   if (ldq < N || ldR < N || ldn < E) return fail(OP2B_EINVAL, "leading dimension below the set size");
   if (N > 0 && (!q || !R || !rowptr)) return fail(OP2B_EINVAL, "null node pointer");
   if (E > 0 && (!n || !edge_first || !edge_second || !ends)) return fail(OP2B_EINVAL, "null edge pointer");
+  // R is zeroed before the edge phase reads q and n: an output that shares
+  // memory with an input would be read after it was overwritten
+  const size_t bR = span(6, ldR, N);
+  if (overlaps(R, bR, q, span(6, ldq, N)) || overlaps(R, bR, n, span(3, ldn, E)))
+    return fail(OP2B_EINVAL, "R overlaps q or n");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return fail(OP2B_ECUDA, "no current CUDA device");
   double* scratch = nullptr;

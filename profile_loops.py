@@ -1,6 +1,6 @@
 """Run selected loops of the library repeatedly on a lattice (for profilers).
 
-    python -m paper_1403_7209_gb300.profile_loops --n 60 --loops flux2,adjoint --reps 3
+    python profile_loops.py --n 60 --loops flux2,adjoint --reps 3
 
 Builds the n^3 lattice with RCM numbering, autotunes every loop once, then
 runs each requested loop `reps` times with a device synchronisation after
@@ -20,7 +20,7 @@ import json
 import os
 import sys
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():

@@ -122,3 +122,29 @@ def test_rcb_partition_order_is_spatially_local(lib):
     steps = np.linalg.norm(np.diff(m.coords[order], axis=0), axis=1)
     rand = np.linalg.norm(np.diff(m.coords, axis=0), axis=1)
     assert np.median(steps) < 0.25 * np.median(rand)
+
+
+def test_noalloc_argument_checks_need_no_device(lib):
+    """The allocation-free entry point rejects an output that overlaps an
+    input and an oversized edge set before it touches the GPU (the
+    addresses below are never dereferenced)."""
+    N, E, ld = 100, 900, 128
+    base = 1 << 40
+    q, n, R = base, base + (1 << 30), base + (2 << 30)
+    ok = dict(edge_first_ptr=base + (3 << 30), edge_second_ptr=base + (4 << 30),
+              rowptr_ptr=base + (5 << 30), ends_ptr=base + (6 << 30))
+
+    def call(q_ptr, n_ptr, R_ptr, e=E):
+        op2b.op2b_edge_flux1_noalloc(q_ptr, ld, n_ptr, 1024, ok["edge_first_ptr"],
+                                     ok["edge_second_ptr"], ok["rowptr_ptr"], ok["ends_ptr"],
+                                     N, e, 1.4, R_ptr, ld, 0)
+    # R's last row ends at 8 (5 ld + N) bytes past R: one byte into q is an overlap
+    for q_ptr, n_ptr, R_ptr in ((q, n, q), (q, n, n + 8 * 1024), (q + 8 * (5 * ld + N) - 8, n, q),
+                                (q, n, q - 8 * (5 * ld + N) + 8)):
+        with pytest.raises(op2b.Op2bError) as e:
+            call(q_ptr, n_ptr, R_ptr)
+        assert e.value.code == op2b.EINVAL
+        assert "overlaps" in op2b.op2b_last_error(None)
+    with pytest.raises(op2b.Op2bError) as e:
+        call(q, n, R, e=op2b.NOALLOC_MAX_EDGES + 1)
+    assert e.value.code == op2b.ERANGE

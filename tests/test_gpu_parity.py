@@ -98,8 +98,9 @@ def test_green_gauss_gather_matches_oracle(gpu_lib, mesh16, ref16, block, renumb
 def test_green_gauss_scaled_is_the_loop_then_the_scaling(gpu_lib, mesh16, ref16, prec, strat):
     """op2b_green_gauss_scaled gives the bits of op2b_green_gauss followed by
     op2b_grad_scale: fused into the node gather (7; the float-float loop,
-    prec 2), the scaling loop after the others (segmented 3, colour 2: both
-    in a fixed order, so bitwise comparable); with and without ZERO_INC."""
+    prec 2) and into the segmented strategy's node phase (3), the scaling
+    loop after the colour strategy (2) (all in a fixed order, so bitwise
+    comparable); with and without ZERO_INC."""
     import torch
     m, q = mesh16
     s = make_solver(gpu_lib, m, q, renumber="rcm", mixed=True, ff=True)
@@ -519,4 +520,30 @@ def test_irregular_graph_all_strategies(gpu_lib, renumber):
         s.residual(2, mixed=True)
         err = np.max(np.abs(s.fetch_nodes("R") - R), axis=0) / np.max(np.abs(R), axis=0)
         assert np.all(err <= 1e-5), (strat, err)
+    s.close()
+
+
+def test_stream_switch_orders_work_after_the_old_stream(gpu_lib, mesh16, ref16):
+    """op2b_set_stream between loops that share the context's scratch: the
+    first-order flux runs on stream a, the second-order residual on stream
+    b, whose segmented Green-Gauss loop grows the scratch buffer (10 instead
+    of 6 values per edge) while a's result is still being copied out."""
+    import torch
+    m, q = mesh16
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    s = make_solver(gpu_lib, m, q, stream=a)
+    for loop in (gpu_lib.LOOP_FLUX1, gpu_lib.LOOP_GREEN_GAUSS, gpu_lib.LOOP_FLUX2):
+        s.set_strategy(loop, 0, gpu_lib.STRAT_SEGMENTED, 256)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(a):
+        s.flux(1)
+        R1 = s.t["R"].clone()
+    gpu_lib.op2b_set_stream(s.ctx, b.cuda_stream)
+    with torch.cuda.stream(b):
+        s.residual(2)
+    torch.cuda.synchronize()
+    R1 = R1[:, :s.N].cpu().numpy().T
+    assert rel_err(R1, ref16["R1"], ref16["R1a"]) <= TOL
+    assert rel_err(s.fetch_nodes("R"), ref16["R2"], ref16["R2a"]) <= TOL
+    assert rel_err(s.fetch_nodes("G"), ref16["G"], ref16["Gabs"]) <= TOL
     s.close()

@@ -475,6 +475,49 @@ int op2b_viscous_prims(op2b_ctx ctx, op2b_dat q, op2b_dat G, op2b_dat W,
 int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
                       const op2b_visc_params* prm);
 
+/* ------------------------------------------- fused FP32-mixed RK stage
+ * One second-order explicit Runge-Kutta stage of Sec. 2's march -- the
+ * Green-Gauss edge loop with the gradient scaling, the van Albada-limited
+ * Rusanov flux edge loop and the node update (Table "loopperfmpi":
+ * accumedges, ifluxedge, updatek) -- in the FP32-mixed precision: FP32 node
+ * state, gradients, normals and flux arithmetic, FP64 residual and update.
+ * The same arithmetic as op2b_green_gauss_scaled + op2b_edge_flux (order 2)
+ * + op2b_node_update on F32 dats, fused into two node passes over packed
+ * FP32 node records (q then G, 96 bytes per node) that the library keeps
+ * between calls:
+ *   Green-Gauss: G_i = (1/V_i) sum over the node's edge ends of
+ *     (q_i + q_j) (x) (+-n_e/2), summed in FP32 (the same bits as the FP32
+ *     node gather);
+ *   flux and update: every edge end evaluates its edge's flux in the edge's
+ *     own orientation (so both ends compute the same bits and the residual
+ *     is exactly antisymmetric), the node sums them with Knuth's two-sum into
+ *     a pair of floats (the sum to about 2^-48 of its running magnitude),
+ *     converts the pair exactly to FP64 once: R_i; then
+ *     q_i = q0_i - alpha (dt_i / V_i) R_i in FP64.
+ * No atomics: the result is bitwise reproducible.
+ *
+ * map: the edge->node map (arity 2).  q0, q, V, dt: F64 node dats (dim 6,
+ * 6, 1, 1); q is read (as its FP32 record) and overwritten with the new
+ * state; q0 is read (and with OP2B_STAGE_STORE_Q0 overwritten by the new
+ * state too, which saves the copy that starts the next step).  n, dx: edge
+ * dats of dim 3, F64 or F32 (converted to FP32).  R: F64 node dat of dim 6
+ * receiving the residual, or -1.  G: F32 node dat of dim 18 receiving the
+ * scaled gradients, or -1.  gamma > 1, eps_lim > 0 as in op2b_flux_params.
+ *
+ * The records carry the state from one call to the next: the library packs
+ * them from q (and the edge geometry from n and dx) on the first call for a
+ * map, after a renumbering, when q, n or dx is a different dat or buffer,
+ * and whenever flags holds OP2B_STAGE_SYNC -- pass it after changing q, n
+ * or dx by any other means.  Library-owned memory per map: 24 bytes per
+ * edge end, 32 per edge, 192 per node.  Errors: OP2B_EINVAL (bad map, flag,
+ * q0 == q, coefficients), OP2B_ESET / OP2B_EDIM / OP2B_ETYPE (dats),
+ * OP2B_ENOMEM, OP2B_ECUDA. */
+#define OP2B_STAGE_SYNC 1
+#define OP2B_STAGE_STORE_Q0 2
+int op2b_stage_mixed(op2b_ctx ctx, op2b_map map, op2b_dat q0, op2b_dat q, op2b_dat V,
+                     op2b_dat dt, op2b_dat n, op2b_dat dx, op2b_dat R, op2b_dat G,
+                     double alpha, double gamma, double eps_lim, int32_t flags);
+
 /* ----------------------------------------------------------- node loops
  * Direct loops over the node set (no map). */
 

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libop2b.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "loops_f64.cu", "loops_f32.cu", "loops_ff.cu", "loops_adj.cu", "loops_visc.cu", "loops_lim.cu",
-           "node_loops.cu", "noalloc.cu", "halo.cu", "host_plan.cpp"]
+           "node_loops.cu", "stage32.cu", "noalloc.cu", "halo.cu", "host_plan.cpp"]
 
 
 def nvcc() -> str:

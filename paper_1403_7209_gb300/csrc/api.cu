@@ -270,6 +270,7 @@ extern "C" int op2b_finalize(op2b_ctx h) {
     cudaFree(kv.second.ptr);
     cudaFree(kv.second.idx);
   }
+  stage32_free_all(c);
   for (auto& m : c.maps) cudaFree(m.dev);
   cudaFree(c.scratch);
   cudaFree(c.aux);

@@ -64,6 +64,24 @@ struct DevOwnPlan {
   int32_t* idx = nullptr;  // E edges, grouped by lower-numbered end
 };
 
+// Packed FP32 records of the fused mixed-precision stage (stage32.cu), per
+// map: the edge ends' adjacency (other end and +-n/2 for the Green-Gauss
+// pass, other end and 2e + side for the flux pass), the edges' geometry
+// (n, dx; 32 bytes per edge) and two node-record buffers (q then G, 24
+// floats per node), the current one holding the state's FP32 copy.
+struct Stage32Plan {
+  uint64_t map_version = ~0ull;
+  int64_t N = 0, E = 0;
+  int4* adjn = nullptr;
+  int2* adje = nullptr;
+  float4* geo = nullptr;
+  float* rec[2] = {nullptr, nullptr};
+  int cur = 0;
+  // the dats the geometry and the records were packed from
+  const void *n_src = nullptr, *dx_src = nullptr, *q_src = nullptr;
+  int n_type = -1, dx_type = -1;
+};
+
 struct Strategy {
   int32_t strategy = OP2B_STRAT_ATOMIC;
   int32_t block = 256;
@@ -135,6 +153,9 @@ int node_minmax(Ctx* c, const DevSegPlan& sp, const int32_t* m0, const int32_t* 
                 int64_t N);
 int node_limiter(Ctx* c, const DevSegPlan& sp, int kind, int type, const LimArgs& a, int64_t N);
 
+// Frees every fused-stage plan of the context (stage32.cu).
+int stage32_free_all(Ctx& c);
+
 // Direct node loops (node_loops.cu).
 int node_grad_scale(Ctx* c, void* G, int type, int64_t ldG, const double* V,
                     int64_t N);
@@ -181,6 +202,7 @@ struct Ctx {
   std::map<std::pair<int, int>, DevBlockPlan> bplans;  // (map, part)
   std::map<int, DevSegPlan> splans;                    // map
   std::map<int, DevOwnPlan> oplans;                    // map
+  std::map<int, Stage32Plan> s32plans;                 // map
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   // node-pass results an edge loop reads (apart from `scratch`, which the

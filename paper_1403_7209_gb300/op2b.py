@@ -28,6 +28,7 @@ LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, LOOP_VISCOUS = 7, 8, 9, 10
 LOOP_FLUX2_PHI, LOOP_JACOBI, LOOP_JACOBI_SUMS, NUM_LOOPS = 11, 12, 13, 14
 LIM_BARTH_JESPERSEN, LIM_VENKATAKRISHNAN = 1, 2
 PREC_F64, PREC_F32, PREC_FF, NUM_PREC = 0, 1, 2, 3
+STAGE_SYNC, STAGE_STORE_Q0 = 1, 2
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
 STRAT_BLOCK_ATOMIC, STRAT_OWNER, STRAT_GATHER, STRAT_HYBRID = 5, 6, 7, 8
 ZERO_INC = 1
@@ -130,6 +131,8 @@ _SIGS = {
     "op2b_time_step": (ctypes.c_int, [_P, _I32, _I32, _D, _I32]),
     "op2b_node_update": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32,
                                         _D, _I32]),
+    "op2b_stage_mixed": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _I32, _I32, _I32,
+                                        _I32, _D, _D, _D, _I32]),
     "op2b_node_update_adjoint": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _I32, _D]),
     "op2b_dat_axpy": (ctypes.c_int, [_P, _I32, _D, _I32]),
     "op2b_dat_fill": (ctypes.c_int, [_P, _I32, _D]),
@@ -401,6 +404,14 @@ def op2b_time_step(ctx, V: int, lam: int, cfl: float, dt: int):
 def op2b_node_update(ctx, q0: int, q: int, R: int, V: int, dt: int,
                      alpha: float, q32: int = -1):
     _check(load().op2b_node_update(ctx, q0, q, R, V, dt, alpha, q32), ctx)
+
+
+def op2b_stage_mixed(ctx, map_: int, q0: int, q: int, V: int, dt: int, n: int, dx: int,
+                     R: int, G: int, alpha: float, gamma: float = 1.4, eps_lim: float = 1e-12,
+                     flags: int = 0):
+    """Fused FP32-mixed second-order RK stage (see op2b.h)."""
+    _check(load().op2b_stage_mixed(ctx, map_, q0, q, V, dt, n, dx, R, G, alpha, gamma,
+                                   eps_lim, flags), ctx)
 
 
 def op2b_node_update_adjoint(ctx, sbar: int, qbar: int, lam: int, V: int, dt: int,

@@ -6,7 +6,9 @@ Builds the n^3 lattice with RCM numbering, autotunes every loop once, then
 runs each requested loop `reps` times with a device synchronisation after
 each repetition, and prints one line per loop with its mean time (CUDA
 events).  Loops: gg, flux2, gg32, flux2_32, adjoint (flux adjoint +
-scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage), visc and
+scaling adjoint + Green-Gauss adjoint), stage (the FP64 RK stage), stage32
+(the FP32-mixed stage of separate loops), fused (the fused FP32-mixed stage,
+op2b_stage_mixed), visc and
 visc32 (viscous node pass + edge loop, FP64 / FP32; not with adjoint),
 gg_ff, flux2_ff and ffstage (the float-float Green-Gauss + scaling, flux,
 and RK stage), adjoint_ff (the float-float flux adjoint with the FP64
@@ -69,11 +71,15 @@ def main():
         "gg_ff": lambda: s.green_gauss(ff=True),
         "flux2_ff": lambda: s.flux(2, ff=True),
         "ffstage": lambda: s.stage(0.25, ff=True),
+        "stage32": lambda: s.stage(0.25, mixed=True),
+        "fused": lambda: s.stage_fused(0.25, residual=False),
     }
     if visc:
         s.green_gauss()
         s.sync_shadow()
         s.green_gauss(mixed=True)
+    if "fused" in names:
+        s.stage_fused(0.25, sync=True, residual=False)
     for nm in names:  # warm-up: tunes and builds plans
         run[nm]()
     torch.cuda.synchronize()

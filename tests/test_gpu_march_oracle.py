@@ -6,13 +6,15 @@ the initial state, CFL 0.5); its final state is cached on disk by
 ``oracle.march_cache`` (the cache key includes the oracle's source).
 
 Bars, normwise per component (max |q_gpu - q_ora| / max |q_ora|):
-- FP64 march: 250 x 1e-12 = 2.5e-10.  Each stage's residual matches the
-  oracle's to 1e-12 of the sum of absolute contributions (only the
-  summation order differs); with no amplification assumed, the 250 stages
-  add at most 250 such differences.
+- FP64 march: 1e-12, the relative bar of the FP64 loops against the oracle
+  applied to the state.  Each stage's residual matches the oracle's to
+  1e-12 of the sum of its absolute contributions (only the summation order
+  differs), and a stage moves the state by alpha (dt/V) R, a small fraction
+  of |q|, so the 250 stages' differences stay far inside it (measured
+  ~2e-15); a loose worst case, 250 x 1e-12, would allow 2.5e-10.
 - FP32-mixed march (FP32 node data, gradients, normals and flux arithmetic,
-  FP64 residual and update): 1e-5, the mixed path's residual bar, applied to
-  the state after the march.
+  FP64 residual and update), by the separate loops and by the fused stage:
+  1e-5, the mixed path's residual bar, applied to the state after the march.
 """
 import numpy as np
 import pytest
@@ -34,7 +36,7 @@ def oracle_state():
     return q
 
 
-def _march(gpu_lib, mixed, strategy=None):
+def _march(gpu_lib, mixed, strategy=None, fused=False):
     from paper_1403_7209_gb300.solver import EdgeSolver
     m = meshgen.lattice(N_SIDE)
     q = meshgen.flow_state(m)
@@ -45,7 +47,7 @@ def _march(gpu_lib, mixed, strategy=None):
             s.set_strategy(loop, prec, *strategy)
     s.time_step(0.5)
     for _ in range(STEPS):
-        s.step(order=2, mixed=mixed)
+        s.step(order=2, mixed=mixed, fused=fused)
     qg = s.fetch_nodes("q")
     s.close()
     return qg
@@ -69,3 +71,10 @@ def test_mixed_march_50_steps_within_bar_of_oracle(gpu_lib, oracle_state, strate
     err = _normwise(_march(gpu_lib, True, strategy), oracle_state)
     assert np.all(err <= BAR_MIXED), err
     assert np.max(err) > 0.0  # the FP32 arithmetic really ran
+
+
+def test_fused_mixed_march_50_steps_within_bar_of_oracle(gpu_lib, oracle_state):
+    """The fused FP32-mixed stage (op2b_stage_mixed) marched 50 steps."""
+    err = _normwise(_march(gpu_lib, True, fused=True), oracle_state)
+    assert np.all(err <= BAR_MIXED), err
+    assert np.max(err) > 0.0

@@ -505,15 +505,35 @@ int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  * scaled gradients, or -1.  gamma > 1, eps_lim > 0 as in op2b_flux_params.
  *
  * The records carry the state from one call to the next: the library packs
- * them from q (and the edge geometry from n and dx) on the first call for a
- * map, after a renumbering, when q, n or dx is a different dat or buffer,
- * and whenever flags holds OP2B_STAGE_SYNC -- pass it after changing q, n
- * or dx by any other means.  Library-owned memory per map: 24 bytes per
- * edge end, 32 per edge, 192 per node.  Errors: OP2B_EINVAL (bad map, flag,
- * q0 == q, coefficients), OP2B_ESET / OP2B_EDIM / OP2B_ETYPE (dats),
- * OP2B_ENOMEM, OP2B_ECUDA. */
+ * them from q on the first call for a map, after a renumbering, when q is a
+ * different buffer, and whenever flags holds OP2B_STAGE_SYNC -- pass it
+ * after changing q by any other means.  It packs the edge geometry (n and
+ * dx in FP32, 32 bytes per edge) on the first call, when n or dx is a
+ * different buffer or type, and with OP2B_STAGE_SYNC_MESH (after changing
+ * their values).
+ *
+ * Two forms of the passes, the same bits.  By default every edge end
+ * gathers its other node's record (three 32-byte loads) and its edge's
+ * geometry from global memory.  With OP2B_STAGE_STAGED the library plans,
+ * on the host at the first such call, blocks of B consecutive nodes (B =
+ * 128, else 64 or 32) and the distinct nodes each block's edge ends reach;
+ * where every such neighbourhood fits 100 KB of shared memory at 112 bytes
+ * per record, both passes run one CTA per node block that first copies the
+ * neighbourhood's records into shared memory (asynchronous copies), and the
+ * ends, laid out sliced-ELL, read the records there (the paper's staging of
+ * a block's indirect data, Sec. 4.1.2); elsewhere the flag has no effect.
+ * A numbering with compact blocks (recursive coordinate bisection) needs
+ * about 0.2 records per edge end; on GB300 the gathering form measured
+ * faster on the lattices tried, hence the default.
+ * Library-owned memory per map: 24 bytes per edge end, 32 per edge, 192 per
+ * node (plus 36 per end and the neighbourhood lists once staged).  Errors:
+ * OP2B_EINVAL (bad map, flag, q0 == q, coefficients), OP2B_ESET / OP2B_EDIM /
+ * OP2B_ETYPE (dats), OP2B_ENOMEM, OP2B_ECUDA. */
 #define OP2B_STAGE_SYNC 1
 #define OP2B_STAGE_STORE_Q0 2
+#define OP2B_STAGE_SYNC_MESH 4
+/* stage each node block's neighbourhood in shared memory (see above) */
+#define OP2B_STAGE_STAGED 8
 int op2b_stage_mixed(op2b_ctx ctx, op2b_map map, op2b_dat q0, op2b_dat q, op2b_dat V,
                      op2b_dat dt, op2b_dat n, op2b_dat dx, op2b_dat R, op2b_dat G,
                      double alpha, double gamma, double eps_lim, int32_t flags);

@@ -430,3 +430,64 @@ bool build_halo_plan(int64_t N, int64_t E, const int32_t* edge, const int32_t* p
 }
 
 }  // namespace op2b
+
+namespace op2b {
+
+void build_node_block_plan(int64_t N, const int32_t* m0, const int32_t* m1,
+                           const std::vector<int64_t>& rowptr, const std::vector<int32_t>& ends,
+                           int32_t B, NodeBlockPlan* out) {
+  NodeBlockPlan& p = *out;
+  p = NodeBlockPlan();
+  p.B = B;
+  p.nblocks = (N + B - 1) / B;
+  p.uoff.assign((size_t)p.nblocks + 1, 0);
+  p.lother.assign(ends.size(), 0);
+  std::vector<int64_t> stamp((size_t)N, -1);
+  std::vector<int32_t> local((size_t)N, 0);
+  std::vector<int32_t> extra;
+  for (int64_t b = 0; b < p.nblocks; b++) {
+    const int64_t n0 = b * B, n1 = std::min<int64_t>(N, n0 + B);
+    p.uoff[b] = (int64_t)p.uniq.size();
+    for (int64_t v = n0; v < n1; v++) {
+      stamp[v] = b;
+      local[v] = (int32_t)(v - n0);
+      p.uniq.push_back((int32_t)v);
+    }
+    extra.clear();
+    for (int64_t t = rowptr[n0]; t < rowptr[n1]; t++) {
+      const int32_t end = ends[t];
+      const int32_t j = (end & 1) ? m0[end >> 1] : m1[end >> 1];
+      if (stamp[j] != b) {
+        stamp[j] = b;
+        extra.push_back(j);
+      }
+    }
+    std::sort(extra.begin(), extra.end());
+    for (size_t k = 0; k < extra.size(); k++) {
+      local[extra[k]] = (int32_t)(n1 - n0 + k);
+      p.uniq.push_back(extra[k]);
+    }
+    for (int64_t t = rowptr[n0]; t < rowptr[n1]; t++) {
+      const int32_t end = ends[t];
+      p.lother[t] = local[(end & 1) ? m0[end >> 1] : m1[end >> 1]];
+    }
+    p.max_unique = std::max<int64_t>(p.max_unique, (int64_t)p.uniq.size() - p.uoff[b]);
+  }
+  p.uoff[p.nblocks] = (int64_t)p.uniq.size();
+  const int64_t nslices = (N + 31) / 32;
+  p.sell_off.assign((size_t)nslices + 1, 0);
+  for (int64_t sl = 0; sl < nslices; sl++) {
+    int64_t kmax = 0;
+    for (int64_t v = sl * 32; v < std::min<int64_t>(N, sl * 32 + 32); v++)
+      kmax = std::max<int64_t>(kmax, rowptr[v + 1] - rowptr[v]);
+    p.sell_off[sl + 1] = p.sell_off[sl] + 32 * kmax;
+  }
+  p.sell_end.assign((size_t)p.sell_off[nslices], -1);
+  for (int64_t v = 0; v < N; v++) {
+    const int64_t base = p.sell_off[v / 32] + (v % 32);
+    for (int64_t t = rowptr[v]; t < rowptr[v + 1]; t++)
+      p.sell_end[base + 32 * (t - rowptr[v])] = (int32_t)t;
+  }
+}
+
+}  // namespace op2b

@@ -96,6 +96,32 @@ struct HaloPart {
 bool build_halo_plan(int64_t N, int64_t E, const int32_t* edge, const int32_t* part,
                      int32_t nparts, std::vector<HaloPart>* out, std::string* err);
 
+// Node-block neighbourhoods (the staging plan of the fused mixed stage):
+// blocks of B consecutive nodes; per block the distinct nodes its nodes'
+// edge ends reach -- the block's own nodes first (local id = node - block
+// start), then the others in increasing id -- and per edge end (in the
+// node-sorted order of node_csr) the local id of the end's other node.
+//
+// The ends are also laid out sliced-ELL (slices of 32 consecutive nodes, one
+// per warp; B is a multiple of 32): the k-th end of the slice's lane l at
+// sell_off[slice] + 32 k + l, for k below the slice's largest degree, so
+// that a warp reads the k-th ends of its 32 nodes from consecutive
+// addresses; sell_end holds the end's index in the node-sorted order, -1
+// where a lane's node has fewer ends.
+struct NodeBlockPlan {
+  int32_t B = 0;
+  int64_t nblocks = 0;
+  int64_t max_unique = 0;
+  std::vector<int64_t> uoff;      // nblocks+1 offsets into uniq
+  std::vector<int32_t> uniq;      // global node ids
+  std::vector<int32_t> lother;    // per end: local id of the other node
+  std::vector<int64_t> sell_off;  // per slice (ceil(N/32)) + 1
+  std::vector<int32_t> sell_end;  // per slot: node-sorted end index or -1
+};
+void build_node_block_plan(int64_t N, const int32_t* m0, const int32_t* m1,
+                           const std::vector<int64_t>& rowptr, const std::vector<int32_t>& ends,
+                           int32_t B, NodeBlockPlan* out);
+
 // Hardware threads to use for host planning.
 int host_threads();
 

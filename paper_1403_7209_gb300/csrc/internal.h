@@ -65,10 +65,13 @@ struct DevOwnPlan {
 };
 
 // Packed FP32 records of the fused mixed-precision stage (stage32.cu), per
-// map: the edge ends' adjacency (other end and +-n/2 for the Green-Gauss
-// pass, other end and 2e + side for the flux pass), the edges' geometry
-// (n, dx; 32 bytes per edge) and two node-record buffers (q then G, 24
-// floats per node), the current one holding the state's FP32 copy.
+// map: the edge ends' adjacency in node-sorted order with the other node's
+// id (other end and +-n/2 for the Green-Gauss pass, other end and 2e + side
+// for the flux pass), the edges' geometry (n, dx; 32 bytes per edge) and two
+// node-record buffers (q then G, 24 floats per node), the current one
+// holding the state's FP32 copy.  Where the node-block staging plan fits
+// (staged), the same adjacency sliced-ELL with the other node's local id in
+// its block's neighbourhood.
 struct Stage32Plan {
   uint64_t map_version = ~0ull;
   int64_t N = 0, E = 0;
@@ -80,6 +83,19 @@ struct Stage32Plan {
   // the dats the geometry and the records were packed from
   const void *n_src = nullptr, *dx_src = nullptr, *q_src = nullptr;
   int n_type = -1, dx_type = -1;
+  // staging plan (blocks of B nodes and their neighbourhoods), built on
+  // the first call that asks for the staged passes
+  bool staging_planned = false;
+  bool staged = false;
+  int32_t B = 0;
+  int64_t nblocks = 0, max_unique = 0, nslots = 0;
+  int64_t* uoff = nullptr;      // nblocks+1
+  int32_t* uniq = nullptr;      // neighbourhood node ids
+  int32_t* lother = nullptr;    // per end (node-sorted): the other node's local id
+  int64_t* sell_off = nullptr;  // per 32-node slice + 1
+  int32_t* sell_end = nullptr;  // per slot: node-sorted end index or -1
+  int4* adjn_s = nullptr;       // sliced-ELL adjacency of the staged passes
+  int2* adje_s = nullptr;
 };
 
 struct Strategy {

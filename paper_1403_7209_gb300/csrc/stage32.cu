@@ -25,32 +25,29 @@
 //     node's edge ends of (q_i + q_j) (x) (+-n/2), written into the record's
 //     G part (and into an optional FP32 G dat);
 //   pass 2 (flux + update, 1 thread per node): for every edge end the edge's
-//     flux in its own orientation (first end, second end: the two ends of an
-//     edge compute bitwise the same value, so the residual stays exactly
-//     antisymmetric), summed with sign; then R_i in FP64 and
+//     flux with the node as the first end (the edge reversed at its second
+//     end, which gives bitwise minus the first end's value, so the residual
+//     stays exactly antisymmetric), summed; then R_i in FP64 and
 //     q_i = q0_i - alpha (dt_i / V_i) R_i, written to q (FP64), to the other
 //     record buffer's q part (FP32) and optionally to R and q0.
 #include <algorithm>
 #include <string>
 
 #include "edge_math.cuh"
+#include "f32x2.cuh"
+#include "host_plan.h"
 #include "internal.h"
 
 namespace op2b {
 
 namespace {
 
-constexpr int REC = 24;  // floats per node record: q (6) then G (18)
-
-// Knuth's two-sum: hi + lo += x with the rounding error of the addition
-// kept in lo (exact: s + err == hi + x)
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
-  const float s = hi + x;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (x - bb);
-  hi = s;
-  lo += err;
-}
+// floats per node record: q (6), then G dimension-major: dq_k/dx for
+// k = 0..5, then dq_k/dy, then dq_k/dz (so that the gradients of two
+// consecutive components are adjacent, as the paired FP32 instructions of
+// the flux pass want them)
+constexpr int REC = 24;
+constexpr int GX = 6, GY = 12, GZ = 18;
 
 template <typename T>
 __device__ __forceinline__ float f32_of(T x) {
@@ -75,6 +72,34 @@ __global__ void k_s32_adjacency(const int32_t* __restrict__ ends, int64_t nends,
     const float hx = f32_of(n[e]) * h, hy = f32_of(n[ldn + e]) * h, hz = f32_of(n[2 * ldn + e]) * h;
     adjn[t] = make_int4(j, __float_as_int(hx), __float_as_int(hy), __float_as_int(hz));
     adje[t] = make_int2(j, end);
+  }
+}
+
+// the staged passes' adjacency, sliced-ELL with local ids: for slot s with
+// node-sorted end t = sell_end[s] (-1: padding), adjn_s = {lother[t], +-n/2},
+// adje_s = {2 lother[t] + side, 2e + side}
+template <typename TN>
+__global__ void k_s32_adjacency_sell(const int32_t* __restrict__ sell_end, int64_t nslots,
+                                     const int32_t* __restrict__ ends,
+                                     const int32_t* __restrict__ lother,
+                                     const TN* __restrict__ n, int64_t ldn,
+                                     int4* __restrict__ adjn_s, int2* __restrict__ adje_s) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslots;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = sell_end[s];
+    if (t < 0) {
+      adjn_s[s] = make_int4(-1, 0, 0, 0);
+      adje_s[s] = make_int2(-1, 0);
+      continue;
+    }
+    const int32_t end = ends[t];
+    const int64_t e = end >> 1;
+    const bool second = end & 1;
+    const int32_t lj = lother[t];
+    const float h = second ? -0.5f : 0.5f;
+    const float hx = f32_of(n[e]) * h, hy = f32_of(n[ldn + e]) * h, hz = f32_of(n[2 * ldn + e]) * h;
+    adjn_s[s] = make_int4(lj, __float_as_int(hx), __float_as_int(hy), __float_as_int(hz));
+    adje_s[s] = make_int2(2 * lj + (int)second, end);
   }
 }
 
@@ -134,70 +159,376 @@ __global__ void __launch_bounds__(128) k_s32_green_gauss(
       acc[8] = fmaf(s2, hz, acc[8]);
     }
     const float r = (float)(1.0 / V[i]);
-    float* g = rec + i * REC + 6 + 9 * h;
+    float* g = rec + i * REC + k0;
 #pragma unroll
-    for (int c = 0; c < 9; c++) {
+    for (int c = 0; c < 9; c++) {  // c = 3 (k - k0) + d
       const float v = acc[c] * r;
-      g[c] = v;
+      g[GX + 6 * (c % 3) + c / 3] = v;
       if (Gout) Gout[(9 * h + c) * ldG + i] = v;
     }
   }
 }
 
+// 32 bytes (8 floats) from a 32-byte aligned address in one load
+__device__ __forceinline__ void ldg8(const float* __restrict__ p, float* v) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+        "=f"(v[7])
+      : "l"(p));
+}
+
+// a node record (96 bytes at a multiple of 96: 32-byte aligned) in three loads
 __device__ __forceinline__ void load_rec(const float* __restrict__ p, float* v) {
-  const float4* p4 = reinterpret_cast<const float4*>(p);
 #pragma unroll
-  for (int k = 0; k < REC / 4; k++) {
-    const float4 x = __ldg(p4 + k);
-    v[4 * k] = x.x;
-    v[4 * k + 1] = x.y;
-    v[4 * k + 2] = x.z;
-    v[4 * k + 3] = x.w;
+  for (int k = 0; k < 3; k++) ldg8(p + 8 * k, v + 8 * k);
+}
+
+__device__ __forceinline__ float rcp_f(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_f(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ f2 rcp2(f2 a) { return mk2(rcp_f(a.x), rcp_f(a.y)); }
+
+struct GasPairs {
+  f2 gm1, gamma, eps, two_eps;
+};
+
+// van Albada phi(a, b) = (a + b)(ab + eps) / (a^2 + (b^2 + 2 eps)) on two
+// components at once (b2e = b^2 + 2 eps); the quotient as the product with
+// the FP32 special-function reciprocal
+__device__ __forceinline__ f2 van_albada2(f2 a, f2 b, f2 eps, f2 b2e) {
+  const f2 num = mul2(add2(a, b), fma2(a, b, eps));
+  return mul2(num, rcp2(fma2(a, a, b2e)));
+}
+
+// The second-order flux of one edge in FP32 on paired instructions: the
+// limited reconstruction on component pairs (0,1), (2,3), (4,5), the Euler
+// fluxes of the two face states on (left, right) pairs, the Rusanov
+// combination per component.  va / vb: the first and the second end's
+// records (q, then G dimension-major); g0 = (n, dx_x), g1 = (dx_y, dx_z).
+__device__ __forceinline__ void flux2_pairs(const float* va, const float* vb, float4 g0,
+                                            float4 g1, GasPairs g, float* F) {
+  const f2 dx2 = splat2(g0.w), dy2 = splat2(g1.x), dz2 = splat2(g1.y);
+  float qL[6], qR[6];
+#pragma unroll
+  for (int k = 0; k < 6; k += 2) {
+    const f2 a = mk2(va[k], va[k + 1]), b = mk2(vb[k], vb[k + 1]);
+    const f2 jump = sub2(b, a);
+    const f2 ai = fma2(mk2(va[GZ + k], va[GZ + k + 1]), dz2,
+                       fma2(mk2(va[GY + k], va[GY + k + 1]), dy2,
+                            mul2(mk2(va[GX + k], va[GX + k + 1]), dx2)));
+    const f2 aj = fma2(mk2(vb[GZ + k], vb[GZ + k + 1]), dz2,
+                       fma2(mk2(vb[GY + k], vb[GY + k + 1]), dy2,
+                            mul2(mk2(vb[GX + k], vb[GX + k + 1]), dx2)));
+    const f2 b2e = fma2(jump, jump, g.two_eps);
+    const f2 l = fma2(splat2(0.5f), van_albada2(ai, jump, g.eps, b2e), a);
+    const f2 r = fma2(splat2(-0.5f), van_albada2(aj, jump, g.eps, b2e), b);
+    qL[k] = l.x;
+    qL[k + 1] = l.y;
+    qR[k] = r.x;
+    qR[k + 1] = r.y;
+  }
+  // Euler flux f(q).n and wave speed |u.n| + a|n| of both face states
+  const float nx = g0.x, ny = g0.y, nz = g0.z;
+  const float nn2 = fmaf(nz, nz, fmaf(ny, ny, nx * nx));
+  const f2 rho = mk2(qL[0], qR[0]), m1 = mk2(qL[1], qR[1]), m2 = mk2(qL[2], qR[2]);
+  const f2 m3 = mk2(qL[3], qR[3]), en = mk2(qL[4], qR[4]), cs = mk2(qL[5], qR[5]);
+  const f2 rr = rcp2(rho);
+  const f2 nx2 = splat2(nx), ny2 = splat2(ny), nz2 = splat2(nz);
+  const f2 un = mul2(fma2(m3, nz2, fma2(m2, ny2, mul2(m1, nx2))), rr);
+  const f2 mm = fma2(m3, m3, fma2(m2, m2, mul2(m1, m1)));
+  const f2 p = mul2(g.gm1, fma2(mul2(splat2(-0.5f), mm), rr, en));
+  const f2 a2n = mul2(mul2(mul2(g.gamma, p), rr), splat2(nn2));
+  const float lL = fabsf(un.x) + sqrt_f(a2n.x), lR = fabsf(un.y) + sqrt_f(a2n.y);
+  const float hs = 0.5f * (lL >= lR ? lL : lR);
+  const f2 f0 = mul2(rho, un);
+  const f2 f1 = fma2(m1, un, mul2(p, nx2));
+  const f2 f2_ = fma2(m2, un, mul2(p, ny2));
+  const f2 f3 = fma2(m3, un, mul2(p, nz2));
+  const f2 f4 = mul2(add2(en, p), un);
+  const f2 f5 = mul2(cs, un);
+  const f2 f[6] = {f0, f1, f2_, f3, f4, f5};
+#pragma unroll
+  for (int k = 0; k < 6; k++) F[k] = fmaf(-hs, qR[k] - qL[k], 0.5f * (f[k].x + f[k].y));
+}
+
+// Pass 2: every edge end evaluates its edge's flux with its own node as the
+// first end -- for a node that is the edge's second end the edge reversed:
+// n -> -n, dx -> -dx, which gives exactly -F of the edge's own orientation
+// (every operation of the flux is odd or even in those signs and rounds
+// symmetrically), the second end's share -- so the node's record is loaded
+// once and no operand is selected.  The shares are summed with two-sum
+// pairs, then the FP64 residual and the node update.
+
+// one edge end: the node's record vi, the other end's record vj, the edge
+// geometry (n, dx; 32 bytes) and the end's side; adds the share to (hi, lo)
+// an edge's geometry (n, dx) as two 16-byte words, loaded in one 32-byte load
+struct Geo {
+  float4 a, b;
+};
+__device__ __forceinline__ Geo ldg_geo(const float* __restrict__ p) {
+  Geo g;
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(g.a.x), "=f"(g.a.y), "=f"(g.a.z), "=f"(g.a.w), "=f"(g.b.x), "=f"(g.b.y),
+        "=f"(g.b.z), "=f"(g.b.w)
+      : "l"(p));
+  return g;
+}
+
+__device__ __forceinline__ void flux_end_g(const float* vi, const float* vj, Geo gv,
+                                           bool second, GasPairs gas, f2* hi, f2* lo) {
+  float4 g0 = gv.a, g1 = make_float4(gv.b.x, gv.b.y, 0.f, 0.f);
+  if (second) {  // the edge reversed
+    g0 = make_float4(neg(g0.x), neg(g0.y), neg(g0.z), neg(g0.w));
+    g1 = make_float4(neg(g1.x), neg(g1.y), 0.0f, 0.0f);
+  }
+  float F[6];
+  flux2_pairs(vi, vj, g0, g1, gas, F);
+#pragma unroll
+  for (int k = 0; k < 3; k++) two_sum_acc2(hi[k], lo[k], mk2(F[2 * k], F[2 * k + 1]));
+}
+
+__device__ __forceinline__ void flux_end(const float* vi, const float* vj,
+                                         const float* __restrict__ geo_e, bool second,
+                                         const GasPairs& gas, f2* hi, f2* lo) {
+  flux_end_g(vi, vj, ldg_geo(geo_e), second, gas, hi, lo);
+}
+
+// R_i from the pair sums (each float converted exactly, one FP64 add) and the
+// update of components [k0, k1) of node i
+__device__ __forceinline__ void finish_node(int64_t i, const f2* hi, const f2* lo, int k0, int k1,
+                                            float* __restrict__ rout, double* __restrict__ q0,
+                                            int64_t ld0, double* __restrict__ q, int64_t ldq,
+                                            const double* __restrict__ V,
+                                            const double* __restrict__ dt, double alpha,
+                                            double* __restrict__ R, int64_t ldR, bool store_q0) {
+  const double a = alpha * (dt[i] / V[i]);
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    if (k < k0 || k >= k1) continue;
+    const float h = k & 1 ? hi[k >> 1].y : hi[k >> 1].x;
+    const float l = k & 1 ? lo[k >> 1].y : lo[k >> 1].x;
+    const double Rk = to_acc<double>(h) + to_acc<double>(l);
+    const double v = q0[k * ld0 + i] - a * Rk;
+    q[k * ldq + i] = v;
+    rout[i * REC + k] = (float)v;
+    if (R) R[k * ldR + i] = Rk;
+    if (store_q0) q0[k * ld0 + i] = v;
   }
 }
 
-// Pass 2: the flux of every edge end in the edge's own orientation (the
-// FP32 reconstruction and Rusanov flux of the mixed flux loop), summed per
-// node with two-sum pairs, then the FP64 residual and the node update.
+// direct form: one thread per node, the other ends' records gathered from
+// global memory (adje.x = the other node's id)
 __global__ void __launch_bounds__(128) k_s32_flux_update(
     int64_t N, const int64_t* __restrict__ rowptr, const int2* __restrict__ adje,
-    const float4* __restrict__ geo, const float* __restrict__ rin, float* __restrict__ rout,
+    const float* __restrict__ geo, const float* __restrict__ rin, float* __restrict__ rout,
     double* __restrict__ q0, int64_t ld0, double* __restrict__ q, int64_t ldq,
     const double* __restrict__ V, const double* __restrict__ dt, double alpha,
-    double* __restrict__ R, int64_t ldR, bool store_q0, Gas<float> gas) {
+    double* __restrict__ R, int64_t ldR, bool store_q0, GasPairs gas) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float hi[6], lo[6];
+    float vi[REC];
+    load_rec(rin + i * REC, vi);
+    f2 hi[3], lo[3];
 #pragma unroll
-    for (int k = 0; k < 6; k++) hi[k] = lo[k] = 0.0f;
+    for (int k = 0; k < 3; k++) hi[k] = lo[k] = splat2(0.0f);
     const int64_t t1 = rowptr[i + 1];
     for (int64_t t = rowptr[i]; t < t1; t++) {
       const int2 a = __ldg(adje + t);
-      const int64_t e = a.y >> 1;
-      const bool second = a.y & 1;
-      const int64_t first_node = second ? (int64_t)a.x : i;
-      const int64_t second_node = second ? i : (int64_t)a.x;
-      float va[REC], vb[REC];
-      load_rec(rin + first_node * REC, va);
-      load_rec(rin + second_node * REC, vb);
-      const float4 g0 = __ldg(geo + 2 * e), g1 = __ldg(geo + 2 * e + 1);
-      float qL[6], qR[6], F[6];
-      reconstruct(va, vb, g0.w, g1.x, g1.y, gas, qL, qR);
-      rusanov(qL, qR, g0.x, g0.y, g0.z, gas, F);
-#pragma unroll
-      for (int k = 0; k < 6; k++) two_sum_acc(hi[k], lo[k], second ? neg(F[k]) : F[k]);
+      float vj[REC];
+      load_rec(rin + (int64_t)a.x * REC, vj);
+      flux_end(vi, vj, geo + 8 * (int64_t)(a.y >> 1), a.y & 1, gas, hi, lo);
     }
-    const double a = alpha * (dt[i] / V[i]);
+    finish_node(i, hi, lo, 0, 6, rout, q0, ld0, q, ldq, V, dt, alpha, R, ldR, store_q0);
+  }
+}
+
+// ------------------------------------------------------------ staged form
+// One CTA per block of B consecutive nodes, one thread per node.  The
+// records of the block's neighbourhood (its own nodes, then every other
+// node its ends reach: the node-block plan) are first copied into shared
+// memory by asynchronous 16-byte copies (cp.async: every copy in flight at
+// once, no register round trip), so that an end reads its other node's
+// record there -- each record is read from global memory once per block
+// instead of once per edge end.  The ends are read sliced-ELL (the k-th
+// ends of a warp's 32 nodes at consecutive addresses, coalesced) and carry
+// the other node's local id.  Several CTAs per SM overlap one block's
+// copies with another block's arithmetic.
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+constexpr int SREC4 = 7;  // 16-byte words per record slot in shared memory
+                          // (112 bytes: an odd multiple of 16, so that the
+                          // 16-byte reads of eight slots fall in different
+                          // bank groups)
+constexpr int SQ4 = 3;    // 16-byte words per q slot of the Green-Gauss pass
+
+// Pass 1, staged: q parts of the neighbourhood in shared memory; adjn_s =
+// {local id of the other node (-1: padding), +-n/2 (FP32 bits)} sliced-ELL.
+// The same operations in the same order as the direct form, so the same bits.
+__global__ void __launch_bounds__(128) k_s32_green_gauss_sell(
+    int64_t N, int32_t B, const int64_t* __restrict__ uoff, const int32_t* __restrict__ uniq,
+    const int64_t* __restrict__ sell_off, const int4* __restrict__ adjn_s,
+    float* __restrict__ rec, const double* __restrict__ V, float* __restrict__ Gout,
+    int64_t ldG) {
+  extern __shared__ float4 sq[];
+  const int64_t b = blockIdx.x;
+  const int64_t u0 = uoff[b];
+  const int U = (int)(uoff[b + 1] - u0);
+  for (int u = threadIdx.x; u < U; u += blockDim.x) {
+    const float* src = rec + (int64_t)uniq[u0 + u] * REC;
+    cp_async16(sq + u * SQ4, src);
+    cp_async8(sq + u * SQ4 + 1, src + 4);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int li = threadIdx.x;
+  const int64_t i = b * B + li;
+  if (li >= B || i >= N) return;
+  const float* sqf = reinterpret_cast<const float*>(sq);
+  float qi[6];
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-      const double Rk = to_acc<double>(hi[k]) + to_acc<double>(lo[k]);
-      const double v = q0[k * ld0 + i] - a * Rk;
-      q[k * ldq + i] = v;
-      rout[i * REC + k] = (float)v;
-      if (R) R[k * ldR + i] = Rk;
-      if (store_q0) q0[k * ld0 + i] = v;
+  for (int k = 0; k < 6; k++) qi[k] = sqf[li * 4 * SQ4 + k];
+  float acc[18];
+#pragma unroll
+  for (int c = 0; c < 18; c++) acc[c] = 0.0f;
+  const int64_t sl = i >> 5;
+  const int64_t base = sell_off[sl] + (i & 31);
+  const int K = (int)((sell_off[sl + 1] - sell_off[sl]) >> 5);
+  int4 a = K > 0 ? __ldg(adjn_s + base) : make_int4(-1, 0, 0, 0);
+  for (int k = 0; k < K; k++) {
+    const int4 an = k + 1 < K ? __ldg(adjn_s + base + 32 * (k + 1)) : make_int4(-1, 0, 0, 0);
+    if (a.x >= 0) {
+      const float* qj = sqf + a.x * 4 * SQ4;
+      const float h[3] = {__int_as_float(a.y), __int_as_float(a.z), __int_as_float(a.w)};
+#pragma unroll
+      for (int c = 0; c < 6; c++) {
+        const float sc = qi[c] + qj[c];
+#pragma unroll
+        for (int d = 0; d < 3; d++) acc[3 * c + d] = fmaf(sc, h[d], acc[3 * c + d]);
+      }
+    }
+    a = an;
+  }
+  const float r = (float)(1.0 / V[i]);
+  float gd[18];  // the record's G part, dimension-major: gd[6 d + k] = G[3 k + d]
+#pragma unroll
+  for (int c = 0; c < 18; c++) {  // c = 3 k + d
+    const float v = acc[c] * r;
+    gd[6 * (c % 3) + c / 3] = v;
+    if (Gout) Gout[c * ldG + i] = v;
+  }
+  // floats 6..23 of the record: one 8-byte and four 16-byte stores
+  float* g = rec + i * REC;
+  *reinterpret_cast<float2*>(g + GX) = make_float2(gd[0], gd[1]);
+#pragma unroll
+  for (int k = 0; k < 4; k++)
+    *reinterpret_cast<float4*>(g + GX + 2 + 4 * k) =
+        make_float4(gd[2 + 4 * k], gd[3 + 4 * k], gd[4 + 4 * k], gd[5 + 4 * k]);
+}
+
+// Pass 2, staged: records of the neighbourhood in shared memory; adje_s =
+// {2 (local id of the other node) + side (-1: padding), 2e + side}
+// sliced-ELL.  Two threads per node: the CTA's first B threads take the
+// node's even-numbered ends, the other B the odd ones (each warp still reads
+// the ends of 32 consecutive nodes from consecutive addresses); the second
+// half leaves its pair sums in shared memory and the first combines them
+// exactly (two-sum) and updates the node.  The other end's record is read
+// from shared memory where the arithmetic needs it (few registers, more
+// warps); each end's geometry is fetched one end ahead and its entry two
+// ahead, so that their latency hides behind the arithmetic of the current end.
+__global__ void __launch_bounds__(256, 3) k_s32_flux_update_sell(
+    int64_t N, int32_t B, const int64_t* __restrict__ uoff, const int32_t* __restrict__ uniq,
+    const int64_t* __restrict__ sell_off, const int2* __restrict__ adje_s,
+    const float* __restrict__ geo, const float* __restrict__ rin, float* __restrict__ rout,
+    double* __restrict__ q0, int64_t ld0, double* __restrict__ q, int64_t ldq,
+    const double* __restrict__ V, const double* __restrict__ dt, double alpha,
+    double* __restrict__ R, int64_t ldR, bool store_q0, GasPairs gas) {
+  extern __shared__ float4 srec[];
+  const int64_t b = blockIdx.x;
+  const int64_t u0 = uoff[b];
+  const int U = (int)(uoff[b + 1] - u0);
+  const float4* rin4 = reinterpret_cast<const float4*>(rin);
+  for (int f = threadIdx.x; f < 6 * U; f += blockDim.x) {
+    const int u = f / 6, k = f - 6 * u;
+    cp_async16(srec + u * SREC4 + k, rin4 + (int64_t)uniq[u0 + u] * (REC / 4) + k);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const float* sf = reinterpret_cast<const float*>(srec);
+  float* spart = reinterpret_cast<float*>(srec + U * SREC4);  // B x 12 floats
+  const int half = threadIdx.x >= B;
+  const int li = threadIdx.x - half * B;
+  const int64_t i = b * B + li;
+  const bool live = i < N;
+  f2 hi[3], lo[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) hi[k] = lo[k] = splat2(0.0f);
+  if (live) {
+    float vi[REC];
+    const float4* si = srec + li * SREC4;
+#pragma unroll
+    for (int k = 0; k < REC / 4; k++) {
+      const float4 x = si[k];
+      vi[4 * k] = x.x;
+      vi[4 * k + 1] = x.y;
+      vi[4 * k + 2] = x.z;
+      vi[4 * k + 3] = x.w;
+    }
+    const int64_t sl = i >> 5;
+    const int64_t base = sell_off[sl] + (i & 31);
+    const int K = (int)((sell_off[sl + 1] - sell_off[sl]) >> 5);
+    const int2 pad = make_int2(-1, 0);
+    int2 a0 = half < K ? __ldg(adje_s + base + 32 * half) : pad;
+    int2 a1 = half + 2 < K ? __ldg(adje_s + base + 32 * (half + 2)) : pad;
+    // padding entries (x < 0) read edge 0's geometry (in bounds), unused
+    Geo g0 = ldg_geo(geo + 8 * (int64_t)(a0.x >= 0 ? a0.y >> 1 : 0));
+    for (int k = half; k < K; k += 2) {
+      const int2 a2 = k + 4 < K ? __ldg(adje_s + base + 32 * (k + 4)) : pad;
+      const Geo g1 = ldg_geo(geo + 8 * (int64_t)(a1.x >= 0 ? a1.y >> 1 : 0));
+      if (a0.x >= 0) flux_end_g(vi, sf + (a0.x >> 1) * 4 * SREC4, g0, a0.x & 1, gas, hi, lo);
+      a0 = a1;
+      a1 = a2;
+      g0 = g1;
+    }
+    if (half) {
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        spart[li * 12 + 4 * k] = hi[k].x;
+        spart[li * 12 + 4 * k + 1] = hi[k].y;
+        spart[li * 12 + 4 * k + 2] = lo[k].x;
+        spart[li * 12 + 4 * k + 3] = lo[k].y;
+      }
     }
   }
+  __syncthreads();
+  if (half || !live) return;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {  // the two halves' pairs, combined exactly
+    const f2 oh = mk2(spart[li * 12 + 4 * k], spart[li * 12 + 4 * k + 1]);
+    const f2 ol = mk2(spart[li * 12 + 4 * k + 2], spart[li * 12 + 4 * k + 3]);
+    f2 h = hi[k], l = splat2(0.0f);
+    two_sum_acc2(h, l, oh);
+    hi[k] = h;
+    lo[k] = add2(add2(lo[k], ol), l);
+  }
+  finish_node(i, hi, lo, 0, 6, rout, q0, ld0, q, ldq, V, dt, alpha, R, ldR, store_q0);
 }
 
 unsigned grid_of(const Ctx& c, int64_t work, int block) {
@@ -206,6 +537,13 @@ unsigned grid_of(const Ctx& c, int64_t work, int block) {
 }
 
 void free_stage32(Stage32Plan& p) {
+  cudaFree(p.uoff);
+  cudaFree(p.uniq);
+  cudaFree(p.lother);
+  cudaFree(p.sell_off);
+  cudaFree(p.sell_end);
+  cudaFree(p.adjn_s);
+  cudaFree(p.adje_s);
   cudaFree(p.adjn);
   cudaFree(p.adje);
   cudaFree(p.geo);
@@ -220,6 +558,16 @@ int alloc(Ctx& c, T** p, size_t count) {
     cudaGetLastError();
     return c.fail(OP2B_ENOMEM, "stage_mixed: allocation of the packed records failed");
   }
+  return OP2B_OK;
+}
+
+template <typename T>
+int upload(Ctx& c, T** p, const std::vector<T>& v) {
+  int rc = alloc(c, p, v.size());
+  if (rc) return rc;
+  if (!v.empty() && cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) !=
+                        cudaSuccess)
+    return c.fail(OP2B_ECUDA, "stage_mixed: upload of the staging plan failed");
   return OP2B_OK;
 }
 
@@ -238,11 +586,60 @@ int check_dat(Ctx& c, op2b_dat d, int dim, op2b_set set, bool f64_only, bool f32
   return OP2B_OK;
 }
 
+// shared memory per CTA of the staged passes for a neighbourhood of U nodes
+size_t smem_gg(int64_t U) { return (size_t)U * SQ4 * 16; }
+size_t smem_flux(int64_t U, int32_t B) { return (size_t)U * SREC4 * 16 + (size_t)B * 12 * 4; }
+// the staged passes run only where at least two CTAs fit on an SM
+constexpr size_t kStageSmemLimit = 100 * 1024;
+constexpr int kStageBlocks[3] = {128, 64, 32};
+
+// The node-block staging plan, on the host from the map in its current
+// numbering: the largest block size whose every neighbourhood fits
+// kStageSmemLimit, or none (p.staged stays false).
+int build_staging(Ctx& c, const MapRec& m, int64_t N, int64_t E, Stage32Plan& p) {
+  p.staged = false;
+  if (N == 0 || E == 0) return OP2B_OK;
+  std::vector<int32_t> m0((size_t)E), m1((size_t)E);
+  for (int64_t e = 0; e < E; e++) {
+    m0[e] = m.host[2 * e];
+    m1[e] = m.host[2 * e + 1];
+  }
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> ends;
+  node_csr(N, E, m0.data(), m1.data(), &rowptr, &ends);
+  NodeBlockPlan bp;
+  bool ok = false;
+  for (int B : kStageBlocks) {
+    build_node_block_plan(N, m0.data(), m1.data(), rowptr, ends, B, &bp);
+    if (smem_flux(bp.max_unique, B) <= kStageSmemLimit) {
+      ok = true;
+      break;
+    }
+  }
+  if (!ok) return OP2B_OK;
+  int rc;
+  if ((rc = upload(c, &p.uoff, bp.uoff)) || (rc = upload(c, &p.uniq, bp.uniq)) ||
+      (rc = upload(c, &p.lother, bp.lother)) || (rc = upload(c, &p.sell_off, bp.sell_off)) ||
+      (rc = upload(c, &p.sell_end, bp.sell_end)) ||
+      (rc = alloc(c, &p.adjn_s, bp.sell_end.size())) ||
+      (rc = alloc(c, &p.adje_s, bp.sell_end.size())))
+    return rc;
+  p.staged = true;
+  p.B = bp.B;
+  p.nblocks = bp.nblocks;
+  p.max_unique = bp.max_unique;
+  p.nslots = (int64_t)bp.sell_end.size();
+  return OP2B_OK;
+}
+
 template <typename TN>
 void launch_adjacency(Ctx& c, const DevSegPlan& sp, int64_t nends, const int32_t* m0,
                       const int32_t* m1, const DatRec& n, Stage32Plan& p) {
   k_s32_adjacency<TN><<<grid_of(c, nends, 256), 256, 0, c.stream>>>(
       sp.ends, nends, m0, m1, (const TN*)n.ptr, n.ld, p.adjn, p.adje);
+  if (p.staged)
+    k_s32_adjacency_sell<TN><<<grid_of(c, p.nslots, 256), 256, 0, c.stream>>>(
+        p.sell_end, p.nslots, sp.ends, p.lother, (const TN*)n.ptr, n.ld, p.adjn_s, p.adje_s);
 }
 
 template <typename TN, typename TD>
@@ -274,7 +671,7 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
   if (map < 0 || map >= (op2b_map)c.maps.size()) return c.fail(OP2B_EINVAL, "stage_mixed: bad map");
   MapRec& m = c.maps[map];
   if (m.arity != 2) return c.fail(OP2B_EINVAL, "stage_mixed: the map must have arity 2");
-  if (flags & ~(OP2B_STAGE_SYNC | OP2B_STAGE_STORE_Q0))
+  if (flags & ~(OP2B_STAGE_SYNC | OP2B_STAGE_STORE_Q0 | OP2B_STAGE_SYNC_MESH | OP2B_STAGE_STAGED))
     return c.fail(OP2B_EINVAL, "stage_mixed: unknown flag");
   if (!(gamma > 1.0) || !(eps_lim > 0.0) || !(alpha == alpha))
     return c.fail(OP2B_EINVAL, "stage_mixed: need gamma > 1, eps_lim > 0 and a finite alpha");
@@ -301,7 +698,7 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
     c.s32plans.erase(it);
     it = c.s32plans.end();
   }
-  bool sync_geo = (flags & OP2B_STAGE_SYNC) != 0, sync_q = sync_geo;
+  bool sync_geo = (flags & OP2B_STAGE_SYNC_MESH) != 0, sync_q = (flags & OP2B_STAGE_SYNC) != 0;
   if (it == c.s32plans.end()) {
     Stage32Plan p;
     p.map_version = m.version;
@@ -317,6 +714,12 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
     sync_geo = sync_q = true;
   }
   Stage32Plan& p = it->second;
+  if ((flags & OP2B_STAGE_STAGED) && !p.staging_planned) {
+    // the node-block staging plan, built on the first request
+    if ((rc = build_staging(c, m, N, E, p))) return rc;
+    p.staging_planned = true;
+    sync_geo = true;  // its adjacency is built with the geometry
+  }
   if (p.n_src != dn.ptr || p.n_type != dn.type || p.dx_src != ddx.ptr || p.dx_type != ddx.type)
     sync_geo = true;
   if (p.q_src != dq.ptr) sync_q = true;
@@ -344,18 +747,40 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
     if ((rc = c.launched("stage_mixed pack"))) return rc;
   }
   p.q_src = dq.ptr;
+  const bool staged = p.staged && (flags & OP2B_STAGE_STAGED);
   const DatRec* dG = G >= 0 ? &c.dats[G] : nullptr;
-  k_s32_green_gauss<<<grid_of(c, 2 * N, 128), 128, 0, c.stream>>>(
-      N, sp->rowptr, p.adjn, rin, (const double*)c.dats[V].ptr, dG ? (float*)dG->ptr : nullptr,
-      dG ? dG->ld : 0);
-  if ((rc = c.launched("stage_mixed green_gauss"))) return rc;
-  Gas<float> gas{(float)gamma, (float)(gamma - 1.0), (float)eps_lim, (float)(2.0 * eps_lim)};
+  float* pG = dG ? (float*)dG->ptr : nullptr;
+  const int64_t ldG = dG ? dG->ld : 0;
+  const double* pV = (const double*)c.dats[V].ptr;
+  const double* pdt = (const double*)c.dats[dt].ptr;
   const DatRec* dR = R >= 0 ? &c.dats[R] : nullptr;
+  double* pR = dR ? (double*)dR->ptr : nullptr;
+  const int64_t ldR = dR ? dR->ld : 0;
   const DatRec& d0 = c.dats[q0];
-  k_s32_flux_update<<<grid_of(c, N, 128), 128, 0, c.stream>>>(
-      N, sp->rowptr, p.adje, p.geo, rin, rout, (double*)d0.ptr, d0.ld, (double*)dq.ptr, dq.ld,
-      (const double*)c.dats[V].ptr, (const double*)c.dats[dt].ptr, alpha,
-      dR ? (double*)dR->ptr : nullptr, dR ? dR->ld : 0, (flags & OP2B_STAGE_STORE_Q0) != 0, gas);
+  const bool sq0 = (flags & OP2B_STAGE_STORE_Q0) != 0;
+  GasPairs gas{splat2((float)(gamma - 1.0)), splat2((float)gamma), splat2((float)eps_lim),
+               splat2((float)(2.0 * eps_lim))};
+  if (staged) {
+    const size_t s1 = smem_gg(p.max_unique), s2 = smem_flux(p.max_unique, p.B);
+    if (cudaFuncSetAttribute(k_s32_green_gauss_sell, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)s1) != cudaSuccess ||
+        cudaFuncSetAttribute(k_s32_flux_update_sell, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)s2) != cudaSuccess)
+      return c.fail(OP2B_ECUDA, "stage_mixed: cudaFuncSetAttribute failed");
+    k_s32_green_gauss_sell<<<(unsigned)p.nblocks, p.B, s1, c.stream>>>(
+        N, p.B, p.uoff, p.uniq, p.sell_off, p.adjn_s, rin, pV, pG, ldG);
+    if ((rc = c.launched("stage_mixed green_gauss"))) return rc;
+    k_s32_flux_update_sell<<<(unsigned)p.nblocks, 2 * p.B, s2, c.stream>>>(
+        N, p.B, p.uoff, p.uniq, p.sell_off, p.adje_s, (const float*)p.geo, rin, rout,
+        (double*)d0.ptr, d0.ld, (double*)dq.ptr, dq.ld, pV, pdt, alpha, pR, ldR, sq0, gas);
+  } else {
+    k_s32_green_gauss<<<grid_of(c, 2 * N, 128), 128, 0, c.stream>>>(N, sp->rowptr, p.adjn, rin,
+                                                                      pV, pG, ldG);
+    if ((rc = c.launched("stage_mixed green_gauss"))) return rc;
+    k_s32_flux_update<<<grid_of(c, N, 128), 128, 0, c.stream>>>(
+        N, sp->rowptr, p.adje, (const float*)p.geo, rin, rout, (double*)d0.ptr, d0.ld,
+        (double*)dq.ptr, dq.ld, pV, pdt, alpha, pR, ldR, sq0, gas);
+  }
   if ((rc = c.launched("stage_mixed flux_update"))) return rc;
   p.cur ^= 1;
   return OP2B_OK;

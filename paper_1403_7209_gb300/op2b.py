@@ -28,7 +28,7 @@ LOOP_FLUX1_TAN, LOOP_FLUX2_TAN, LOOP_GG_TAN, LOOP_VISCOUS = 7, 8, 9, 10
 LOOP_FLUX2_PHI, LOOP_JACOBI, LOOP_JACOBI_SUMS, NUM_LOOPS = 11, 12, 13, 14
 LIM_BARTH_JESPERSEN, LIM_VENKATAKRISHNAN = 1, 2
 PREC_F64, PREC_F32, PREC_FF, NUM_PREC = 0, 1, 2, 3
-STAGE_SYNC, STAGE_STORE_Q0 = 1, 2
+STAGE_SYNC, STAGE_STORE_Q0, STAGE_SYNC_MESH, STAGE_STAGED = 1, 2, 4, 8
 STRAT_AUTO, STRAT_ATOMIC, STRAT_COLOUR, STRAT_SEGMENTED, STRAT_AUTO_DET = 0, 1, 2, 3, 4
 STRAT_BLOCK_ATOMIC, STRAT_OWNER, STRAT_GATHER, STRAT_HYBRID = 5, 6, 7, 8
 ZERO_INC = 1

@@ -402,20 +402,24 @@ class EdgeSolver:
         self.residual(order, mixed, ff)
         self.update(alpha, mixed, ff, sigma)
 
-    def stage_fused(self, alpha, sync=False, residual=True, gradient=False, store_q0=False):
+    def stage_fused(self, alpha, sync=False, residual=True, gradient=False, store_q0=False,
+                    staged=False):
         """One fused FP32-mixed second-order stage (op2b_stage_mixed): q is
         advanced in place; R (with ``residual``) and G32 (with ``gradient``)
         are written too.  ``sync`` re-packs the library's FP32 records from
-        q, n and dx (needed after q was changed by anything but this call)."""
+        q (needed after q was changed by anything but this call); ``staged``
+        asks for the shared-memory staged form of the passes."""
         if self.visc is not None or LIMITERS[self.limiter]:
             raise NotImplementedError("the fused stage is the inviscid van Albada scheme")
         d = self.d
-        flags = (L.STAGE_SYNC if sync else 0) | (L.STAGE_STORE_Q0 if store_q0 else 0)
+        flags = ((L.STAGE_SYNC if sync else 0) | (L.STAGE_STORE_Q0 if store_q0 else 0)
+                 | (L.STAGE_STAGED if staged else 0))
         L.op2b_stage_mixed(self.ctx, self.map, d["q0"], d["q"], d["V"], d["dt"], d["n"], d["dx"],
                            d["R"] if residual else -1, d["G32"] if gradient else -1, alpha,
                            self.gamma, self.eps_lim, flags)
 
-    def step(self, order=2, mixed=False, stages=5, ff=False, sigma=None, fused=False):
+    def step(self, order=2, mixed=False, stages=5, ff=False, sigma=None, fused=False,
+             staged=False):
         """One explicit RK step (q0 <- q, then `stages` stages).  With
         ``sigma``: block-Jacobi preconditioned, the blocks formed from the
         step's initial state and kept for its stages.  With ``fused`` (the
@@ -426,7 +430,7 @@ class EdgeSolver:
             if order != 2 or ff or sigma is not None:
                 raise ValueError("the fused stage is the second-order FP32-mixed scheme")
             for k, a in enumerate(RK5_ALPHA[5 - stages:]):
-                self.stage_fused(a, sync=(k == 0), residual=False)
+                self.stage_fused(a, sync=(k == 0), residual=False, staged=staged)
             return
         if sigma is not None:
             self.precondition()

@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--loops", default="flux2")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--tune-cache", default="")
+    ap.add_argument("--numbering", default="rcm", choices=["rcm", "rcb", "random", "none"])
     ap.add_argument("--force", action="append", default=[],
                     help="fix a strategy instead of tuning: loop:prec:strategy:block:part:staged "
                          "(loop and strategy as numbers of include/op2b.h)")
@@ -43,7 +44,8 @@ def main():
     q = meshgen.flow_state(m)
     names = args.loops.split(",")
     visc = any(nm.startswith("visc") for nm in names)
-    s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber="rcm", mixed=True,
+    s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber=args.numbering, mixed=True,
+                   coords=m.coords,
                    adjoint=not visc, viscous=(1e-3, 0.72, 1e-3) if visc else None,
                    ff=not visc, precond="jacobi" in names)
     if args.tune_cache and os.path.exists(args.tune_cache):
@@ -73,6 +75,7 @@ def main():
         "ffstage": lambda: s.stage(0.25, ff=True),
         "stage32": lambda: s.stage(0.25, mixed=True),
         "fused": lambda: s.stage_fused(0.25, residual=False),
+        "fused_staged": lambda: s.stage_fused(0.25, residual=False, staged=True),
     }
     if visc:
         s.green_gauss()

@@ -25,7 +25,8 @@ def _normwise(x, ref):
 
 def _solver(m, q, renumber="rcm", **kw):
     from paper_1403_7209_gb300.solver import EdgeSolver
-    return EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber=renumber, mixed=True, **kw)
+    return EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, renumber=renumber, mixed=True,
+                      coords=m.coords, **kw)
 
 
 @pytest.fixture(scope="module")
@@ -41,14 +42,15 @@ def ref16(mesh16):
     return R, G, Ra
 
 
-@pytest.mark.parametrize("renumber", ["none", "rcm"])
-def test_fused_residual_and_gradient_match_oracle(gpu_lib, mesh16, ref16, renumber):
+@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+@pytest.mark.parametrize("renumber", ["none", "rcm", "rcb"])
+def test_fused_residual_and_gradient_match_oracle(gpu_lib, mesh16, ref16, renumber, staged):
     m, q = mesh16
     R_ora, G_ora, Ra = ref16
     s = _solver(m, q, renumber=renumber)
     gpu_lib.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
     s.time_step(0.5)
-    s.stage_fused(0.0, gradient=True)  # alpha = 0: q = q0, R and G of q
+    s.stage_fused(0.0, gradient=True, staged=staged)  # alpha = 0: q = q0, R and G of q
     R, G = s.fetch_nodes("R"), s.fetch_nodes("G32")
     assert np.all(_normwise(R, R_ora) <= BAR), _normwise(R, R_ora)
     assert np.max(_normwise(R, R_ora)) > 0.0  # computed in FP32
@@ -71,13 +73,19 @@ def test_fused_matches_separate_fp32_loops(gpu_lib, mesh16):
     s.sync_shadow()
     s.residual(2, mixed=True)
     G_sep, R_sep = s.t["G32"].clone(), s.t["R"].clone()
-    s.t["G32"].fill_(float("nan"))
-    s.stage_fused(0.0, sync=True, gradient=True)
-    torch.cuda.synchronize()
-    assert torch.equal(s.t["G32"], G_sep)  # the same FP32 gather, bit for bit
-    R = s.t["R"][:, :s.N].cpu().numpy().T
-    Rs = R_sep[:, :s.N].cpu().numpy().T
-    assert np.all(_normwise(R, Rs) <= 1e-6), _normwise(R, Rs)
+    Rf = {}
+    for staged in (True, False):
+        s.t["G32"].fill_(float("nan"))
+        s.stage_fused(0.0, sync=True, gradient=True, staged=staged)
+        torch.cuda.synchronize()
+        assert torch.equal(s.t["G32"], G_sep)  # the same FP32 gather, bit for bit
+        R = s.t["R"][:, :s.N].cpu().numpy().T
+        Rs = R_sep[:, :s.N].cpu().numpy().T
+        assert np.all(_normwise(R, Rs) <= 1e-6), _normwise(R, Rs)
+        Rf[staged] = R
+    # the staged form sums a node's ends in two interleaved halves: the
+    # pairs hold each sum to ~2^-48, so the forms agree far below FP32
+    assert np.all(_normwise(Rf[False], Rf[True]) <= 1e-12)
     s.close()
 
 
@@ -124,30 +132,32 @@ def test_fused_stage_is_bitwise_reproducible_and_sync_repacks(gpu_lib, mesh16):
     s.close()
 
 
-def test_fused_march_within_bar_of_oracle(gpu_lib):
+@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+def test_fused_march_within_bar_of_oracle(gpu_lib, staged):
     m = meshgen.lattice(8)
     q = meshgen.flow_state(m)
     s = _solver(m, q)
     s.time_step(0.5)
     for _ in range(10):
-        s.step(fused=True)
+        s.step(fused=True, staged=staged)
     qo, st = oracle.march(2, 10, m.edge, q, m.normal, m.dx, m.volume)
     assert st == 0
     assert np.all(_normwise(s.fetch_nodes("q"), qo) <= BAR)
     s.close()
 
 
-@pytest.mark.parametrize("n", [3, 5, 7])
-def test_fused_ragged_lattices(gpu_lib, n):
-    """Node counts that fill no block (27, 125, 343 nodes; 2 threads per
-    node in the Green-Gauss pass), against the oracle."""
+@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+@pytest.mark.parametrize("n", [3, 5, 7, 11])
+def test_fused_ragged_lattices(gpu_lib, n, staged):
+    """Node counts that fill no block (27, 125, 343, 1331 nodes: the last
+    node block is partial), against the oracle."""
     m = meshgen.lattice(n, seed=n)
     q = meshgen.flow_state(m, seed=n)
     R_ora, G_ora, _ = oracle.residual(2, m.edge, q, m.normal, m.dx, m.volume, with_abs=True)
     s = _solver(m, q, renumber="none")
     gpu_lib.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
     s.time_step(0.5)
-    s.stage_fused(0.0, gradient=True)
+    s.stage_fused(0.0, gradient=True, staged=staged)
     assert np.all(_normwise(s.fetch_nodes("R"), R_ora) <= BAR)
     assert np.all(_normwise(s.fetch_nodes("G32"), G_ora) <= BAR)
     s.close()
@@ -174,9 +184,10 @@ def test_fused_irregular_graph(gpu_lib):
     s = EdgeSolver(edge, nrm, dx, V, q, renumber="rcm", mixed=True)
     gpu_lib.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
     s.time_step(0.5)
-    s.stage_fused(0.0, gradient=True)
-    assert np.all(_normwise(s.fetch_nodes("R"), R_ora) <= BAR)
-    assert np.all(_normwise(s.fetch_nodes("G32"), G_ora) <= BAR)
+    for staged in (False, True):
+        s.stage_fused(0.0, gradient=True, staged=staged)
+        assert np.all(_normwise(s.fetch_nodes("R"), R_ora) <= BAR)
+        assert np.all(_normwise(s.fetch_nodes("G32"), G_ora) <= BAR)
     s.close()
 
 
@@ -211,6 +222,6 @@ def test_fused_argument_errors(gpu_lib, mesh16):
         assert e.value.code == code, (a, e.value)
     with pytest.raises(gpu_lib.Op2bError) as e:
         gpu_lib.op2b_stage_mixed(c, s.map, d["q0"], d["q"], d["V"], d["dt"], d["n"], d["dx"], -1,
-                                 -1, 0.25, flags=8)
+                                 -1, 0.25, flags=16)
     assert e.value.code == gpu_lib.EINVAL
     s.close()

@@ -124,57 +124,69 @@ __global__ void k_s32_pack_q(int64_t N, const double* __restrict__ q, int64_t ld
   }
 }
 
-// Pass 1: Green-Gauss with the scaling, two threads per node (components
-// 0-2 and 3-5 of q, so G entries 0-8 and 9-17).  Same operations in the
-// same order as the FP32 Green-Gauss node gather, so the same bits.
-__global__ void __launch_bounds__(128) k_s32_green_gauss(
-    int64_t N, const int64_t* __restrict__ rowptr, const int4* __restrict__ adjn,
-    float* __restrict__ rec, const double* __restrict__ V, float* __restrict__ Gout,
-    int64_t ldG) {
-  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < 2 * N;
-       t0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t0 >> 1;
-    const int h = (int)(t0 & 1);
-    const int k0 = 3 * h;
-    const float* qi = rec + i * REC + k0;
-    const float qi0 = __ldg(qi), qi1 = __ldg(qi + 1), qi2 = __ldg(qi + 2);
-    float acc[9];
-#pragma unroll
-    for (int c = 0; c < 9; c++) acc[c] = 0.0f;
-    const int64_t t1 = rowptr[i + 1];
-#pragma unroll 4
-    for (int64_t t = rowptr[i]; t < t1; t++) {
-      const int4 a = __ldg(adjn + t);
-      const float* qj = rec + (int64_t)a.x * REC + k0;
-      const float hx = __int_as_float(a.y), hy = __int_as_float(a.z), hz = __int_as_float(a.w);
-      const float s0 = qi0 + __ldg(qj), s1 = qi1 + __ldg(qj + 1), s2 = qi2 + __ldg(qj + 2);
-      acc[0] = fmaf(s0, hx, acc[0]);
-      acc[1] = fmaf(s0, hy, acc[1]);
-      acc[2] = fmaf(s0, hz, acc[2]);
-      acc[3] = fmaf(s1, hx, acc[3]);
-      acc[4] = fmaf(s1, hy, acc[4]);
-      acc[5] = fmaf(s1, hz, acc[5]);
-      acc[6] = fmaf(s2, hx, acc[6]);
-      acc[7] = fmaf(s2, hy, acc[7]);
-      acc[8] = fmaf(s2, hz, acc[8]);
-    }
-    const float r = (float)(1.0 / V[i]);
-    float* g = rec + i * REC + k0;
-#pragma unroll
-    for (int c = 0; c < 9; c++) {  // c = 3 (k - k0) + d
-      const float v = acc[c] * r;
-      g[GX + 6 * (c % 3) + c / 3] = v;
-      if (Gout) Gout[(9 * h + c) * ldG + i] = v;
-    }
-  }
-}
-
 // 32 bytes (8 floats) from a 32-byte aligned address in one load
 __device__ __forceinline__ void ldg8(const float* __restrict__ p, float* v) {
   asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
         "=f"(v[7])
       : "l"(p));
+}
+
+// the same through the coherent path: for records whose other bytes the
+// running kernel writes (the Green-Gauss pass writes the G parts while it
+// reads the q parts)
+__device__ __forceinline__ void ld8(const float* p, float* v) {
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+
+// Pass 1: Green-Gauss with the scaling, one thread per node: each end's
+// other node's q comes in one 32-byte load (the record's first 8 floats: q
+// and two G values, unused, which other threads may be writing: coherent
+// loads).  Same operations in the same order as the FP32
+// Green-Gauss node gather, so the same bits.
+__global__ void __launch_bounds__(128) k_s32_green_gauss(
+    int64_t N, const int64_t* __restrict__ rowptr, const int4* __restrict__ adjn,
+    float* __restrict__ rec, const double* __restrict__ V, float* __restrict__ Gout,
+    int64_t ldG) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float qi[8];
+    ld8(rec + i * REC, qi);
+    float acc[18];
+#pragma unroll
+    for (int c = 0; c < 18; c++) acc[c] = 0.0f;
+    const int64_t t1 = rowptr[i + 1];
+#pragma unroll 2
+    for (int64_t t = rowptr[i]; t < t1; t++) {
+      const int4 a = __ldg(adjn + t);
+      float qj[8];
+      ld8(rec + (int64_t)a.x * REC, qj);
+      const float h[3] = {__int_as_float(a.y), __int_as_float(a.z), __int_as_float(a.w)};
+#pragma unroll
+      for (int c = 0; c < 6; c++) {
+        const float sc = qi[c] + qj[c];
+#pragma unroll
+        for (int d = 0; d < 3; d++) acc[3 * c + d] = fmaf(sc, h[d], acc[3 * c + d]);
+      }
+    }
+    const float r = (float)(1.0 / V[i]);
+    float gd[18];  // the record's G part, dimension-major: gd[6 d + k] = G[3 k + d]
+#pragma unroll
+    for (int c = 0; c < 18; c++) {  // c = 3 k + d
+      const float v = acc[c] * r;
+      gd[6 * (c % 3) + c / 3] = v;
+      if (Gout) Gout[c * ldG + i] = v;
+    }
+    float* g = rec + i * REC;
+    *reinterpret_cast<float2*>(g + GX) = make_float2(gd[0], gd[1]);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      *reinterpret_cast<float4*>(g + GX + 2 + 4 * k) =
+          make_float4(gd[2 + 4 * k], gd[3 + 4 * k], gd[4 + 4 * k], gd[5 + 4 * k]);
+  }
 }
 
 // a node record (96 bytes at a multiple of 96: 32-byte aligned) in three loads
@@ -325,7 +337,9 @@ __device__ __forceinline__ void finish_node(int64_t i, const f2* hi, const f2* l
 
 // direct form: one thread per node, the other ends' records gathered from
 // global memory (adje.x = the other node's id)
-__global__ void __launch_bounds__(128) k_s32_flux_update(
+constexpr int kFluxBlock = 128;
+
+__global__ void __launch_bounds__(kFluxBlock) k_s32_flux_update(
     int64_t N, const int64_t* __restrict__ rowptr, const int2* __restrict__ adje,
     const float* __restrict__ geo, const float* __restrict__ rin, float* __restrict__ rout,
     double* __restrict__ q0, int64_t ld0, double* __restrict__ q, int64_t ldq,
@@ -774,10 +788,10 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
         N, p.B, p.uoff, p.uniq, p.sell_off, p.adje_s, (const float*)p.geo, rin, rout,
         (double*)d0.ptr, d0.ld, (double*)dq.ptr, dq.ld, pV, pdt, alpha, pR, ldR, sq0, gas);
   } else {
-    k_s32_green_gauss<<<grid_of(c, 2 * N, 128), 128, 0, c.stream>>>(N, sp->rowptr, p.adjn, rin,
-                                                                      pV, pG, ldG);
+    k_s32_green_gauss<<<grid_of(c, N, 128), 128, 0, c.stream>>>(N, sp->rowptr, p.adjn, rin, pV,
+                                                                  pG, ldG);
     if ((rc = c.launched("stage_mixed green_gauss"))) return rc;
-    k_s32_flux_update<<<grid_of(c, N, 128), 128, 0, c.stream>>>(
+    k_s32_flux_update<<<grid_of(c, N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
         N, sp->rowptr, p.adje, (const float*)p.geo, rin, rout, (double*)d0.ptr, d0.ld,
         (double*)dq.ptr, dq.ld, pV, pdt, alpha, pR, ldR, sq0, gas);
   }

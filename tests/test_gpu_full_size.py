@@ -1,7 +1,8 @@
 """Parity at the benchmark's sizes, with the autotuned strategies.
 
 100^3 lattice (1M nodes, 9M edges): every node of the FP64 residual and of
-the adjoint against the oracle; FP32-mixed residual error.
+the adjoint against the oracle; FP32-mixed residual error, by the separate
+loops and by the fused stage (both forms).
 200^3 lattice (8M nodes, 72M edges): sampled nodes and edges.  For a sample
 S the oracle runs on a local sub-mesh that holds every edge touching the
 nodes within two rings of S, which is exactly what R at S and the adjoint
@@ -52,6 +53,16 @@ def test_config1_full_parity(gpu_lib):
     R32 = s.fetch_nodes("R")
     err = np.max(np.abs(R32 - Ro), axis=0) / np.max(np.abs(Ro), axis=0)
     assert np.all(err <= 1e-5), err
+    # the fused FP32-mixed stage at alpha = 0 (q unchanged): its residual
+    import paper_1403_7209_gb300.op2b as L
+    L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
+    s.time_step(0.5)
+    for staged in (False, True):
+        s.stage_fused(0.0, sync=True, staged=staged)
+        Rf = s.fetch_nodes("R")
+        err = np.max(np.abs(Rf - Ro), axis=0) / np.max(np.abs(Ro), axis=0)
+        assert np.all(err <= 1e-5), err
+        assert np.array_equal(s.fetch_nodes("q"), q)
     s.load_nodes("lam", lam)
     s.adjoint(2)
     qb, nb = oracle.residual_reverse(2, m.edge, q, m.normal, m.dx, m.volume, lam)

@@ -676,7 +676,7 @@ def march_adjoint_extra(torch, L, s, q, args, stream, E, steps=10):
             "stored_gb": stored / 1e9, "edges_per_s_per_stage": E * 5 * steps / (r_ms * 1e-3)}
 
 
-def config0_extra(torch, L, args):
+def lattice16_extra(torch, L, args):
     """First-order Rusanov residual on the 16^3 lattice (random numbering),
     the correctness configuration; launch-bound at 36,864 edges, so timed
     as a captured CUDA graph of 100 loop calls."""
@@ -896,7 +896,7 @@ def tuned_solver(L, m, q, args, stream, device, **kw):
     return s
 
 
-def config1_extra(torch, L, args, stream, device):
+def lattice100_extra(torch, L, args, stream, device):
     """The 100^3 lattice (1M nodes, 9M edges): the FP64 stage with per-loop
     times, the FP32-mixed stage, the adjoint at 1M nodes, and the library's
     other loops (tangent, viscous, march adjoint, node limiters,
@@ -1068,15 +1068,15 @@ def main():
     }
 
     if not args.no_extras:
-        # the same mesh: FP32-mixed stage (config 3), adjoint at 8M nodes
-        # (config 4), 50-step marches (config 2)
+        # the same mesh: the FP32-mixed stage, the adjoint at 8M nodes, the
+        # 50-step marches
         line["mixed"] = mixed_extra(torch, L, s, args, stream, ms, E, N)
         line["float_float"] = ff_extra(torch, L, s, args, stream, ms, E, N)
         line["adjoint"] = adjoint_extra(torch, L, s, args, stream, E)
         line["march"] = march_extra(torch, L, s, q, args, stream)
         L.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
-        line["config1"] = config1_extra(torch, L, args, stream, local)
-        line["config0"] = config0_extra(torch, L, args)
+        line["lattice_100"] = lattice100_extra(torch, L, args, stream, local)
+        line["lattice_16"] = lattice16_extra(torch, L, args)
         if child is not None:
             child.join()
             q_ora, st = cpu_baseline_march_result(args.oracle_march_n, 50)

@@ -65,19 +65,22 @@ struct DevOwnPlan {
 };
 
 // Packed FP32 records of the fused mixed-precision stage (stage32.cu), per
-// map: the edge ends' adjacency in node-sorted order with the other node's
-// id (other end and +-n/2 for the Green-Gauss pass, other end and 2e + side
-// for the flux pass), the edges' geometry (n, dx; 32 bytes per edge) and two
-// node-record buffers (q then G, 24 floats per node), the current one
-// holding the state's FP32 copy.  Where the node-block staging plan fits
-// (staged), the same adjacency sliced-ELL with the other node's local id in
-// its block's neighbourhood.
+// map: the edge ends' adjacency, sliced-ELL (per 32-node slice: width = the
+// slice's largest degree, ell_off = 32 x the widths' prefix sums; per slot
+// the other node's id with +-n/2 for the Green-Gauss pass, with the signed
+// edge geometry for the flux pass) and two node-record buffers (q then G,
+// 24 floats per node), the current one holding the state's FP32 copy.
+// Where the node-block staging plan fits (staged), the adjacency sliced-ELL
+// with the other node's local id in its block's neighbourhood and the
+// edges' geometry (n, dx; 32 bytes per edge).
 struct Stage32Plan {
   uint64_t map_version = ~0ull;
   int64_t N = 0, E = 0;
-  int4* adjn = nullptr;
-  int2* adje = nullptr;
-  float4* geo = nullptr;
+  int64_t nell = 0;
+  int64_t* ell_off = nullptr;  // per slice + 1
+  int4* adjn_l = nullptr;      // per slot: {j, +-n/2}
+  float4* ende = nullptr;      // per slot, two words: {j, s n}, {s dx, 0}
+  float4* geo = nullptr;       // staged passes only
   float* rec[2] = {nullptr, nullptr};
   int cur = 0;
   // the dats the geometry and the records were packed from

@@ -21,7 +21,7 @@
 // two-sum, converted exactly to FP64 once per node: the pair holds the sum
 // of the FP32 fluxes to about 2^-48 of its running magnitude.
 //
-//   pass 1 (Green-Gauss, 2 threads per node): G_i = (1/V_i) sum over the
+//   pass 1 (Green-Gauss, 1 thread per node): G_i = (1/V_i) sum over the
 //     node's edge ends of (q_i + q_j) (x) (+-n/2), written into the record's
 //     G part (and into an optional FP32 G dat);
 //   pass 2 (flux + update, 1 thread per node): for every edge end the edge's
@@ -52,27 +52,6 @@ constexpr int GX = 6, GY = 12, GZ = 18;
 template <typename T>
 __device__ __forceinline__ float f32_of(T x) {
   return (float)x;
-}
-
-// per edge end t (the segmented plan's node-sorted ends, value 2e + side):
-// adjn[t] = {other end j, +-n_e/2 (FP32 bits)} for the Green-Gauss pass,
-// adje[t] = {j, 2e + side} for the flux pass
-template <typename TN>
-__global__ void k_s32_adjacency(const int32_t* __restrict__ ends, int64_t nends,
-                                const int32_t* __restrict__ m0, const int32_t* __restrict__ m1,
-                                const TN* __restrict__ n, int64_t ldn, int4* __restrict__ adjn,
-                                int2* __restrict__ adje) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nends;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t end = ends[t];
-    const int64_t e = end >> 1;
-    const bool second = end & 1;
-    const int32_t j = second ? m0[e] : m1[e];
-    const float h = second ? -0.5f : 0.5f;
-    const float hx = f32_of(n[e]) * h, hy = f32_of(n[ldn + e]) * h, hz = f32_of(n[2 * ldn + e]) * h;
-    adjn[t] = make_int4(j, __float_as_int(hx), __float_as_int(hy), __float_as_int(hz));
-    adje[t] = make_int2(j, end);
-  }
 }
 
 // the staged passes' adjacency, sliced-ELL with local ids: for slot s with
@@ -114,6 +93,43 @@ __global__ void k_s32_geometry(int64_t E, const TN* __restrict__ n, int64_t ldn,
   }
 }
 
+// The direct passes' adjacency, sliced-ELL: the k-th end of node i (in the
+// node-sorted order) at slot ell_off[i / 32] + 32 k + i % 32, so that the
+// ends a warp's 32 nodes read together are contiguous.  Per slot
+// adjn_l = {other end j, +-n/2 (FP32 bits)} (Green-Gauss pass) and
+// ende = {j (bits), s n, s dx, 0} with s = -1 at the edge's second end, the
+// edge already reversed (flux pass; 32 bytes, one sector).
+template <typename TN, typename TD>
+__global__ void k_s32_adjacency_ell(const int32_t* __restrict__ ends, int64_t nends,
+                                    const int64_t* __restrict__ rowptr,
+                                    const int64_t* __restrict__ ell_off,
+                                    const int32_t* __restrict__ m0, const int32_t* __restrict__ m1,
+                                    const TN* __restrict__ n, int64_t ldn,
+                                    const TD* __restrict__ dx, int64_t lddx,
+                                    int4* __restrict__ adjn_l, float4* __restrict__ ende) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nends;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t end = ends[t];
+    const int64_t e = end >> 1;
+    const bool second = end & 1;
+    const int32_t i = second ? m1[e] : m0[e];
+    const int32_t j = second ? m0[e] : m1[e];
+    const int64_t s = ell_off[i >> 5] + 32 * (t - rowptr[i]) + (i & 31);
+    const float nx = f32_of(n[e]), ny = f32_of(n[ldn + e]), nz = f32_of(n[2 * ldn + e]);
+    const float h = second ? -0.5f : 0.5f;
+    adjn_l[s] = make_int4(j, __float_as_int(nx * h), __float_as_int(ny * h),
+                          __float_as_int(nz * h));
+    const float dxx = f32_of(dx[e]), dxy = f32_of(dx[lddx + e]), dxz = f32_of(dx[2 * lddx + e]);
+    if (second) {
+      ende[2 * s] = make_float4(__int_as_float(j), -nx, -ny, -nz);
+      ende[2 * s + 1] = make_float4(-dxx, -dxy, -dxz, 0.0f);
+    } else {
+      ende[2 * s] = make_float4(__int_as_float(j), nx, ny, nz);
+      ende[2 * s + 1] = make_float4(dxx, dxy, dxz, 0.0f);
+    }
+  }
+}
+
 // record q part <- (float) q
 __global__ void k_s32_pack_q(int64_t N, const double* __restrict__ q, int64_t ldq,
                              float* __restrict__ rec) {
@@ -140,53 +156,6 @@ __device__ __forceinline__ void ld8(const float* p, float* v) {
                : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
                  "=f"(v[6]), "=f"(v[7])
                : "l"(p));
-}
-
-// Pass 1: Green-Gauss with the scaling, one thread per node: each end's
-// other node's q comes in one 32-byte load (the record's first 8 floats: q
-// and two G values, unused, which other threads may be writing: coherent
-// loads).  Same operations in the same order as the FP32
-// Green-Gauss node gather, so the same bits.
-__global__ void __launch_bounds__(128) k_s32_green_gauss(
-    int64_t N, const int64_t* __restrict__ rowptr, const int4* __restrict__ adjn,
-    float* __restrict__ rec, const double* __restrict__ V, float* __restrict__ Gout,
-    int64_t ldG) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float qi[8];
-    ld8(rec + i * REC, qi);
-    float acc[18];
-#pragma unroll
-    for (int c = 0; c < 18; c++) acc[c] = 0.0f;
-    const int64_t t1 = rowptr[i + 1];
-#pragma unroll 2
-    for (int64_t t = rowptr[i]; t < t1; t++) {
-      const int4 a = __ldg(adjn + t);
-      float qj[8];
-      ld8(rec + (int64_t)a.x * REC, qj);
-      const float h[3] = {__int_as_float(a.y), __int_as_float(a.z), __int_as_float(a.w)};
-#pragma unroll
-      for (int c = 0; c < 6; c++) {
-        const float sc = qi[c] + qj[c];
-#pragma unroll
-        for (int d = 0; d < 3; d++) acc[3 * c + d] = fmaf(sc, h[d], acc[3 * c + d]);
-      }
-    }
-    const float r = (float)(1.0 / V[i]);
-    float gd[18];  // the record's G part, dimension-major: gd[6 d + k] = G[3 k + d]
-#pragma unroll
-    for (int c = 0; c < 18; c++) {  // c = 3 k + d
-      const float v = acc[c] * r;
-      gd[6 * (c % 3) + c / 3] = v;
-      if (Gout) Gout[c * ldG + i] = v;
-    }
-    float* g = rec + i * REC;
-    *reinterpret_cast<float2*>(g + GX) = make_float2(gd[0], gd[1]);
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-      *reinterpret_cast<float4*>(g + GX + 2 + 4 * k) =
-          make_float4(gd[2 + 4 * k], gd[3 + 4 * k], gd[4 + 4 * k], gd[5 + 4 * k]);
-  }
 }
 
 // a node record (96 bytes at a multiple of 96: 32-byte aligned) in three loads
@@ -306,12 +275,6 @@ __device__ __forceinline__ void flux_end_g(const float* vi, const float* vj, Geo
   for (int k = 0; k < 3; k++) two_sum_acc2(hi[k], lo[k], mk2(F[2 * k], F[2 * k + 1]));
 }
 
-__device__ __forceinline__ void flux_end(const float* vi, const float* vj,
-                                         const float* __restrict__ geo_e, bool second,
-                                         const GasPairs& gas, f2* hi, f2* lo) {
-  flux_end_g(vi, vj, ldg_geo(geo_e), second, gas, hi, lo);
-}
-
 // R_i from the pair sums (each float converted exactly, one FP64 add) and the
 // update of components [k0, k1) of node i
 __device__ __forceinline__ void finish_node(int64_t i, const f2* hi, const f2* lo, int k0, int k1,
@@ -335,13 +298,85 @@ __device__ __forceinline__ void finish_node(int64_t i, const f2* hi, const f2* l
   }
 }
 
-// direct form: one thread per node, the other ends' records gathered from
-// global memory (adje.x = the other node's id)
+// the adjacency is read once per stage: loaded without allocating in L1,
+// which the node records use
+__device__ __forceinline__ int4 ld_stream4(const int4* p) {
+  int4 a;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w)
+      : "l"(p));
+  return a;
+}
+__device__ __forceinline__ Geo ld_stream8(const float* p) {
+  Geo g;
+  asm("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(g.a.x), "=f"(g.a.y), "=f"(g.a.z), "=f"(g.a.w), "=f"(g.b.x), "=f"(g.b.y),
+        "=f"(g.b.z), "=f"(g.b.w)
+      : "l"(p));
+  return g;
+}
+
+// Direct form of both passes: one thread per node, CTAs of 128 consecutive
+// nodes, every other end's record (or q part) gathered from global memory
+// through the sliced-ELL adjacency (the k-th ends of a warp's 32 nodes read
+// in one coalesced load).
+
+// Pass 1: Green-Gauss with the scaling: each end's other node's q comes in
+// one 32-byte load (the record's first 8 floats: q and two G values, unused,
+// which other threads may be writing: coherent loads).  Same operations in
+// the same order as the FP32 Green-Gauss node gather, so the same bits.
+// The pass waits on its gathers; six ends per unrolled iteration keep six
+// gathers in flight per thread (4% faster per stage than two).
+__global__ void __launch_bounds__(128) k_s32_green_gauss(
+    int64_t N, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ ell_off,
+    const int4* __restrict__ adjn_l, float* __restrict__ rec, const double* __restrict__ V,
+    float* __restrict__ Gout, int64_t ldG) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float qi[8];
+    ld8(rec + i * REC, qi);
+    float acc[18];
+#pragma unroll
+    for (int c = 0; c < 18; c++) acc[c] = 0.0f;
+    const int64_t deg = rowptr[i + 1] - rowptr[i];
+    const int4* a_i = adjn_l + ell_off[i >> 5] + (i & 31);
+#pragma unroll 6
+    for (int64_t k = 0; k < deg; k++) {
+      const int4 a = ld_stream4(a_i + 32 * k);
+      float qj[8];
+      ld8(rec + (int64_t)a.x * REC, qj);
+      const float h[3] = {__int_as_float(a.y), __int_as_float(a.z), __int_as_float(a.w)};
+#pragma unroll
+      for (int c = 0; c < 6; c++) {
+        const float sc = qi[c] + qj[c];
+#pragma unroll
+        for (int d = 0; d < 3; d++) acc[3 * c + d] = fmaf(sc, h[d], acc[3 * c + d]);
+      }
+    }
+    const float r = (float)(1.0 / V[i]);
+    float gd[18];  // the record's G part, dimension-major: gd[6 d + k] = G[3 k + d]
+#pragma unroll
+    for (int c = 0; c < 18; c++) {  // c = 3 k + d
+      const float v = acc[c] * r;
+      gd[6 * (c % 3) + c / 3] = v;
+      if (Gout) Gout[c * ldG + i] = v;
+    }
+    float* g = rec + i * REC;
+    *reinterpret_cast<float2*>(g + GX) = make_float2(gd[0], gd[1]);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      *reinterpret_cast<float4*>(g + GX + 2 + 4 * k) =
+          make_float4(gd[2 + 4 * k], gd[3 + 4 * k], gd[4 + 4 * k], gd[5 + 4 * k]);
+  }
+}
+
+// Pass 2: flux + update; per end one 32-byte load of {j, s n, s dx} (the
+// edge already reversed at its second end) and the other node's record
 constexpr int kFluxBlock = 128;
 
 __global__ void __launch_bounds__(kFluxBlock) k_s32_flux_update(
-    int64_t N, const int64_t* __restrict__ rowptr, const int2* __restrict__ adje,
-    const float* __restrict__ geo, const float* __restrict__ rin, float* __restrict__ rout,
+    int64_t N, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ ell_off,
+    const float* __restrict__ ende, const float* __restrict__ rin, float* __restrict__ rout,
     double* __restrict__ q0, int64_t ld0, double* __restrict__ q, int64_t ldq,
     const double* __restrict__ V, const double* __restrict__ dt, double alpha,
     double* __restrict__ R, int64_t ldR, bool store_q0, GasPairs gas) {
@@ -352,12 +387,18 @@ __global__ void __launch_bounds__(kFluxBlock) k_s32_flux_update(
     f2 hi[3], lo[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) hi[k] = lo[k] = splat2(0.0f);
-    const int64_t t1 = rowptr[i + 1];
-    for (int64_t t = rowptr[i]; t < t1; t++) {
-      const int2 a = __ldg(adje + t);
+    const int64_t deg = rowptr[i + 1] - rowptr[i];
+    const float* e_i = ende + 8 * (ell_off[i >> 5] + (i & 31));
+#pragma unroll 1  // not unrolled: 80 registers, 6 CTAs per SM (unrolled: 96, 5)
+    for (int64_t k = 0; k < deg; k++) {
+      const Geo g = ld_stream8(e_i + 256 * k);
       float vj[REC];
-      load_rec(rin + (int64_t)a.x * REC, vj);
-      flux_end(vi, vj, geo + 8 * (int64_t)(a.y >> 1), a.y & 1, gas, hi, lo);
+      load_rec(rin + (int64_t)__float_as_int(g.a.x) * REC, vj);
+      float F[6];
+      flux2_pairs(vi, vj, make_float4(g.a.y, g.a.z, g.a.w, g.b.x),
+                  make_float4(g.b.y, g.b.z, 0.0f, 0.0f), gas, F);
+#pragma unroll
+      for (int c = 0; c < 3; c++) two_sum_acc2(hi[c], lo[c], mk2(F[2 * c], F[2 * c + 1]));
     }
     finish_node(i, hi, lo, 0, 6, rout, q0, ld0, q, ldq, V, dt, alpha, R, ldR, store_q0);
   }
@@ -558,9 +599,10 @@ void free_stage32(Stage32Plan& p) {
   cudaFree(p.sell_end);
   cudaFree(p.adjn_s);
   cudaFree(p.adje_s);
-  cudaFree(p.adjn);
-  cudaFree(p.adje);
   cudaFree(p.geo);
+  cudaFree(p.ell_off);
+  cudaFree(p.adjn_l);
+  cudaFree(p.ende);
   cudaFree(p.rec[0]);
   cudaFree(p.rec[1]);
   p = Stage32Plan();
@@ -607,6 +649,24 @@ size_t smem_flux(int64_t U, int32_t B) { return (size_t)U * SREC4 * 16 + (size_t
 constexpr size_t kStageSmemLimit = 100 * 1024;
 constexpr int kStageBlocks[3] = {128, 64, 32};
 
+// The sliced-ELL offsets of the direct passes from the map's node degrees:
+// slice s (nodes 32 s .. 32 s + 31) holds width_s = its largest degree
+// rows of 32 slots.
+void ell_offsets(const MapRec& m, int64_t N, int64_t E, std::vector<int64_t>* off) {
+  std::vector<int32_t> deg((size_t)N, 0);
+  for (int64_t e = 0; e < E; e++) {
+    deg[m.host[2 * e]]++;
+    deg[m.host[2 * e + 1]]++;
+  }
+  const int64_t S = (N + 31) / 32;
+  off->assign((size_t)S + 1, 0);
+  for (int64_t sl = 0; sl < S; sl++) {
+    int32_t w = 0;
+    for (int64_t i = 32 * sl; i < std::min<int64_t>(N, 32 * sl + 32); i++) w = std::max(w, deg[i]);
+    (*off)[sl + 1] = (*off)[sl] + 32 * (int64_t)w;
+  }
+}
+
 // The node-block staging plan, on the host from the map in its current
 // numbering: the largest block size whose every neighbourhood fits
 // kStageSmemLimit, or none (p.staged stays false).
@@ -636,7 +696,7 @@ int build_staging(Ctx& c, const MapRec& m, int64_t N, int64_t E, Stage32Plan& p)
       (rc = upload(c, &p.lother, bp.lother)) || (rc = upload(c, &p.sell_off, bp.sell_off)) ||
       (rc = upload(c, &p.sell_end, bp.sell_end)) ||
       (rc = alloc(c, &p.adjn_s, bp.sell_end.size())) ||
-      (rc = alloc(c, &p.adje_s, bp.sell_end.size())))
+      (rc = alloc(c, &p.adje_s, bp.sell_end.size())) || (rc = alloc(c, &p.geo, (size_t)2 * E)))
     return rc;
   p.staged = true;
   p.B = bp.B;
@@ -646,18 +706,20 @@ int build_staging(Ctx& c, const MapRec& m, int64_t N, int64_t E, Stage32Plan& p)
   return OP2B_OK;
 }
 
-template <typename TN>
-void launch_adjacency(Ctx& c, const DevSegPlan& sp, int64_t nends, const int32_t* m0,
-                      const int32_t* m1, const DatRec& n, Stage32Plan& p) {
-  k_s32_adjacency<TN><<<grid_of(c, nends, 256), 256, 0, c.stream>>>(
-      sp.ends, nends, m0, m1, (const TN*)n.ptr, n.ld, p.adjn, p.adje);
-  if (p.staged)
-    k_s32_adjacency_sell<TN><<<grid_of(c, p.nslots, 256), 256, 0, c.stream>>>(
-        p.sell_end, p.nslots, sp.ends, p.lother, (const TN*)n.ptr, n.ld, p.adjn_s, p.adje_s);
+template <typename TN, typename TD>
+void launch_adjacency_ell(Ctx& c, const DevSegPlan& sp, int64_t nends, const int32_t* m0,
+                          const int32_t* m1, const DatRec& n, const DatRec& dx, Stage32Plan& p) {
+  k_s32_adjacency_ell<TN, TD><<<grid_of(c, nends, 256), 256, 0, c.stream>>>(
+      sp.ends, nends, sp.rowptr, p.ell_off, m0, m1, (const TN*)n.ptr, n.ld, (const TD*)dx.ptr,
+      dx.ld, p.adjn_l, p.ende);
 }
 
+// the staged passes' sliced-ELL adjacency (local ids) and edge geometry
 template <typename TN, typename TD>
-void launch_geometry(Ctx& c, int64_t E, const DatRec& n, const DatRec& dx, Stage32Plan& p) {
+void launch_staged_adjacency(Ctx& c, const DevSegPlan& sp, int64_t E, const DatRec& n,
+                             const DatRec& dx, Stage32Plan& p) {
+  k_s32_adjacency_sell<TN><<<grid_of(c, p.nslots, 256), 256, 0, c.stream>>>(
+      p.sell_end, p.nslots, sp.ends, p.lother, (const TN*)n.ptr, n.ld, p.adjn_s, p.adje_s);
   k_s32_geometry<TN, TD><<<grid_of(c, E, 256), 256, 0, c.stream>>>(
       E, (const TN*)n.ptr, n.ld, (const TD*)dx.ptr, dx.ld, p.geo);
 }
@@ -718,8 +780,11 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
     p.map_version = m.version;
     p.N = N;
     p.E = E;
-    if ((rc = alloc(c, &p.adjn, (size_t)2 * E)) || (rc = alloc(c, &p.adje, (size_t)2 * E)) ||
-        (rc = alloc(c, &p.geo, (size_t)2 * E)) || (rc = alloc(c, &p.rec[0], (size_t)REC * N)) ||
+    std::vector<int64_t> eoff;
+    ell_offsets(m, N, E, &eoff);
+    p.nell = eoff.back();
+    if ((rc = upload(c, &p.ell_off, eoff)) || (rc = alloc(c, &p.adjn_l, (size_t)p.nell)) ||
+        (rc = alloc(c, &p.ende, (size_t)2 * p.nell)) || (rc = alloc(c, &p.rec[0], (size_t)REC * N)) ||
         (rc = alloc(c, &p.rec[1], (size_t)REC * N))) {
       free_stage32(p);
       return rc;
@@ -740,14 +805,19 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
   const int32_t* m0 = m.dev;
   const int32_t* m1 = m.dev + E;
   if (sync_geo && E > 0) {
-    if (dn.type == OP2B_F64) launch_adjacency<double>(c, *sp, 2 * E, m0, m1, dn, p);
-    else launch_adjacency<float>(c, *sp, 2 * E, m0, m1, dn, p);
+    const bool n64 = dn.type == OP2B_F64, dx64 = ddx.type == OP2B_F64;
+    if (n64 && dx64) launch_adjacency_ell<double, double>(c, *sp, 2 * E, m0, m1, dn, ddx, p);
+    else if (n64) launch_adjacency_ell<double, float>(c, *sp, 2 * E, m0, m1, dn, ddx, p);
+    else if (dx64) launch_adjacency_ell<float, double>(c, *sp, 2 * E, m0, m1, dn, ddx, p);
+    else launch_adjacency_ell<float, float>(c, *sp, 2 * E, m0, m1, dn, ddx, p);
     if ((rc = c.launched("stage_mixed adjacency"))) return rc;
-    if (dn.type == OP2B_F64 && ddx.type == OP2B_F64) launch_geometry<double, double>(c, E, dn, ddx, p);
-    else if (dn.type == OP2B_F64) launch_geometry<double, float>(c, E, dn, ddx, p);
-    else if (ddx.type == OP2B_F64) launch_geometry<float, double>(c, E, dn, ddx, p);
-    else launch_geometry<float, float>(c, E, dn, ddx, p);
-    if ((rc = c.launched("stage_mixed geometry"))) return rc;
+    if (p.staged) {
+      if (n64 && dx64) launch_staged_adjacency<double, double>(c, *sp, E, dn, ddx, p);
+      else if (n64) launch_staged_adjacency<double, float>(c, *sp, E, dn, ddx, p);
+      else if (dx64) launch_staged_adjacency<float, double>(c, *sp, E, dn, ddx, p);
+      else launch_staged_adjacency<float, float>(c, *sp, E, dn, ddx, p);
+      if ((rc = c.launched("stage_mixed staged adjacency"))) return rc;
+    }
   }
   p.n_src = dn.ptr;
   p.n_type = dn.type;
@@ -788,11 +858,11 @@ extern "C" int op2b_stage_mixed(op2b_ctx h, op2b_map map, op2b_dat q0, op2b_dat 
         N, p.B, p.uoff, p.uniq, p.sell_off, p.adje_s, (const float*)p.geo, rin, rout,
         (double*)d0.ptr, d0.ld, (double*)dq.ptr, dq.ld, pV, pdt, alpha, pR, ldR, sq0, gas);
   } else {
-    k_s32_green_gauss<<<grid_of(c, N, 128), 128, 0, c.stream>>>(N, sp->rowptr, p.adjn, rin, pV,
-                                                                  pG, ldG);
+    k_s32_green_gauss<<<grid_of(c, N, 128), 128, 0, c.stream>>>(N, sp->rowptr, p.ell_off,
+                                                                  p.adjn_l, rin, pV, pG, ldG);
     if ((rc = c.launched("stage_mixed green_gauss"))) return rc;
     k_s32_flux_update<<<grid_of(c, N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
-        N, sp->rowptr, p.adje, (const float*)p.geo, rin, rout, (double*)d0.ptr, d0.ld,
+        N, sp->rowptr, p.ell_off, (const float*)p.ende, rin, rout, (double*)d0.ptr, d0.ld,
         (double*)dq.ptr, dq.ld, pV, pdt, alpha, pR, ldR, sq0, gas);
   }
   if ((rc = c.launched("stage_mixed flux_update"))) return rc;

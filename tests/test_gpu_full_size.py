@@ -40,7 +40,7 @@ def tuned_solver(op2b, m, q, **kw):
     return s
 
 
-def test_config1_full_parity(gpu_lib):
+def test_lattice100_full_parity(gpu_lib):
     m = meshgen.lattice(100)
     q = meshgen.flow_state(m)
     lam = meshgen.adjoint_seed(m.num_nodes)
@@ -88,7 +88,7 @@ def _submesh(m, sample):
     return keep, nodes, local
 
 
-def test_config2_sampled_parity(gpu_lib):
+def test_lattice200_sampled_parity(gpu_lib):
     m = meshgen.lattice(200)
     q = meshgen.flow_state(m)
     lam = meshgen.adjoint_seed(m.num_nodes)
@@ -118,8 +118,8 @@ def test_config2_sampled_parity(gpu_lib):
                   np.median(np.abs(nbar), axis=0))
 
 
-def test_config4_adjoint_fd_and_dot_product_1M(gpu_lib):
-    """Config 4 on the 1M-node mesh: central differences of the GPU forward
+def test_adjoint_fd_and_dot_product_1M(gpu_lib):
+    """The adjoint on the 1M-node mesh: central differences of the GPU forward
     residual on 64 entries (h = 1e-6, 1e-8 for the passive scalar,
     Richardson-combined) against the GPU adjoint, and the dot-product test
     <lam, J v> (oracle tangent sweep) = <J^T lam, v> (GPU reverse sweep)."""

@@ -191,6 +191,36 @@ def test_fused_irregular_graph(gpu_lib):
     s.close()
 
 
+def test_fused_hub_node(gpu_lib):
+    """One node joined to every other node plus a ring through the rest
+    (degrees N-1+... and 3): the adjacency's 32-node slices differ in width
+    by a factor of ~30; against the oracle, in both numberings."""
+    rng = np.random.default_rng(5)
+    N = 203
+    ring = np.column_stack([np.arange(1, N), np.r_[np.arange(2, N), 1]])
+    hub = np.column_stack([np.zeros(N - 1, dtype=np.int64), np.arange(1, N)])
+    edge = np.vstack([ring, hub]).astype(np.int32)
+    E = edge.shape[0]
+    nrm = rng.uniform(-1.0, 1.0, size=(E, 3))
+    dx = rng.uniform(-1.0, 1.0, size=(E, 3))
+    V = rng.uniform(0.9, 1.1, size=N)
+    rho = rng.uniform(0.9, 1.1, size=N)
+    u = np.array([0.5, 0.0, 0.0]) + rng.uniform(-0.3, 0.3, size=(N, 3))
+    p = rng.uniform(0.9, 1.1, size=N)
+    q = np.column_stack([rho, rho[:, None] * u, p / 0.4 + 0.5 * rho * (u * u).sum(1),
+                         rng.uniform(0.0, 1e-3, size=N)])
+    R_ora, G_ora, _ = oracle.residual(2, edge, q, nrm, dx, V, with_abs=True)
+    from paper_1403_7209_gb300.solver import EdgeSolver
+    for renumber in ("none", "rcm"):
+        s = EdgeSolver(edge, nrm, dx, V, q, renumber=renumber, mixed=True)
+        gpu_lib.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
+        s.time_step(0.5)
+        s.stage_fused(0.0, gradient=True)
+        assert np.all(_normwise(s.fetch_nodes("R"), R_ora) <= BAR)
+        assert np.all(_normwise(s.fetch_nodes("G32"), G_ora) <= BAR)
+        s.close()
+
+
 def test_fused_empty_edge_set(gpu_lib):
     N = 10
     q = np.tile([1.0, 0.5, 0.0, 0.0, 2.5, 0.0], (N, 1))

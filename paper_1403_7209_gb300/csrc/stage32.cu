@@ -307,13 +307,24 @@ __device__ __forceinline__ int4 ld_stream4(const int4* p) {
       : "l"(p));
   return a;
 }
-__device__ __forceinline__ Geo ld_stream8(const float* p) {
-  Geo g;
-  asm("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=f"(g.a.x), "=f"(g.a.y), "=f"(g.a.z), "=f"(g.a.w), "=f"(g.b.x), "=f"(g.b.y),
-        "=f"(g.b.z), "=f"(g.b.w)
-      : "l"(p));
-  return g;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
 }
 
 // Direct form of both passes: one thread per node, CTAs of 128 consecutive
@@ -370,16 +381,30 @@ __global__ void __launch_bounds__(128) k_s32_green_gauss(
   }
 }
 
-// Pass 2: flux + update; per end one 32-byte load of {j, s n, s dx} (the
-// edge already reversed at its second end) and the other node's record
+// Pass 2: flux + update.  Per end a 32-byte end record {j, s n, s dx} (the
+// edge already reversed at its second end) and the other node's record.
+// The end records stream from DRAM; each thread copies them by cp.async
+// into its own ring of kRing shared-memory slots, kRing - 1 ends ahead of
+// their use, so that an end waits only for its node-record gather, not for
+// the DRAM read of the index that gather needs.  At most 80 registers
+// (6 CTAs of 128 per SM).
 constexpr int kFluxBlock = 128;
+constexpr int kRing = 4;
 
-__global__ void __launch_bounds__(kFluxBlock) k_s32_flux_update(
+__global__ void __launch_bounds__(kFluxBlock, 6) k_s32_flux_update(
     int64_t N, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ ell_off,
     const float* __restrict__ ende, const float* __restrict__ rin, float* __restrict__ rout,
     double* __restrict__ q0, int64_t ld0, double* __restrict__ q, int64_t ldq,
     const double* __restrict__ V, const double* __restrict__ dt, double alpha,
     double* __restrict__ R, int64_t ldR, bool store_q0, GasPairs gas) {
+  constexpr int PD = kRing, B = kFluxBlock;
+  // word h of ring slot s of thread t at ring[2 (s B + t) + h]: each slot
+  // holds the warp's 32 end records as they lie in global memory (a
+  // thread's two 16-byte words adjacent).  Measured: with each word's 32
+  // threads contiguous instead (no bank conflicts on the reads) the copies
+  // made 2.3x the L2 requests and the stage ran 11% slower.
+  __shared__ float4 ring[PD * 2 * B];
+  float4* my = ring + 2 * threadIdx.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     float vi[REC];
@@ -387,11 +412,32 @@ __global__ void __launch_bounds__(kFluxBlock) k_s32_flux_update(
     f2 hi[3], lo[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) hi[k] = lo[k] = splat2(0.0f);
-    const int64_t deg = rowptr[i + 1] - rowptr[i];
+    const int deg = (int)(rowptr[i + 1] - rowptr[i]);
     const float* e_i = ende + 8 * (ell_off[i >> 5] + (i & 31));
-#pragma unroll 1  // not unrolled: 80 registers, 6 CTAs per SM (unrolled: 96, 5)
-    for (int64_t k = 0; k < deg; k++) {
-      const Geo g = ld_stream8(e_i + 256 * k);
+#pragma unroll
+    for (int s = 0; s < PD - 1; s++) {
+      if (s < deg) {
+        cp_async16(my + 2 * s * B, e_i + 256 * s);
+        cp_async16(my + 2 * s * B + 1, e_i + 256 * s + 4);
+      }
+      cp_async_commit();  // one group per end, empty past the row's end
+    }
+    int sw = PD - 1, sr = 0;  // the ring slots written and read next
+    const float* src = e_i + 256 * (PD - 1);  // end k + PD - 1 (read only below deg)
+#pragma unroll 1
+    for (int k = 0; k < deg; k++) {
+      if (k + PD - 1 < deg) {
+        cp_async16(my + 2 * sw * B, src);
+        cp_async16(my + 2 * sw * B + 1, src + 4);
+      }
+      cp_async_commit();
+      src += 256;
+      sw = sw == PD - 1 ? 0 : sw + 1;
+      cp_async_wait_group<PD - 1>();  // end k's group is complete
+      Geo g;
+      g.a = my[2 * sr * B];
+      g.b = my[2 * sr * B + 1];
+      sr = sr == PD - 1 ? 0 : sr + 1;
       float vj[REC];
       load_rec(rin + (int64_t)__float_as_int(g.a.x) * REC, vj);
       float F[6];
@@ -400,6 +446,7 @@ __global__ void __launch_bounds__(kFluxBlock) k_s32_flux_update(
 #pragma unroll
       for (int c = 0; c < 3; c++) two_sum_acc2(hi[c], lo[c], mk2(F[2 * c], F[2 * c + 1]));
     }
+    cp_async_wait_all();
     finish_node(i, hi, lo, 0, 6, rout, q0, ld0, q, ldq, V, dt, alpha, R, ldR, store_q0);
   }
 }
@@ -415,18 +462,6 @@ __global__ void __launch_bounds__(kFluxBlock) k_s32_flux_update(
 // ends of a warp's 32 nodes at consecutive addresses, coalesced) and carry
 // the other node's local id.  Several CTAs per SM overlap one block's
 // copies with another block's arithmetic.
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
 
 constexpr int SREC4 = 7;  // 16-byte words per record slot in shared memory
                           // (112 bytes: an odd multiple of 16, so that the

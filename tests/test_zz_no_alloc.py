@@ -7,7 +7,7 @@ on two calls in a row on two different meshes, and compared with the
 oracle's first-order residual on the library's numbering and with the
 context entry point op2b_edge_flux (first order, segmented strategy).  The
 second call runs on the scratch array the first call left behind, and
-neither the driver's free device memory nor torch's allocator may change
+neither the device's free memory (cudaMemGetInfo) nor torch's allocator may change
 across it.
 
 This file is named to be collected last.

@@ -488,10 +488,11 @@ int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *   Green-Gauss: G_i = (1/V_i) sum over the node's edge ends of
  *     (q_i + q_j) (x) (+-n_e/2), summed in FP32 (the same bits as the FP32
  *     node gather);
- *   flux and update: every edge end evaluates its edge's flux in the edge's
- *     own orientation (so both ends compute the same bits and the residual
- *     is exactly antisymmetric), the node sums them with Knuth's two-sum into
- *     a pair of floats (the sum to about 2^-48 of its running magnitude),
+ *   flux and update: every edge end evaluates its edge's flux with its own
+ *     node as the first end -- at the edge's second end the edge reversed
+ *     (n -> -n, dx -> -dx), which gives bitwise minus the first end's value,
+ *     so the residual is exactly antisymmetric -- the node sums them with
+ *     Knuth's two-sum into a pair of floats (the sum to about 2^-48 of its running magnitude),
  *     converts the pair exactly to FP64 once: R_i; then
  *     q_i = q0_i - alpha (dt_i / V_i) R_i in FP64.
  * No atomics: the result is bitwise reproducible.
@@ -507,28 +508,32 @@ int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  * The records carry the state from one call to the next: the library packs
  * them from q on the first call for a map, after a renumbering, when q is a
  * different buffer, and whenever flags holds OP2B_STAGE_SYNC -- pass it
- * after changing q by any other means.  It packs the edge geometry (n and
- * dx in FP32, 32 bytes per edge) on the first call, when n or dx is a
- * different buffer or type, and with OP2B_STAGE_SYNC_MESH (after changing
- * their values).
+ * after changing q by any other means.  It packs the edge ends' adjacency
+ * and geometry (n and dx in FP32, the edge reversed at its second end) on
+ * the first call, when n or dx is a different buffer or type, and with
+ * OP2B_STAGE_SYNC_MESH (after changing their values).
  *
- * Two forms of the passes, the same bits.  By default every edge end
- * gathers its other node's record (three 32-byte loads) and its edge's
- * geometry from global memory.  With OP2B_STAGE_STAGED the library plans,
- * on the host at the first such call, blocks of B consecutive nodes (B =
- * 128, else 64 or 32) and the distinct nodes each block's edge ends reach;
- * where every such neighbourhood fits 100 KB of shared memory at 112 bytes
- * per record, both passes run one CTA per node block that first copies the
- * neighbourhood's records into shared memory (asynchronous copies), and the
- * ends, laid out sliced-ELL, read the records there (the paper's staging of
- * a block's indirect data, Sec. 4.1.2); elsewhere the flag has no effect.
- * A numbering with compact blocks (recursive coordinate bisection) needs
- * about 0.2 records per edge end; on GB300 the gathering form measured
- * faster on the lattices tried, hence the default.
- * Library-owned memory per map: 24 bytes per edge end, 32 per edge, 192 per
- * node (plus 36 per end and the neighbourhood lists once staged).  Errors:
- * OP2B_EINVAL (bad map, flag, q0 == q, coefficients), OP2B_ESET / OP2B_EDIM /
- * OP2B_ETYPE (dats), OP2B_ENOMEM, OP2B_ECUDA. */
+ * Two forms of the passes, the same bits.  By default one thread per node
+ * walks the node's edge ends, laid out sliced-ELL (the k-th ends of 32
+ * consecutive nodes contiguous: 16 bytes per end for the Green-Gauss pass,
+ * 32 for the flux pass), and gathers each other node's record from global
+ * memory (three 32-byte loads); the flux pass streams its 32-byte end
+ * records through a small shared-memory ring a few ends ahead.  With
+ * OP2B_STAGE_STAGED the library plans, on the host at the first such call,
+ * blocks of B consecutive nodes (B = 128, else 64 or 32) and the distinct
+ * nodes each block's edge ends reach; where every such neighbourhood fits
+ * 100 KB of shared memory at 112 bytes per record, both passes run one CTA
+ * per node block that first copies the neighbourhood's records into shared
+ * memory (asynchronous copies), and the ends read the records there (the
+ * paper's staging of a block's indirect data, Sec. 4.1.2); elsewhere the
+ * flag has no effect.  A numbering with compact blocks (recursive
+ * coordinate bisection) needs about 0.2 records per edge end; on GB300 the
+ * gathering form measured faster on the lattices tried, hence the default.
+ * Library-owned memory per map: 48 bytes per edge end (sliced-ELL slots,
+ * padded per 32-node slice to its largest degree) and 192 per node (plus,
+ * once staged, 36 per end, 32 per edge and the neighbourhood lists).
+ * Errors: OP2B_EINVAL (bad map, flag, q0 == q, coefficients), OP2B_ESET /
+ * OP2B_EDIM / OP2B_ETYPE (dats), OP2B_ENOMEM, OP2B_ECUDA. */
 #define OP2B_STAGE_SYNC 1
 #define OP2B_STAGE_STORE_Q0 2
 #define OP2B_STAGE_SYNC_MESH 4

@@ -492,8 +492,8 @@ int op2b_viscous_flux(op2b_ctx ctx, const op2b_arg* args, int32_t nargs,
  *     node as the first end -- at the edge's second end the edge reversed
  *     (n -> -n, dx -> -dx), which gives bitwise minus the first end's value,
  *     so the residual is exactly antisymmetric -- the node sums them with
- *     Knuth's two-sum into a pair of floats (the sum to about 2^-48 of its running magnitude),
- *     converts the pair exactly to FP64 once: R_i; then
+ *     Knuth's two-sum into a pair of floats (the sum to about 2^-48 of its
+ *     running magnitude), converts the pair exactly to FP64 once: R_i; then
  *     q_i = q0_i - alpha (dt_i / V_i) R_i in FP64.
  * No atomics: the result is bitwise reproducible.
  *

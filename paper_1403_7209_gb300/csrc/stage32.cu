@@ -10,7 +10,7 @@
 //
 // Why it is laid out this way on GB300.  Gathering a node's 24 FP32 values
 // from structure-of-arrays dats touches 24 separate 32-byte sectors; the
-// packed record (q then G, 96 bytes: three sectors, six 16-byte loads) cuts
+// packed record (q then G, 96 bytes: three sectors, three 32-byte loads) cuts
 // the L2 traffic of every gather by 8x.  Accumulating the edge fluxes into
 // FP64 needs 12 FP64 additions per edge, which GB300's FP64 pipe (2 per
 // clock per SM) cannot absorb -- 108M per stage on the 1M-node lattice,

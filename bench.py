@@ -956,7 +956,7 @@ def main():
     ap.add_argument("--oracle-march-n", type=int, default=40,
                     help="lattice of the 50-step marches checked against the oracle's")
     ap.add_argument("--numbering", default="rcm", choices=["rcm", "random", "none"])
-    ap.add_argument("--cpu-stages", type=int, default=3, help="oracle sample size (stages)")
+    ap.add_argument("--cpu-stages", type=int, default=5, help="oracle sample size (stages, about 2.5 s each on one host core)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--tune-cache", default="",
                     help="JSON strategy table: loaded if present, written after tuning")

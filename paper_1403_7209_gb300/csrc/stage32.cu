@@ -336,9 +336,12 @@ __device__ __forceinline__ void cp_async_wait_group() {
 // one 32-byte load (the record's first 8 floats: q and two G values, unused,
 // which other threads may be writing: coherent loads).  Same operations in
 // the same order as the FP32 Green-Gauss node gather, so the same bits.
-// The pass waits on its gathers; six ends per unrolled iteration keep six
-// gathers in flight per thread (4% faster per stage than two).
-__global__ void __launch_bounds__(128) k_s32_green_gauss(
+// The pass waits on its gathers; six ends per unrolled iteration keep
+// several gathers in flight per thread (4% faster per stage than two).  A
+// minimum of 7 blocks per SM gives it 72 registers (measured: 1.5% faster
+// per stage than with no minimum, 66 registers; minima of 8, 9 or 1 blocks,
+// 64, 56 or 108 registers, slower).
+__global__ void __launch_bounds__(128, 7) k_s32_green_gauss(
     int64_t N, const int64_t* __restrict__ rowptr, const int64_t* __restrict__ ell_off,
     const int4* __restrict__ adjn_l, float* __restrict__ rec, const double* __restrict__ V,
     float* __restrict__ Gout, int64_t ldG) {

@@ -3,7 +3,8 @@
 100^3 lattice (1M nodes, 9M edges): every node of the FP64 residual and of
 the adjoint against the oracle; FP32-mixed residual error, by the separate
 loops and by the fused stage (both forms).
-200^3 lattice (8M nodes, 72M edges): sampled nodes and edges.  For a sample
+200^3 lattice (8M nodes, 72M edges): sampled nodes and edges (FP64 residual
+and adjoint, fused FP32-mixed residual).  For a sample
 S the oracle runs on a local sub-mesh that holds every edge touching the
 nodes within two rings of S, which is exactly what R at S and the adjoint
 at S (and at edges meeting S) depend on.
@@ -92,13 +93,20 @@ def test_lattice200_sampled_parity(gpu_lib):
     m = meshgen.lattice(200)
     q = meshgen.flow_state(m)
     lam = meshgen.adjoint_seed(m.num_nodes)
-    s = tuned_solver(gpu_lib, m, q, adjoint=True)
+    s = tuned_solver(gpu_lib, m, q, adjoint=True, mixed=True)
     s.residual(2)
     R = s.fetch_nodes("R")
     s.load_nodes("lam", lam)
     s.adjoint(2)
     qbar = s.fetch_nodes("qbar")
     nbar = s.fetch_edges("nbar")
+    # the fused FP32-mixed stage at alpha = 0 (q unchanged): its residual,
+    # as the bench times it (direct form, RCM numbering)
+    gpu_lib.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
+    s.time_step(0.5)
+    s.stage_fused(0.0, sync=True)
+    Rf = s.fetch_nodes("R")
+    assert np.array_equal(s.fetch_nodes("q"), q)
     s.close()
     sample = np.unique(meshgen.fd_picks(200, m.num_nodes, seed=11))
     keep, nodes, local = _submesh(m, sample)
@@ -107,6 +115,9 @@ def test_lattice200_sampled_parity(gpu_lib):
     Rs, _, Ras = oracle.residual(2, se, sq, sn, sd, sv, with_abs=True)
     ls = local[sample]
     assert rel_err(R[sample], Rs[ls], Ras[ls]) <= TOL
+    # FP32-mixed bar, per component against the field's largest |R|
+    err = np.max(np.abs(Rf[sample] - Rs[ls]), axis=0) / np.max(np.abs(R), axis=0)
+    assert np.all(err <= 1e-5), err
     qb, nb = oracle.residual_reverse(2, se, sq, sn, sd, sv, lam[nodes])
     assert adj_ok(qbar[sample], qb[ls], np.max(np.abs(qbar), axis=0),
                   np.median(np.abs(qbar), axis=0))

@@ -101,7 +101,7 @@ int launch_gg_gather(Ctx* c, const LoopLaunch& L, int block) {
   if (block < 32 || block > 1024 || block % 32)
     return c->fail(OP2B_EINVAL, "block size must be a multiple of 32 in [32, 1024]");
   const int64_t grid =
-      std::min<int64_t>((L.N * SPLIT + block - 1) / block, (int64_t)c->sm_count * 64);
+      std::min<int64_t>((L.N * SPLIT + block - 1) / block, 0x7fffffff);  // all blocks, node order
   k_gg_gather<T, SPLIT><<<(unsigned)grid, block, 0, c->stream>>>(
       sp->rowptr, sp->ends, L.m0, L.m1, (const T*)L.q, L.ldq, (const T*)L.n, L.ldn, (T*)L.t0,
       L.ldt0, L.N, !(L.flags & OP2B_ZERO_INC), L.vol);

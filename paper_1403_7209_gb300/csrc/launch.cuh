@@ -73,6 +73,17 @@ static int run_colour(Ctx* c, const P& ph, const LoopLaunch& L,
   return OP2B_OK;
 }
 
+// Grid of a node-parallel kernel (one node per thread): every block is
+// launched, so that blocks are dispatched in node order and the nodes in
+// flight form one moving window of the mesh whose neighbours stay in L2.
+// (A grid capped at 64 blocks per SM makes each resident block stride over
+// the whole mesh: measured 3.4% slower for the FP32-mixed stage's owner and
+// gather loops at 200^3.  The edge-parallel atomic kernels keep the cap:
+// without it the FP64 stage measured 0.2% slower.)
+static inline int64_t full_grid(int64_t n, int block) {
+  return std::min<int64_t>((n + block - 1) / block, 0x7fffffff);
+}
+
 template <class P>
 static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
                     const Strategy& s, Targets<typename P::TA, P::DIM0> tg) {
@@ -96,7 +107,8 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
       int rc = c->own_plan(L.map, &op);
       if (rc) return rc;
       if ((rc = check_block(c, k_owner<P>, block))) return rc;
-      int64_t grid = std::min<int64_t>((L.N + block - 1) / block, cap);
+      // node-parallel: every block launched (see full_grid)
+      int64_t grid = full_grid(L.N, block);
       if (grid == 0) return OP2B_OK;
       k_owner<P><<<(unsigned)grid, block, 0, c->stream>>>(ph, L.m0, L.m1, L.N, op->ptr, op->idx, tg);
       return c->launched("owner");
@@ -136,7 +148,7 @@ static int run_body(Ctx* c, const P& ph, const LoopLaunch& L,
         int rc = c->seg_plan(L.map, &sp);
         if (rc) return rc;
         if ((rc = check_block(c, k_gather_nodes<P>, block))) return rc;
-        int64_t grid = std::min<int64_t>((L.N + block - 1) / block, cap);
+        int64_t grid = full_grid(L.N, block);
         if (grid == 0) return OP2B_OK;
         k_gather_nodes<P><<<(unsigned)grid, block, 0, c->stream>>>(
             ph, sp->rowptr, sp->ends, L.m0, L.m1, L.N, tg, !(L.flags & OP2B_ZERO_INC));

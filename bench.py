@@ -777,30 +777,51 @@ def cpu_baseline_march_result(n, steps):
 def march_oracle_extra(torch, L, args, stream, device, q_ora, n, steps):
     """50-step marches (250 stages) on the n^3 lattice in FP64 and in
     FP32-mixed against the oracle's march of the same mesh: normwise state
-    error per component (max |q - q_oracle| / max |q_oracle|)."""
+    error per component (max |q - q_oracle| / max |q_oracle|); the fused
+    march also replayed from a CUDA graph (bitwise the eager march)."""
     from paper_1403_7209_gb300.solver import EdgeSolver
     m, q = build_mesh(n)
     out = {"mesh": "%d^3 lattice, %d nodes, %d edges, RCM" % (n, m.num_nodes, m.num_edges),
            "steps": steps, "stages_per_step": 5}
     for tag, mixed, fused in (("fp64", False, False), ("mixed", True, False),
                               ("fused_mixed", True, True)):
-        s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device, renumber="rcm",
-                       mixed=mixed, stream=stream)
-        prec = L.PREC_F32 if mixed else L.PREC_F64
-        for loop in range(L.NUM_LOOPS):
-            s.set_strategy(loop, prec, L.STRAT_AUTO)
-        s.time_step(0.5)
-        s.residual(2, mixed=mixed)  # tunes the loops before the timed march
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(steps):
-            s.step(order=2, mixed=mixed, fused=fused)
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t
-        qg = s.fetch_nodes("q")
-        s.close()
-        err = (np.max(np.abs(qg - q_ora), axis=0) / np.max(np.abs(q_ora), axis=0)).tolist()
-        out[tag] = {"state_err_vs_oracle_per_component": err, "gpu_march_s": t}
+        # the fused march runs on a side stream, so that its steps can also be
+        # captured in a CUDA graph below (same solver, same time step)
+        st = torch.cuda.Stream(device=device) if fused else stream
+        with torch.cuda.stream(st):
+            s = EdgeSolver(m.edge, m.normal, m.dx, m.volume, q, device=device, renumber="rcm",
+                           mixed=mixed, stream=st)
+            prec = L.PREC_F32 if mixed else L.PREC_F64
+            for loop in range(L.NUM_LOOPS):
+                s.set_strategy(loop, prec, L.STRAT_AUTO)
+            s.time_step(0.5)
+            s.residual(2, mixed=mixed)  # tunes the loops before the timed march
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            for _ in range(steps):
+                s.step(order=2, mixed=mixed, fused=fused)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t
+            qg = s.fetch_nodes("q")
+            err = (np.max(np.abs(qg - q_ora), axis=0) / np.max(np.abs(q_ora), axis=0)).tolist()
+            out[tag] = {"state_err_vs_oracle_per_component": err, "gpu_march_s": t}
+            if fused:
+                # the same march, every step one replay of a CUDA graph captured
+                # from a step (the launches of this small mesh's stages dominate)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=st):
+                    s.step(fused=True)
+                s.load_nodes("q", q)
+                st.synchronize()
+                t = time.perf_counter()
+                for _ in range(steps):
+                    g.replay()
+                st.synchronize()
+                t = time.perf_counter() - t
+                out["fused_mixed_graph"] = {
+                    "gpu_march_s": t,
+                    "bitwise_equal_to_eager": bool(np.array_equal(s.fetch_nodes("q"), qg))}
+            s.close()
     out["mixed_state_err_vs_oracle"] = max(out["mixed"]["state_err_vs_oracle_per_component"])
     out["fused_mixed_state_err_vs_oracle"] = max(
         out["fused_mixed"]["state_err_vs_oracle_per_component"])

@@ -191,6 +191,35 @@ def test_fused_irregular_graph(gpu_lib):
     s.close()
 
 
+@pytest.mark.parametrize("kinds", [("n32", "dx32"), ("n32", "dx"), ("n", "dx32")],
+                         ids=["f32_f32", "f32_f64", "f64_f32"])
+def test_fused_stage_takes_fp32_geometry(gpu_lib, mesh16, kinds):
+    """n and dx given as F32 dats (each the FP32 rounding of the F64 values)
+    give bitwise the stage of the F64 dats: the library converts them to
+    FP32 either way; switching the geometry dats re-packs the adjacency."""
+    m, q = mesh16
+    s = _solver(m, q)
+    d = s.d
+    gpu_lib.op2b_dat_copy(s.ctx, d["q0"], d["q"])
+    s.time_step(0.5)
+
+    def stage(n, dx):
+        s.load_nodes("q", q)
+        gpu_lib.op2b_dat_copy(s.ctx, d["q0"], d["q"])
+        gpu_lib.op2b_stage_mixed(s.ctx, s.map, d["q0"], d["q"], d["V"], d["dt"], d[n], d[dx],
+                                 d["R"], d["G32"], 0.25, s.gamma, s.eps_lim,
+                                 gpu_lib.STAGE_SYNC)
+        return s.fetch_nodes("q"), s.fetch_nodes("R"), s.fetch_nodes("G32")
+
+    ref = stage("n", "dx")
+    got = stage(*kinds)
+    back = stage("n", "dx")
+    for a, b, c in zip(ref, got, back):
+        assert np.array_equal(a, b)
+        assert np.array_equal(a, c)
+    s.close()
+
+
 def test_fused_march_replayed_from_cuda_graph(gpu_lib, mesh16):
     """A fused step (q0 <- q, five op2b_stage_mixed calls, the first
     re-packing the records) captured once in a CUDA graph and replayed three

@@ -220,6 +220,30 @@ def test_fused_stage_takes_fp32_geometry(gpu_lib, mesh16, kinds):
     s.close()
 
 
+def test_fused_stage_after_renumbering(gpu_lib, mesh16, ref16):
+    """The library renumbers the map (and permutes the declared dats in
+    place) after a fused stage has built its records and adjacency: the next
+    stage rebuilds them for the new numbering and matches the oracle."""
+    from paper_1403_7209_gb300.solver import RENUMBER
+    m, q = mesh16
+    R_ora, G_ora, _ = ref16
+    s = _solver(m, q, renumber="none")
+    gpu_lib.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
+    s.time_step(0.5)
+    s.stage_fused(0.0, sync=True, gradient=True)
+    R1 = s.fetch_nodes("R")
+    assert np.all(_normwise(R1, R_ora) <= BAR)
+    perm, order = gpu_lib.op2b_renumber(s.ctx, s.map, RENUMBER["rcm"], 0, s.N, s.E)
+    assert not np.array_equal(perm, np.arange(s.N))
+    s.perm, s.order = perm.astype(np.int64), order
+    s.stage_fused(0.0, sync=True, gradient=True)
+    R2, G2 = s.fetch_nodes("R"), s.fetch_nodes("G32")
+    assert np.all(_normwise(R2, R_ora) <= BAR), _normwise(R2, R_ora)
+    assert np.all(_normwise(G2, G_ora) <= BAR)
+    assert np.array_equal(s.fetch_nodes("q"), q)
+    s.close()
+
+
 def test_fused_march_replayed_from_cuda_graph(gpu_lib, mesh16):
     """A fused step (q0 <- q, five op2b_stage_mixed calls, the first
     re-packing the records) captured once in a CUDA graph and replayed three

@@ -277,7 +277,7 @@ def test_fused_march_replayed_from_cuda_graph(gpu_lib, mesh16):
 def test_fused_hub_node(gpu_lib):
     """One node joined to every other node plus a ring through the rest
     (degrees N-1+... and 3): the adjacency's 32-node slices differ in width
-    by a factor of ~30; against the oracle, in both numberings."""
+    by a factor of ~30; against the oracle, in both numberings and both forms."""
     rng = np.random.default_rng(5)
     N = 203
     ring = np.column_stack([np.arange(1, N), np.r_[np.arange(2, N), 1]])
@@ -298,9 +298,10 @@ def test_fused_hub_node(gpu_lib):
         s = EdgeSolver(edge, nrm, dx, V, q, renumber=renumber, mixed=True)
         gpu_lib.op2b_dat_copy(s.ctx, s.d["q0"], s.d["q"])
         s.time_step(0.5)
-        s.stage_fused(0.0, gradient=True)
-        assert np.all(_normwise(s.fetch_nodes("R"), R_ora) <= BAR)
-        assert np.all(_normwise(s.fetch_nodes("G32"), G_ora) <= BAR)
+        for staged in (False, True):
+            s.stage_fused(0.0, gradient=True, staged=staged)
+            assert np.all(_normwise(s.fetch_nodes("R"), R_ora) <= BAR)
+            assert np.all(_normwise(s.fetch_nodes("G32"), G_ora) <= BAR)
         s.close()
 
 
